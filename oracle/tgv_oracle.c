@@ -1,0 +1,738 @@
+/*
+ * FP64 CPU oracle for the histogram + TGV primal-dual path of
+ * "Out-of-Core Surface Reconstruction via Global TGV Minimization" (arXiv 2107.14790).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline / reference legs may load this library.  The product path (the
+ * CUDA library in paper_2107_14790_b300/) never calls it, and this file shares
+ * no code, header, table or helper with that library.
+ *
+ * Plain, slow, obviously correct loops.  Each function names the passage it
+ * follows.  Where the paper is silent, the reading taken is stated inline and
+ * listed in DESIGN.md ("readings").
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC
+ *   -ffp-contract=off is required: the histogram decision (Alg. 1) is taken in
+ *   FP32 with one rounding per listed operation, exactly like the kernel.
+ *
+ * Parity status: every function here is pinned by a test in tests/test_oracle_*.py
+ * (closed forms, invariants, brute force); none is "parity unpinned".  The
+ * converged field is pinned only against the sphere's geometry.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_BRICK 8
+#define ORC_BVOX 512
+
+/* ======================================================================== */
+/* Depth pyramid (Sec. 3.4: depth maps get mipmap pyramids; Alg. 1 projects  */
+/* into the pyramid level matching the voxel's projected size).              */
+/* Reading: level l+1 has ceil(W_l/2) x ceil(H_l/2) pixels; each pixel is    */
+/* the minimum of its existing, valid children; invalid if none is valid.    */
+/* Levels run up to Lmax = floor(log2(max(W, H))).  Invalid = NaN, inf, <=0. */
+/* ======================================================================== */
+int orc_pyramid_nlevels(int W, int H)
+{
+    int m = W > H ? W : H;
+    int L = 0;
+    while ((1 << (L + 1)) <= m) L++;
+    return L + 1;
+}
+
+/* dims[2*l], dims[2*l+1] = width, height of level l; offs[l] = element offset. */
+int64_t orc_pyramid_layout(int W, int H, int32_t* dims, int64_t* offs)
+{
+    int n = orc_pyramid_nlevels(W, H);
+    int64_t off = 0;
+    int w = W, h = H;
+    for (int l = 0; l < n; ++l) {
+        dims[2 * l] = w;
+        dims[2 * l + 1] = h;
+        offs[l] = off;
+        off += (int64_t)w * h;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    return off;
+}
+
+static int orc_valid_depth(float d) { return isfinite(d) && d > 0.0f; }
+
+void orc_build_pyramid(const float* depth, int W, int H, int64_t pitch, float* pyr)
+{
+    int32_t dims[64];
+    int64_t offs[32];
+    int n = orc_pyramid_nlevels(W, H);
+    orc_pyramid_layout(W, H, dims, offs);
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            float d = depth[(int64_t)j * pitch + i];
+            pyr[(int64_t)j * W + i] = orc_valid_depth(d) ? d : NAN;
+        }
+    for (int l = 1; l < n; ++l) {
+        int wp = dims[2 * (l - 1)], hp = dims[2 * (l - 1) + 1];
+        int w = dims[2 * l], h = dims[2 * l + 1];
+        const float* src = pyr + offs[l - 1];
+        float* dst = pyr + offs[l];
+        for (int j = 0; j < h; ++j)
+            for (int i = 0; i < w; ++i) {
+                float best = NAN;
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int di = 0; di < 2; ++di) {
+                        int ci = 2 * i + di, cj = 2 * j + dj;
+                        if (ci >= wp || cj >= hp) continue;
+                        float c = src[(int64_t)cj * wp + ci];
+                        if (isnan(c)) continue;
+                        if (isnan(best) || c < best) best = c;
+                    }
+                dst[(int64_t)j * w + i] = best;
+            }
+    }
+}
+
+/* ======================================================================== */
+/* Algorithm 1 (add_to_voxel_histograms), one voxel and one depth map.       */
+/*                                                                          */
+/* The decision is taken in FP32, one rounding per operation, in this order  */
+/* (the kernel takes the same decision in the same precision):               */
+/*   X   = o + ((float)idx + 0.5) * h            per axis                     */
+/*   d   = X - C;  Xc = (R0 d0 + R1 d1) + R2 d2  (rows of R), likewise Yc, Zc */
+/*   in front of the camera iff Zc > 0                                        */
+/*   x   = (fx*Xc)/Zc + cx,  y = (fy*Yc)/Zc + cy                              */
+/*   fp  = (fx*(2r))/Zc    projected voxel diameter in level-0 pixels         */
+/*   LOD = largest l in [0, Lmax] with 2^l <= max(1, fp)   (exact compares)   */
+/*   pixel at LOD: (floor(x/2^l), floor(y/2^l)), must lie inside the level    */
+/*   depth = pyramid[l][pixel]; invalid -> no vote                            */
+/*   a = depth - Zc  (Alg. 1: depth minus distance; distance = z-depth)       */
+/*   delta = 6 r, eta = 3 delta (Sec. 3.1);  a < -eta -> no vote              */
+/*   a' = max(-1, min(1, a/delta));  bin = floor(((a'+1)/2) * n)              */
+/*   bin = min(bin, n-1)   (reading: Alg. 1 gives bin = n at a' = +1)         */
+/* Camera parameters arrive as FP64 and are rounded once to FP32.            */
+/* Returns 1 and sets *bin when the map votes for the voxel, else 0.         */
+/* ======================================================================== */
+typedef struct {
+    float fx, fy, cx, cy, R[9], C[3];
+    int W, H;
+} orc_cam32;
+
+static orc_cam32 orc_cam_from_f64(const double* cam, int W, int H)
+{
+    orc_cam32 c;
+    c.fx = (float)cam[0];
+    c.fy = (float)cam[1];
+    c.cx = (float)cam[2];
+    c.cy = (float)cam[3];
+    for (int k = 0; k < 9; ++k) c.R[k] = (float)cam[4 + k];
+    for (int k = 0; k < 3; ++k) c.C[k] = (float)cam[13 + k];
+    c.W = W;
+    c.H = H;
+    return c;
+}
+
+static int orc_vote_f32(const orc_cam32* cam, const float* pyr, int nlev, const int32_t* dims,
+                        const int64_t* offs, const float o[3], float h, float r, const int64_t idx[3],
+                        int nbins, int* bin_out)
+{
+    float X[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+        float t = (float)idx[a] + 0.5f;
+        float m = t * h;
+        X[a] = o[a] + m;
+        d[a] = X[a] - cam->C[a];
+    }
+    const float* R = cam->R;
+    float xc = R[0] * d[0] + R[1] * d[1];
+    xc = xc + R[2] * d[2];
+    float yc = R[3] * d[0] + R[4] * d[1];
+    yc = yc + R[5] * d[2];
+    float zc = R[6] * d[0] + R[7] * d[1];
+    zc = zc + R[8] * d[2];
+    if (!(zc > 0.0f)) return 0;
+    float px = (cam->fx * xc) / zc + cam->cx;
+    float py = (cam->fy * yc) / zc + cam->cy;
+    float diam = r * 2.0f;
+    float fp = (cam->fx * diam) / zc;
+    int L = 0;
+    float p2 = 2.0f;
+    while (L + 1 < nlev && p2 <= fp) {
+        L++;
+        p2 = p2 * 2.0f;
+    }
+    float scale = ldexpf(1.0f, -L);
+    float xl = px * scale, yl = py * scale;
+    int wl = dims[2 * L], hl = dims[2 * L + 1];
+    if (!(xl >= 0.0f && xl < (float)wl)) return 0;
+    if (!(yl >= 0.0f && yl < (float)hl)) return 0;
+    int i = (int)floorf(xl), j = (int)floorf(yl);
+    float depth = pyr[offs[L] + (int64_t)j * wl + i];
+    if (isnan(depth)) return 0;
+    float a = depth - zc;
+    float delta = 6.0f * r;
+    float eta = 3.0f * delta;
+    if (a < -eta) return 0;
+    float ac = a / delta;
+    if (ac > 1.0f) ac = 1.0f;
+    if (ac < -1.0f) ac = -1.0f;
+    float t1 = ac + 1.0f;
+    float t2 = t1 / 2.0f;
+    float t3 = t2 * (float)nbins;
+    int bin = (int)floorf(t3);
+    if (bin > nbins - 1) bin = nbins - 1;
+    *bin_out = bin;
+    return 1;
+}
+
+/* Same decision in FP64 throughout (diagnostic: counts votes whose bin or
+ * acceptance differs from the FP32 decision). */
+static int orc_vote_f64(const double* cam, int L32, const float* pyr, const int32_t* dims,
+                        const int64_t* offs, const double o[3], double h, double r, const int64_t idx[3],
+                        int nbins, int* bin_out)
+{
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = o[a] + ((double)idx[a] + 0.5) * h - cam[13 + a];
+    const double* R = cam + 4;
+    double xc = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
+    double yc = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
+    double zc = R[6] * d[0] + R[7] * d[1] + R[8] * d[2];
+    if (!(zc > 0.0)) return 0;
+    double px = cam[0] * xc / zc + cam[2], py = cam[1] * yc / zc + cam[3];
+    int L = L32; /* use the FP32 LOD so the diagnostic isolates binning */
+    double xl = ldexp(px, -L), yl = ldexp(py, -L);
+    int wl = dims[2 * L], hl = dims[2 * L + 1];
+    if (!(xl >= 0.0 && xl < wl && yl >= 0.0 && yl < hl)) return 0;
+    int i = (int)floor(xl), j = (int)floor(yl);
+    float depth = pyr[offs[L] + (int64_t)j * wl + i];
+    if (isnan(depth)) return 0;
+    double a = (double)depth - zc;
+    double delta = 6.0 * r, eta = 3.0 * delta;
+    if (a < -eta) return 0;
+    double ac = fmax(-1.0, fmin(1.0, a / delta));
+    int bin = (int)floor((ac + 1.0) / 2.0 * nbins);
+    if (bin > nbins - 1) bin = nbins - 1;
+    *bin_out = bin;
+    return 1;
+}
+
+/* LOD the FP32 decision picks (for the FP64 diagnostic). */
+static int orc_lod_f32(const orc_cam32* cam, int nlev, const float o[3], float h, float r, const int64_t idx[3])
+{
+    float d[3];
+    for (int a = 0; a < 3; ++a) {
+        float t = (float)idx[a] + 0.5f;
+        float m = t * h;
+        d[a] = (o[a] + m) - cam->C[a];
+    }
+    float zc = cam->R[6] * d[0] + cam->R[7] * d[1];
+    zc = zc + cam->R[8] * d[2];
+    float fp = (cam->fx * (r * 2.0f)) / zc;
+    int L = 0;
+    float p2 = 2.0f;
+    while (L + 1 < nlev && p2 <= fp) {
+        L++;
+        p2 = p2 * 2.0f;
+    }
+    return L;
+}
+
+/*
+ * Gather form of Alg. 1 over every voxel of a brick level for one depth map.
+ *   bricks[3*b+a]: brick coordinates; voxel (i,j,k) of brick b has global index
+ *   8*brick + (i,j,k) and flat id b*512 + i + 8 j + 64 k.
+ *   hist: uint32 [nvox][nbins], incremented by `vote` in place.
+ *   cam: 16 doubles (fx, fy, cx, cy, R row-major, C).
+ *   r: voxel radius (Sec. 3.3, Eq. 5; reading: r = h/2 on a dense level).
+ * Returns the number of votes cast; *ndiff64 (nullable) receives the number of
+ * voxels where the FP64 decision differs from the FP32 one.
+ */
+int64_t orc_accumulate(int64_t nbricks, const int32_t* bricks, const double* origin, double h, double r,
+                       const double* cam, int W, int H, const float* pyr, int nbins, uint32_t vote,
+                       uint32_t* hist, int64_t* ndiff64)
+{
+    orc_cam32 c32 = orc_cam_from_f64(cam, W, H);
+    int32_t dims[64];
+    int64_t offs[32];
+    int nlev = orc_pyramid_nlevels(W, H);
+    orc_pyramid_layout(W, H, dims, offs);
+    float o32[3] = {(float)origin[0], (float)origin[1], (float)origin[2]};
+    float h32 = (float)h, r32 = (float)r;
+    int64_t votes = 0, diffs = 0;
+    for (int64_t b = 0; b < nbricks; ++b)
+        for (int v = 0; v < ORC_BVOX; ++v) {
+            int64_t idx[3] = {(int64_t)ORC_BRICK * bricks[3 * b + 0] + (v & 7),
+                              (int64_t)ORC_BRICK * bricks[3 * b + 1] + ((v >> 3) & 7),
+                              (int64_t)ORC_BRICK * bricks[3 * b + 2] + (v >> 6)};
+            int bin = -1;
+            int ok = orc_vote_f32(&c32, pyr, nlev, dims, offs, o32, h32, r32, idx, nbins, &bin);
+            if (ok) {
+                hist[(b * ORC_BVOX + v) * nbins + bin] += vote;
+                votes++;
+            }
+            if (ndiff64) {
+                int bin64 = -1, ok64 = 0;
+                double zc_test;
+                {
+                    double d[3];
+                    for (int a = 0; a < 3; ++a) d[a] = origin[a] + ((double)idx[a] + 0.5) * h - cam[13 + a];
+                    zc_test = cam[10] * d[0] + cam[11] * d[1] + cam[12] * d[2];
+                }
+                if (zc_test > 0.0) {
+                    int L = orc_lod_f32(&c32, nlev, o32, h32, r32, idx);
+                    ok64 = orc_vote_f64(cam, L, pyr, dims, offs, origin, h, r, idx, nbins, &bin64);
+                }
+                if (ok != ok64 || (ok && bin != bin64)) diffs++;
+            }
+        }
+    if (ndiff64) *ndiff64 = diffs;
+    return votes;
+}
+
+/* Per-voxel decision for a list of global voxel indices (for analytic pins):
+ * out[k] = bin, or -1 if no vote. */
+void orc_vote_list(int64_t n, const int64_t* idx3, const double* origin, double h, double r,
+                   const double* cam, int W, int H, const float* pyr, int nbins, int32_t* out)
+{
+    orc_cam32 c32 = orc_cam_from_f64(cam, W, H);
+    int32_t dims[64];
+    int64_t offs[32];
+    int nlev = orc_pyramid_nlevels(W, H);
+    orc_pyramid_layout(W, H, dims, offs);
+    float o32[3] = {(float)origin[0], (float)origin[1], (float)origin[2]};
+    for (int64_t k = 0; k < n; ++k) {
+        int bin = -1;
+        if (!orc_vote_f32(&c32, pyr, nlev, dims, offs, o32, (float)h, (float)r, idx3 + 3 * k, nbins, &bin))
+            bin = -1;
+        out[k] = bin;
+    }
+}
+
+/* ======================================================================== */
+/* Brick domain links.                                                      */
+/* For each active voxel x and axis a: fwd(x,a), bwd(x,a) in                */
+/*   ACT(y)  -> y >= 0 (active voxel id)                                    */
+/*   NONE    -> -1     (outside the domain: Neumann, no difference)         */
+/*   FRZ(k)  -> -2-k   (frozen voxel k = frozen_brick*512 + local; its u, v */
+/*                      are constants: Sec. 4.5, set B keeps the parent's   */
+/*                      indicator; reading: v is frozen too)                */
+/* Returns 0, or -1 on a duplicate brick.                                   */
+/* ======================================================================== */
+typedef struct {
+    int64_t key;
+    int64_t id; /* >= 0 active brick; < 0: frozen brick -1-id */
+} orc_bkey;
+
+static int64_t orc_key(int64_t x, int64_t y, int64_t z)
+{
+    const int64_t B = 1 << 20;
+    return ((z + B) * (2 * B) + (y + B)) * (2 * B) + (x + B);
+}
+
+static int orc_cmp(const void* a, const void* b)
+{
+    int64_t ka = ((const orc_bkey*)a)->key, kb = ((const orc_bkey*)b)->key;
+    return ka < kb ? -1 : (ka > kb ? 1 : 0);
+}
+
+static int64_t orc_find(const orc_bkey* t, int64_t n, int64_t key)
+{
+    int64_t lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (t[mid].key == key) return mid;
+        if (t[mid].key < key) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+int orc_build_links(int64_t nb, const int32_t* bricks, int64_t nf, const int32_t* frozen, int64_t* fwd,
+                    int64_t* bwd)
+{
+    int64_t n = nb + nf;
+    orc_bkey* t = (orc_bkey*)malloc(sizeof(orc_bkey) * (size_t)(n > 0 ? n : 1));
+    for (int64_t b = 0; b < nb; ++b) {
+        t[b].key = orc_key(bricks[3 * b], bricks[3 * b + 1], bricks[3 * b + 2]);
+        t[b].id = b;
+    }
+    for (int64_t f = 0; f < nf; ++f) {
+        t[nb + f].key = orc_key(frozen[3 * f], frozen[3 * f + 1], frozen[3 * f + 2]);
+        t[nb + f].id = -1 - f;
+    }
+    qsort(t, (size_t)n, sizeof(orc_bkey), orc_cmp);
+    for (int64_t k = 1; k < n; ++k)
+        if (t[k].key == t[k - 1].key) {
+            free(t);
+            return -1;
+        }
+    for (int64_t b = 0; b < nb; ++b)
+        for (int v = 0; v < ORC_BVOX; ++v) {
+            int64_t g[3] = {(int64_t)ORC_BRICK * bricks[3 * b] + (v & 7),
+                            (int64_t)ORC_BRICK * bricks[3 * b + 1] + ((v >> 3) & 7),
+                            (int64_t)ORC_BRICK * bricks[3 * b + 2] + (v >> 6)};
+            int64_t x = b * ORC_BVOX + v;
+            for (int a = 0; a < 3; ++a)
+                for (int s = 0; s < 2; ++s) {
+                    int64_t q[3] = {g[0], g[1], g[2]};
+                    q[a] += s == 0 ? 1 : -1;
+                    /* floor division by 8 for negative coordinates */
+                    int64_t bq[3], lq[3];
+                    for (int c = 0; c < 3; ++c) {
+                        bq[c] = q[c] >= 0 ? q[c] / ORC_BRICK : -((-q[c] + ORC_BRICK - 1) / ORC_BRICK);
+                        lq[c] = q[c] - ORC_BRICK * bq[c];
+                    }
+                    int64_t pos = orc_find(t, n, orc_key(bq[0], bq[1], bq[2]));
+                    int64_t link;
+                    if (pos < 0) {
+                        link = -1;
+                    } else {
+                        int64_t lv = lq[0] + 8 * lq[1] + 64 * lq[2];
+                        if (t[pos].id >= 0) link = t[pos].id * ORC_BVOX + lv;
+                        else link = -2 - ((-1 - t[pos].id) * ORC_BVOX + lv);
+                    }
+                    if (s == 0) fwd[3 * x + a] = link;
+                    else bwd[3 * x + a] = link;
+                }
+        }
+    free(t);
+    return 0;
+}
+
+/* ======================================================================== */
+/* TGV operators (Eq. 2-3), finite differences on the voxel grid with unit   */
+/* index spacing (reading: spacing 1 on every level).                        */
+/*   forward gradient       (grad u)_a(x) = u(fwd) - u(x), 0 if NONE          */
+/*   backward difference    d-_a w(x)     = w(x) - w(bwd), 0 if NONE          */
+/*   symmetric gradient     E(v)_ab = (d-_a v_b + d-_b v_a)/2   (Eq. 3)       */
+/* FRZ neighbours contribute their frozen u / v.  The divergences below are  */
+/* the exact negative adjoints of the linear parts (FRZ constants set to 0). */
+/* q is stored as (q00, q11, q22, q01, q02, q12); Frobenius inner products   */
+/* count the off-diagonal pair twice.                                        */
+/* ======================================================================== */
+static const int orc_qidx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+
+static double orc_u_at(int64_t link, const double* u, const double* fu)
+{
+    return link >= 0 ? u[link] : fu[-2 - link];
+}
+
+static void orc_grad_at(int64_t x, const int64_t* fwd, const double* u, const double* fu, double g[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        int64_t l = fwd[3 * x + a];
+        g[a] = l == -1 ? 0.0 : orc_u_at(l, u, fu) - u[x];
+    }
+}
+
+static void orc_symgrad_at(int64_t x, const int64_t* bwd, const double* v, const double* fv, double e[6])
+{
+    double dm[3][3]; /* dm[a][b] = d-_a v_b */
+    for (int a = 0; a < 3; ++a) {
+        int64_t l = bwd[3 * x + a];
+        for (int b = 0; b < 3; ++b) {
+            if (l == -1) dm[a][b] = 0.0;
+            else if (l >= 0) dm[a][b] = v[3 * x + b] - v[3 * l + b];
+            else dm[a][b] = v[3 * x + b] - fv[3 * (-2 - l) + b];
+        }
+    }
+    e[0] = dm[0][0];
+    e[1] = dm[1][1];
+    e[2] = dm[2][2];
+    e[3] = 0.5 * (dm[0][1] + dm[1][0]);
+    e[4] = 0.5 * (dm[0][2] + dm[2][0]);
+    e[5] = 0.5 * (dm[1][2] + dm[2][1]);
+}
+
+/* div1 p (x) = sum_a ( [fwd(x,a) != NONE] p_a(x) - [bwd(x,a) = ACT] p_a(bwd) ) */
+static double orc_div1_at(int64_t x, const int64_t* fwd, const int64_t* bwd, const double* p)
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (fwd[3 * x + a] != -1) s += p[3 * x + a];
+        int64_t l = bwd[3 * x + a];
+        if (l >= 0) s -= p[3 * l + a];
+    }
+    return s;
+}
+
+/* (div2 q)_b (x) = sum_a ( [fwd(x,a) = ACT] q_ab(fwd) - [bwd(x,a) != NONE] q_ab(x) ) */
+static void orc_div2_at(int64_t x, const int64_t* fwd, const int64_t* bwd, const double* q, double w[3])
+{
+    for (int b = 0; b < 3; ++b) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            int64_t lf = fwd[3 * x + a];
+            if (lf >= 0) s += q[6 * lf + orc_qidx[a][b]];
+            if (bwd[3 * x + a] != -1) s -= q[6 * x + orc_qidx[a][b]];
+        }
+        w[b] = s;
+    }
+}
+
+/* Whole-field operator entry points (used by the adjoint / affine pins). */
+void orc_grad(int64_t n, const int64_t* fwd, const double* u, const double* fu, double* g)
+{
+    for (int64_t x = 0; x < n; ++x) orc_grad_at(x, fwd, u, fu, g + 3 * x);
+}
+void orc_symgrad(int64_t n, const int64_t* bwd, const double* v, const double* fv, double* e)
+{
+    for (int64_t x = 0; x < n; ++x) orc_symgrad_at(x, bwd, v, fv, e + 6 * x);
+}
+void orc_div1(int64_t n, const int64_t* fwd, const int64_t* bwd, const double* p, double* d)
+{
+    for (int64_t x = 0; x < n; ++x) d[x] = orc_div1_at(x, fwd, bwd, p);
+}
+void orc_div2(int64_t n, const int64_t* fwd, const int64_t* bwd, const double* q, double* w)
+{
+    for (int64_t x = 0; x < n; ++x) orc_div2_at(x, fwd, bwd, q, w + 3 * x);
+}
+
+/* ======================================================================== */
+/* Projections onto the dual constraint sets of Eq. 2:                       */
+/*   |p|_2 <= alpha1,   |q|_F <= alpha0  (isotropic per voxel).              */
+/* ======================================================================== */
+static void orc_proj_p(double p[3], double alpha1)
+{
+    double n = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    double s = n / alpha1;
+    if (s > 1.0)
+        for (int a = 0; a < 3; ++a) p[a] /= s;
+}
+
+static void orc_proj_q(double q[6], double alpha0)
+{
+    double n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0 * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    double s = sqrt(n2) / alpha0;
+    if (s > 1.0)
+        for (int c = 0; c < 6; ++c) q[c] /= s;
+}
+
+void orc_project_p(int64_t n, double* p, double alpha1)
+{
+    for (int64_t x = 0; x < n; ++x) orc_proj_p(p + 3 * x, alpha1);
+}
+void orc_project_q(int64_t n, double* q, double alpha0)
+{
+    for (int64_t x = 0; x < n; ++x) orc_proj_q(q + 6 * x, alpha0);
+}
+
+/* ======================================================================== */
+/* Histogram data term (Sec. 3.4, histograms after Zach 2008):               */
+/*   sum_b h_b |u - c_b|,  bin centres c_b.                                  */
+/* Reading: centres = 0 -> c_b = -1 + 2b/(n-1) (bin 0 = occluded -1, bin n-1 */
+/*          = free space +1); centres = 1 -> interval midpoints              */
+/*          c_b = -1 + (2b+1)/n.                                             */
+/* Prox (generalised median): argmin_u (u-ut)^2/(2 tau) + lam sum h_b|u-c_b| */
+/* = median of {c_0..c_{n-1}} U {ut - tau lam W_i, i = 0..n},                */
+/*   W_i = sum_{b<i} h_b - sum_{b>=i} h_b.                                   */
+/* ======================================================================== */
+double orc_centre(int b, int n, int centres)
+{
+    return centres == 0 ? -1.0 + 2.0 * b / (double)(n - 1) : -1.0 + (2.0 * b + 1.0) / (double)n;
+}
+
+static int orc_dcmp(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+double orc_prox(double ut, const uint32_t* hb, int n, double tau, double lam, int centres)
+{
+    double vals[2 * 64 + 1];
+    int m = 0;
+    for (int b = 0; b < n; ++b) vals[m++] = orc_centre(b, n, centres);
+    for (int i = 0; i <= n; ++i) {
+        double W = 0.0;
+        for (int b = 0; b < n; ++b) W += b < i ? (double)hb[b] : -(double)hb[b];
+        vals[m++] = ut - tau * lam * W;
+    }
+    qsort(vals, (size_t)m, sizeof(double), orc_dcmp);
+    return vals[n]; /* the middle of 2n+1 sorted values */
+}
+
+/* Data term for one voxel. */
+static double orc_data_at(double u, const uint32_t* hb, int n, double lam, int centres)
+{
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += (double)hb[b] * fabs(u - orc_centre(b, n, centres));
+    return lam * s;
+}
+
+/* ======================================================================== */
+/* One primal-dual iteration (Sec. 3.2: the primal-dual method of Pock et    */
+/* al. 2011 for Eq. 2; reading: the Chambolle-Pock order below, theta = 1).  */
+/*   1. p <- proj_alpha1(p + sigma (grad ubar - vbar))                       */
+/*   2. q <- proj_alpha0(q + sigma E(vbar))                                  */
+/*   3. ut <- u + tau div1 p                                                 */
+/*   4. u+ <- clamp(prox(ut), -1, 1)   (clamp_u: indicator range, Sec. 3.2)  */
+/*   5. v+ <- v + tau (p + div2 q)                                           */
+/*   6. ubar <- 2u+ - u, vbar <- 2v+ - v;  u <- u+, v <- v+                  */
+/* Steps 1-2 finish for every voxel before steps 3-6 start (Jacobi).         */
+/* prm: alpha1, alpha0, lambda, tau, sigma.  Per-voxel loops are independent,*/
+/* so the result does not depend on the thread count.                        */
+/* ======================================================================== */
+void orc_tgv_iterate(int64_t n, const int64_t* fwd, const int64_t* bwd, const double* fu, const double* fv,
+                     const uint32_t* hist, int nbins, const double* prm, int clamp_u, int centres, double* u,
+                     double* ubar, double* v, double* vbar, double* p, double* q, int iters, int nthreads)
+{
+    double alpha1 = prm[0], alpha0 = prm[1], lam = prm[2], tau = prm[3], sigma = prm[4];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double* pn = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* qn = (double*)malloc(sizeof(double) * 6 * (size_t)(n > 0 ? n : 1));
+    for (int it = 0; it < iters; ++it) {
+#pragma omp parallel for schedule(static)
+        for (int64_t x = 0; x < n; ++x) {
+            double g[3], e[6];
+            orc_grad_at(x, fwd, ubar, fu, g);
+            for (int a = 0; a < 3; ++a) pn[3 * x + a] = p[3 * x + a] + sigma * (g[a] - vbar[3 * x + a]);
+            orc_proj_p(pn + 3 * x, alpha1);
+            orc_symgrad_at(x, bwd, vbar, fv, e);
+            for (int c = 0; c < 6; ++c) qn[6 * x + c] = q[6 * x + c] + sigma * e[c];
+            orc_proj_q(qn + 6 * x, alpha0);
+        }
+        memcpy(p, pn, sizeof(double) * 3 * (size_t)n);
+        memcpy(q, qn, sizeof(double) * 6 * (size_t)n);
+#pragma omp parallel for schedule(static)
+        for (int64_t x = 0; x < n; ++x) {
+            double ut = u[x] + tau * orc_div1_at(x, fwd, bwd, p);
+            double un = orc_prox(ut, hist + x * nbins, nbins, tau, lam, centres);
+            if (clamp_u) un = un < -1.0 ? -1.0 : (un > 1.0 ? 1.0 : un);
+            double w[3];
+            orc_div2_at(x, fwd, bwd, q, w);
+            for (int a = 0; a < 3; ++a) {
+                double vn = v[3 * x + a] + tau * (p[3 * x + a] + w[a]);
+                vbar[3 * x + a] = 2.0 * vn - v[3 * x + a];
+                v[3 * x + a] = vn;
+            }
+            ubar[x] = 2.0 * un - u[x];
+            u[x] = un;
+        }
+    }
+    free(pn);
+    free(qn);
+}
+
+/* ======================================================================== */
+/* Energy of Eq. 2 on the discrete domain, dual value and gap.              */
+/*   E(u,v) = alpha1 sum |grad u - v|_2 + alpha0 sum |E v|_F                */
+/*            + lam sum_x sum_b h_b |u - c_b|         (FRZ constants in)    */
+/* Reading (bounded primal sets so the gap is finite): u in [-1, 1] and    */
+/* every component |v_a| <= Bv.  With K(u,v) = K0(u,v) + k0 (k0 = the FRZ    */
+/* constants, i.e. K(0,0)):                                                 */
+/*   D(p,q) = <k0,(p,q)> - sum_x phi*_x(div1 p(x)) - Bv |p + div2 q|_1       */
+/*   phi*_x(w) = max over u in {-1, c_0..c_{n-1}, +1} of                     */
+/*               w u - lam sum_b h_b |u - c_b|    (concave piecewise linear) */
+/* out[0] = E, out[1] = D, out[2] = E - D, out[3] = 1 if every |v_a| <= Bv.  */
+/* Sums run serially in voxel order.                                        */
+/* ======================================================================== */
+void orc_energy(int64_t n, const int64_t* fwd, const int64_t* bwd, const double* fu, const double* fv,
+                const uint32_t* hist, int nbins, const double* prm, int centres, double Bv, const double* u,
+                const double* v, const double* p, const double* q, double* out)
+{
+    double alpha1 = prm[0], alpha0 = prm[1], lam = prm[2];
+    double E = 0.0, D = 0.0;
+    int certified = 1;
+    double* zeros_u = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* zeros_v = (double*)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t x = 0; x < n; ++x) {
+        double g[3], e[6], w[3];
+        /* primal */
+        orc_grad_at(x, fwd, u, fu, g);
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double t = g[a] - v[3 * x + a];
+            s += t * t;
+            if (fabs(v[3 * x + a]) > Bv) certified = 0;
+        }
+        E += alpha1 * sqrt(s);
+        orc_symgrad_at(x, bwd, v, fv, e);
+        double f2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.0 * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+        E += alpha0 * sqrt(f2);
+        E += orc_data_at(u[x], hist + x * nbins, nbins, lam, centres);
+        /* dual: <k0, (p, q)> */
+        orc_grad_at(x, fwd, zeros_u, fu, g);
+        orc_symgrad_at(x, bwd, zeros_v, fv, e);
+        double k = 0.0;
+        for (int a = 0; a < 3; ++a) k += g[a] * p[3 * x + a];
+        k += e[0] * q[6 * x] + e[1] * q[6 * x + 1] + e[2] * q[6 * x + 2] +
+             2.0 * (e[3] * q[6 * x + 3] + e[4] * q[6 * x + 4] + e[5] * q[6 * x + 5]);
+        D += k;
+        /* dual: - phi*(div1 p) */
+        double dv = orc_div1_at(x, fwd, bwd, p);
+        double best = -INFINITY;
+        for (int c = -1; c <= nbins; ++c) {
+            double uu = c < 0 ? -1.0 : (c == nbins ? 1.0 : orc_centre(c, nbins, centres));
+            double val = dv * uu - orc_data_at(uu, hist + x * nbins, nbins, lam, centres);
+            if (val > best) best = val;
+        }
+        D -= best;
+        /* dual: - Bv |p + div2 q|_1 */
+        orc_div2_at(x, fwd, bwd, q, w);
+        for (int a = 0; a < 3; ++a) D -= Bv * fabs(p[3 * x + a] + w[a]);
+    }
+    free(zeros_u);
+    free(zeros_v);
+    out[0] = E;
+    out[1] = D;
+    out[2] = E - D;
+    out[3] = certified ? 1.0 : 0.0;
+}
+
+/* ======================================================================== */
+/* Coarse-to-fine initialisation (Sec. 4.5; reading: piecewise-constant     */
+/* prolongation of u, v halved because the index spacing halves, duals      */
+/* restart at zero).  Level l+1 shares the origin of level l and has half   */
+/* its voxel edge, so fine voxel g has parent floor(g/2).                   */
+/* fine_vox3: (nf, 3) global fine voxel indices; parent lookup by the       */
+/* coarse brick list.  Missing parents leave u = v = 0 and are counted.     */
+/* ======================================================================== */
+int64_t orc_prolong(int64_t nbc, const int32_t* cbricks, const double* cu, const double* cv, int64_t nfv,
+                    const int64_t* fine_vox3, double* fu, double* fv)
+{
+    orc_bkey* t = (orc_bkey*)malloc(sizeof(orc_bkey) * (size_t)(nbc > 0 ? nbc : 1));
+    for (int64_t b = 0; b < nbc; ++b) {
+        t[b].key = orc_key(cbricks[3 * b], cbricks[3 * b + 1], cbricks[3 * b + 2]);
+        t[b].id = b;
+    }
+    qsort(t, (size_t)nbc, sizeof(orc_bkey), orc_cmp);
+    int64_t missing = 0;
+    for (int64_t k = 0; k < nfv; ++k) {
+        int64_t c[3], bq[3], lq[3];
+        for (int a = 0; a < 3; ++a) {
+            int64_t g = fine_vox3[3 * k + a];
+            c[a] = g >= 0 ? g / 2 : -((-g + 1) / 2);
+            bq[a] = c[a] >= 0 ? c[a] / ORC_BRICK : -((-c[a] + ORC_BRICK - 1) / ORC_BRICK);
+            lq[a] = c[a] - ORC_BRICK * bq[a];
+        }
+        int64_t pos = orc_find(t, nbc, orc_key(bq[0], bq[1], bq[2]));
+        if (pos < 0) {
+            fu[k] = 0.0;
+            for (int a = 0; a < 3; ++a) fv[3 * k + a] = 0.0;
+            missing++;
+            continue;
+        }
+        int64_t cx = t[pos].id * ORC_BVOX + lq[0] + 8 * lq[1] + 64 * lq[2];
+        fu[k] = cu[cx];
+        for (int a = 0; a < 3; ++a) fv[3 * k + a] = 0.5 * cv[3 * cx + a];
+    }
+    free(t);
+    return missing;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

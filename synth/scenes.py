@@ -1,0 +1,441 @@
+"""Scene generators: cameras, depth maps, brick lists, chunk workloads.
+
+Conventions shared with the C-ABI (``include/tgv.h``):
+
+* Camera frame: ``Xc = R (X - C)``; pixel ``x = fx*Xc/Zc + cx``, ``y = fy*Yc/Zc + cy``;
+  pixel (i, j) covers ``[i, i+1) x [j, j+1)``; the rows of R are the camera's
+  right, down and forward axes in world coordinates.
+* Depth maps store the camera-frame z-depth ``Zc`` of the observed surface
+  point (float32, row-major, NaN where the ray hits nothing).
+* A domain level is a list of 8^3 bricks given by integer brick coordinates;
+  voxel (i, j, k) of brick (bx, by, bz) is the global voxel
+  (8*bx+i, 8*by+j, 8*bz+k) whose centre is ``origin + (idx + 0.5) * h``.
+* Seeds: configuration c gets seed 1000 + c (``CONFIG_SEEDS``).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+CONFIG_SEEDS = {1: 1001, 2: 1002, 3: 1003, 4: 1004, 5: 1005}
+BRICK = 8
+
+
+# --------------------------------------------------------------------------- cameras
+@dataclass
+class Camera:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    R: np.ndarray  # (3, 3) float64, rows = right, down, forward
+    C: np.ndarray  # (3,) float64, camera centre
+    width: int
+    height: int
+
+    def as_array(self) -> np.ndarray:
+        """16 doubles: fx, fy, cx, cy, R (row-major), C."""
+        return np.concatenate([[self.fx, self.fy, self.cx, self.cy],
+                               np.asarray(self.R, np.float64).reshape(9),
+                               np.asarray(self.C, np.float64).reshape(3)]).astype(np.float64)
+
+    def ray_directions(self):
+        """World direction per pixel centre, scaled so its camera-frame z is 1.
+
+        Returns (H, W, 3) float64; a point at parameter t along the ray has
+        camera z-depth t.
+        """
+        i = np.arange(self.width, dtype=np.float64) + 0.5
+        j = np.arange(self.height, dtype=np.float64) + 0.5
+        xx, yy = np.meshgrid((i - self.cx) / self.fx, (j - self.cy) / self.fy)
+        dc = np.stack([xx, yy, np.ones_like(xx)], axis=-1)
+        return dc @ np.asarray(self.R, np.float64)  # (dc @ R) == (R^T dc^T)^T
+
+
+def look_at(C, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    C = np.asarray(C, np.float64)
+    f = np.asarray(target, np.float64) - C
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(up, np.float64))
+    if np.linalg.norm(r) < 1e-9:  # looking along `up`: pick any orthogonal right axis
+        r = np.cross(f, np.array([0.0, 1.0, 0.0]))
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)
+    return np.stack([r, d, f])
+
+
+def pinhole_intrinsics(width: int, height: int, hfov_deg: float):
+    fx = (width / 2.0) / math.tan(math.radians(hfov_deg) / 2.0)
+    return fx, fx, width / 2.0, height / 2.0
+
+
+# --------------------------------------------------------------------------- domains
+@dataclass
+class DomainDesc:
+    """One level of a brick domain (active bricks plus optional frozen bricks)."""
+    origin: np.ndarray
+    h: float
+    bricks: np.ndarray                     # (nb, 3) int32 brick coordinates
+    frozen: Optional[np.ndarray] = None    # (nf, 3) int32
+    frozen_u: Optional[np.ndarray] = None  # (nf, 512) float32
+    frozen_v: Optional[np.ndarray] = None  # (nf, 3, 512) float32
+    radius: float = 0.0                    # voxel radius for binning; <= 0 means h/2
+
+    @property
+    def nbricks(self) -> int:
+        return int(self.bricks.shape[0])
+
+    @property
+    def nvox(self) -> int:
+        return 512 * self.nbricks
+
+    @property
+    def nfrozen(self) -> int:
+        return 0 if self.frozen is None else int(self.frozen.shape[0])
+
+
+def dense_bricks(nbx: int, nby: int = None, nbz: int = None, offset=(0, 0, 0)) -> np.ndarray:
+    """Brick coordinates of a dense box of bricks, x fastest."""
+    nby = nbx if nby is None else nby
+    nbz = nbx if nbz is None else nbz
+    z, y, x = np.meshgrid(np.arange(nbz), np.arange(nby), np.arange(nbx), indexing="ij")
+    c = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1) + np.asarray(offset)[None, :]
+    return c.astype(np.int32)
+
+
+@dataclass
+class Scene:
+    name: str
+    domain: DomainDesc
+    cameras: List[Camera]
+    depths: List[np.ndarray]      # float32 (H, W), NaN = no sample
+    nbins: int
+    iterations: int
+    alpha1: float = 1.0
+    alpha0: float = 2.0
+    votes: Sequence[int] = field(default_factory=list)
+    meta: dict = field(default_factory=dict)
+
+
+# --------------------------------------------------------------------------- depth maps
+def plane_depth(width: int, height: int, depth: float) -> np.ndarray:
+    """Fronto-parallel plane at camera z-depth `depth` (every pixel equal)."""
+    return np.full((height, width), depth, dtype=np.float32)
+
+
+def _sphere_hit(cam: Camera, centre, radius) -> np.ndarray:
+    d = cam.ray_directions()
+    oc = np.asarray(cam.C, np.float64) - np.asarray(centre, np.float64)
+    a = np.einsum("hwk,hwk->hw", d, d)
+    b = np.einsum("hwk,k->hw", d, oc)
+    c = float(oc @ oc) - radius * radius
+    disc = b * b - a * c
+    t = np.full(a.shape, np.nan)
+    ok = disc >= 0.0
+    t[ok] = (-b[ok] - np.sqrt(disc[ok])) / a[ok]
+    t[t <= 0.0] = np.nan
+    return t
+
+
+def sphere_scene(seed: int = CONFIG_SEEDS[1], n: int = 64, nmaps: int = 16, res: int = 128,
+                 radius: float = 0.35, ring: float = 1.2, noise_frac: float = 0.005,
+                 nbins: int = 8, iterations: int = 200) -> Scene:
+    """Sphere of radius 0.35 centred in the unit cube, seen by a ring of pinhole cameras.
+
+    Cameras: `nmaps` on a ring of radius `ring` about the centre, elevation
+    alternating +20/-20 degrees, looking at the centre, 45 degree field of view.
+    Depth: analytic ray/sphere z-depth plus N(0, (noise_frac*radius)^2).
+    """
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.5, 0.5, 0.5])
+    fx, fy, cx, cy = pinhole_intrinsics(res, res, 45.0)
+    cams, depths = [], []
+    for k in range(nmaps):
+        az = 2.0 * math.pi * k / nmaps
+        el = math.radians(20.0 if k % 2 == 0 else -20.0)
+        C = centre + ring * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        cam = Camera(fx, fy, cx, cy, look_at(C, centre), C, res, res)
+        t = _sphere_hit(cam, centre, radius)
+        t = t + rng.normal(0.0, noise_frac * radius, size=t.shape)
+        cams.append(cam)
+        depths.append(t.astype(np.float32))
+    nb = n // BRICK
+    dom = DomainDesc(origin=np.zeros(3), h=1.0 / n, bricks=dense_bricks(nb))
+    return Scene("sphere", dom, cams, depths, nbins, iterations, votes=[1] * nmaps,
+                 meta=dict(centre=centre, radius=radius, seed=seed))
+
+
+# terrain --------------------------------------------------------------------------
+@dataclass
+class Terrain:
+    amp: np.ndarray    # (6,)
+    freq: np.ndarray   # (6, 2)
+    phase: np.ndarray  # (6,)
+    boxes: np.ndarray  # (nbox, 6): x0, x1, y0, y1, z0, z1
+    base: float = 0.3
+
+    def height(self, x, y, xp=np):
+        z = self.base + 0.0 * x
+        for k in range(self.amp.shape[0]):
+            z = z + float(self.amp[k]) * xp.sin(2.0 * math.pi * (float(self.freq[k, 0]) * x + float(self.freq[k, 1]) * y)
+                                                 + float(self.phase[k]))
+        return z
+
+    @property
+    def lipschitz(self) -> float:
+        return float(np.sum(2.0 * math.pi * np.linalg.norm(self.freq, axis=1) * self.amp))
+
+
+def make_terrain(rng: np.random.Generator, nbox: int = 40) -> Terrain:
+    amp = rng.uniform(0.01, 0.05, size=6)
+    fmag = rng.uniform(1.0, 8.0, size=6)
+    fdir = rng.uniform(0.0, 2.0 * math.pi, size=6)
+    freq = np.stack([fmag * np.cos(fdir), fmag * np.sin(fdir)], axis=1)
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=6)
+    t = Terrain(amp, freq, phase, np.zeros((0, 6)))
+    boxes = []
+    for _ in range(nbox):
+        sx, sy = rng.uniform(0.02, 0.12, size=2)
+        cxb, cyb = rng.uniform(0.1, 0.9, size=2)
+        top = float(t.height(np.array(cxb), np.array(cyb))) + rng.uniform(0.05, 0.3)
+        boxes.append([cxb - sx / 2, cxb + sx / 2, cyb - sy / 2, cyb + sy / 2, -1.0, top])
+    t.boxes = np.array(boxes, dtype=np.float64)
+    return t
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _terrain_depth_torch(terrain: Terrain, cam: Camera, step: float, device) -> np.ndarray:
+    """Ray-cast the height field (Lipschitz-bounded march + bisection) and the boxes."""
+    torch = _torch()
+    d = torch.as_tensor(cam.ray_directions().reshape(-1, 3), dtype=torch.float64, device=device)
+    C = torch.as_tensor(np.asarray(cam.C), dtype=torch.float64, device=device)
+    n = d.shape[0]
+    ztop = terrain.base + float(np.sum(terrain.amp)) + 1e-6
+    zbot = terrain.base - float(np.sum(terrain.amp)) - 1e-6
+    L = terrain.lipschitz
+    dz = d[:, 2]
+    dxy = torch.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2)
+    dn = torch.sqrt(dz * dz + dxy * dxy)
+    down = dz < -1e-9
+    big = torch.full((n,), float("inf"), dtype=torch.float64, device=device)
+    t0 = torch.where(down, torch.clamp((ztop - C[2]) / torch.where(down, dz, -torch.ones_like(dz)), min=0.0), big)
+    t1 = torch.where(down, (zbot - C[2]) / torch.where(down, dz, -torch.ones_like(dz)), big)
+
+    def g(t, idx):
+        p = C[None, :] + t[:, None] * d[idx]
+        return p[:, 2] - terrain.height(p[:, 0], p[:, 1], xp=torch)
+
+    t_hit = big.clone()
+    idx = torch.nonzero(down).squeeze(1)
+    t = t0[idx].clone()
+    gv = g(t, idx)
+    denom = (-dz[idx]) + L * dxy[idx]
+    dtmin = step / dn[idx]
+    for _ in range(20000):
+        if idx.numel() == 0:
+            break
+        tn = t + torch.maximum(gv / denom, dtmin)
+        gn = g(tn, idx)
+        crossed = gn <= 0.0
+        lo, hi = t[crossed], tn[crossed]
+        ci = idx[crossed]
+        for _b in range(40):
+            mid = 0.5 * (lo + hi)
+            gm = g(mid, ci)
+            below = gm <= 0.0
+            hi = torch.where(below, mid, hi)
+            lo = torch.where(below, lo, mid)
+        t_hit[ci] = hi
+        keep = (~crossed) & (tn <= t1[idx])
+        idx, t, gv = idx[keep], tn[keep], gn[keep]
+        denom, dtmin = denom[keep], dtmin[keep]
+    # boxes: slab test
+    if terrain.boxes.shape[0]:
+        inv = 1.0 / torch.where(d.abs() < 1e-300, torch.full_like(d, 1e-300), d)
+        for bx in terrain.boxes:
+            lo = torch.as_tensor(bx[[0, 2, 4]], dtype=torch.float64, device=device)
+            hi = torch.as_tensor(bx[[1, 3, 5]], dtype=torch.float64, device=device)
+            ta = (lo[None, :] - C[None, :]) * inv
+            tb = (hi[None, :] - C[None, :]) * inv
+            tnear = torch.minimum(ta, tb).max(dim=1).values
+            tfar = torch.maximum(ta, tb).min(dim=1).values
+            hit = (tnear <= tfar) & (tnear > 0.0)
+            t_hit = torch.where(hit & (tnear < t_hit), tnear, t_hit)
+    out = t_hit.reshape(cam.height, cam.width)
+    out = torch.where(torch.isinf(out), torch.full_like(out, float("nan")), out)
+    return out.cpu().numpy()
+
+
+def terrain_scene(seed: int = CONFIG_SEEDS[2], n: int = 256, nmaps: int = 64, res: int = 512,
+                  nbins: int = 10, iterations: int = 500, noise_vox: float = 0.3,
+                  outlier_frac: float = 0.05, device=None) -> Scene:
+    """Terrain of 6 random sinusoids plus 40 box buildings over the unit square.
+
+    Cameras: 16 nadir cameras on a 4x4 grid at altitude 1.5 (40 degree field of
+    view) and 48 oblique cameras (4 azimuths x 12, tilted 40 degrees from nadir,
+    50 degree field of view).  If `nmaps` < 64 the first `nmaps` of the interleaved
+    list are used.  Depth noise N(0, (noise_vox*h)^2); a fraction `outlier_frac`
+    of valid pixels is replaced by U(min, max) of that map's depths.
+    """
+    torch = _torch()
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    rng = np.random.default_rng(seed)
+    terrain = make_terrain(rng)
+    h = 1.0 / n
+    cams: List[Camera] = []
+    fxn = pinhole_intrinsics(res, res, 40.0)
+    for gy in range(4):
+        for gx in range(4):
+            C = np.array([0.125 + 0.25 * gx, 0.125 + 0.25 * gy, 1.5])
+            cams.append(Camera(*fxn, look_at(C, C - np.array([0, 0, 1.0]), up=(0, 1, 0)), C, res, res))
+    fxo = pinhole_intrinsics(res, res, 50.0)
+    tilt = math.radians(40.0)
+    obl = []
+    for k in range(4):
+        az = k * math.pi / 2
+        for gy in range(3):
+            for gx in range(4):
+                tx, ty = 0.2 + 0.2 * gx - 0.5, 0.25 + 0.25 * gy - 0.5
+                ca, sa = math.cos(az), math.sin(az)
+                T = np.array([0.5 + ca * tx - sa * ty, 0.5 + sa * tx + ca * ty, terrain.base])
+                off = 1.2 * math.tan(tilt)
+                C = T + np.array([-ca * off, -sa * off, 1.2])
+                obl.append(Camera(*fxo, look_at(C, T), C, res, res))
+    # interleave so that a prefix of the list mixes nadir and oblique views
+    allc = []
+    for k in range(48):
+        if k % 3 == 0 and k // 3 < 16:
+            allc.append(cams[k // 3])
+        allc.append(obl[k])
+    cams = allc[:nmaps]
+    depths = []
+    for cam in cams:
+        t = _terrain_depth_torch(terrain, cam, step=h / 4, device=device)
+        valid = np.isfinite(t)
+        t = t + rng.normal(0.0, noise_vox * h, size=t.shape)
+        if valid.any():
+            lo, hi = float(np.nanmin(t[valid])), float(np.nanmax(t[valid]))
+            out = (rng.random(t.shape) < outlier_frac) & valid
+            t[out] = rng.uniform(lo, hi, size=int(out.sum()))
+        depths.append(t.astype(np.float32))
+    dom = DomainDesc(origin=np.zeros(3), h=h, bricks=dense_bricks(n // BRICK))
+    return Scene("terrain", dom, cams, depths, nbins, iterations, votes=[1] * len(cams),
+                 meta=dict(seed=seed, terrain=terrain))
+
+
+# --------------------------------------------------------------------------- histograms
+def random_histograms(rng: np.random.Generator, nvox: int, nbins: int, max_count: int = 20,
+                      empty_frac: float = 0.1) -> np.ndarray:
+    """Uniform random per-voxel counts (uint32, (nvox, nbins)); a fraction of voxels empty."""
+    hst = rng.integers(0, max_count + 1, size=(nvox, nbins)).astype(np.uint32)
+    hst[rng.random(nvox) < empty_frac] = 0
+    return hst
+
+
+# --------------------------------------------------------------------------- chunk workloads
+@dataclass
+class ChunkSpec:
+    """One chunk-solve request: a box of bricks with a frozen one-brick face shell."""
+    domain: DomainDesc
+    hist: np.ndarray   # (nvox, nbins) uint32
+    nbins: int
+    iterations: int
+    arrival: float = 0.0
+
+
+def _box_dims(nb: int, rng) -> tuple:
+    s = max(1, round(nb ** (1.0 / 3.0)))
+    a, b = s, s
+    c = max(1, round(nb / (a * b)))
+    return a, b, c
+
+
+def _synthetic_votes(s_vox: np.ndarray, nbins: int, rng, views: int) -> np.ndarray:
+    """Synthetic per-voxel counts from the height above a surface (voxel units).
+
+    Statistical input model (not Alg. 1): each of `views` virtual observations
+    of a voxel with height s above the surface lands in a bin drawn around
+    (n-1)/2 + s*(n-1)/6 with unit Gaussian jitter, clipped to the bin range;
+    voxels deeper than 9 voxels below the surface get no observations; 5% of
+    observations are uniform outliers.
+    """
+    nv = s_vox.shape[0]
+    out = np.zeros((nv, nbins), np.uint32)
+    seen = s_vox > -9.0
+    centre = (nbins - 1) / 2.0 + s_vox * (nbins - 1) / 6.0
+    for _ in range(views):
+        b = np.rint(centre + rng.normal(0.0, 1.0, size=nv))
+        outl = rng.random(nv) < 0.05
+        b[outl] = rng.integers(0, nbins, size=int(outl.sum()))
+        b = np.clip(b, 0, nbins - 1).astype(np.int64)
+        np.add.at(out, (np.nonzero(seen)[0], b[seen]), 1)
+    return out
+
+
+def chunk_workload(seed: int, nchunks: int, min_vox: int, max_vox: int, nbins_range=(10, 10),
+                   iters_range=(300, 300), rate: float = 0.0, max_total_vox: Optional[int] = None,
+                   views: int = 12) -> List[ChunkSpec]:
+    """Chunks cut from an unbounded terrain-style scene (sum of 6 sinusoids).
+
+    Active voxel count log-uniform in [min_vox, max_vox], rounded to whole
+    bricks and shaped as a near-cubic box of bricks placed at a random position;
+    its frozen halo is every brick face-adjacent to the box, carrying
+    u = clip(s/3, -1, 1) (s = height above the surface in voxels) and v = 0.
+    `rate` > 0 draws Poisson arrival times (requests/s).
+    """
+    rng = np.random.default_rng(seed)
+    terrain = make_terrain(rng, nbox=0)
+    specs = []
+    t_arr = 0.0
+    for c in range(nchunks):
+        nvox = math.exp(rng.uniform(math.log(min_vox), math.log(max_vox)))
+        nb = max(1, int(round(nvox / 512)))
+        a, b, cdim = _box_dims(nb, rng)
+        n = 256
+        h = 1.0 / n
+        off = np.array([rng.integers(0, 32), rng.integers(0, 32), 0])
+        bricks = dense_bricks(a, b, cdim, offset=off)
+        # vertical placement: centre the box on the terrain height at its centre
+        cxw = (off[0] + a / 2) * 8 * h
+        cyw = (off[1] + b / 2) * 8 * h
+        zc = float(terrain.height(np.array(cxw), np.array(cyw)))
+        oz = int(round(zc / (8 * h) - cdim / 2))
+        bricks[:, 2] += oz
+        # frozen face shell
+        act = {tuple(x) for x in bricks.tolist()}
+        fro = set()
+        for x in act:
+            for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                y = (x[0] + dx, x[1] + dy, x[2] + dz)
+                if y not in act:
+                    fro.add(y)
+        frozen = np.array(sorted(fro), dtype=np.int32).reshape(-1, 3)
+        nbins = int(rng.integers(nbins_range[0], nbins_range[1] + 1))
+        iters = int(rng.integers(iters_range[0], iters_range[1] + 1))
+
+        def heights(bc):
+            li = np.arange(512)
+            lx, ly, lz = li % 8, (li // 8) % 8, li // 64
+            gx = (bc[:, 0:1] * 8 + lx[None, :] + 0.5) * h
+            gy = (bc[:, 1:2] * 8 + ly[None, :] + 0.5) * h
+            gz = (bc[:, 2:3] * 8 + lz[None, :] + 0.5) * h
+            return (gz - terrain.height(gx, gy)) / h  # (nb, 512) voxel units
+
+        s_act = heights(bricks).reshape(-1)
+        hist = _synthetic_votes(s_act, nbins, rng, views)
+        fu = np.clip(heights(frozen) / 3.0, -1.0, 1.0).astype(np.float32) if len(frozen) else None
+        fv = np.zeros((len(frozen), 3, 512), np.float32) if len(frozen) else None
+        dom = DomainDesc(origin=np.zeros(3), h=h, bricks=bricks,
+                         frozen=frozen if len(frozen) else None, frozen_u=fu, frozen_v=fv)
+        if rate > 0:
+            t_arr += rng.exponential(1.0 / rate)
+        specs.append(ChunkSpec(dom, hist, nbins, iters, t_arr))
+    return specs
