@@ -1,0 +1,237 @@
+/*
+ * tgv.h -- C-ABI of the B300 (sm_103a) histogram + TGV primal-dual library.
+ *
+ * The calls follow the problem statement of "Out-of-Core Surface Reconstruction
+ * via Global TGV Minimization" (arXiv 2107.14790): aligned depth maps
+ * (Sec. 3.1) are turned into per-voxel visibility histograms (Sec. 3.4, Alg. 1,
+ * Sec. 4.4), the TGV functional of Eq. 2-3 is minimised by primal-dual
+ * iterations (Sec. 3.2, Sec. 4.5), and the indicator field u, whose zero level
+ * set is the surface, is read back (Sec. 4.6).
+ *
+ * Conventions shared by every call
+ *  - Domain: a level is a set of 8x8x8-voxel bricks given by integer brick
+ *    coordinates (Sec. 3.3 bounds the neighbours per cube; here every brick has
+ *    a fixed neighbour table).  Voxel (i,j,k) of brick (bx,by,bz) is the global
+ *    voxel (8bx+i, 8by+j, 8bz+k) with centre origin + (index + 0.5) * h.
+ *    Voxel order in every host/device array exchanged through this ABI: active
+ *    brick b in the order given at creation, then local index i + 8j + 64k.
+ *    Multi-component fields are voxel-major: element [voxel * ncomp + c].
+ *  - Frozen bricks (Sec. 4.5, set B): bricks outside the solved set whose u and
+ *    v are constants.  A voxel link into a frozen brick uses those constants;
+ *    a link to a position in neither set is "none" (no difference is taken).
+ *  - Ownership: the domain owns all of its device state.  The caller owns every
+ *    input and output buffer; a device input must stay valid until the
+ *    domain's stream has reached the call.  Pointers may be host or device
+ *    memory wherever a call says "host or device" (detected per call).
+ *  - Streams: all device work of a domain runs on the CUDA stream given at
+ *    creation (NULL = legacy default stream).  Calls that return host data
+ *    synchronise that stream.
+ *  - Errors: every call returns a tgv_status and never throws across the ABI.
+ *    A CUDA error is sticky: later calls on that domain return TGV_ERR_STATE.
+ *    tgv_last_error() gives a message for the last failure on a domain.
+ *  - Device code requires sm_103a (B300).
+ */
+#ifndef TGV_H_
+#define TGV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TGV_API __attribute__((visibility("default")))
+#else
+#define TGV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TGV_OK = 0,
+    TGV_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or parameter */
+    TGV_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed */
+    TGV_ERR_BUDGET = 3,        /* a stated limit would be exceeded (vote counts, HBM budget) */
+    TGV_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    TGV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    TGV_ERR_STATE = 6,         /* the domain is unusable after an earlier CUDA error */
+    TGV_ERR_UNSUPPORTED = 7    /* a recognised option that is not built */
+} tgv_status;
+
+/* Storage type of v, vbar, p, q (u and ubar are always FP32; arithmetic is FP32). */
+enum { TGV_STORAGE_FP32 = 0, TGV_STORAGE_BF16 = 1, TGV_STORAGE_FP16 = 2 };
+
+/* Histogram bin centres c_b (the data term sum_b h_b |u - c_b|, Sec. 3.4).
+ * ENDPOINTS: c_b = -1 + 2b/(n-1)  (bin 0 = occluded -1, bin n-1 = free space +1)
+ * MIDPOINTS: c_b = -1 + (2b+1)/n */
+enum { TGV_CENTRES_ENDPOINTS = 0, TGV_CENTRES_MIDPOINTS = 1 };
+
+/* Field ids for tgv_extract_field / tgv_set_field, with their component counts. */
+enum {
+    TGV_FIELD_U = 0,    /* 1 component */
+    TGV_FIELD_UBAR = 1, /* 1 */
+    TGV_FIELD_V = 2,    /* 3: v_x, v_y, v_z */
+    TGV_FIELD_VBAR = 3, /* 3 */
+    TGV_FIELD_P = 4,    /* 3 */
+    TGV_FIELD_Q = 5     /* 6: q_xx, q_yy, q_zz, q_xy, q_xz, q_yz (symmetric) */
+};
+
+enum { TGV_PINHOLE = 0, TGV_SPHERICAL = 1 };
+
+typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
+
+/* Solver parameters (Eq. 2 with the primal-dual step sizes of Sec. 3.2).
+ * Defaults (tgv_default_params): nbins 8 (Alg. 1), alpha1 1, alpha0 2, lambda 1,
+ * tau = sigma = 0.2 (tau*sigma*24 < 1: ||K||^2 <= 24 for the forward/backward
+ * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2. */
+typedef struct {
+    int32_t nbins;       /* histogram bins, 2..16 */
+    float alpha1;        /* weight of |grad u - v| */
+    float alpha0;        /* weight of |E(v)| */
+    float lambda;        /* weight of the histogram data term */
+    float tau;           /* primal step */
+    float sigma;         /* dual step */
+    int32_t storage;     /* TGV_STORAGE_* */
+    int32_t clamp_u;     /* 1: project u onto [-1, 1] after the prox */
+    int32_t centres;     /* TGV_CENTRES_* */
+    float box_v;         /* bound B_v on |v_a| used by the duality gap */
+} tgv_params;
+
+/* One level of a domain (all arrays host memory, copied at creation).
+ *  origin, h: voxel grid of this level; radius: the voxel radius r of Alg. 1
+ *  (r <= 0 selects h/2).  brick_coords: 3*nbricks int32 (x, y, z) of the
+ *  active bricks, no duplicates.  frozen_coords: 3*nfrozen int32 of frozen
+ *  bricks (disjoint from the active ones).  frozen_u: 512*nfrozen floats,
+ *  frozen_v: 3*512*nfrozen floats laid out [brick][component][512]; either may
+ *  be NULL (zeros, or filled later by tgv_prolong). */
+typedef struct {
+    double origin[3];
+    double h;
+    double radius;
+    int64_t nbricks;
+    const int32_t* brick_coords;
+    int64_t nfrozen;
+    const int32_t* frozen_coords;
+    const float* frozen_u;
+    const float* frozen_v;
+} tgv_level_desc;
+
+/* Pinhole camera (Sec. 3.1 depth maps).  Camera frame Xc = R (X - C), R
+ * row-major with rows = right, down, forward; pixel x = fx Xc/Zc + cx,
+ * y = fy Yc/Zc + cy; pixel (i, j) covers [i, i+1) x [j, j+1).  Depth maps
+ * hold the camera-frame z-depth of the observed point; NaN, inf and values
+ * <= 0 mark pixels without a sample.  model must be TGV_PINHOLE. */
+typedef struct {
+    double fx, fy, cx, cy;
+    double R[9];
+    double C[3];
+    int32_t width, height;
+    int32_t model;
+} tgv_camera;
+
+/* Fills *out with the defaults listed at tgv_params. */
+TGV_API tgv_status tgv_default_params(tgv_params* out);
+
+/* Creates a domain of nlevels levels (level 0 coarsest).  Allocates all device
+ * state on the current device; u, v, p, q and the histograms start at zero.
+ * stream: a cudaStream_t (NULL = legacy default stream) used for every call.
+ * Errors: INVALID_ARG (bad sizes, duplicate or overlapping bricks, nbins out of
+ * range, unknown storage), OUT_OF_MEMORY, CUDA. */
+TGV_API tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, const tgv_params* prm,
+                             void* stream, tgv_domain** out);
+
+/* Frees all device state.  NULL is ignored. */
+TGV_API void tgv_destroy_domain(tgv_domain* d);
+
+/* Alg. 1 (Sec. 3.4) for one depth map: builds the map's mipmap pyramid on the
+ * device (each coarser pixel = minimum of its valid children) and adds `vote`
+ * (1, or 5 for noise-free LIDAR) to bin
+ *   floor(((clamp(a/delta, -1, 1) + 1)/2) * nbins)   (clamped to nbins-1)
+ * of every voxel whose centre projects to a valid pixel at its level of
+ * detail and has a = depth - Zc >= -eta, with delta = 6r, eta = 3 delta
+ * (Sec. 3.1).  The decision is taken in FP32 with one rounding per operation.
+ * depth_dev: device pointer, height rows of pitch_elems floats.
+ * Errors: INVALID_ARG (level, camera, pitch < width, NULL), BUDGET (a voxel
+ * count could pass 65535: counts are stored as 16-bit integers), CUDA. */
+TGV_API tgv_status tgv_accumulate_depthmap(tgv_domain* d, int32_t level, const tgv_camera* cam,
+                                   const float* depth_dev, int64_t pitch_elems, uint32_t vote);
+
+/* Same as tgv_accumulate_depthmap for nmaps maps of one size in one pass:
+ * map m starts at depth_dev + m * map_stride_elems; cams[m] and votes[m]
+ * (votes may be NULL: all 1) are host arrays.  Results equal nmaps single
+ * calls in any order (integer counts). */
+TGV_API tgv_status tgv_accumulate_depthmaps(tgv_domain* d, int32_t level, const tgv_camera* cams, int32_t nmaps,
+                                    const float* depth_dev, int64_t pitch_elems, int64_t map_stride_elems,
+                                    const uint32_t* votes);
+
+/* Runs `iterations` primal-dual iterations (Sec. 3.2; Chambolle-Pock order,
+ * theta = 1) of Eq. 2 on one level:
+ *   p <- proj_{|p|<=alpha1}(p + sigma (grad ubar - vbar))
+ *   q <- proj_{|q|_F<=alpha0}(q + sigma E(vbar))
+ *   u+ <- clamp(prox_{tau lambda hist}(u + tau div1 p)),  v+ <- v + tau (p + div2 q)
+ *   ubar <- 2u+ - u,  vbar <- 2v+ - v
+ * with forward differences for grad, backward differences for E (Eq. 3) and
+ * their exact negative adjoints; frozen bricks stay fixed (Sec. 4.5).
+ * energy_gap_out: NULL, or 4 doubles receiving (energy, dual value, gap,
+ * certified) after the last iteration (see tgv_energy); a non-NULL pointer
+ * synchronises the stream.  Errors: INVALID_ARG, STATE, CUDA. */
+TGV_API tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out);
+
+/* Energy of Eq. 2 on the level (FP64 accumulation of FP32 per-voxel terms,
+ * fixed-order deterministic reduction) and the value of the dual problem
+ * with u in [-1, 1] and |v_a| <= box_v:
+ *   out[0] = alpha1 sum|grad u - v| + alpha0 sum|E v|_F + lambda sum_x sum_b h_b|u - c_b|
+ *   out[1] = <k0,(p,q)> - sum_x phi*_x(div1 p) - box_v |p + div2 q|_1
+ *   out[2] = out[0] - out[1]  (>= 0 when out[3] = 1)
+ *   out[3] = 1 if every |v_a| <= box_v, else 0
+ * (k0 = the frozen-neighbour constants; phi*_x the conjugate of the clamped
+ * data term.)  out: host, 4 doubles.  Synchronises the stream. */
+TGV_API tgv_status tgv_energy(tgv_domain* d, int32_t level, double* out);
+
+/* Copies a field of one level to `out` (host or device), voxel-major FP32,
+ * count = number of active voxels * components of the field. */
+TGV_API tgv_status tgv_extract_field(tgv_domain* d, int32_t level, int32_t field, float* out, int64_t count);
+
+/* Overwrites a field of one level from `in` (host or device, same layout as
+ * tgv_extract_field; values are rounded to the storage type). */
+TGV_API tgv_status tgv_set_field(tgv_domain* d, int32_t level, int32_t field, const float* in, int64_t count);
+
+/* Copies the histograms of one level to `out` (host or device):
+ * uint32 [voxel][nbins], count = active voxels * nbins. */
+TGV_API tgv_status tgv_extract_histograms(tgv_domain* d, int32_t level, uint32_t* out, int64_t count);
+
+/* Overwrites the histograms of one level from `in` (host or device, same
+ * layout).  Errors: BUDGET if a count exceeds 65535. */
+TGV_API tgv_status tgv_set_histograms(tgv_domain* d, int32_t level, const uint32_t* in, int64_t count);
+
+/* Zeroes u, ubar, v, vbar, p, q of a level (frozen bricks keep their values);
+ * clear_hist != 0 also zeroes its histograms. */
+TGV_API tgv_status tgv_reset(tgv_domain* d, int32_t level, int32_t clear_hist);
+
+/* Coarse-to-fine start of level from_level+1 (Sec. 4.5): every active and
+ * frozen voxel of the fine level takes u from its parent voxel on level
+ * from_level and v halved (the index spacing halves); ubar = u, vbar = v,
+ * p = q = 0.  Requires equal origins and h_fine = h_coarse / 2.  Fine voxels
+ * without an active parent get u = v = 0.  Errors: INVALID_ARG. */
+TGV_API tgv_status tgv_prolong(tgv_domain* d, int32_t from_level);
+
+/* Waits for all work queued on the domain's stream. */
+TGV_API tgv_status tgv_synchronize(tgv_domain* d);
+
+/* Device bytes held by the domain (state, tables, scratch). */
+TGV_API int64_t tgv_domain_bytes(const tgv_domain* d);
+
+/* Number of active voxels of a level (0 for a bad level). */
+TGV_API int64_t tgv_level_voxels(const tgv_domain* d, int32_t level);
+
+/* Number of kernels this library launched on the domain so far. */
+TGV_API int64_t tgv_launch_count(const tgv_domain* d);
+
+TGV_API const char* tgv_status_string(tgv_status s);
+TGV_API const char* tgv_last_error(const tgv_domain* d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TGV_H_ */

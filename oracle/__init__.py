@@ -267,5 +267,24 @@ class OracleLevel:
         return int(missing)
 
 
+def prolong_frozen(fine: OracleLevel, coarse: OracleLevel) -> int:
+    """Frozen voxels of `fine` take u from their parent voxel on `coarse` and v halved (Sec. 4.5)."""
+    fr = getattr(fine.desc, "frozen", None)
+    if fr is None or len(fr) == 0:
+        return 0
+    fr = _c(fr, np.int32).reshape(-1, 3)
+    li = np.arange(512)
+    loc = np.stack([li % 8, (li // 8) % 8, li // 64], axis=1)
+    g = _c((8 * fr[:, None, :] + loc[None]).reshape(-1, 3), np.int64)
+    n = g.shape[0]
+    fu = np.empty(n)
+    fv = np.empty(3 * n)
+    missing = lib().orc_prolong(coarse.bricks.shape[0], _p(coarse.bricks), _p(coarse.u),
+                                _p(_c(coarse.v, np.float64)), n, _p(g), _p(fu), _p(fv))
+    fine.fu[:n] = fu
+    fine.fv[:3 * n] = fv
+    return int(missing)
+
+
 def max_threads() -> int:
     return int(lib().orc_max_threads())

@@ -1,0 +1,752 @@
+// Host side of the C-ABI declared in include/tgv.h: domain creation (brick
+// neighbour tables, device state), field and histogram transfers, reset,
+// coarse-to-fine prolongation, error handling.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+
+#include "tgv_internal.cuh"
+
+// ------------------------------------------------------------------------- errors
+tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg)
+{
+    if (d) d->last_error = msg;
+    return s;
+}
+
+tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return TGV_OK;
+    if (d) {
+        d->broken = true;
+        d->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return TGV_ERR_CUDA;
+}
+
+tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes)
+{
+    if (bytes <= s.cap) return TGV_OK;
+    if (s.ptr) {
+        // the old buffer may still be read by queued work
+        cudaError_t e = cudaStreamSynchronize(d->stream);
+        if (e != cudaSuccess) return tgv_cuda_check(d, e, "scratch sync");
+        cudaFree(s.ptr);
+        d->bytes -= (int64_t)s.cap;
+        s.ptr = nullptr;
+        s.cap = 0;
+    }
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&s.ptr, cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s.ptr = nullptr;
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "scratch allocation failed");
+    }
+    s.cap = cap;
+    d->bytes += (int64_t)cap;
+    return TGV_OK;
+}
+
+void tgv_bin_centres(const tgv_params& prm, float* c)
+{
+    const int n = prm.nbins;
+    for (int b = 0; b < TGV_MAX_BINS; ++b) {
+        double v = 0.0;
+        if (b < n)
+            v = prm.centres == TGV_CENTRES_ENDPOINTS ? -1.0 + 2.0 * b / (double)(n - 1)
+                                                     : -1.0 + (2.0 * b + 1.0) / (double)n;
+        c[b] = (float)v;
+    }
+}
+
+namespace {
+
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+        else old = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
+inline uint64_t brick_key(int32_t x, int32_t y, int32_t z)
+{
+    const uint64_t B = (uint64_t)1 << 20;
+    return (((uint64_t)(z + (int64_t)B) * (2 * B)) + (uint64_t)(y + (int64_t)B)) * (2 * B) + (uint64_t)(x + (int64_t)B);
+}
+
+const int kSlotOffset[TGV_NNBR][3] = {
+    {+1, 0, 0}, {-1, 0, 0}, {0, +1, 0}, {0, -1, 0}, {0, 0, +1}, {0, 0, -1},
+    {-1, +1, 0}, {-1, 0, +1}, {+1, -1, 0}, {0, -1, +1}, {+1, 0, -1}, {0, +1, -1}};
+
+int ncomp_of(int field)
+{
+    switch (field) {
+    case TGV_FIELD_U:
+    case TGV_FIELD_UBAR: return 1;
+    case TGV_FIELD_V:
+    case TGV_FIELD_VBAR:
+    case TGV_FIELD_P: return 3;
+    case TGV_FIELD_Q: return 6;
+    }
+    return 0;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+unsigned grid1(int64_t n, int block, int sms)
+{
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)sms * 32;
+    if (g > cap) g = cap;
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+// ------------------------------------------------------------------------- kernels
+template <typename S>
+__global__ void f32_to_s_kernel(const float* __restrict__ src, S* __restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        st_s(dst + i, src[i]);
+}
+
+// brick-major [brick][comp][512] storage <-> voxel-major [voxel][comp] float
+template <typename S>
+__global__ void field_extract_kernel(const S* __restrict__ f, float* __restrict__ out, int64_t nvox, int ncomp)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * ncomp;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vox = i / ncomp;
+        const int c = (int)(i - vox * ncomp);
+        const int64_t b = vox >> 9, l = vox & 511;
+        out[i] = ld_s(f + (b * ncomp + c) * TGV_BVOX + l);
+    }
+}
+
+template <typename S>
+__global__ void field_set_kernel(S* __restrict__ f, const float* __restrict__ in, int64_t nvox, int ncomp)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * ncomp;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vox = i / ncomp;
+        const int c = (int)(i - vox * ncomp);
+        const int64_t b = vox >> 9, l = vox & 511;
+        st_s(f + (b * ncomp + c) * TGV_BVOX + l, in[i]);
+    }
+}
+
+__global__ void hist_unpack_kernel(const uint32_t* __restrict__ h, uint32_t* __restrict__ out, int64_t nvox, int nbins,
+                                   int npairs)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * nbins;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vox = i / nbins;
+        const int k = (int)(i - vox * nbins);
+        const int64_t b = vox >> 9, l = vox & 511;
+        const uint32_t w = h[(b * npairs + (k >> 1)) * TGV_BVOX + l];
+        out[i] = (w >> ((k & 1) * 16)) & 0xffffu;
+    }
+}
+
+// one thread per (voxel, pair); records the largest input count in *maxc
+__global__ void hist_pack_kernel(uint32_t* __restrict__ h, const uint32_t* __restrict__ in, int64_t nvox, int nbins,
+                                 int npairs, unsigned int* maxc)
+{
+    unsigned int m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * npairs;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vox = i / npairs;
+        const int k = (int)(i - vox * npairs);
+        const int64_t b = vox >> 9, l = vox & 511;
+        const uint32_t lo = in[vox * nbins + 2 * k];
+        const uint32_t hi = 2 * k + 1 < nbins ? in[vox * nbins + 2 * k + 1] : 0u;
+        m = max(m, max(lo, hi));
+        h[(b * npairs + k) * TGV_BVOX + l] = (lo & 0xffffu) | ((hi & 0xffffu) << 16);
+    }
+    if (m) atomicMax(maxc, m);
+}
+
+// Fine voxel (brick fb, local l) takes u and v/2 of its parent voxel; all 512
+// voxels of a fine brick share one parent brick (parent[fb], -1 = none).
+template <typename S>
+__global__ void prolong_kernel(const float* __restrict__ cu, const S* __restrict__ cv, const int32_t* __restrict__ parent,
+                               const int32_t* __restrict__ fcoords, int64_t nfall, int64_t nfact, float* fu,
+                               float* fub0, float* fub1, S* fv, S* fvb0, S* fvb1)
+{
+    const int64_t fb = blockIdx.x;
+    const int l = threadIdx.x;
+    const int loc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+    const int32_t pb = parent[fb];
+    float u = 0.0f, v[3] = {0.0f, 0.0f, 0.0f};
+    if (pb >= 0) {
+        int cl[3];
+        for (int a = 0; a < 3; ++a) cl[a] = 4 * (fcoords[3 * fb + a] & 1) + (loc[a] >> 1);
+        const int64_t ci = (int64_t)cl[0] + 8 * cl[1] + 64 * cl[2];
+        u = cu[(int64_t)pb * TGV_BVOX + ci];
+        for (int c = 0; c < 3; ++c) v[c] = 0.5f * ld_s(cv + ((int64_t)pb * 3 + c) * TGV_BVOX + ci);
+    }
+    const int64_t vi = fb * TGV_BVOX + l;
+    fu[vi] = u;
+    fub0[vi] = u;
+    fub1[vi] = u;
+    for (int c = 0; c < 3; ++c) {
+        const int64_t oi = (fb * 3 + c) * TGV_BVOX + l;
+        st_s(fv + oi, v[c]);
+        st_s(fvb0 + oi, v[c]);
+        st_s(fvb1 + oi, v[c]);
+    }
+    (void)nfall;
+    (void)nfact;
+}
+
+tgv_status check_domain(tgv_domain* d)
+{
+    if (!d) return TGV_ERR_INVALID_ARG;
+    if (d->broken) return tgv_fail(d, TGV_ERR_STATE, "domain unusable after an earlier CUDA error: " + d->last_error);
+    return TGV_OK;
+}
+
+tgv_status get_level(tgv_domain* d, int32_t level, TgvLevel** L)
+{
+    if (level < 0 || level >= (int32_t)d->levels.size()) return tgv_fail(d, TGV_ERR_INVALID_ARG, "level out of range");
+    *L = &d->levels[level];
+    return TGV_OK;
+}
+
+tgv_status dalloc(tgv_domain* d, void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    d->bytes += (int64_t)bytes;
+    return TGV_OK;
+}
+
+void free_level(TgvLevel& L)
+{
+    void* ptrs[] = {L.u, L.ubar[0], L.ubar[1], L.v, L.vbar[0], L.vbar[1], L.p[0], L.p[1],
+                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+void* field_ptr(TgvLevel& L, int field)
+{
+    switch (field) {
+    case TGV_FIELD_U: return L.u;
+    case TGV_FIELD_UBAR: return L.ubar[L.cur];
+    case TGV_FIELD_V: return L.v;
+    case TGV_FIELD_VBAR: return L.vbar[L.cur];
+    case TGV_FIELD_P: return L.p[L.cur];
+    case TGV_FIELD_Q: return L.q[L.cur];
+    }
+    return nullptr;
+}
+
+template <typename S>
+void launch_f32_to_s(tgv_domain* d, const float* src, void* dst, int64_t n)
+{
+    f32_to_s_kernel<S><<<grid1(n, 256, d->sm_count), 256, 0, d->stream>>>(src, (S*)dst, n);
+    d->launches++;
+}
+
+void f32_to_storage(tgv_domain* d, const float* src, void* dst, int64_t n)
+{
+    switch (d->prm.storage) {
+    case TGV_STORAGE_FP32: launch_f32_to_s<float>(d, src, dst, n); break;
+    case TGV_STORAGE_BF16: launch_f32_to_s<__nv_bfloat16>(d, src, dst, n); break;
+    default: launch_f32_to_s<__half>(d, src, dst, n); break;
+    }
+}
+
+tgv_status build_level(tgv_domain* d, const tgv_level_desc& desc, TgvLevel& L)
+{
+    if (desc.nbricks < 0 || desc.nfrozen < 0 || (desc.nbricks > 0 && !desc.brick_coords) ||
+        (desc.nfrozen > 0 && !desc.frozen_coords))
+        return tgv_fail(d, TGV_ERR_INVALID_ARG, "bad brick list");
+    if (!(desc.h > 0.0) || !isfinite(desc.h)) return tgv_fail(d, TGV_ERR_INVALID_ARG, "h must be positive");
+    const int64_t nb = desc.nbricks, nf = desc.nfrozen, na = nb + nf;
+    if (na > ((int64_t)1 << 31) / 2) return tgv_fail(d, TGV_ERR_INVALID_ARG, "too many bricks");
+    L.nb = nb;
+    L.nf = nf;
+    for (int a = 0; a < 3; ++a) L.origin[a] = desc.origin[a];
+    L.h = desc.h;
+    L.radius = desc.radius > 0.0 ? desc.radius : desc.h / 2.0;
+    L.coords.resize(3 * (size_t)na);
+    std::unordered_map<uint64_t, int32_t> index;
+    index.reserve((size_t)na * 2);
+    for (int64_t i = 0; i < na; ++i) {
+        const int32_t* c = i < nb ? desc.brick_coords + 3 * i : desc.frozen_coords + 3 * (i - nb);
+        for (int a = 0; a < 3; ++a) {
+            if (c[a] < -(1 << 19) || c[a] >= (1 << 19))
+                return tgv_fail(d, TGV_ERR_INVALID_ARG, "brick coordinate out of range");
+            L.coords[3 * i + a] = c[a];
+        }
+        if (!index.emplace(brick_key(c[0], c[1], c[2]), (int32_t)i).second)
+            return tgv_fail(d, TGV_ERR_INVALID_ARG, "duplicate brick coordinates");
+    }
+    std::vector<int32_t> nbr((size_t)nb * TGV_NNBR);
+    for (int64_t i = 0; i < nb; ++i)
+        for (int s = 0; s < TGV_NNBR; ++s) {
+            auto it = index.find(brick_key(L.coords[3 * i] + kSlotOffset[s][0], L.coords[3 * i + 1] + kSlotOffset[s][1],
+                                           L.coords[3 * i + 2] + kSlotOffset[s][2]));
+            nbr[(size_t)i * TGV_NNBR + s] = it == index.end() ? -1 : it->second;
+        }
+    const size_t sb = storage_bytes(d->prm.storage);
+    const int npairs = (d->prm.nbins + 1) / 2;
+    const size_t va = (size_t)na * TGV_BVOX, vn = (size_t)nb * TGV_BVOX;
+    tgv_status st = TGV_OK;
+    void** fl[] = {(void**)&L.u, (void**)&L.ubar[0], (void**)&L.ubar[1]};
+    for (void** p : fl)
+        if ((st = dalloc(d, p, va * 4)) != TGV_OK) return st;
+    void** vl[] = {&L.v, &L.vbar[0], &L.vbar[1]};
+    for (void** p : vl)
+        if ((st = dalloc(d, p, 3 * va * sb)) != TGV_OK) return st;
+    for (int k = 0; k < 2; ++k) {
+        if ((st = dalloc(d, &L.p[k], 3 * vn * sb)) != TGV_OK) return st;
+        if ((st = dalloc(d, &L.q[k], 6 * vn * sb)) != TGV_OK) return st;
+    }
+    if ((st = dalloc(d, (void**)&L.hist, (size_t)npairs * vn * 4)) != TGV_OK) return st;
+    if ((st = dalloc(d, (void**)&L.nbr, nbr.size() * 4)) != TGV_OK) return st;
+    if ((st = dalloc(d, (void**)&L.coords_dev, L.coords.size() * 4)) != TGV_OK) return st;
+    cudaStream_t s = d->stream;
+    cudaError_t e = cudaSuccess;
+    e = cudaMemsetAsync(L.u, 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[0], 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[1], 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.v, 0, 3 * va * sb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[0], 0, 3 * va * sb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[1], 0, 3 * va * sb, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(L.p[k], 0, 3 * vn * sb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.q[k], 0, 6 * vn * sb, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.hist, 0, (size_t)npairs * vn * 4, s);
+    if (e == cudaSuccess && !nbr.empty())
+        e = cudaMemcpyAsync(L.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !L.coords.empty())
+        e = cudaMemcpyAsync(L.coords_dev, L.coords.data(), L.coords.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are about to go away
+    if ((st = tgv_cuda_check(d, e, "level initialisation")) != TGV_OK) return st;
+    // frozen values (set B): constant u and v, mirrored into both ping-pong copies
+    if (nf > 0 && desc.frozen_u) {
+        const size_t n = (size_t)nf * TGV_BVOX;
+        for (float* dst : {L.u, L.ubar[0], L.ubar[1]}) {
+            e = cudaMemcpyAsync(dst + vn, desc.frozen_u, n * 4, cudaMemcpyHostToDevice, s);
+            if ((st = tgv_cuda_check(d, e, "frozen u upload")) != TGV_OK) return st;
+        }
+    }
+    if (nf > 0 && desc.frozen_v) {
+        const size_t n = 3 * (size_t)nf * TGV_BVOX;
+        if ((st = tgv_scratch(d, d->tmp, n * 4)) != TGV_OK) return st;
+        e = cudaMemcpyAsync(d->tmp.ptr, desc.frozen_v, n * 4, cudaMemcpyHostToDevice, s);
+        if ((st = tgv_cuda_check(d, e, "frozen v upload")) != TGV_OK) return st;
+        for (void* dst : {L.v, L.vbar[0], L.vbar[1]})
+            f32_to_storage(d, (const float*)d->tmp.ptr, (char*)dst + 3 * vn * sb, (int64_t)n);
+        e = cudaStreamSynchronize(s);
+        if ((st = tgv_cuda_check(d, e, "frozen v conversion")) != TGV_OK) return st;
+    }
+    return TGV_OK;
+}
+
+}  // namespace
+
+// ========================================================================= C-ABI
+extern "C" {
+
+const char* tgv_status_string(tgv_status s)
+{
+    switch (s) {
+    case TGV_OK: return "ok";
+    case TGV_ERR_INVALID_ARG: return "invalid argument";
+    case TGV_ERR_OUT_OF_MEMORY: return "out of memory";
+    case TGV_ERR_BUDGET: return "budget exceeded";
+    case TGV_ERR_CUDA: return "CUDA error";
+    case TGV_ERR_TIMEOUT: return "device wait timed out";
+    case TGV_ERR_STATE: return "domain in error state";
+    case TGV_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* tgv_last_error(const tgv_domain* d) { return d ? d->last_error.c_str() : "null domain"; }
+
+tgv_status tgv_default_params(tgv_params* out)
+{
+    if (!out) return TGV_ERR_INVALID_ARG;
+    out->nbins = 8;
+    out->alpha1 = 1.0f;
+    out->alpha0 = 2.0f;
+    out->lambda = 1.0f;
+    out->tau = 0.2f;
+    out->sigma = 0.2f;
+    out->storage = TGV_STORAGE_FP32;
+    out->clamp_u = 1;
+    out->centres = TGV_CENTRES_ENDPOINTS;
+    out->box_v = 2.0f;
+    return TGV_OK;
+}
+
+tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, const tgv_params* prm, void* stream,
+                             tgv_domain** out)
+{
+    if (!out) return TGV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!levels || nlevels <= 0 || nlevels > 32 || !prm) return TGV_ERR_INVALID_ARG;
+    if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
+    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (prm->centres != TGV_CENTRES_ENDPOINTS && prm->centres != TGV_CENTRES_MIDPOINTS) return TGV_ERR_INVALID_ARG;
+    if (!(prm->alpha1 > 0.0f) || !(prm->alpha0 > 0.0f) || !(prm->lambda >= 0.0f) || !(prm->tau > 0.0f) ||
+        !(prm->sigma > 0.0f) || !(prm->box_v > 0.0f))
+        return TGV_ERR_INVALID_ARG;
+    tgv_domain* d = new (std::nothrow) tgv_domain();
+    if (!d) return TGV_ERR_OUT_OF_MEMORY;
+    d->prm = *prm;
+    d->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device);
+    tgv_status st = tgv_cuda_check(d, e, "device query");
+    if (st == TGV_OK) st = dalloc(d, (void**)&d->red_out, 4 * sizeof(double));
+    d->levels.resize((size_t)nlevels);
+    for (int32_t l = 0; l < nlevels && st == TGV_OK; ++l) st = build_level(d, levels[l], d->levels[l]);
+    if (st != TGV_OK) {
+        std::string msg = d->last_error;
+        tgv_destroy_domain(d);
+        (void)msg;
+        return st;
+    }
+    *out = d;
+    return TGV_OK;
+}
+
+void tgv_destroy_domain(tgv_domain* d)
+{
+    if (!d) return;
+    DeviceGuard g(d->device);
+    cudaStreamSynchronize(d->stream);
+    for (TgvLevel& L : d->levels) free_level(L);
+    for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table})
+        if (s->ptr) cudaFree(s->ptr);
+    if (d->red_out) cudaFree(d->red_out);
+    cudaGetLastError();
+    delete d;
+}
+
+tgv_status tgv_accumulate_depthmaps(tgv_domain* d, int32_t level, const tgv_camera* cams, int32_t nmaps,
+                                    const float* depth_dev, int64_t pitch_elems, int64_t map_stride_elems,
+                                    const uint32_t* votes)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    if (nmaps < 0 || (nmaps > 0 && (!cams || !depth_dev))) return tgv_fail(d, TGV_ERR_INVALID_ARG, "bad map batch");
+    if (nmaps == 0) return TGV_OK;
+    const int W = cams[0].width, H = cams[0].height;
+    if (W <= 0 || H <= 0 || W > 32768 || H > 32768) return tgv_fail(d, TGV_ERR_INVALID_ARG, "bad map size");
+    if (pitch_elems < W) return tgv_fail(d, TGV_ERR_INVALID_ARG, "pitch smaller than width");
+    if (nmaps > 1 && map_stride_elems < pitch_elems * H) return tgv_fail(d, TGV_ERR_INVALID_ARG, "map stride too small");
+    uint64_t add = 0;
+    for (int m = 0; m < nmaps; ++m) {
+        const tgv_camera& c = cams[m];
+        if (c.width != W || c.height != H) return tgv_fail(d, TGV_ERR_INVALID_ARG, "maps of one batch differ in size");
+        if (c.model != TGV_PINHOLE) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "only pinhole cameras are built");
+        bool ok = isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy) && c.fx > 0 && c.fy > 0;
+        for (int k = 0; k < 9; ++k) ok = ok && isfinite(c.R[k]);
+        for (int k = 0; k < 3; ++k) ok = ok && isfinite(c.C[k]);
+        if (!ok) return tgv_fail(d, TGV_ERR_INVALID_ARG, "camera parameters must be finite, fx and fy positive");
+        const uint32_t v = votes ? votes[m] : 1u;
+        if (v == 0 || v > 65535) return tgv_fail(d, TGV_ERR_INVALID_ARG, "vote must be in 1..65535");
+        add += v;
+    }
+    if (L->max_votes + add > 65535)
+        return tgv_fail(d, TGV_ERR_BUDGET, "a histogram count could exceed 65535 (16-bit bins)");
+    if (L->nb == 0) return TGV_OK;
+    st = tgv_launch_accumulate(d, *L, cams, nmaps, depth_dev, pitch_elems, nmaps > 1 ? map_stride_elems : 0, votes);
+    if (st == TGV_OK) L->max_votes += add;
+    return st;
+}
+
+tgv_status tgv_accumulate_depthmap(tgv_domain* d, int32_t level, const tgv_camera* cam, const float* depth_dev,
+                                   int64_t pitch_elems, uint32_t vote)
+{
+    return tgv_accumulate_depthmaps(d, level, cam, 1, depth_dev, pitch_elems, 0, &vote);
+}
+
+tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    if (iterations < 0) return tgv_fail(d, TGV_ERR_INVALID_ARG, "iterations must be >= 0");
+    if ((st = tgv_launch_iterations(d, *L, iterations)) != TGV_OK) return st;
+    if (energy_gap_out) return tgv_launch_energy(d, *L, energy_gap_out);
+    return TGV_OK;
+}
+
+tgv_status tgv_energy(tgv_domain* d, int32_t level, double* out)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    if (!out) return tgv_fail(d, TGV_ERR_INVALID_ARG, "null output");
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    return tgv_launch_energy(d, *L, out);
+}
+
+tgv_status tgv_extract_field(tgv_domain* d, int32_t level, int32_t field, float* out, int64_t count)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    const int nc = ncomp_of(field);
+    if (nc == 0) return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown field");
+    const int64_t nvox = L->nb * TGV_BVOX;
+    if (!out || count != nvox * nc) return tgv_fail(d, TGV_ERR_INVALID_ARG, "output size must be voxels * components");
+    if (nvox == 0) return TGV_OK;
+    const bool dev = is_device_ptr(out);
+    float* dst = out;
+    if (!dev) {
+        if ((st = tgv_scratch(d, d->tmp, (size_t)count * 4)) != TGV_OK) return st;
+        dst = (float*)d->tmp.ptr;
+    }
+    const void* f = field_ptr(*L, field);
+    const bool fp32 = field == TGV_FIELD_U || field == TGV_FIELD_UBAR || d->prm.storage == TGV_STORAGE_FP32;
+    const unsigned gr = grid1(count, 256, d->sm_count);
+    if (fp32) field_extract_kernel<float><<<gr, 256, 0, d->stream>>>((const float*)f, dst, nvox, nc);
+    else if (d->prm.storage == TGV_STORAGE_BF16)
+        field_extract_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((const __nv_bfloat16*)f, dst, nvox, nc);
+    else field_extract_kernel<__half><<<gr, 256, 0, d->stream>>>((const __half*)f, dst, nvox, nc);
+    d->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, (size_t)count * 4, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "extract field");
+}
+
+tgv_status tgv_set_field(tgv_domain* d, int32_t level, int32_t field, const float* in, int64_t count)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    const int nc = ncomp_of(field);
+    if (nc == 0) return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown field");
+    const int64_t nvox = L->nb * TGV_BVOX;
+    if (!in || count != nvox * nc) return tgv_fail(d, TGV_ERR_INVALID_ARG, "input size must be voxels * components");
+    if (nvox == 0) return TGV_OK;
+    const float* src = in;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(in)) {
+        if ((st = tgv_scratch(d, d->tmp, (size_t)count * 4)) != TGV_OK) return st;
+        e = cudaMemcpyAsync(d->tmp.ptr, in, (size_t)count * 4, cudaMemcpyHostToDevice, d->stream);
+        src = (const float*)d->tmp.ptr;
+    }
+    void* f = field_ptr(*L, field);
+    const bool fp32 = field == TGV_FIELD_U || field == TGV_FIELD_UBAR || d->prm.storage == TGV_STORAGE_FP32;
+    const unsigned gr = grid1(count, 256, d->sm_count);
+    if (e == cudaSuccess) {
+        if (fp32) field_set_kernel<float><<<gr, 256, 0, d->stream>>>((float*)f, src, nvox, nc);
+        else if (d->prm.storage == TGV_STORAGE_BF16)
+            field_set_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((__nv_bfloat16*)f, src, nvox, nc);
+        else field_set_kernel<__half><<<gr, 256, 0, d->stream>>>((__half*)f, src, nvox, nc);
+        d->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "set field");
+}
+
+tgv_status tgv_extract_histograms(tgv_domain* d, int32_t level, uint32_t* out, int64_t count)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    const int64_t nvox = L->nb * TGV_BVOX;
+    if (!out || count != nvox * d->prm.nbins) return tgv_fail(d, TGV_ERR_INVALID_ARG, "output size must be voxels * nbins");
+    if (nvox == 0) return TGV_OK;
+    const bool dev = is_device_ptr(out);
+    uint32_t* dst = out;
+    if (!dev) {
+        if ((st = tgv_scratch(d, d->tmp, (size_t)count * 4)) != TGV_OK) return st;
+        dst = (uint32_t*)d->tmp.ptr;
+    }
+    hist_unpack_kernel<<<grid1(count, 256, d->sm_count), 256, 0, d->stream>>>(L->hist, dst, nvox, d->prm.nbins,
+                                                                             (d->prm.nbins + 1) / 2);
+    d->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, (size_t)count * 4, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "extract histograms");
+}
+
+tgv_status tgv_set_histograms(tgv_domain* d, int32_t level, const uint32_t* in, int64_t count)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    const int64_t nvox = L->nb * TGV_BVOX;
+    if (!in || count != nvox * d->prm.nbins) return tgv_fail(d, TGV_ERR_INVALID_ARG, "input size must be voxels * nbins");
+    if (nvox == 0) return TGV_OK;
+    const int npairs = (d->prm.nbins + 1) / 2;
+    if ((st = tgv_scratch(d, d->tmp, (size_t)count * 4 + 256)) != TGV_OK) return st;
+    unsigned int* maxc = (unsigned int*)((char*)d->tmp.ptr + (size_t)count * 4);
+    const uint32_t* src = in;
+    cudaError_t e = cudaMemsetAsync(maxc, 0, sizeof(unsigned int), d->stream);
+    if (e == cudaSuccess && !is_device_ptr(in)) {
+        e = cudaMemcpyAsync(d->tmp.ptr, in, (size_t)count * 4, cudaMemcpyHostToDevice, d->stream);
+        src = (const uint32_t*)d->tmp.ptr;
+    }
+    if (e == cudaSuccess) {
+        hist_pack_kernel<<<grid1(nvox * npairs, 256, d->sm_count), 256, 0, d->stream>>>(L->hist, src, nvox,
+                                                                                      d->prm.nbins, npairs, maxc);
+        d->launches++;
+        e = cudaGetLastError();
+    }
+    unsigned int mx = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mx, maxc, sizeof(mx), cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if ((st = tgv_cuda_check(d, e, "set histograms")) != TGV_OK) return st;
+    if (mx > 65535) {
+        cudaMemsetAsync(L->hist, 0, (size_t)npairs * nvox * 4, d->stream);
+        L->max_votes = 0;
+        return tgv_fail(d, TGV_ERR_BUDGET, "a histogram count exceeds 65535 (16-bit bins); histograms cleared");
+    }
+    L->max_votes = mx;
+    return TGV_OK;
+}
+
+tgv_status tgv_reset(tgv_domain* d, int32_t level, int32_t clear_hist)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    const size_t vn = (size_t)L->nb * TGV_BVOX, sb = storage_bytes(d->prm.storage);
+    cudaStream_t s = d->stream;
+    cudaError_t e = cudaMemsetAsync(L->u, 0, vn * 4, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(L->ubar[k], 0, vn * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L->vbar[k], 0, 3 * vn * sb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L->p[k], 0, 3 * vn * sb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L->q[k], 0, 6 * vn * sb, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->v, 0, 3 * vn * sb, s);
+    if (e == cudaSuccess && clear_hist) {
+        e = cudaMemsetAsync(L->hist, 0, (size_t)((d->prm.nbins + 1) / 2) * vn * 4, s);
+        L->max_votes = 0;
+    }
+    L->cur = 0;
+    return tgv_cuda_check(d, e, "reset");
+}
+
+tgv_status tgv_prolong(tgv_domain* d, int32_t from_level)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    if (from_level < 0 || from_level + 1 >= (int32_t)d->levels.size())
+        return tgv_fail(d, TGV_ERR_INVALID_ARG, "no finer level after from_level");
+    TgvLevel& C = d->levels[from_level];
+    TgvLevel& F = d->levels[from_level + 1];
+    for (int a = 0; a < 3; ++a)
+        if (C.origin[a] != F.origin[a]) return tgv_fail(d, TGV_ERR_INVALID_ARG, "levels must share the origin");
+    if (fabs(F.h * 2.0 - C.h) > 1e-12 * C.h) return tgv_fail(d, TGV_ERR_INVALID_ARG, "fine h must be half the coarse h");
+    const int64_t nfall = F.nb + F.nf;
+    if (nfall == 0) return TGV_OK;
+    std::unordered_map<uint64_t, int32_t> cidx;
+    cidx.reserve((size_t)C.nb * 2);
+    for (int64_t i = 0; i < C.nb; ++i)
+        cidx.emplace(brick_key(C.coords[3 * i], C.coords[3 * i + 1], C.coords[3 * i + 2]), (int32_t)i);
+    std::vector<int32_t> parent((size_t)nfall);
+    auto fdiv2 = [](int32_t v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); };
+    for (int64_t i = 0; i < nfall; ++i) {
+        auto it = cidx.find(
+            brick_key(fdiv2(F.coords[3 * i]), fdiv2(F.coords[3 * i + 1]), fdiv2(F.coords[3 * i + 2])));
+        parent[(size_t)i] = it == cidx.end() ? -1 : it->second;
+    }
+    if ((st = tgv_scratch(d, d->table, parent.size() * 4)) != TGV_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(d->table.ptr, parent.data(), parent.size() * 4, cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) {
+        const int o = 1 - F.cur;
+        switch (d->prm.storage) {
+        case TGV_STORAGE_FP32:
+            prolong_kernel<float><<<(unsigned)nfall, TGV_BVOX, 0, d->stream>>>(
+                C.u, (const float*)C.v, (const int32_t*)d->table.ptr, F.coords_dev, nfall, F.nb, F.u, F.ubar[F.cur],
+                F.ubar[o], (float*)F.v, (float*)F.vbar[F.cur], (float*)F.vbar[o]);
+            break;
+        case TGV_STORAGE_BF16:
+            prolong_kernel<__nv_bfloat16><<<(unsigned)nfall, TGV_BVOX, 0, d->stream>>>(
+                C.u, (const __nv_bfloat16*)C.v, (const int32_t*)d->table.ptr, F.coords_dev, nfall, F.nb, F.u,
+                F.ubar[F.cur], F.ubar[o], (__nv_bfloat16*)F.v, (__nv_bfloat16*)F.vbar[F.cur],
+                (__nv_bfloat16*)F.vbar[o]);
+            break;
+        default:
+            prolong_kernel<__half><<<(unsigned)nfall, TGV_BVOX, 0, d->stream>>>(
+                C.u, (const __half*)C.v, (const int32_t*)d->table.ptr, F.coords_dev, nfall, F.nb, F.u, F.ubar[F.cur],
+                F.ubar[o], (__half*)F.v, (__half*)F.vbar[F.cur], (__half*)F.vbar[o]);
+        }
+        d->launches++;
+        e = cudaGetLastError();
+    }
+    const size_t vn = (size_t)F.nb * TGV_BVOX, sb = storage_bytes(d->prm.storage);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(F.p[k], 0, 3 * vn * sb, d->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F.q[k], 0, 6 * vn * sb, d->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);  // `parent` is a host temporary
+    return tgv_cuda_check(d, e, "prolong");
+}
+
+tgv_status tgv_synchronize(tgv_domain* d)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    return tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "synchronize");
+}
+
+int64_t tgv_domain_bytes(const tgv_domain* d) { return d ? d->bytes : 0; }
+
+int64_t tgv_level_voxels(const tgv_domain* d, int32_t level)
+{
+    if (!d || level < 0 || level >= (int32_t)d->levels.size()) return 0;
+    return d->levels[level].nb * TGV_BVOX;
+}
+
+int64_t tgv_launch_count(const tgv_domain* d) { return d ? d->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations of the TGV library (not part of the C-ABI).
+//
+// Device layout of one level (all arrays brick-major, 512 voxels per brick,
+// local voxel index i + 8j + 64k):
+//   bricks [0, nb) are active, [nb, nb + nf) frozen (Sec. 4.5, set B).
+//   u      float [nb+nf][512]            (in place: only a voxel's own thread reads it)
+//   ubar   float [2][nb+nf][512]         (ping-pong: neighbours read the old copy)
+//   v      S     [nb+nf][3][512]         (in place)
+//   vbar   S     [2][nb+nf][3][512]      (ping-pong)
+//   p      S     [2][nb][3][512]         (ping-pong, active bricks only)
+//   q      S     [2][nb][6][512]         (ping-pong; q_xx, q_yy, q_zz, q_xy, q_xz, q_yz)
+//   hist   u32   [nb][npairs][512]       (bins 2k and 2k+1 as the low/high 16 bits)
+//   nbr    int32 [nb][12]                (neighbour brick per slot; -1 = none;
+//                                         index >= nb = frozen brick)
+// S is float, __nv_bfloat16 or __half (the storage form of v, vbar, p, q).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tgv.h"
+
+#define TGV_BVOX 512
+#define TGV_NNBR 12
+#define TGV_MAX_BINS 16
+#define TGV_MAPS_PER_LAUNCH 32
+
+// Neighbour slots: the six faces, then the six edge bricks whose offset has
+// -1 on one axis and +1 on another ("MX_PY" = offset (-1, +1, 0)).  The edge
+// bricks are the only non-face bricks a fused iteration reads: the new dual
+// at a -a face halo voxel needs ubar one step along +b, and the new q at a +a
+// face halo voxel needs vbar one step along -b.
+enum {
+    NB_PX = 0, NB_MX = 1, NB_PY = 2, NB_MY = 3, NB_PZ = 4, NB_MZ = 5,
+    NB_MX_PY = 6, NB_MX_PZ = 7, NB_MY_PX = 8, NB_MY_PZ = 9, NB_MZ_PX = 10, NB_MZ_PY = 11
+};
+
+__host__ __device__ inline int nb_plus(int a) { return 2 * a; }
+__host__ __device__ inline int nb_minus(int a) { return 2 * a + 1; }
+// slot of the edge brick with offset -1 on axis `m` and +1 on axis `p` (m != p)
+__host__ __device__ inline int nb_edge(int m, int p)
+{
+    return 6 + 2 * m + (p > m ? p - 1 : p);
+}
+
+// ---------------------------------------------------------------- storage types
+template <typename S> __device__ __forceinline__ float ld_s(const S* p);
+template <> __device__ __forceinline__ float ld_s<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float ld_s<__half>(const __half* p) { return __half2float(*p); }
+
+template <typename S> __device__ __forceinline__ void st_s(S* p, float x);
+template <> __device__ __forceinline__ void st_s<float>(float* p, float x) { *p = x; }
+template <> __device__ __forceinline__ void st_s<__nv_bfloat16>(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ void st_s<__half>(__half* p, float x) { *p = __float2half_rn(x); }
+
+inline size_t storage_bytes(int storage) { return storage == TGV_STORAGE_FP32 ? 4 : 2; }
+
+// ---------------------------------------------------------------- host state
+struct TgvLevel {
+    int64_t nb = 0, nf = 0;  // active and frozen bricks
+    double origin[3] = {0, 0, 0};
+    double h = 1.0, radius = 0.5;
+    std::vector<int32_t> coords;  // 3*(nb+nf), active first
+    float* u = nullptr;
+    float* ubar[2] = {nullptr, nullptr};
+    void* v = nullptr;
+    void* vbar[2] = {nullptr, nullptr};
+    void* p[2] = {nullptr, nullptr};
+    void* q[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;
+    int32_t* nbr = nullptr;
+    int32_t* coords_dev = nullptr;  // 3*(nb+nf) brick coordinates
+    int cur = 0;               // ping-pong copy holding the current ubar/vbar/p/q
+    uint64_t max_votes = 0;    // upper bound on any voxel's total count
+};
+
+// Arguments of one fused primal-dual iteration over the active bricks of a level.
+template <typename S>
+struct IterArgs {
+    float* u;
+    const float* ubar_in;
+    float* ubar_out;
+    S* v;
+    const S* vbar_in;
+    S* vbar_out;
+    const S* p_in;
+    S* p_out;
+    const S* q_in;
+    S* q_out;
+    const uint32_t* hist;
+    const int32_t* nbr;
+    int64_t nb;    // active bricks
+    int64_t nall;  // active + frozen bricks (stride of the in-place fields' brick index)
+    int nbins, npairs, clamp_u;
+    float alpha1, alpha0, tau, sigma, taulam;
+    float c[TGV_MAX_BINS];  // bin centres
+};
+
+struct TgvScratch {
+    void* ptr = nullptr;
+    size_t cap = 0;
+};
+
+struct tgv_domain {
+    std::vector<TgvLevel> levels;
+    tgv_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    bool broken = false;
+    std::string last_error;
+    int64_t launches = 0;
+    int64_t bytes = 0;
+    TgvScratch pyr;     // depth pyramids of one accumulation batch
+    TgvScratch red;     // per-block partial sums of the energy reduction
+    TgvScratch tmp;     // staging for host <-> device field copies
+    TgvScratch table;   // per-brick parent table of tgv_prolong
+    double* red_out = nullptr;   // 4 doubles: final reduction result (device)
+};
+
+// helpers implemented in tgv_domain.cu
+tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg);
+tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what);
+tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes);
+void tgv_bin_centres(const tgv_params& prm, float* c);
+
+// launchers implemented in tgv_solve.cu / tgv_hist.cu
+tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters);
+tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out);
+tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& L, const tgv_camera* cams, int nmaps,
+                                 const float* depth, int64_t pitch, int64_t stride, const uint32_t* votes);

@@ -1,0 +1,603 @@
+// Fused TGV primal-dual iteration over 8^3 bricks, and the energy / gap
+// reduction (Eq. 2-3; primal-dual method of Sec. 3.2).
+//
+// One CTA of 512 threads owns one active brick (one thread per voxel) and
+// performs a whole iteration for it in a single pass over HBM:
+//   phase A  new p, q at its own voxels from the old ubar/vbar/p/q;
+//            new p on the three -face halo layers and new q on the three
+//            +face halo layers are recomputed from the neighbours' old data
+//            (the primal step needs them and another CTA owns them);
+//   phase B  div1 p, div2 q from shared memory, histogram prox, clamp,
+//            v update and over-relaxation; write u, v in place and
+//            ubar, vbar, p, q to the other ping-pong copy.
+// Traffic per voxel and iteration: read u, ubar, v, vbar, p, q, hist and write
+// u, ubar, v, vbar, p, q once (halo re-reads hit L2).
+#include <math.h>
+
+#include "tgv_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int face_index(int a, int x, int y, int z)
+{
+    return a == 0 ? y + 8 * z : (a == 1 ? x + 8 * z : x + 8 * y);
+}
+
+__device__ __forceinline__ void proj3(float p[3], float alpha)
+{
+    float n = sqrtf(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    float s = n / alpha;
+    if (s > 1.0f) {
+        float r = 1.0f / s;
+        p[0] *= r;
+        p[1] *= r;
+        p[2] *= r;
+    }
+}
+
+__device__ __forceinline__ void proj6(float q[6], float alpha)
+{
+    float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0f * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    float s = sqrtf(n2) / alpha;
+    if (s > 1.0f) {
+        float r = 1.0f / s;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] *= r;
+    }
+}
+
+// index of q_ab in the 6-component storage
+__device__ __forceinline__ int qi(int a, int b)
+{
+    return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+}
+
+}  // namespace
+
+template <typename S>
+__global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
+{
+    __shared__ float s_ub[TGV_BVOX];
+    __shared__ float s_vb[3][TGV_BVOX];
+    __shared__ float s_p[3][TGV_BVOX + 192];
+    __shared__ float s_q[6][TGV_BVOX + 192];
+    __shared__ int s_nbr[TGV_NNBR];
+
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    const int x = t & 7, y = (t >> 3) & 7, z = t >> 6;
+    const int crd[3] = {x, y, z};
+    const int strd[3] = {1, 8, 64};
+
+    if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
+    const float ub = A.ubar_in[b * TGV_BVOX + t];
+    s_ub[t] = ub;
+    float vb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        vb[c] = ld_s(A.vbar_in + (b * 3 + c) * TGV_BVOX + t);
+        s_vb[c][t] = vb[c];
+    }
+    __syncthreads();
+
+    // ---------------- phase A: dual ascent + projection at the own voxel
+    float pn[3], qn[6];
+    {
+        float g[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float nv = ub;  // "none" -> zero difference
+            if (crd[a] < 7) {
+                nv = s_ub[t + strd[a]];
+            } else {
+                int n = s_nbr[nb_plus(a)];
+                if (n >= 0) nv = A.ubar_in[(int64_t)n * TGV_BVOX + t - 7 * strd[a]];
+            }
+            g[a] = nv - ub;
+        }
+        float dm[3][3];  // dm[a][c] = backward difference of vbar_c along a
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int n = -2;
+            if (crd[a] == 0) n = s_nbr[nb_minus(a)];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float w = vb[c];
+                if (crd[a] > 0) w = s_vb[c][t - strd[a]];
+                else if (n >= 0) w = ld_s(A.vbar_in + ((int64_t)n * 3 + c) * TGV_BVOX + t + 7 * strd[a]);
+                dm[a][c] = vb[c] - w;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pn[c] = ld_s(A.p_in + (b * 3 + c) * TGV_BVOX + t) + A.sigma * (g[c] - vb[c]);
+        proj3(pn, A.alpha1);
+        float e[6] = {dm[0][0], dm[1][1], dm[2][2], 0.5f * (dm[0][1] + dm[1][0]), 0.5f * (dm[0][2] + dm[2][0]),
+                      0.5f * (dm[1][2] + dm[2][1])};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) qn[c] = ld_s(A.q_in + (b * 6 + c) * TGV_BVOX + t) + A.sigma * e[c];
+        proj6(qn, A.alpha0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_p[c][t] = pn[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s_q[c][t] = qn[c];
+    }
+
+    // ---------------- phase A': halo duals owned by neighbouring bricks
+    if (t < 192) {
+        // new p on the -a face halo (voxel at coordinate -1 along a)
+        const int a = t >> 6, k = t & 63;
+        const int n = s_nbr[nb_minus(a)];
+        if (n >= 0 && n < A.nb) {
+            const int u0 = k & 7, u1 = k >> 3;  // the two face coordinates, lower axis first
+            int hc[3];
+            hc[a] = 7;
+            hc[a == 0 ? 1 : 0] = u0;
+            hc[a == 2 ? 1 : 2] = u1;
+            const int lh = hc[0] + 8 * hc[1] + 64 * hc[2];
+            const int lo = lh - 7 * strd[a];  // own voxel at coordinate 0 along a
+            const float* ubn = A.ubar_in + (int64_t)n * TGV_BVOX;
+            const float uh = ubn[lh];
+            float g[3];
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+                float nv = uh;
+                if (bb == a) {
+                    nv = s_ub[lo];
+                } else if (hc[bb] < 7) {
+                    nv = ubn[lh + strd[bb]];
+                } else {
+                    int e = s_nbr[nb_edge(a, bb)];
+                    if (e >= 0) nv = A.ubar_in[(int64_t)e * TGV_BVOX + lh - 7 * strd[bb]];
+                }
+                g[bb] = nv - uh;
+            }
+            float ph[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float vh = ld_s(A.vbar_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh);
+                ph[c] = ld_s(A.p_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh) + A.sigma * (g[c] - vh);
+            }
+            proj3(ph, A.alpha1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_p[c][TGV_BVOX + a * 64 + k] = ph[c];
+        }
+    } else if (t < 384) {
+        // new q on the +a face halo (voxel at coordinate 8 along a)
+        const int tt = t - 192;
+        const int a = tt >> 6, k = tt & 63;
+        const int n = s_nbr[nb_plus(a)];
+        if (n >= 0 && n < A.nb) {
+            const int u0 = k & 7, u1 = k >> 3;
+            int hc[3];
+            hc[a] = 0;
+            hc[a == 0 ? 1 : 0] = u0;
+            hc[a == 2 ? 1 : 2] = u1;
+            const int lh = hc[0] + 8 * hc[1] + 64 * hc[2];
+            const int lo = lh + 7 * strd[a];  // own voxel at coordinate 7 along a
+            float vh[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vh[c] = ld_s(A.vbar_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh);
+            float dm[3][3];
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+                int src = -1;  // brick to read from, -1: none
+                int li = 0;
+                bool own = false;
+                if (bb == a) {
+                    own = true;
+                } else if (hc[bb] > 0) {
+                    src = n;
+                    li = lh - strd[bb];
+                } else {
+                    src = s_nbr[nb_edge(bb, a)];  // offset +1 along a, -1 along bb
+                    li = lh + 7 * strd[bb];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float w = vh[c];
+                    if (own) w = s_vb[c][lo];
+                    else if (src >= 0) w = ld_s(A.vbar_in + ((int64_t)src * 3 + c) * TGV_BVOX + li);
+                    dm[bb][c] = vh[c] - w;
+                }
+            }
+            float e[6] = {dm[0][0], dm[1][1], dm[2][2], 0.5f * (dm[0][1] + dm[1][0]), 0.5f * (dm[0][2] + dm[2][0]),
+                          0.5f * (dm[1][2] + dm[2][1])};
+            float qh[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+                qh[c] = ld_s(A.q_in + ((int64_t)n * 6 + c) * TGV_BVOX + lh) + A.sigma * e[c];
+            proj6(qh, A.alpha0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s_q[c][TGV_BVOX + a * 64 + k] = qh[c];
+        }
+    }
+    __syncthreads();
+
+    // ---------------- phase B: primal descent, prox, over-relaxation
+    float div1 = 0.0f;
+    float div2[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int np = crd[a] < 7 ? 0 : s_nbr[nb_plus(a)];   // >= 0: forward exists (same brick = 0)
+        const int nm = crd[a] > 0 ? 0 : s_nbr[nb_minus(a)];  // >= 0: backward exists
+        const bool fwd_any = np >= 0;
+        const bool fwd_act = np >= 0 && (crd[a] < 7 || np < A.nb);
+        const bool bwd_any = nm >= 0;
+        const bool bwd_act = nm >= 0 && (crd[a] > 0 || nm < A.nb);
+        if (fwd_any) div1 += pn[a];
+        if (bwd_act) div1 -= crd[a] > 0 ? s_p[a][t - strd[a]] : s_p[a][TGV_BVOX + a * 64 + face_index(a, x, y, z)];
+        const int fi = crd[a] < 7 ? t + strd[a] : TGV_BVOX + a * 64 + face_index(a, x, y, z);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (fwd_act) div2[c] += s_q[qi(a, c)][fi];
+            if (bwd_any) div2[c] -= qn[qi(a, c)];
+        }
+    }
+
+    const int64_t vi = b * TGV_BVOX + t;
+    const float u0 = A.u[vi];
+    const float ut = u0 + A.tau * div1;
+    // prox of tau*lambda*sum_b h_b|u - c_b|: the generalised median of
+    // {c_b} and {ut - tau*lambda*W_i}, W_i = sum_{b<i} h_b - sum_{b>=i} h_b.
+    // With c ascending and the W_i ascending, the median equals
+    // max_i min(ut - tau*lambda*W_i, c_i) (c_n = +inf).
+    float hsum = 0.0f;
+    uint32_t hw[TGV_MAX_BINS / 2];
+#pragma unroll
+    for (int k = 0; k < TGV_MAX_BINS / 2; ++k) {
+        hw[k] = k < A.npairs ? A.hist[((int64_t)b * A.npairs + k) * TGV_BVOX + t] : 0u;
+        hsum += (float)(hw[k] & 0xffffu) + (float)(hw[k] >> 16);
+    }
+    float W = -hsum;
+    float un = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < TGV_MAX_BINS; ++i) {
+        if (i < A.nbins) {
+            const float hi = (float)((hw[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
+            un = fmaxf(un, fminf(ut - A.taulam * W, A.c[i]));
+            W += 2.0f * hi;
+        }
+    }
+    un = fmaxf(un, ut - A.taulam * W);
+    if (A.clamp_u) un = fminf(1.0f, fmaxf(-1.0f, un));
+
+    A.u[vi] = un;
+    A.ubar_out[vi] = 2.0f * un - u0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int64_t oi = (b * 3 + c) * TGV_BVOX + t;
+        const float v0 = ld_s(A.v + oi);
+        const float v1 = v0 + A.tau * (pn[c] + div2[c]);
+        st_s(A.v + oi, v1);
+        st_s(A.vbar_out + oi, 2.0f * v1 - v0);
+        st_s(A.p_out + oi, pn[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) st_s(A.q_out + (b * 6 + c) * TGV_BVOX + t, qn[c]);
+}
+
+// =====================================================================================
+// Energy, dual value and gap (FP32 per-voxel terms, FP64 accumulation,
+// fixed-order reduction: per-block partials, then one block sums them in order).
+// =====================================================================================
+template <typename S>
+struct EnergyArgs {
+    const float* u;
+    const S* v;
+    const S* p;
+    const S* q;
+    const uint32_t* hist;
+    const int32_t* nbr;
+    int64_t nb, nall;
+    int nbins, npairs;
+    float alpha1, alpha0, lambda, box_v;
+    float c[TGV_MAX_BINS];
+    double* partial;  // [gridDim.x][3]: energy, dual, max|v|
+};
+
+namespace {
+
+// value of a field component at the neighbour of voxel t along axis a (dir +1/-1);
+// returns false for "none".  Frozen bricks are in the same arrays.
+__device__ __forceinline__ int nbr_voxel(const int32_t* s_nbr, int64_t b, int t, int a, int dir, int crd_a,
+                                         int strd_a, int64_t* nbrick)
+{
+    if (dir > 0) {
+        if (crd_a < 7) {
+            *nbrick = b;
+            return t + strd_a;
+        }
+        int n = s_nbr[nb_plus(a)];
+        if (n < 0) return -1;
+        *nbrick = n;
+        return t - 7 * strd_a;
+    }
+    if (crd_a > 0) {
+        *nbrick = b;
+        return t - strd_a;
+    }
+    int n = s_nbr[nb_minus(a)];
+    if (n < 0) return -1;
+    *nbrick = n;
+    return t + 7 * strd_a;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace
+
+template <typename S>
+__global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
+{
+    __shared__ int32_t s_nbr[TGV_NNBR];
+    __shared__ double s_red[3][16];
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    const int strd[3] = {1, 8, 64};
+    if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
+    __syncthreads();
+
+    const int64_t vi = b * TGV_BVOX + t;
+    const float u = A.u[vi];
+    float v[3], p[3], q[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = ld_s(A.v + (b * 3 + c) * TGV_BVOX + t);
+        p[c] = ld_s(A.p + (b * 3 + c) * TGV_BVOX + t);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) q[c] = ld_s(A.q + (b * 6 + c) * TGV_BVOX + t);
+
+    float gmv2 = 0.0f, k0 = 0.0f, dm[3][3], dk[3][3], div1 = 0.0f, div2[3] = {0, 0, 0};
+    float vmax = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vmax = fmaxf(vmax, fabsf(v[a]));
+        int64_t nf = 0, nbk = 0;
+        int lf = nbr_voxel(s_nbr, b, t, a, +1, crd[a], strd[a], &nf);
+        int lb = nbr_voxel(s_nbr, b, t, a, -1, crd[a], strd[a], &nbk);
+        // forward gradient of u (frozen neighbours give their constant)
+        float g = 0.0f;
+        if (lf >= 0) {
+            float un = A.u[nf * TGV_BVOX + lf];
+            g = un - u;
+            if (nf >= A.nb) k0 += un * p[a];  // frozen constant paired with p
+        }
+        const float d = g - v[a];
+        gmv2 += d * d;
+        // backward differences of v
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dm[a][c] = 0.0f;
+            dk[a][c] = 0.0f;
+        }
+        if (lb >= 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float w = ld_s(A.v + (nbk * 3 + c) * TGV_BVOX + lb);
+                dm[a][c] = v[c] - w;
+                if (nbk >= A.nb) dk[a][c] = -w;  // frozen constant part of E(v)
+            }
+        }
+        // div1 p and div2 q
+        if (lf >= 0) div1 += p[a];
+        if (lb >= 0 && nbk < A.nb) div1 -= ld_s(A.p + (nbk * 3 + a) * TGV_BVOX + lb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (lf >= 0 && nf < A.nb) div2[c] += ld_s(A.q + (nf * 6 + qi(a, c)) * TGV_BVOX + lf);
+            if (lb >= 0) div2[c] -= q[qi(a, c)];
+        }
+    }
+    const float e[6] = {dm[0][0], dm[1][1], dm[2][2], 0.5f * (dm[0][1] + dm[1][0]), 0.5f * (dm[0][2] + dm[2][0]),
+                        0.5f * (dm[1][2] + dm[2][1])};
+    const float ek[6] = {dk[0][0], dk[1][1], dk[2][2], 0.5f * (dk[0][1] + dk[1][0]), 0.5f * (dk[0][2] + dk[2][0]),
+                         0.5f * (dk[1][2] + dk[2][1])};
+    float ef2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.0f * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+    k0 += ek[0] * q[0] + ek[1] * q[1] + ek[2] * q[2] + 2.0f * (ek[3] * q[3] + ek[4] * q[4] + ek[5] * q[5]);
+
+    // data term and its conjugate phi*(div1 p) over the breakpoints {-1, c_b, +1}
+    float hb[TGV_MAX_BINS];
+#pragma unroll
+    for (int k = 0; k < TGV_MAX_BINS; ++k) {
+        hb[k] = 0.0f;
+        if (k < A.nbins) {
+            uint32_t w = A.hist[((int64_t)b * A.npairs + (k >> 1)) * TGV_BVOX + t];
+            hb[k] = (float)((w >> ((k & 1) * 16)) & 0xffffu);
+        }
+    }
+    auto data = [&](float uu) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < TGV_MAX_BINS; ++k)
+            if (k < A.nbins) s += hb[k] * fabsf(uu - A.c[k]);
+        return A.lambda * s;
+    };
+    float best = fmaxf(-div1 - data(-1.0f), div1 - data(1.0f));
+#pragma unroll
+    for (int k = 0; k < TGV_MAX_BINS; ++k)
+        if (k < A.nbins) best = fmaxf(best, div1 * A.c[k] - data(A.c[k]));
+    float l1 = fabsf(p[0] + div2[0]) + fabsf(p[1] + div2[1]) + fabsf(p[2] + div2[2]);
+
+    double en = (double)A.alpha1 * (double)sqrtf(gmv2) + (double)A.alpha0 * (double)sqrtf(ef2) + (double)data(u);
+    double du = (double)k0 - (double)best - (double)A.box_v * (double)l1;
+    double vm = (double)vmax;
+
+    en = warp_sum(en);
+    du = warp_sum(du);
+    vm = warp_max(vm);
+    const int w = t >> 5, lane = t & 31;
+    if (lane == 0) {
+        s_red[0][w] = en;
+        s_red[1][w] = du;
+        s_red[2][w] = vm;
+    }
+    __syncthreads();
+    if (w == 0) {
+        en = lane < 16 ? s_red[0][lane] : 0.0;
+        du = lane < 16 ? s_red[1][lane] : 0.0;
+        vm = lane < 16 ? s_red[2][lane] : 0.0;
+        en = warp_sum(en);
+        du = warp_sum(du);
+        vm = warp_max(vm);
+        if (lane == 0) {
+            A.partial[3 * b + 0] = en;
+            A.partial[3 * b + 1] = du;
+            A.partial[3 * b + 2] = vm;
+        }
+    }
+}
+
+// One block sums the per-block partials in a fixed order.
+__global__ void __launch_bounds__(1024) tgv_reduce_partials(const double* partial, int64_t n, float box_v, double* out)
+{
+    __shared__ double s[3][32];
+    const int t = threadIdx.x;
+    double en = 0.0, du = 0.0, vm = 0.0;
+    for (int64_t i = t; i < n; i += blockDim.x) {
+        en += partial[3 * i];
+        du += partial[3 * i + 1];
+        vm = fmax(vm, partial[3 * i + 2]);
+    }
+    en = warp_sum(en);
+    du = warp_sum(du);
+    vm = warp_max(vm);
+    const int w = t >> 5, lane = t & 31;
+    if (lane == 0) {
+        s[0][w] = en;
+        s[1][w] = du;
+        s[2][w] = vm;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        en = lane < nw ? s[0][lane] : 0.0;
+        du = lane < nw ? s[1][lane] : 0.0;
+        vm = lane < nw ? s[2][lane] : 0.0;
+        en = warp_sum(en);
+        du = warp_sum(du);
+        vm = warp_max(vm);
+        if (lane == 0) {
+            out[0] = en;
+            out[1] = du;
+            out[2] = en - du;
+            out[3] = vm <= (double)box_v ? 1.0 : 0.0;
+        }
+    }
+}
+
+// =====================================================================================
+// host launchers
+// =====================================================================================
+template <typename S>
+static IterArgs<S> make_iter_args(tgv_domain* d, TgvLevel& L)
+{
+    IterArgs<S> A;
+    const int c = L.cur, o = 1 - L.cur;
+    A.u = L.u;
+    A.ubar_in = L.ubar[c];
+    A.ubar_out = L.ubar[o];
+    A.v = (S*)L.v;
+    A.vbar_in = (const S*)L.vbar[c];
+    A.vbar_out = (S*)L.vbar[o];
+    A.p_in = (const S*)L.p[c];
+    A.p_out = (S*)L.p[o];
+    A.q_in = (const S*)L.q[c];
+    A.q_out = (S*)L.q[o];
+    A.hist = L.hist;
+    A.nbr = L.nbr;
+    A.nb = L.nb;
+    A.nall = L.nb + L.nf;
+    A.nbins = d->prm.nbins;
+    A.npairs = (d->prm.nbins + 1) / 2;
+    A.clamp_u = d->prm.clamp_u;
+    A.alpha1 = d->prm.alpha1;
+    A.alpha0 = d->prm.alpha0;
+    A.tau = d->prm.tau;
+    A.sigma = d->prm.sigma;
+    A.taulam = d->prm.tau * d->prm.lambda;
+    tgv_bin_centres(d->prm, A.c);
+    return A;
+}
+
+template <typename S>
+static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
+{
+    for (int it = 0; it < iters; ++it) {
+        IterArgs<S> A = make_iter_args<S>(d, L);
+        tgv_iter_kernel<S><<<(unsigned)L.nb, TGV_BVOX, 0, d->stream>>>(A);
+        d->launches++;
+        L.cur ^= 1;
+    }
+    return tgv_cuda_check(d, cudaGetLastError(), "tgv_iter_kernel launch");
+}
+
+tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters)
+{
+    if (L.nb == 0 || iters == 0) return TGV_OK;
+    switch (d->prm.storage) {
+    case TGV_STORAGE_FP32: return launch_iters_t<float>(d, L, iters);
+    case TGV_STORAGE_BF16: return launch_iters_t<__nv_bfloat16>(d, L, iters);
+    case TGV_STORAGE_FP16: return launch_iters_t<__half>(d, L, iters);
+    }
+    return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
+}
+
+template <typename S>
+static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
+{
+    tgv_status st = tgv_scratch(d, d->red, sizeof(double) * 3 * (size_t)L.nb);
+    if (st != TGV_OK) return st;
+    EnergyArgs<S> A;
+    A.u = L.u;
+    A.v = (const S*)L.v;
+    A.p = (const S*)L.p[L.cur];
+    A.q = (const S*)L.q[L.cur];
+    A.hist = L.hist;
+    A.nbr = L.nbr;
+    A.nb = L.nb;
+    A.nall = L.nb + L.nf;
+    A.nbins = d->prm.nbins;
+    A.npairs = (d->prm.nbins + 1) / 2;
+    A.alpha1 = d->prm.alpha1;
+    A.alpha0 = d->prm.alpha0;
+    A.lambda = d->prm.lambda;
+    A.box_v = d->prm.box_v;
+    tgv_bin_centres(d->prm, A.c);
+    A.partial = (double*)d->red.ptr;
+    tgv_energy_kernel<S><<<(unsigned)L.nb, TGV_BVOX, 0, d->stream>>>(A);
+    tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, L.nb, d->prm.box_v, d->red_out);
+    d->launches += 2;
+    st = tgv_cuda_check(d, cudaGetLastError(), "tgv_energy_kernel launch");
+    if (st != TGV_OK) return st;
+    st = tgv_cuda_check(d, cudaMemcpyAsync(host_out, d->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, d->stream),
+                        "energy copy");
+    if (st != TGV_OK) return st;
+    return tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "energy sync");
+}
+
+tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)
+{
+    if (L.nb == 0) {
+        for (int k = 0; k < 4; ++k) host_out[k] = k == 3 ? 1.0 : 0.0;
+        return TGV_OK;
+    }
+    switch (d->prm.storage) {
+    case TGV_STORAGE_FP32: return launch_energy_t<float>(d, L, host_out);
+    case TGV_STORAGE_BF16: return launch_energy_t<__nv_bfloat16>(d, L, host_out);
+    case TGV_STORAGE_FP16: return launch_energy_t<__half>(d, L, host_out);
+    }
+    return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
+}

@@ -1,0 +1,325 @@
+"""ctypes binding of the C-ABI in include/tgv.h (argument marshalling only).
+
+Every function named ``tgv_*`` here calls the C entry point of the same name;
+all arithmetic runs in the library's CUDA kernels.  The library must have been
+built (``python -m paper_2107_14790_b300.build``); there is no fallback: a
+missing or unloadable ``libtgv.so`` raises ImportError.
+
+Device buffers are passed as raw pointers (``torch.Tensor.data_ptr()``); host
+buffers as numpy arrays.  PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtgv.so")
+
+TGV_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "budget exceeded", 4: "CUDA error",
+          5: "device wait timed out", 6: "domain in error state", 7: "unsupported"}
+STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+FIELDS = {"u": (0, 1), "ubar": (1, 1), "v": (2, 3), "vbar": (3, 3), "p": (4, 3), "q": (5, 6)}
+
+
+class TgvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tgv_params(ctypes.Structure):
+    _fields_ = [("nbins", ctypes.c_int32), ("alpha1", ctypes.c_float), ("alpha0", ctypes.c_float),
+                ("lam", ctypes.c_float), ("tau", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("storage", ctypes.c_int32), ("clamp_u", ctypes.c_int32), ("centres", ctypes.c_int32),
+                ("box_v", ctypes.c_float)]
+
+
+class tgv_level_desc(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("h", ctypes.c_double), ("radius", ctypes.c_double),
+                ("nbricks", ctypes.c_int64), ("brick_coords", ctypes.c_void_p),
+                ("nfrozen", ctypes.c_int64), ("frozen_coords", ctypes.c_void_p),
+                ("frozen_u", ctypes.c_void_p), ("frozen_v", ctypes.c_void_p)]
+
+
+class tgv_camera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("R", ctypes.c_double * 9), ("C", ctypes.c_double * 3), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("model", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libtgv.so once; raises ImportError if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} not built: run `python -m paper_2107_14790_b300.build`")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "tgv_default_params": (i32, [P]),
+        "tgv_create_domain": (i32, [P, i32, P, P, P]),
+        "tgv_destroy_domain": (None, [P]),
+        "tgv_accumulate_depthmap": (i32, [P, i32, P, P, i64, u32]),
+        "tgv_accumulate_depthmaps": (i32, [P, i32, P, i32, P, i64, i64, P]),
+        "tgv_solve": (i32, [P, i32, i32, P]),
+        "tgv_energy": (i32, [P, i32, P]),
+        "tgv_extract_field": (i32, [P, i32, i32, P, i64]),
+        "tgv_set_field": (i32, [P, i32, i32, P, i64]),
+        "tgv_extract_histograms": (i32, [P, i32, P, i64]),
+        "tgv_set_histograms": (i32, [P, i32, P, i64]),
+        "tgv_reset": (i32, [P, i32, i32]),
+        "tgv_prolong": (i32, [P, i32]),
+        "tgv_synchronize": (i32, [P]),
+        "tgv_domain_bytes": (i64, [P]),
+        "tgv_level_voxels": (i64, [P, i32]),
+        "tgv_launch_count": (i64, [P]),
+        "tgv_status_string": (ctypes.c_char_p, [i32]),
+        "tgv_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> Sequence[str]:
+    """Names of the C entry points this binding expects the library to export."""
+    lib()
+    return [n for n in dir(_lib) if n.startswith("tgv_")]
+
+
+def _check(d, status: int):
+    if status != TGV_OK:
+        msg = lib().tgv_last_error(d).decode() if d else ""
+        raise TgvError(status, msg)
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def make_camera(cam) -> tgv_camera:
+    c = tgv_camera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, np.float64).reshape(9)
+    C = np.asarray(cam.C, np.float64).reshape(3)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.C[k] = float(C[k])
+    c.width, c.height, c.model = int(cam.width), int(cam.height), 0
+    return c
+
+
+def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, storage="fp32", clamp_u=True,
+                centres=0, box_v=2.0) -> tgv_params:
+    p = tgv_params()
+    _check(None, lib().tgv_default_params(ctypes.byref(p)))
+    p.nbins, p.alpha1, p.alpha0, p.lam, p.tau, p.sigma = int(nbins), alpha1, alpha0, lam, tau, sigma
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.clamp_u, p.centres, p.box_v = int(bool(clamp_u)), int(centres), box_v
+    return p
+
+
+# ------------------------------------------------------------------------------------ C entry points
+def tgv_create_domain(levels, params: tgv_params, stream: int = 0):
+    """levels: objects with origin, h, radius, bricks, frozen, frozen_u, frozen_v (synth.DomainDesc)."""
+    keep = []
+    descs = (tgv_level_desc * len(levels))()
+    for k, lv in enumerate(levels):
+        bc = _host(lv.bricks, np.int32).reshape(-1, 3)
+        fr = getattr(lv, "frozen", None)
+        fc = _host(fr, np.int32).reshape(-1, 3) if fr is not None else np.zeros((0, 3), np.int32)
+        fu = getattr(lv, "frozen_u", None)
+        fv = getattr(lv, "frozen_v", None)
+        fu = _host(fu, np.float32) if (fu is not None and len(fc)) else None
+        fv = _host(fv, np.float32) if (fv is not None and len(fc)) else None
+        keep += [bc, fc, fu, fv]
+        d = descs[k]
+        for a in range(3):
+            d.origin[a] = float(np.asarray(lv.origin)[a])
+        d.h = float(lv.h)
+        d.radius = float(getattr(lv, "radius", 0.0) or 0.0)
+        d.nbricks, d.brick_coords = bc.shape[0], _ptr(bc)
+        d.nfrozen, d.frozen_coords = fc.shape[0], _ptr(fc) if len(fc) else None
+        d.frozen_u, d.frozen_v = _ptr(fu), _ptr(fv)
+    out = ctypes.c_void_p()
+    st = lib().tgv_create_domain(descs, len(levels), ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                 ctypes.byref(out))
+    _check(None, st)
+    del keep
+    return out
+
+
+def tgv_destroy_domain(d):
+    lib().tgv_destroy_domain(d)
+
+
+def tgv_accumulate_depthmaps(d, level: int, cams, depth, votes=None):
+    """depth: CUDA tensor (nmaps, H, W) or (H, W) float32, contiguous rows."""
+    if depth.dim() == 2:
+        depth = depth.unsqueeze(0)
+    nmaps, H, W = depth.shape
+    arr = (tgv_camera * nmaps)(*[make_camera(c) for c in cams])
+    vts = None if votes is None else np.ascontiguousarray(votes, np.uint32)
+    st = lib().tgv_accumulate_depthmaps(d, level, arr, nmaps, depth.data_ptr(), depth.stride(1), depth.stride(0),
+                                        _ptr(vts))
+    _check(d, st)
+
+
+def tgv_accumulate_depthmap(d, level: int, cam, depth, vote: int = 1):
+    c = make_camera(cam)
+    _check(d, lib().tgv_accumulate_depthmap(d, level, ctypes.byref(c), depth.data_ptr(), depth.stride(0), vote))
+
+
+def tgv_solve(d, level: int, iterations: int, energy: bool = False):
+    out = np.zeros(4) if energy else None
+    _check(d, lib().tgv_solve(d, level, iterations, _ptr(out)))
+    return out
+
+
+def tgv_energy(d, level: int) -> np.ndarray:
+    out = np.zeros(4)
+    _check(d, lib().tgv_energy(d, level, _ptr(out)))
+    return out
+
+
+def tgv_extract_field(d, level: int, field: str, out=None):
+    fid, nc = FIELDS[field]
+    n = lib().tgv_level_voxels(d, level)
+    if out is None:
+        out = np.empty((n, nc), np.float32)
+    _check(d, lib().tgv_extract_field(d, level, fid, _ptr(out), n * nc))
+    return out
+
+
+def tgv_set_field(d, level: int, field: str, values):
+    fid, nc = FIELDS[field]
+    n = lib().tgv_level_voxels(d, level)
+    vals = values if hasattr(values, "data_ptr") else _host(values, np.float32)
+    _check(d, lib().tgv_set_field(d, level, fid, _ptr(vals), n * nc))
+
+
+def tgv_extract_histograms(d, level: int, nbins: int, out=None):
+    n = lib().tgv_level_voxels(d, level)
+    if out is None:
+        out = np.empty((n, nbins), np.uint32)
+    _check(d, lib().tgv_extract_histograms(d, level, _ptr(out), n * nbins))
+    return out
+
+
+def tgv_set_histograms(d, level: int, hist):
+    h = hist if hasattr(hist, "data_ptr") else _host(hist, np.uint32)
+    n = h.shape[0] * h.shape[1]
+    _check(d, lib().tgv_set_histograms(d, level, _ptr(h), n))
+
+
+def tgv_reset(d, level: int, clear_hist: bool = False):
+    _check(d, lib().tgv_reset(d, level, int(clear_hist)))
+
+
+def tgv_prolong(d, from_level: int):
+    _check(d, lib().tgv_prolong(d, from_level))
+
+
+def tgv_synchronize(d):
+    _check(d, lib().tgv_synchronize(d))
+
+
+def tgv_domain_bytes(d) -> int:
+    return int(lib().tgv_domain_bytes(d))
+
+
+def tgv_level_voxels(d, level: int) -> int:
+    return int(lib().tgv_level_voxels(d, level))
+
+
+def tgv_launch_count(d) -> int:
+    return int(lib().tgv_launch_count(d))
+
+
+# ------------------------------------------------------------------------------------ convenience
+class Domain:
+    """Owns one tgv_domain handle; methods forward to the C entry points."""
+
+    def __init__(self, levels, nbins=8, storage="fp32", stream: int = 0, **kw):
+        self.nbins = int(nbins)
+        self.params = make_params(nbins=nbins, storage=storage, **kw)
+        self.levels = list(levels)
+        self.handle = tgv_create_domain(self.levels, self.params, stream)
+
+    def close(self):
+        if self.handle:
+            tgv_destroy_domain(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def accumulate(self, level, cams, depth, votes=None):
+        tgv_accumulate_depthmaps(self.handle, level, cams, depth, votes)
+
+    def solve(self, level, iterations, energy=False):
+        return tgv_solve(self.handle, level, iterations, energy)
+
+    def energy(self, level=0):
+        return tgv_energy(self.handle, level)
+
+    def field(self, level, name, out=None):
+        return tgv_extract_field(self.handle, level, name, out)
+
+    def set_field(self, level, name, values):
+        tgv_set_field(self.handle, level, name, values)
+
+    def histograms(self, level=0, out=None):
+        return tgv_extract_histograms(self.handle, level, self.nbins, out)
+
+    def set_histograms(self, level, hist):
+        tgv_set_histograms(self.handle, level, hist)
+
+    def reset(self, level, clear_hist=False):
+        tgv_reset(self.handle, level, clear_hist)
+
+    def prolong(self, from_level):
+        tgv_prolong(self.handle, from_level)
+
+    def synchronize(self):
+        tgv_synchronize(self.handle)
+
+    def voxels(self, level=0):
+        return tgv_level_voxels(self.handle, level)
+
+    @property
+    def launches(self):
+        return tgv_launch_count(self.handle)
+
+    @property
+    def nbytes(self):
+        return tgv_domain_bytes(self.handle)

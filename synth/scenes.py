@@ -211,11 +211,16 @@ def _torch():
     return torch
 
 
-def _terrain_depth_torch(terrain: Terrain, cam: Camera, step: float, device) -> np.ndarray:
-    """Ray-cast the height field (Lipschitz-bounded march + bisection) and the boxes."""
+def _terrain_depth_torch(terrain: Terrain, cams: List[Camera], step: float, device) -> List[np.ndarray]:
+    """Ray-cast the height field (Lipschitz-bounded march + bisection) and the boxes.
+
+    All rays of all cameras are marched together; returns one (H, W) float64 z-depth
+    map per camera (NaN where the ray leaves the scene without a hit).
+    """
     torch = _torch()
-    d = torch.as_tensor(cam.ray_directions().reshape(-1, 3), dtype=torch.float64, device=device)
-    C = torch.as_tensor(np.asarray(cam.C), dtype=torch.float64, device=device)
+    d = torch.cat([torch.as_tensor(c.ray_directions().reshape(-1, 3), dtype=torch.float64) for c in cams]).to(device)
+    C = torch.cat([torch.as_tensor(np.asarray(c.C, np.float64)[None, :].repeat(c.width * c.height, 0))
+                   for c in cams]).to(device)
     n = d.shape[0]
     ztop = terrain.base + float(np.sum(terrain.amp)) + 1e-6
     zbot = terrain.base - float(np.sum(terrain.amp)) - 1e-6
@@ -225,11 +230,12 @@ def _terrain_depth_torch(terrain: Terrain, cam: Camera, step: float, device) -> 
     dn = torch.sqrt(dz * dz + dxy * dxy)
     down = dz < -1e-9
     big = torch.full((n,), float("inf"), dtype=torch.float64, device=device)
-    t0 = torch.where(down, torch.clamp((ztop - C[2]) / torch.where(down, dz, -torch.ones_like(dz)), min=0.0), big)
-    t1 = torch.where(down, (zbot - C[2]) / torch.where(down, dz, -torch.ones_like(dz)), big)
+    safe_dz = torch.where(down, dz, -torch.ones_like(dz))
+    t0 = torch.where(down, torch.clamp((ztop - C[:, 2]) / safe_dz, min=0.0), big)
+    t1 = torch.where(down, (zbot - C[:, 2]) / safe_dz, big)
 
     def g(t, idx):
-        p = C[None, :] + t[:, None] * d[idx]
+        p = C[idx] + t[:, None] * d[idx]
         return p[:, 2] - terrain.height(p[:, 0], p[:, 1], xp=torch)
 
     t_hit = big.clone()
@@ -238,21 +244,21 @@ def _terrain_depth_torch(terrain: Terrain, cam: Camera, step: float, device) -> 
     gv = g(t, idx)
     denom = (-dz[idx]) + L * dxy[idx]
     dtmin = step / dn[idx]
-    for _ in range(20000):
+    for _ in range(200000):
         if idx.numel() == 0:
             break
         tn = t + torch.maximum(gv / denom, dtmin)
         gn = g(tn, idx)
         crossed = gn <= 0.0
-        lo, hi = t[crossed], tn[crossed]
-        ci = idx[crossed]
-        for _b in range(40):
-            mid = 0.5 * (lo + hi)
-            gm = g(mid, ci)
-            below = gm <= 0.0
-            hi = torch.where(below, mid, hi)
-            lo = torch.where(below, lo, mid)
-        t_hit[ci] = hi
+        if bool(crossed.any()):
+            lo, hi = t[crossed], tn[crossed]
+            ci = idx[crossed]
+            for _b in range(40):
+                mid = 0.5 * (lo + hi)
+                below = g(mid, ci) <= 0.0
+                hi = torch.where(below, mid, hi)
+                lo = torch.where(below, lo, mid)
+            t_hit[ci] = hi
         keep = (~crossed) & (tn <= t1[idx])
         idx, t, gv = idx[keep], tn[keep], gn[keep]
         denom, dtmin = denom[keep], dtmin[keep]
@@ -262,15 +268,18 @@ def _terrain_depth_torch(terrain: Terrain, cam: Camera, step: float, device) -> 
         for bx in terrain.boxes:
             lo = torch.as_tensor(bx[[0, 2, 4]], dtype=torch.float64, device=device)
             hi = torch.as_tensor(bx[[1, 3, 5]], dtype=torch.float64, device=device)
-            ta = (lo[None, :] - C[None, :]) * inv
-            tb = (hi[None, :] - C[None, :]) * inv
+            ta = (lo[None, :] - C) * inv
+            tb = (hi[None, :] - C) * inv
             tnear = torch.minimum(ta, tb).max(dim=1).values
             tfar = torch.maximum(ta, tb).min(dim=1).values
             hit = (tnear <= tfar) & (tnear > 0.0)
             t_hit = torch.where(hit & (tnear < t_hit), tnear, t_hit)
-    out = t_hit.reshape(cam.height, cam.width)
-    out = torch.where(torch.isinf(out), torch.full_like(out, float("nan")), out)
-    return out.cpu().numpy()
+    t_hit = torch.where(torch.isinf(t_hit), torch.full_like(t_hit, float("nan")), t_hit).cpu().numpy()
+    out, o = [], 0
+    for c in cams:
+        out.append(t_hit[o:o + c.width * c.height].reshape(c.height, c.width))
+        o += c.width * c.height
+    return out
 
 
 def terrain_scene(seed: int = CONFIG_SEEDS[2], n: int = 256, nmaps: int = 64, res: int = 512,
@@ -317,8 +326,7 @@ def terrain_scene(seed: int = CONFIG_SEEDS[2], n: int = 256, nmaps: int = 64, re
         allc.append(obl[k])
     cams = allc[:nmaps]
     depths = []
-    for cam in cams:
-        t = _terrain_depth_torch(terrain, cam, step=h / 4, device=device)
+    for t in _terrain_depth_torch(terrain, cams, step=h / 4, device=device):
         valid = np.isfinite(t)
         t = t + rng.normal(0.0, noise_vox * h, size=t.shape)
         if valid.any():
