@@ -227,6 +227,55 @@ TGV_API int64_t tgv_level_voxels(const tgv_domain* d, int32_t level);
 /* Number of kernels this library launched on the domain so far. */
 TGV_API int64_t tgv_launch_count(const tgv_domain* d);
 
+/* ---------------------------------------------------------------------------
+ * Energy / gap without any allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: a serving process that reserved all of its HBM
+ * up front for admitted requests, or a host framework whose own memory pool
+ * owns the device (a stray cudaMalloc there can fail for lack of unreserved
+ * memory, and cudaMalloc/cudaFree may synchronise the device and stall the
+ * other streams).  Such a caller keeps a level's state in buffers it owns,
+ * laid out as described by tgv_state_view, and gets the same four numbers as
+ * tgv_energy.
+ *
+ * The reduction scratch is a fixed array inside this library (on every GPU
+ * that loads the library, held until the process exits), so the call
+ * allocates nothing and frees nothing.  Consequences:
+ *  - at most TGV_NOALLOC_MAX_BRICKS active bricks; larger levels are rejected
+ *    with TGV_ERR_BUDGET before any device work;
+ *  - every call on a device uses the same scratch: calls whose device work
+ *    overlaps (different streams, or other host threads) race and may return
+ *    wrong numbers; serialise them (one stream, or wait for the previous
+ *    call);
+ *  - the first call on a device looks up the scratch array's device address
+ *    (once per device, with that device current); make that first call before
+ *    any stream capture begins.
+ * `stream`: the cudaStream_t to run on (NULL = legacy default stream); the
+ * call waits for its own work.  `out`: 4 doubles, host or device memory,
+ * receiving the same values as tgv_energy.  Errors: INVALID_ARG (null
+ * pointers, bad parameters), BUDGET (too many bricks), CUDA.
+ * ------------------------------------------------------------------------- */
+#define TGV_NOALLOC_MAX_BRICKS 65536
+
+/* One level's state in device memory owned by the caller (the library's
+ * layout: brick-major, 512 voxels per brick, local index i + 8j + 64k;
+ * active bricks first, then frozen ones). */
+typedef struct {
+    int64_t nbricks;        /* active bricks (nb) */
+    int64_t nall;           /* active + frozen bricks */
+    const float* u;         /* [nall][512] */
+    const void* v;          /* [nall][3][512], storage type of the params */
+    const void* p;          /* [nb][3][512] */
+    const void* q;          /* [nb][6][512]: xx, yy, zz, xy, xz, yz */
+    const uint32_t* hist;   /* [nb][(nbins+1)/2][512]: bin 2k in the low 16 bits, 2k+1 in the high */
+    const int32_t* nbr;     /* [nb][12] neighbour brick per slot, offsets (+x), (-x), (+y), (-y), (+z), (-z),
+                               (-x,+y), (-x,+z), (+x,-y), (-y,+z), (+x,-z), (+y,-z); -1 = none,
+                               >= nbricks = frozen (only the six faces are read here) */
+} tgv_state_view;
+
+TGV_API tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_params* prm, void* stream, double* out);
+
 TGV_API const char* tgv_status_string(tgv_status s);
 TGV_API const char* tgv_last_error(const tgv_domain* d);
 

@@ -133,5 +133,7 @@ void tgv_bin_centres(const tgv_params& prm, float* c);
 // launchers implemented in tgv_solve.cu / tgv_hist.cu
 tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters);
 tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out);
+cudaError_t tgv_launch_energy_view(const tgv_state_view& s, const tgv_params& prm, cudaStream_t stream,
+                                   double* partial, double* result);
 tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& L, const tgv_camera* cams, int nmaps,
                                  const float* depth, int64_t pitch, int64_t stride, const uint32_t* votes);

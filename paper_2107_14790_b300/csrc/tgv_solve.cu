@@ -601,3 +601,42 @@ tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
 }
+
+// Energy of a caller-described state with caller-given scratch: `partial`
+// holds 3 doubles per active brick, `result` 4 doubles.  Launches the same two
+// kernels as tgv_launch_energy on `stream`; no allocation, no synchronisation.
+template <typename S>
+static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_params& prm, cudaStream_t stream,
+                                       double* partial, double* result)
+{
+    EnergyArgs<S> A;
+    A.u = s.u;
+    A.v = (const S*)s.v;
+    A.p = (const S*)s.p;
+    A.q = (const S*)s.q;
+    A.hist = s.hist;
+    A.nbr = s.nbr;
+    A.nb = s.nbricks;
+    A.nall = s.nall;
+    A.nbins = prm.nbins;
+    A.npairs = (prm.nbins + 1) / 2;
+    A.alpha1 = prm.alpha1;
+    A.alpha0 = prm.alpha0;
+    A.lambda = prm.lambda;
+    A.box_v = prm.box_v;
+    tgv_bin_centres(prm, A.c);
+    A.partial = partial;
+    tgv_energy_kernel<S><<<(unsigned)s.nbricks, TGV_BVOX, 0, stream>>>(A);
+    tgv_reduce_partials<<<1, 1024, 0, stream>>>(partial, s.nbricks, prm.box_v, result);
+    return cudaGetLastError();
+}
+
+cudaError_t tgv_launch_energy_view(const tgv_state_view& s, const tgv_params& prm, cudaStream_t stream,
+                                   double* partial, double* result)
+{
+    switch (prm.storage) {
+    case TGV_STORAGE_FP32: return launch_energy_view_t<float>(s, prm, stream, partial, result);
+    case TGV_STORAGE_BF16: return launch_energy_view_t<__nv_bfloat16>(s, prm, stream, partial, result);
+    default: return launch_energy_view_t<__half>(s, prm, stream, partial, result);
+    }
+}

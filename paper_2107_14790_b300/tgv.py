@@ -51,6 +51,12 @@ class tgv_camera(ctypes.Structure):
                 ("height", ctypes.c_int32), ("model", ctypes.c_int32)]
 
 
+class tgv_state_view(ctypes.Structure):
+    _fields_ = [("nbricks", ctypes.c_int64), ("nall", ctypes.c_int64), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("hist", ctypes.c_void_p), ("nbr", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -81,6 +87,7 @@ def lib() -> ctypes.CDLL:
         "tgv_domain_bytes": (i64, [P]),
         "tgv_level_voxels": (i64, [P, i32]),
         "tgv_launch_count": (i64, [P]),
+        "tgv_energy_noalloc": (i32, [P, P, P, P]),
         "tgv_status_string": (ctypes.c_char_p, [i32]),
         "tgv_last_error": (ctypes.c_char_p, [P]),
     }
@@ -200,6 +207,26 @@ def tgv_energy(d, level: int) -> np.ndarray:
     out = np.zeros(4)
     _check(d, lib().tgv_energy(d, level, _ptr(out)))
     return out
+
+
+def tgv_energy_noalloc(nbricks: int, nall: int, u, v, p, q, hist, nbr, params: tgv_params, stream: int = 0,
+                       out=None) -> np.ndarray:
+    """Energy / dual / gap of a state held in caller-owned device buffers (no allocation).
+
+    For callers that may not allocate device memory; u, v, p, q, hist, nbr are
+    device tensors in the layout documented at tgv_state_view in include/tgv.h.
+    Raises TgvError on a non-zero status (BUDGET: more than
+    TGV_NOALLOC_MAX_BRICKS active bricks).
+    """
+    view = tgv_state_view(int(nbricks), int(nall), _ptr(u), _ptr(v), _ptr(p), _ptr(q), _ptr(hist), _ptr(nbr))
+    if out is None:
+        out = np.zeros(4)
+    st = lib().tgv_energy_noalloc(ctypes.byref(view), ctypes.byref(params), ctypes.c_void_p(stream or 0), _ptr(out))
+    _check(None, st)
+    return out
+
+
+NOALLOC_MAX_BRICKS = 65536
 
 
 def tgv_extract_field(d, level: int, field: str, out=None):
