@@ -34,7 +34,8 @@ WORKLOAD = dict(workload="dense-256^3-terrain-64x512^2-maps-10bins-500it", n=256
                 iterations=500, check_every=25)
 SMALL = dict(workload="dense-64^3-sphere-16x128^2-maps-8bins-200it", n=64, nmaps=16, res=128, nbins=8,
              iterations=200, check_every=25)
-ITER_KERNEL_SRC = os.path.join(ROOT, "paper_2107_14790_b300", "csrc", "tgv_solve.cu")
+ITER_KERNEL_SRCS = [os.path.join(ROOT, "paper_2107_14790_b300", "csrc", f)
+                    for f in ("tgv_solve.cu", "tgv_iter_pipe.cu", "tgv_iter_pair.cu", "tgv_internal.cuh", "tgv_async.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tgv_iter_kernel_dense256_traffic.json")
 
 
@@ -46,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="64^3 sphere case instead of the 256^3 terrain")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--iter-kernel", default="paired", choices=["paired", "pipelined", "one_brick_per_cta"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
@@ -77,7 +79,10 @@ def algorithmic_bytes_per_voxel(nbins: int, storage: str) -> int:
 
 
 def kernel_hash() -> str:
-    return hashlib.sha256(open(ITER_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in ITER_KERNEL_SRCS:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -151,7 +156,8 @@ def run_ours(args, cfg):
     with torch.cuda.stream(stream):
         depth_dev = depth_host.to(f"cuda:{local}", non_blocking=True)
     stream.synchronize()
-    dom = tgv.Domain([sc.domain], nbins=nbins, storage=args.storage, stream=stream.cuda_stream)
+    dom = tgv.Domain([sc.domain], nbins=nbins, storage=args.storage, stream=stream.cuda_stream,
+                     iter_kernel=args.iter_kernel)
     nvox = dom.voxels(0)
     iters, ce = cfg["iterations"], cfg["check_every"]
     blocks = [ce] * (iters // ce) + ([iters % ce] if iters % ce else [])
@@ -214,7 +220,8 @@ def run_ours(args, cfg):
     traffic = None
     try:
         tr = json.load(open(TRAFFIC_FILE))
-        if tr.get("kernel_sha") == kernel_hash() and tr.get("storage", "fp32") == args.storage:
+        if (tr.get("kernel_sha") == kernel_hash() and tr.get("storage", "fp32") == args.storage
+                and tr.get("iter_kernel") == args.iter_kernel):
             traffic = tr["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -230,7 +237,9 @@ def run_ours(args, cfg):
                    "l2": "inputs larger than L2 (state %.2f GB)" % (dom.nbytes / 1e9),
                    "parallelism": f"independent instance per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "tgv_iter_kernel", "peak_source": peak_src,
+                     "traffic": traffic, "peak_source": peak_src,
+                     "kernel": {"paired": "tgv_iter_pair_kernel", "pipelined": "tgv_iter_pipe_kernel",
+                                "one_brick_per_cta": "tgv_iter_kernel"}[args.iter_kernel],
                      "algorithmic_bytes_per_voxel": bpv, "mean_launch_us": per_launch_s * 1e6},
         "energy_gap": {"energy": last[0], "dual": last[1], "gap": last[2], "certified": bool(last[3])},
         "gpu_launches": launches,
@@ -334,7 +343,8 @@ def run_profile_case(args):
     desc = synth.DomainDesc(np.zeros(3), 1.0 / n, synth.dense_bricks(n // 8))
     hist = synth.random_histograms(np.random.default_rng(7), desc.nvox, 10, max_count=20)
     stream = torch.cuda.Stream()
-    dom = tgv.Domain([desc], nbins=10, storage=args.storage, stream=stream.cuda_stream)
+    dom = tgv.Domain([desc], nbins=10, storage=args.storage, stream=stream.cuda_stream,
+                     iter_kernel=args.iter_kernel)
     dom.set_histograms(0, hist)
     tgv.tgv_solve(dom.handle, 0, 6, False)
     tgv.tgv_solve(dom.handle, 0, 4, False)

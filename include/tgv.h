@@ -53,7 +53,7 @@ typedef enum {
     TGV_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed */
     TGV_ERR_BUDGET = 3,        /* a stated limit would be exceeded (vote counts, HBM budget) */
     TGV_ERR_CUDA = 4,          /* a CUDA runtime call failed */
-    TGV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    TGV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (the domain becomes unusable) */
     TGV_ERR_STATE = 6,         /* the domain is unusable after an earlier CUDA error */
     TGV_ERR_UNSUPPORTED = 7    /* a recognised option that is not built */
 } tgv_status;
@@ -78,12 +78,22 @@ enum {
 
 enum { TGV_PINHOLE = 0, TGV_SPHERICAL = 1 };
 
+/* Form of the fused iteration kernel (same arithmetic):
+ * PAIRED:    persistent CTAs stream each brick's state into shared memory with
+ *            bulk asynchronous copies (two bricks in flight per CTA); each
+ *            thread owns an x-adjacent voxel pair (default);
+ * PIPELINED: the same pipeline with one voxel per thread;
+ * ONE_BRICK_PER_CTA: one CTA per brick, plain loads.
+ * Levels whose arrays reach 2^32 elements always use ONE_BRICK_PER_CTA. */
+enum { TGV_ITER_PIPELINED = 0, TGV_ITER_ONE_BRICK_PER_CTA = 1, TGV_ITER_PAIRED = 2 };
+
 typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
 
 /* Solver parameters (Eq. 2 with the primal-dual step sizes of Sec. 3.2).
  * Defaults (tgv_default_params): nbins 8 (Alg. 1), alpha1 1, alpha0 2, lambda 1,
  * tau = sigma = 0.2 (tau*sigma*24 < 1: ||K||^2 <= 24 for the forward/backward
- * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2. */
+ * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2,
+ * paired iteration kernel. */
 typedef struct {
     int32_t nbins;       /* histogram bins, 2..16 */
     float alpha1;        /* weight of |grad u - v| */
@@ -95,6 +105,7 @@ typedef struct {
     int32_t clamp_u;     /* 1: project u onto [-1, 1] after the prox */
     int32_t centres;     /* TGV_CENTRES_* */
     float box_v;         /* bound B_v on |v_a| used by the duality gap */
+    int32_t iter_kernel; /* TGV_ITER_* form of the fused iteration kernel */
 } tgv_params;
 
 /* One level of a domain (all arrays host memory, copied at creation).

@@ -27,6 +27,20 @@ tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what)
     return TGV_ERR_CUDA;
 }
 
+// Reads the device error flag (the stream must be synchronised by the caller).
+tgv_status tgv_check_device_error(tgv_domain* d)
+{
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, d->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "error flag read");
+    if (flag) {
+        d->broken = true;
+        d->last_error = "a bounded device-side wait gave up (pipelined iteration kernel)";
+        return TGV_ERR_TIMEOUT;
+    }
+    return TGV_OK;
+}
+
 tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes)
 {
     if (bytes <= s.cap) return TGV_OK;
@@ -405,6 +419,7 @@ tgv_status tgv_default_params(tgv_params* out)
     out->clamp_u = 1;
     out->centres = TGV_CENTRES_ENDPOINTS;
     out->box_v = 2.0f;
+    out->iter_kernel = TGV_ITER_PAIRED;
     return TGV_OK;
 }
 
@@ -417,6 +432,9 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
     if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
     if (prm->centres != TGV_CENTRES_ENDPOINTS && prm->centres != TGV_CENTRES_MIDPOINTS) return TGV_ERR_INVALID_ARG;
+    if (prm->iter_kernel != TGV_ITER_PIPELINED && prm->iter_kernel != TGV_ITER_ONE_BRICK_PER_CTA &&
+        prm->iter_kernel != TGV_ITER_PAIRED)
+        return TGV_ERR_INVALID_ARG;
     if (!(prm->alpha1 > 0.0f) || !(prm->alpha0 > 0.0f) || !(prm->lambda >= 0.0f) || !(prm->tau > 0.0f) ||
         !(prm->sigma > 0.0f) || !(prm->box_v > 0.0f))
         return TGV_ERR_INVALID_ARG;
@@ -428,6 +446,8 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device);
     tgv_status st = tgv_cuda_check(d, e, "device query");
     if (st == TGV_OK) st = dalloc(d, (void**)&d->red_out, 4 * sizeof(double));
+    if (st == TGV_OK) st = dalloc(d, (void**)&d->err, sizeof(int));
+    if (st == TGV_OK) st = tgv_cuda_check(d, cudaMemsetAsync(d->err, 0, sizeof(int), d->stream), "error flag");
     d->levels.resize((size_t)nlevels);
     for (int32_t l = 0; l < nlevels && st == TGV_OK; ++l) st = build_level(d, levels[l], d->levels[l]);
     if (st != TGV_OK) {
@@ -449,6 +469,7 @@ void tgv_destroy_domain(tgv_domain* d)
     for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table})
         if (s->ptr) cudaFree(s->ptr);
     if (d->red_out) cudaFree(d->red_out);
+    if (d->err) cudaFree(d->err);
     cudaGetLastError();
     delete d;
 }
@@ -736,7 +757,9 @@ tgv_status tgv_synchronize(tgv_domain* d)
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);
-    return tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "synchronize");
+    st = tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "synchronize");
+    if (st != TGV_OK) return st;
+    return tgv_check_device_error(d);
 }
 
 int64_t tgv_domain_bytes(const tgv_domain* d) { return d ? d->bytes : 0; }

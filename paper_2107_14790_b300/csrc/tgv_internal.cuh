@@ -122,6 +122,7 @@ struct tgv_domain {
     TgvScratch tmp;     // staging for host <-> device field copies
     TgvScratch table;   // per-brick parent table of tgv_prolong
     double* red_out = nullptr;   // 4 doubles: final reduction result (device)
+    int* err = nullptr;          // device flag: 1 after a bounded device-side wait gave up
 };
 
 // helpers implemented in tgv_domain.cu
@@ -130,8 +131,44 @@ tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what);
 tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes);
 void tgv_bin_centres(const tgv_params& prm, float* c);
 
-// launchers implemented in tgv_solve.cu / tgv_hist.cu
+// Iteration arguments for the current ping-pong copy of a level.
+template <typename S>
+inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
+{
+    IterArgs<S> A;
+    const int c = L.cur, o = 1 - L.cur;
+    A.u = L.u;
+    A.ubar_in = L.ubar[c];
+    A.ubar_out = L.ubar[o];
+    A.v = (S*)L.v;
+    A.vbar_in = (const S*)L.vbar[c];
+    A.vbar_out = (S*)L.vbar[o];
+    A.p_in = (const S*)L.p[c];
+    A.p_out = (S*)L.p[o];
+    A.q_in = (const S*)L.q[c];
+    A.q_out = (S*)L.q[o];
+    A.hist = L.hist;
+    A.nbr = L.nbr;
+    A.nb = L.nb;
+    A.nall = L.nb + L.nf;
+    A.nbins = d->prm.nbins;
+    A.npairs = (d->prm.nbins + 1) / 2;
+    A.clamp_u = d->prm.clamp_u;
+    A.alpha1 = d->prm.alpha1;
+    A.alpha0 = d->prm.alpha0;
+    A.tau = d->prm.tau;
+    A.sigma = d->prm.sigma;
+    A.taulam = d->prm.tau * d->prm.lambda;
+    tgv_bin_centres(d->prm, A.c);
+    return A;
+}
+
+// launchers implemented in tgv_solve.cu / tgv_iter_pipe.cu / tgv_hist.cu
 tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters);
+tgv_status tgv_launch_iterations_pipe(tgv_domain* d, TgvLevel& L, int iters);
+bool tgv_pipe_supports(const TgvLevel& L);
+tgv_status tgv_launch_iterations_pair(tgv_domain* d, TgvLevel& L, int iters);
+tgv_status tgv_check_device_error(tgv_domain* d);
 tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out);
 cudaError_t tgv_launch_energy_view(const tgv_state_view& s, const tgv_params& prm, cudaStream_t stream,
                                    double* partial, double* result);

@@ -1,0 +1,857 @@
+// Pipelined, paired form of the fused TGV primal-dual iteration (the
+// arithmetic of tgv_iter_kernel in tgv_solve.cu: Eq. 2-3, Sec. 3.2).
+//
+// Persistent CTAs of 256 threads walk the active bricks with a grid stride;
+// each thread owns the x-adjacent voxel pair (2j, 2j+1) of one row of the
+// brick in hand, so shared-memory and global accesses are 64-bit (two FP32 or
+// two 16-bit values) and the x-neighbour inside the pair comes from registers.
+// Each brick's whole state -- u, ubar, v, vbar, p, q and the packed
+// histogram, contiguous per brick -- arrives in shared memory through seven
+// cp.async.bulk copies completed on an mbarrier, double-buffered: while brick
+// i is computed, brick i + grid is in flight.
+//
+// Halo duals (new p on the three -face layers, new q on the three +face
+// layers, which neighbouring bricks own) are recomputed here; the 384 halo
+// voxels split into exactly one warp-uniform task per thread (single voxels on
+// the x faces, pairs on the y and z faces), and their inputs are loaded into
+// registers before the CTA waits for its stage.
+//
+// Element offsets are 32-bit (selected only when every array of the level
+// has fewer than 2^32 elements); the bin count is a template parameter for 8,
+// 10 and 12 bins (0 = read at run time).  Every mbarrier wait is bounded
+// (about a second); a CTA that gives up sets the domain's error flag, waits
+// (bounded) for its copies in flight and returns.
+#include <math.h>
+
+#include "tgv_async.cuh"
+#include "tgv_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- paired storage access
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 ld(const float* p) { return *(const float2*)p; }
+    static __device__ __forceinline__ void st(float* p, float2 v) { *(float2*)p = v; }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p)
+    {
+        return __bfloat1622float2(*(const __nv_bfloat162*)p);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float2 v)
+    {
+        *(__nv_bfloat162*)p = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
+template <> struct Pair<__half> {
+    static __device__ __forceinline__ float2 ld(const __half* p) { return __half22float2(*(const __half2*)p); }
+    static __device__ __forceinline__ void st(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
+};
+
+__device__ __forceinline__ float2 ldf2(const float* p) { return *(const float2*)p; }
+__device__ __forceinline__ void stf2(float* p, float2 v) { *(float2*)p = v; }
+
+__device__ __forceinline__ int qidx(int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); }
+
+// p <- proj(p_old + sigma (g - vb)) and q <- proj(q_old + sigma E) for one voxel
+__device__ __forceinline__ void dual_update(const float g[3], const float vb[3], const float dm[3][3], float pn[3],
+                                            float qn[6], float sigma, float alpha1, float a1sq, float alpha0,
+                                            float a0sq)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pn[c] += sigma * (g[c] - vb[c]);
+    const float pn2 = pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2];
+    if (pn2 > a1sq) {
+        const float s = alpha1 * rsqrtf(pn2);
+        pn[0] *= s;
+        pn[1] *= s;
+        pn[2] *= s;
+    }
+    qn[0] += sigma * dm[0][0];
+    qn[1] += sigma * dm[1][1];
+    qn[2] += sigma * dm[2][2];
+    qn[3] += sigma * (0.5f * (dm[0][1] + dm[1][0]));
+    qn[4] += sigma * (0.5f * (dm[0][2] + dm[2][0]));
+    qn[5] += sigma * (0.5f * (dm[1][2] + dm[2][1]));
+    const float qn2 = qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + 2.0f * (qn[3] * qn[3] + qn[4] * qn[4] + qn[5] * qn[5]);
+    if (qn2 > a0sq) {
+        const float s = alpha0 * rsqrtf(qn2);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) qn[c] *= s;
+    }
+}
+
+__device__ __forceinline__ void proj_p(float p[3], float alpha1, float a1sq)
+{
+    const float n2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    if (n2 > a1sq) {
+        const float s = alpha1 * rsqrtf(n2);
+        p[0] *= s;
+        p[1] *= s;
+        p[2] *= s;
+    }
+}
+
+__device__ __forceinline__ void proj_q(float q[6], float alpha0, float a0sq)
+{
+    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0f * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    if (n2 > a0sq) {
+        const float s = alpha0 * rsqrtf(n2);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] *= s;
+    }
+}
+
+__device__ __forceinline__ void sym6(const float dm[3][3], float e[6])
+{
+    e[0] = dm[0][0];
+    e[1] = dm[1][1];
+    e[2] = dm[2][2];
+    e[3] = 0.5f * (dm[0][1] + dm[1][0]);
+    e[4] = 0.5f * (dm[0][2] + dm[2][0]);
+    e[5] = 0.5f * (dm[1][2] + dm[2][1]);
+}
+
+
+// new p for the halo pair (2hj, 7, hw) / (2hj, hw, 7) on the -AX face (AX = 1: y, 2: z)
+template <int AX>
+__device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const float* sub, float* hal_p, int tk,
+                                            float sigma, float alpha1, float a1sq)
+{
+    constexpr int OA = 3 - AX;  // the other face axis
+    const int hj = tk & 3, hw = tk >> 2;
+    const uint32_t lo = AX == 1 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;  // own voxel at coordinate 0 along AX
+    const float2 own = ldf2(sub + lo);
+    float ga[3], gb[3];
+    ga[0] = h[1] - h[0];                          // x-forward of voxel 0 is voxel 1
+    gb[0] = (hm & 1u) ? h[2] - h[1] : 0.0f;
+    ga[AX] = own.x - h[0];
+    gb[AX] = own.y - h[1];
+    ga[OA] = (hm & 2u) ? h[4] - h[0] : 0.0f;
+    gb[OA] = (hm & 2u) ? h[5] - h[1] : 0.0f;
+    float pa[3], pb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pa[c] = h[12 + 2 * c] + sigma * (ga[c] - h[6 + 2 * c]);
+        pb[c] = h[13 + 2 * c] + sigma * (gb[c] - h[7 + 2 * c]);
+    }
+    proj_p(pa, alpha1, a1sq);
+    proj_p(pb, alpha1, a1sq);
+    const int fi = 2 * hj + 8 * hw;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) stf2(hal_p + c * 192 + AX * 64 + fi, make_float2(pa[c], pb[c]));
+}
+
+// new q for the halo pair (2hj, 0, hw) / (2hj, hw, 0) on the +AX face
+template <typename S, int AX>
+__device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S* svb, float* hal_q, int tk,
+                                            float sigma, float alpha0, float a0sq)
+{
+    constexpr int OA = 3 - AX;
+    const int hj = tk & 3, hw = tk >> 2;
+    const uint32_t lo = AX == 1 ? 2 * hj + 56 + 64 * hw : 2 * hj + 8 * hw + 448;  // own voxel at coordinate 7
+    float dma[3][3], dmb[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 own = Pair<S>::ld(svb + c * 512 + lo);
+        const float va = h[2 * c], vbv = h[2 * c + 1];
+        dma[0][c] = (hm & 1u) ? va - h[6 + 2 * c] : 0.0f;  // backward x of voxel 0
+        dmb[0][c] = vbv - va;                              // backward x of voxel 1 is voxel 0
+        dma[AX][c] = va - own.x;
+        dmb[AX][c] = vbv - own.y;
+        dma[OA][c] = (hm & 2u) ? va - h[12 + 2 * c] : 0.0f;
+        dmb[OA][c] = (hm & 2u) ? vbv - h[13 + 2 * c] : 0.0f;
+    }
+    float ea[6], eb[6];
+    sym6(dma, ea);
+    sym6(dmb, eb);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        ea[c] = h[18 + 2 * c] + sigma * ea[c];
+        eb[c] = h[19 + 2 * c] + sigma * eb[c];
+    }
+    proj_q(ea, alpha0, a0sq);
+    proj_q(eb, alpha0, a0sq);
+    const int fi = 2 * hj + 8 * hw;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) stf2(hal_q + c * 192 + AX * 64 + fi, make_float2(ea[c], eb[c]));
+}
+
+}  // namespace
+
+template <typename S>
+struct PairArgs {
+    IterArgs<S> it;
+    int* err;
+    long long wait_budget;
+    uint32_t stage_bytes, tx_bytes;
+    uint32_t pn_bytes;                 // bytes of one own-new-dual buffer (0 when it aliases the stage)
+    uint32_t off_pn, off_hal, off_nbr, off_bar;
+};
+
+// Per-thread view of one CTA: thread t owns the voxel pair (2j, y, z), (2j+1, y, z).
+//
+// Halo task of thread t (warp-uniform):
+//   [0,64)    new p, -x face, single voxel (7, y, z) of the -x brick, y = k&7, z = k>>3
+//   [64,96)   new p, -y face, pair (2j, 7, z), (2j+1, 7, z), j = k&3, z = k>>2
+//   [96,128)  new p, -z face, pair (2j, y, 7), (2j+1, y, 7), j = k&3, y = k>>2
+//   [128,192) new q, +x face, single voxel (0, y, z) of the +x brick
+//   [192,224) new q, +y face, pair (2j, 0, z), (2j+1, 0, z)
+//   [224,256) new q, +z face, pair (2j, y, 0), (2j+1, y, 0)
+// Halo arrays of a stage: hal_p[c][a*64 + face index] (3 x 192 floats), then
+// hal_q[c][a*64 + face index] (6 x 192); face index y+8z (a = x), x+8z (a = y), x+8y (a = z).
+template <typename S, int NB>
+struct PairCta {
+    using PS = Pair<S>;
+    static constexpr uint32_t SB = sizeof(S);
+    static constexpr uint32_t O_U = 0, O_UB = 2048, O_V = 4096, O_VB = O_V + 3 * 512 * SB,
+                              O_P = O_VB + 3 * 512 * SB, O_Q = O_P + 3 * 512 * SB, O_H = O_Q + 6 * 512 * SB;
+    static constexpr int NP_MAX = NB ? (NB + 1) / 2 : TGV_MAX_BINS / 2;
+    static constexpr int NB_MAX = NB ? NB : TGV_MAX_BINS;
+
+    const PairArgs<S>& P;
+    const IterArgs<S>& A;
+    unsigned char* smem;
+    int t, j, y, z, x0, task, tk, nbk, nbins, npairs;
+    uint32_t l0;
+    float sigma, alpha1, alpha0, a1sq, a0sq;
+
+    // inputs of the next brick's phase A held in registers
+    float ubf_x;
+    float2 ubf_y, ubf_z;
+    float vbb_x[3];
+    float2 vbb_y[3], vbb_z[3];
+    float h[30];
+    uint32_t hm;
+    int hn;
+
+    __device__ __forceinline__ PairCta(const PairArgs<S>& p, unsigned char* sm)
+        : P(p), A(p.it), smem(sm)
+    {
+        t = threadIdx.x;
+        j = t & 3;
+        y = (t >> 2) & 7;
+        z = t >> 5;
+        x0 = 2 * j;
+        l0 = x0 + 8 * y + 64 * z;
+        task = t < 64 ? 0 : (t < 96 ? 1 : (t < 128 ? 2 : (t < 192 ? 3 : (t < 224 ? 4 : 5))));
+        tk = t < 64 ? t : (t < 96 ? t - 64 : (t < 128 ? t - 96 : (t < 192 ? t - 128 : (t < 224 ? t - 192 : t - 224))));
+        nbk = (int)A.nb;
+        nbins = NB ? NB : A.nbins;
+        npairs = NB ? (NB + 1) / 2 : A.npairs;
+        sigma = A.sigma;
+        alpha1 = A.alpha1;
+        alpha0 = A.alpha0;
+        a1sq = alpha1 * alpha1;
+        a0sq = alpha0 * alpha0;
+    }
+
+    __device__ __forceinline__ unsigned char* stage(int s) const { return smem + (size_t)s * P.stage_bytes; }
+    __device__ __forceinline__ float* pn_own(int s) const
+    {
+        return (float*)(SB == 4 ? stage(s) + O_P : smem + P.off_pn + (size_t)s * P.pn_bytes);
+    }
+    __device__ __forceinline__ float* qn_own(int s) const
+    {
+        return (float*)(SB == 4 ? stage(s) + O_Q : smem + P.off_pn + (size_t)s * P.pn_bytes + 3 * 512 * 4);
+    }
+    __device__ __forceinline__ float* hal_p(int s) const { return (float*)(smem + P.off_hal) + s * (9 * 192); }
+    __device__ __forceinline__ float* hal_q(int s) const { return hal_p(s) + 3 * 192; }
+    __device__ __forceinline__ uint64_t* bar() const { return (uint64_t*)(smem + P.off_bar); }
+    __device__ __forceinline__ int* nbr_row(int s) const { return (int*)(smem + P.off_nbr) + s * TGV_NNBR; }
+
+    __device__ __forceinline__ void issue(int s, uint32_t brick) const
+    {
+        unsigned char* st = stage(s);
+        uint64_t* b = bar() + s;
+        mbar_arrive_expect_tx(b, P.tx_bytes);
+        bulk_copy_g2s(st + O_U, A.u + brick * TGV_BVOX, 2048, b);
+        bulk_copy_g2s(st + O_UB, A.ubar_in + brick * TGV_BVOX, 2048, b);
+        bulk_copy_g2s(st + O_V, A.v + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_VB, A.vbar_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_P, A.p_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_Q, A.q_in + brick * 6 * TGV_BVOX, 6 * 512 * SB, b);
+        bulk_copy_g2s(st + O_H, A.hist + brick * (uint32_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, b);
+    }
+
+    // ---- global loads a brick's phase A needs besides its stage (own boundary neighbours, halo inputs)
+    __device__ __forceinline__ void load_inputs(const int* nrow)
+    {
+        const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
+        const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
+        ubf_x = 0.0f;
+        ubf_y = ubf_z = make_float2(0, 0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            vbb_x[c] = 0.0f;
+            vbb_y[c] = vbb_z[c] = make_float2(0, 0);
+        }
+        if (j == 3 && n_px >= 0) ubf_x = A.ubar_in[(uint32_t)n_px * TGV_BVOX + l0 + 1 - 7];
+        if (y == 7 && n_py >= 0) ubf_y = ldf2(A.ubar_in + (uint32_t)n_py * TGV_BVOX + l0 - 56);
+        if (z == 7 && n_pz >= 0) ubf_z = ldf2(A.ubar_in + (uint32_t)n_pz * TGV_BVOX + l0 - 448);
+        if (j == 0 && n_mx >= 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vbb_x[c] = ld_s(A.vbar_in + ((uint32_t)n_mx * 3 + c) * TGV_BVOX + l0 + 7);
+        }
+        if (y == 0 && n_my >= 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vbb_y[c] = PS::ld(A.vbar_in + ((uint32_t)n_my * 3 + c) * TGV_BVOX + l0 + 56);
+        }
+        if (z == 0 && n_mz >= 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(A.vbar_in + ((uint32_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
+        }
+        // halo inputs.  p tasks: h[0..1] ubar(h0,h1), h[2..3] forward along the first face
+        // axis, h[4..5] along the second, h[6..11] vbar (3 x pair), h[12..17] p (3 x pair).
+        // q tasks: h[0..5] vbar (3 x pair), h[6..11] backward along the first face axis,
+        // h[12..17] along the second, h[18..29] q (6 x pair).  Singles use the even slots.
+        hm = 0;
+        {
+            const int a = task % 3;
+            hn = task < 3 ? nrow[nb_minus(a)] : nrow[nb_plus(a)];
+            if (hn >= nbk) hn = -1;  // frozen: no dual variables there
+        }
+        if (hn < 0) return;
+        const uint32_t nb0 = (uint32_t)hn * TGV_BVOX;
+        if (task == 0) {  // -x face single: (7, hy, hz)
+            const int hy = tk & 7, hz = tk >> 3;
+            const uint32_t lh = 7 + 8 * hy + 64 * hz;
+            h[0] = A.ubar_in[nb0 + lh];
+            if (hy < 7) {
+                h[2] = A.ubar_in[nb0 + lh + 8];
+                hm |= 1u;
+            } else if (nrow[NB_MX_PY] >= 0) {
+                h[2] = A.ubar_in[(uint32_t)nrow[NB_MX_PY] * TGV_BVOX + lh - 56];
+                hm |= 1u;
+            }
+            if (hz < 7) {
+                h[4] = A.ubar_in[nb0 + lh + 64];
+                hm |= 2u;
+            } else if (nrow[NB_MX_PZ] >= 0) {
+                h[4] = A.ubar_in[(uint32_t)nrow[NB_MX_PZ] * TGV_BVOX + lh - 448];
+                hm |= 2u;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[12 + 2 * c] = ld_s(A.p_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+            }
+        } else if (task == 1 || task == 2) {  // -y / -z face pairs
+            const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 1) or y (task 2)
+            const uint32_t lh = task == 1 ? 2 * hj + 56 + 64 * hw : 2 * hj + 8 * hw + 448;
+            float2 u2 = ldf2(A.ubar_in + nb0 + lh);
+            h[0] = u2.x;
+            h[1] = u2.y;
+            if (hj < 3) {  // forward along x of the pair's second voxel
+                h[2] = A.ubar_in[nb0 + lh + 2];
+                hm |= 1u;
+            } else {
+                const int e = nrow[task == 1 ? NB_MY_PX : NB_MZ_PX];
+                if (e >= 0) {
+                    h[2] = A.ubar_in[(uint32_t)e * TGV_BVOX + lh + 1 - 7];
+                    hm |= 1u;
+                }
+            }
+            const uint32_t ostr = task == 1 ? 64 : 8;  // the other face axis: z (task 1) or y (task 2)
+            if (hw < 7) {
+                u2 = ldf2(A.ubar_in + nb0 + lh + ostr);
+                h[4] = u2.x;
+                h[5] = u2.y;
+                hm |= 2u;
+            } else {
+                const int e = nrow[task == 1 ? NB_MY_PZ : NB_MZ_PY];
+                if (e >= 0) {
+                    u2 = ldf2(A.ubar_in + (uint32_t)e * TGV_BVOX + lh - 7 * ostr);
+                    h[4] = u2.x;
+                    h[5] = u2.y;
+                    hm |= 2u;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[6 + 2 * c] = w.x;
+                h[7 + 2 * c] = w.y;
+                w = PS::ld(A.p_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[12 + 2 * c] = w.x;
+                h[13 + 2 * c] = w.y;
+            }
+        } else if (task == 3) {  // +x face single: (0, hy, hz)
+            const int hy = tk & 7, hz = tk >> 3;
+            const uint32_t lh = 8 * hy + 64 * hz;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+            if (hy > 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 8);
+                hm |= 1u;
+            } else if (nrow[NB_MY_PX] >= 0) {
+                const uint32_t e = (uint32_t)nrow[NB_MY_PX];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 56);
+                hm |= 1u;
+            }
+            if (hz > 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 64);
+                hm |= 2u;
+            } else if (nrow[NB_MZ_PX] >= 0) {
+                const uint32_t e = (uint32_t)nrow[NB_MZ_PX];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 448);
+                hm |= 2u;
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_s(A.q_in + ((uint32_t)hn * 6 + c) * TGV_BVOX + lh);
+        } else {  // task 4 / 5: +y / +z face pairs
+            const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 4) or y (task 5)
+            const uint32_t lh = task == 4 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[2 * c] = w.x;
+                h[2 * c + 1] = w.y;
+            }
+            if (hj > 0) {  // backward along x of the pair's first voxel
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 1);
+                hm |= 1u;
+            } else {
+                const int e = nrow[task == 4 ? NB_MX_PY : NB_MX_PZ];
+                if (e >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7);
+                    hm |= 1u;
+                }
+            }
+            const uint32_t ostr = task == 4 ? 64 : 8;  // the other face axis: z (task 4) or y (task 5)
+            if (hw > 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - ostr);
+                    h[12 + 2 * c] = w.x;
+                    h[13 + 2 * c] = w.y;
+                }
+                hm |= 2u;
+            } else {
+                const int e = nrow[task == 4 ? NB_MZ_PY : NB_MY_PZ];
+                if (e >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 w = PS::ld(A.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7 * ostr);
+                        h[12 + 2 * c] = w.x;
+                        h[13 + 2 * c] = w.y;
+                    }
+                    hm |= 2u;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float2 w = PS::ld(A.q_in + ((uint32_t)hn * 6 + c) * TGV_BVOX + lh);
+                h[18 + 2 * c] = w.x;
+                h[19 + 2 * c] = w.y;
+            }
+        }
+    }
+
+    // ---- phase A of the brick in stage s: new p, q at the own pair (into pn_own / qn_own)
+    // and the halo duals (into hal_p / hal_q).  Returns the link bits phase B needs.
+    __device__ __forceinline__ uint32_t phase_a(int s, const int* nrow)
+    {
+        const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
+        const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
+        unsigned char* st = stage(s);
+        const float* sub = (const float*)(st + O_UB);
+        const S* svb = (const S*)(st + O_VB);
+        const S* sp = (const S*)(st + O_P);
+        const S* sq = (const S*)(st + O_Q);
+        const float2 ub = ldf2(sub + l0);
+        float vb0[3], vb1[3], pn0[3], pn1[3], qn0[6], qn1[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 w = PS::ld(svb + c * 512 + l0);
+            vb0[c] = w.x;
+            vb1[c] = w.y;
+            w = PS::ld(sp + c * 512 + l0);
+            pn0[c] = w.x;
+            pn1[c] = w.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float2 w = PS::ld(sq + c * 512 + l0);
+            qn0[c] = w.x;
+            qn1[c] = w.y;
+        }
+        const bool fx1 = j < 3 || n_px >= 0, fy = y < 7 || n_py >= 0, fz = z < 7 || n_pz >= 0;
+        const bool bx0 = j > 0 || n_mx >= 0, by = y > 0 || n_my >= 0, bz = z > 0 || n_mz >= 0;
+        {
+            const float2 uy = y < 7 ? ldf2(sub + l0 + 8) : ubf_y;
+            const float2 uz = z < 7 ? ldf2(sub + l0 + 64) : ubf_z;
+            const float ux1 = j < 3 ? sub[l0 + 2] : ubf_x;
+            const float g0[3] = {ub.y - ub.x, fy ? uy.x - ub.x : 0.0f, fz ? uz.x - ub.x : 0.0f};
+            const float g1[3] = {fx1 ? ux1 - ub.y : 0.0f, fy ? uy.y - ub.y : 0.0f, fz ? uz.y - ub.y : 0.0f};
+            float dm0[3][3], dm1[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float wx0 = j > 0 ? ld_s(svb + c * 512 + l0 - 1) : vbb_x[c];
+                const float2 wy = y > 0 ? PS::ld(svb + c * 512 + l0 - 8) : vbb_y[c];
+                const float2 wz = z > 0 ? PS::ld(svb + c * 512 + l0 - 64) : vbb_z[c];
+                dm0[0][c] = bx0 ? vb0[c] - wx0 : 0.0f;
+                dm1[0][c] = vb1[c] - vb0[c];
+                dm0[1][c] = by ? vb0[c] - wy.x : 0.0f;
+                dm1[1][c] = by ? vb1[c] - wy.y : 0.0f;
+                dm0[2][c] = bz ? vb0[c] - wz.x : 0.0f;
+                dm1[2][c] = bz ? vb1[c] - wz.y : 0.0f;
+            }
+            dual_update(g0, vb0, dm0, pn0, qn0, sigma, alpha1, a1sq, alpha0, a0sq);
+            dual_update(g1, vb1, dm1, pn1, qn1, sigma, alpha1, a1sq, alpha0, a0sq);
+        }
+        // own old p / q were read above by this thread only; overwrite in place (FP32) or store
+        float* pno = pn_own(s);
+        float* qno = qn_own(s);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stf2(pno + c * 512 + l0, make_float2(pn0[c], pn1[c]));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) stf2(qno + c * 512 + l0, make_float2(qn0[c], qn1[c]));
+
+        // halo duals
+        float* hp = hal_p(s);
+        float* hq = hal_q(s);
+        if (hn >= 0) {
+            if (task == 0) {  // p at (7, hy, hz) of the -x brick
+                const int hy = tk & 7, hz = tk >> 3;
+                float g[3] = {sub[8 * hy + 64 * hz] - h[0], (hm & 1u) ? h[2] - h[0] : 0.0f,
+                              (hm & 2u) ? h[4] - h[0] : 0.0f};
+                float pp[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) pp[c] = h[12 + 2 * c] + sigma * (g[c] - h[6 + 2 * c]);
+                proj_p(pp, alpha1, a1sq);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hp[c * 192 + tk] = pp[c];
+            } else if (task == 1) {
+                halo_p_pair<1>(h, hm, sub, hp, tk, sigma, alpha1, a1sq);
+            } else if (task == 2) {
+                halo_p_pair<2>(h, hm, sub, hp, tk, sigma, alpha1, a1sq);
+            } else if (task == 3) {  // q at (0, hy, hz) of the +x brick
+                const int hy = tk & 7, hz = tk >> 3;
+                const uint32_t lo = 7 + 8 * hy + 64 * hz;
+                float dm[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dm[0][c] = h[2 * c] - ld_s(svb + c * 512 + lo);
+                    dm[1][c] = (hm & 1u) ? h[2 * c] - h[6 + 2 * c] : 0.0f;
+                    dm[2][c] = (hm & 2u) ? h[2 * c] - h[12 + 2 * c] : 0.0f;
+                }
+                float e[6];
+                sym6(dm, e);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) e[c] = h[18 + 2 * c] + sigma * e[c];
+                proj_q(e, alpha0, a0sq);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) hq[c * 192 + tk] = e[c];
+            } else if (task == 4) {
+                halo_q_pair<S, 1>(h, hm, svb, hq, tk, sigma, alpha0, a0sq);
+            } else {
+                halo_q_pair<S, 2>(h, hm, svb, hq, tk, sigma, alpha0, a0sq);
+            }
+        }
+        // link bits for phase B: bit 2k "any", bit 2k+1 "active", k = 0 (-x of voxel 0),
+        // 1 (+x of voxel 1), 2 (+y), 3 (-y), 4 (+z), 5 (-z)
+        uint32_t L = 0;
+        L |= (bx0 ? 1u : 0u) | ((j > 0 || (n_mx >= 0 && n_mx < nbk)) ? 2u : 0u);
+        L |= (fx1 ? 4u : 0u) | ((j < 3 || (n_px >= 0 && n_px < nbk)) ? 8u : 0u);
+        L |= (fy ? 16u : 0u) | ((y < 7 || (n_py >= 0 && n_py < nbk)) ? 32u : 0u);
+        L |= (by ? 64u : 0u) | ((y > 0 || (n_my >= 0 && n_my < nbk)) ? 128u : 0u);
+        L |= (fz ? 256u : 0u) | ((z < 7 || (n_pz >= 0 && n_pz < nbk)) ? 512u : 0u);
+        L |= (bz ? 1024u : 0u) | ((z > 0 || (n_mz >= 0 && n_mz < nbk)) ? 2048u : 0u);
+        return L;
+    }
+
+    // ---- phase B of brick b in stage s: divergences, prox, over-relaxation, global stores
+    __device__ __forceinline__ void phase_b(int s, uint32_t b, uint32_t L) const
+    {
+        unsigned char* st = stage(s);
+        const float* su = (const float*)(st + O_U);
+        const S* sv = (const S*)(st + O_V);
+        const uint32_t* sh = (const uint32_t*)(st + O_H);
+        const float* pno = pn_own(s);
+        const float* qno = qn_own(s);
+        const float* hp = hal_p(s);
+        const float* hq = hal_q(s);
+        float pn0[3], pn1[3], qn0[6], qn1[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 w = ldf2(pno + c * 512 + l0);
+            pn0[c] = w.x;
+            pn1[c] = w.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float2 w = ldf2(qno + c * 512 + l0);
+            qn0[c] = w.x;
+            qn1[c] = w.y;
+        }
+        float d1a = 0.0f, d1b = 0.0f;
+        float d2a[3] = {0, 0, 0}, d2b[3] = {0, 0, 0};
+        // x: voxel 0: forward = voxel 1, backward = (x0-1) or the -x brick;
+        //    voxel 1: backward = voxel 0, forward = (x0+2) or the +x brick
+        d1a += pn0[0];
+        if (L & 2u) d1a -= j > 0 ? pno[l0 - 1] : hp[y + 8 * z];
+        if (L & 4u) d1b += pn1[0];
+        d1b -= pn0[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int qc = qidx(0, c);
+            d2a[c] += qn1[qc];
+            if (L & 1u) d2a[c] -= qn0[qc];
+            if (L & 8u) d2b[c] += j < 3 ? qno[qc * 512 + l0 + 2] : hq[qc * 192 + y + 8 * z];
+            d2b[c] -= qn1[qc];
+        }
+        // y
+        const uint32_t fyi = 64 + x0 + 8 * z;
+        if (L & 16u) {
+            d1a += pn0[1];
+            d1b += pn1[1];
+        }
+        if (L & 128u) {
+            const float2 w = y > 0 ? ldf2(pno + 512 + l0 - 8) : ldf2(hp + 192 + fyi);
+            d1a -= w.x;
+            d1b -= w.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int qc = qidx(1, c);
+            if (L & 32u) {
+                const float2 w = y < 7 ? ldf2(qno + qc * 512 + l0 + 8) : ldf2(hq + qc * 192 + fyi);
+                d2a[c] += w.x;
+                d2b[c] += w.y;
+            }
+            if (L & 64u) {
+                d2a[c] -= qn0[qc];
+                d2b[c] -= qn1[qc];
+            }
+        }
+        // z
+        const uint32_t fzi = 128 + x0 + 8 * y;
+        if (L & 256u) {
+            d1a += pn0[2];
+            d1b += pn1[2];
+        }
+        if (L & 2048u) {
+            const float2 w = z > 0 ? ldf2(pno + 1024 + l0 - 64) : ldf2(hp + 384 + fzi);
+            d1a -= w.x;
+            d1b -= w.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int qc = qidx(2, c);
+            if (L & 512u) {
+                const float2 w = z < 7 ? ldf2(qno + qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi);
+                d2a[c] += w.x;
+                d2b[c] += w.y;
+            }
+            if (L & 1024u) {
+                d2a[c] -= qn0[qc];
+                d2b[c] -= qn1[qc];
+            }
+        }
+        const float2 u0 = ldf2(su + l0);
+        const float uta = u0.x + A.tau * d1a, utb = u0.y + A.tau * d1b;
+        // prox: generalised median = max_i min(ut - tau*lambda*W_i, c_i), c_n = +inf
+        uint32_t hwa[NP_MAX], hwb[NP_MAX];
+        float hsa = 0.0f, hsb = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NP_MAX; ++k) {
+            uint2 w = make_uint2(0u, 0u);
+            if (NB || k < npairs) w = *(const uint2*)(sh + k * 512 + l0);
+            hwa[k] = w.x;
+            hwb[k] = w.y;
+            hsa += (float)(w.x & 0xffffu) + (float)(w.x >> 16);
+            hsb += (float)(w.y & 0xffffu) + (float)(w.y >> 16);
+        }
+        float Wa = -hsa, Wb = -hsb;
+        float una = -INFINITY, unb = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < NB_MAX; ++i) {
+            if (NB || i < nbins) {
+                const float ci = A.c[i];
+                una = fmaxf(una, fminf(uta - A.taulam * Wa, ci));
+                unb = fmaxf(unb, fminf(utb - A.taulam * Wb, ci));
+                Wa += 2.0f * (float)((hwa[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
+                Wb += 2.0f * (float)((hwb[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
+            }
+        }
+        una = fmaxf(una, uta - A.taulam * Wa);
+        unb = fmaxf(unb, utb - A.taulam * Wb);
+        if (A.clamp_u) {
+            una = fminf(1.0f, fmaxf(-1.0f, una));
+            unb = fminf(1.0f, fmaxf(-1.0f, unb));
+        }
+        const uint32_t vi = b * TGV_BVOX + l0;
+        stf2(A.u + vi, make_float2(una, unb));
+        stf2(A.ubar_out + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t oi = (b * 3 + c) * TGV_BVOX + l0;
+            const float2 v0 = PS::ld(sv + c * 512 + l0);
+            const float2 v1 = make_float2(v0.x + A.tau * (pn0[c] + d2a[c]), v0.y + A.tau * (pn1[c] + d2b[c]));
+            PS::st(A.v + oi, v1);
+            PS::st(A.vbar_out + oi, make_float2(2.0f * v1.x - v0.x, 2.0f * v1.y - v0.y));
+            PS::st(A.p_out + oi, make_float2(pn0[c], pn1[c]));
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) PS::st(A.q_out + (b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
+    }
+};
+
+// Software-pipelined over bricks: in one barrier interval a CTA finishes brick
+// b (phase B) and starts brick b + grid (its halo loads are issued first, so
+// their latency overlaps phase B; then phase A once its stage has landed).
+template <typename S, int NB>
+__global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairArgs<S> P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    PairCta<S, NB> C(P, smem);
+    const uint32_t G = gridDim.x;
+    const uint32_t nb = (uint32_t)C.nbk;
+    uint32_t b = blockIdx.x;
+    uint64_t* bar = C.bar();
+    const int t = C.t;
+
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    if (t < TGV_NNBR) {
+        C.nbr_row(0)[t] = P.it.nbr[b * TGV_NNBR + t];
+        if (b + G < nb) C.nbr_row(1)[t] = P.it.nbr[(b + G) * TGV_NNBR + t];
+    }
+    __syncthreads();
+    if (t == 0) {
+        C.issue(0, b);
+        if (b + G < nb) C.issue(1, b + G);
+    }
+    uint32_t parity = 0;
+    bool bail = false;
+    int s = 0;
+    // prologue: phase A of the first brick
+    C.load_inputs(C.nbr_row(0));
+    {
+        const bool ok = mbar_wait_bounded(&bar[0], 0, P.wait_budget);
+        if (__syncthreads_or(!ok)) bail = true;
+    }
+    uint32_t links = 0;
+    if (!bail) {
+        parity ^= 1u;
+        links = C.phase_a(0, C.nbr_row(0));
+        __syncthreads();
+    }
+    while (!bail) {
+        const uint32_t bn = b + G;
+        const int ns = s ^ 1;
+        uint32_t next_links = 0;
+        if (bn < nb) C.load_inputs(C.nbr_row(ns));
+        // the row of brick b is no longer read: reuse it for brick bn + G
+        if (t < TGV_NNBR && bn + G < nb) C.nbr_row(s)[t] = P.it.nbr[(bn + G) * TGV_NNBR + t];
+        C.phase_b(s, b, links);
+        if (bn < nb) {
+            const bool ok = mbar_wait_bounded(&bar[ns], (parity >> ns) & 1u, P.wait_budget);
+            if (__syncthreads_or(!ok)) {
+                bail = true;
+                b = bn;
+                s = ns;
+                break;
+            }
+            parity ^= 1u << ns;
+            next_links = C.phase_a(ns, C.nbr_row(ns));
+        }
+        __syncthreads();  // stage s and the phase A results of bn are settled
+        if (t == 0 && b + 2 * G < nb) {
+            fence_proxy_async_smem();
+            C.issue(s, b + 2 * G);
+        }
+        if (bn >= nb) break;
+        b = bn;
+        s = ns;
+        links = next_links;
+    }
+    if (bail && t == 0) {
+        atomicExch(P.err, 1);
+        // the stage being waited for (and, in the prologue, the second one) may still receive data
+        mbar_wait_bounded(&bar[s], (parity >> s) & 1u, P.wait_budget);
+        if (b + G < nb) mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, P.wait_budget);
+    }
+}
+
+namespace {
+
+template <typename S, int NB>
+tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
+{
+    const uint32_t SB = sizeof(S);
+    const int npairs = (d->prm.nbins + 1) / 2;
+    const uint32_t stage = (uint32_t)((4096 + 15 * 512 * SB + npairs * 2048 + 127) / 128 * 128);
+    const uint32_t tx = 4096 + 15 * 512 * SB + npairs * 2048;
+    uint32_t off = 2 * stage;
+    PairArgs<S> P;
+    P.pn_bytes = SB == 4 ? 0 : 9 * 512 * 4;
+    P.off_pn = off;
+    off += 2 * P.pn_bytes;
+    P.off_hal = off;
+    off += 2 * 9 * 192 * 4;
+    P.off_nbr = off;
+    off += 2 * TGV_NNBR * 4;
+    off = (off + 15) / 16 * 16;
+    P.off_bar = off;
+    off += 2 * 8;
+    const size_t smem = off;
+    auto kern = tgv_iter_pair_kernel<S, NB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pair kernel smem attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pair kernel occupancy");
+    if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "paired iteration kernel does not fit on an SM");
+    int64_t grid = (int64_t)per_sm * d->sm_count;
+    if (grid > L.nb) grid = L.nb;
+    P.err = d->err;
+    P.wait_budget = 2000000000LL;  // about one second at 2 GHz
+    P.stage_bytes = stage;
+    P.tx_bytes = tx;
+    for (int it = 0; it < iters; ++it) {
+        P.it = tgv_make_iter_args<S>(d, L);
+        kern<<<(unsigned)grid, kThreads, smem, d->stream>>>(P);
+        d->launches++;
+        L.cur ^= 1;
+    }
+    return tgv_cuda_check(d, cudaGetLastError(), "tgv_iter_pair_kernel launch");
+}
+
+template <typename S>
+tgv_status launch_pair_bins(tgv_domain* d, TgvLevel& L, int iters)
+{
+    switch (d->prm.nbins) {
+    case 8: return launch_pair_t<S, 8>(d, L, iters);
+    case 10: return launch_pair_t<S, 10>(d, L, iters);
+    case 12: return launch_pair_t<S, 12>(d, L, iters);
+    default: return launch_pair_t<S, 0>(d, L, iters);
+    }
+}
+
+}  // namespace
+
+tgv_status tgv_launch_iterations_pair(tgv_domain* d, TgvLevel& L, int iters)
+{
+    if (L.nb == 0 || iters == 0) return TGV_OK;
+    switch (d->prm.storage) {
+    case TGV_STORAGE_FP32: return launch_pair_bins<float>(d, L, iters);
+    case TGV_STORAGE_BF16: return launch_pair_bins<__nv_bfloat16>(d, L, iters);
+    case TGV_STORAGE_FP16: return launch_pair_bins<__half>(d, L, iters);
+    }
+    return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
+}

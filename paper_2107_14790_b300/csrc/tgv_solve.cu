@@ -23,26 +23,25 @@ __device__ __forceinline__ int face_index(int a, int x, int y, int z)
     return a == 0 ? y + 8 * z : (a == 1 ? x + 8 * z : x + 8 * y);
 }
 
+// Projections onto |p|_2 <= alpha and |q|_F <= alpha: scale by alpha/|.| when outside.
 __device__ __forceinline__ void proj3(float p[3], float alpha)
 {
-    float n = sqrtf(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    float s = n / alpha;
-    if (s > 1.0f) {
-        float r = 1.0f / s;
-        p[0] *= r;
-        p[1] *= r;
-        p[2] *= r;
+    const float n2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    if (n2 > alpha * alpha) {
+        const float s = alpha * rsqrtf(n2);
+        p[0] *= s;
+        p[1] *= s;
+        p[2] *= s;
     }
 }
 
 __device__ __forceinline__ void proj6(float q[6], float alpha)
 {
-    float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0f * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
-    float s = sqrtf(n2) / alpha;
-    if (s > 1.0f) {
-        float r = 1.0f / s;
+    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0f * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    if (n2 > alpha * alpha) {
+        const float s = alpha * rsqrtf(n2);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) q[c] *= r;
+        for (int c = 0; c < 6; ++c) q[c] *= s;
     }
 }
 
@@ -408,30 +407,41 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
     float ef2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.0f * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
     k0 += ek[0] * q[0] + ek[1] * q[1] + ek[2] * q[2] + 2.0f * (ek[3] * q[3] + ek[4] * q[4] + ek[5] * q[5]);
 
-    // data term and its conjugate phi*(div1 p) over the breakpoints {-1, c_b, +1}
+    // data term lambda*sum_b h_b|u - c_b| at u, and its conjugate phi*(div1 p): the
+    // maximum of w*u - data(u) over the breakpoints {-1, c_0..c_{n-1}, +1}.  With
+    // prefix sums H_< , S_< (counts and count-weighted centres below bin k):
+    //   data(c_k) = lambda (c_k (H_< - H_>) - (S_< - S_>)).
     float hb[TGV_MAX_BINS];
+    float H = 0.0f, Sc = 0.0f, du_own = 0.0f;
 #pragma unroll
     for (int k = 0; k < TGV_MAX_BINS; ++k) {
         hb[k] = 0.0f;
         if (k < A.nbins) {
-            uint32_t w = A.hist[((int64_t)b * A.npairs + (k >> 1)) * TGV_BVOX + t];
+            const uint32_t w = A.hist[((int64_t)b * A.npairs + (k >> 1)) * TGV_BVOX + t];
             hb[k] = (float)((w >> ((k & 1) * 16)) & 0xffffu);
+            H += hb[k];
+            Sc += hb[k] * A.c[k];
+            du_own += hb[k] * fabsf(u - A.c[k]);
         }
     }
-    auto data = [&](float uu) {
-        float s = 0.0f;
+    float best = fmaxf(-div1 - A.lambda * (Sc + H), div1 - A.lambda * (H - Sc));
+    {
+        float Hlt = 0.0f, Slt = 0.0f;
 #pragma unroll
-        for (int k = 0; k < TGV_MAX_BINS; ++k)
-            if (k < A.nbins) s += hb[k] * fabsf(uu - A.c[k]);
-        return A.lambda * s;
-    };
-    float best = fmaxf(-div1 - data(-1.0f), div1 - data(1.0f));
-#pragma unroll
-    for (int k = 0; k < TGV_MAX_BINS; ++k)
-        if (k < A.nbins) best = fmaxf(best, div1 * A.c[k] - data(A.c[k]));
+        for (int k = 0; k < TGV_MAX_BINS; ++k) {
+            if (k < A.nbins) {
+                const float Hgt = H - Hlt - hb[k], Sgt = Sc - Slt - hb[k] * A.c[k];
+                const float dk = A.lambda * (A.c[k] * (Hlt - Hgt) - (Slt - Sgt));
+                best = fmaxf(best, div1 * A.c[k] - dk);
+                Hlt += hb[k];
+                Slt += hb[k] * A.c[k];
+            }
+        }
+    }
     float l1 = fabsf(p[0] + div2[0]) + fabsf(p[1] + div2[1]) + fabsf(p[2] + div2[2]);
 
-    double en = (double)A.alpha1 * (double)sqrtf(gmv2) + (double)A.alpha0 * (double)sqrtf(ef2) + (double)data(u);
+    double en = (double)A.alpha1 * (double)sqrtf(gmv2) + (double)A.alpha0 * (double)sqrtf(ef2) +
+                (double)(A.lambda * du_own);
     double du = (double)k0 - (double)best - (double)A.box_v * (double)l1;
     double vm = (double)vmax;
 
@@ -502,41 +512,10 @@ __global__ void __launch_bounds__(1024) tgv_reduce_partials(const double* partia
 // host launchers
 // =====================================================================================
 template <typename S>
-static IterArgs<S> make_iter_args(tgv_domain* d, TgvLevel& L)
-{
-    IterArgs<S> A;
-    const int c = L.cur, o = 1 - L.cur;
-    A.u = L.u;
-    A.ubar_in = L.ubar[c];
-    A.ubar_out = L.ubar[o];
-    A.v = (S*)L.v;
-    A.vbar_in = (const S*)L.vbar[c];
-    A.vbar_out = (S*)L.vbar[o];
-    A.p_in = (const S*)L.p[c];
-    A.p_out = (S*)L.p[o];
-    A.q_in = (const S*)L.q[c];
-    A.q_out = (S*)L.q[o];
-    A.hist = L.hist;
-    A.nbr = L.nbr;
-    A.nb = L.nb;
-    A.nall = L.nb + L.nf;
-    A.nbins = d->prm.nbins;
-    A.npairs = (d->prm.nbins + 1) / 2;
-    A.clamp_u = d->prm.clamp_u;
-    A.alpha1 = d->prm.alpha1;
-    A.alpha0 = d->prm.alpha0;
-    A.tau = d->prm.tau;
-    A.sigma = d->prm.sigma;
-    A.taulam = d->prm.tau * d->prm.lambda;
-    tgv_bin_centres(d->prm, A.c);
-    return A;
-}
-
-template <typename S>
 static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
 {
     for (int it = 0; it < iters; ++it) {
-        IterArgs<S> A = make_iter_args<S>(d, L);
+        IterArgs<S> A = tgv_make_iter_args<S>(d, L);
         tgv_iter_kernel<S><<<(unsigned)L.nb, TGV_BVOX, 0, d->stream>>>(A);
         d->launches++;
         L.cur ^= 1;
@@ -547,6 +526,8 @@ static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
 tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters)
 {
     if (L.nb == 0 || iters == 0) return TGV_OK;
+    if (d->prm.iter_kernel == TGV_ITER_PAIRED && tgv_pipe_supports(L)) return tgv_launch_iterations_pair(d, L, iters);
+    if (d->prm.iter_kernel == TGV_ITER_PIPELINED && tgv_pipe_supports(L)) return tgv_launch_iterations_pipe(d, L, iters);
     switch (d->prm.storage) {
     case TGV_STORAGE_FP32: return launch_iters_t<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_iters_t<__nv_bfloat16>(d, L, iters);
@@ -585,7 +566,9 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     st = tgv_cuda_check(d, cudaMemcpyAsync(host_out, d->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, d->stream),
                         "energy copy");
     if (st != TGV_OK) return st;
-    return tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "energy sync");
+    st = tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "energy sync");
+    if (st != TGV_OK) return st;
+    return tgv_check_device_error(d);
 }
 
 tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)

@@ -35,7 +35,7 @@ class tgv_params(ctypes.Structure):
     _fields_ = [("nbins", ctypes.c_int32), ("alpha1", ctypes.c_float), ("alpha0", ctypes.c_float),
                 ("lam", ctypes.c_float), ("tau", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("clamp_u", ctypes.c_int32), ("centres", ctypes.c_int32),
-                ("box_v", ctypes.c_float)]
+                ("box_v", ctypes.c_float), ("iter_kernel", ctypes.c_int32)]
 
 
 class tgv_level_desc(ctypes.Structure):
@@ -136,13 +136,17 @@ def make_camera(cam) -> tgv_camera:
     return c
 
 
+ITER_KERNELS = {"pipelined": 0, "one_brick_per_cta": 1, "paired": 2}
+
+
 def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, storage="fp32", clamp_u=True,
-                centres=0, box_v=2.0) -> tgv_params:
+                centres=0, box_v=2.0, iter_kernel="paired") -> tgv_params:
     p = tgv_params()
     _check(None, lib().tgv_default_params(ctypes.byref(p)))
     p.nbins, p.alpha1, p.alpha0, p.lam, p.tau, p.sigma = int(nbins), alpha1, alpha0, lam, tau, sigma
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.clamp_u, p.centres, p.box_v = int(bool(clamp_u)), int(centres), box_v
+    p.iter_kernel = ITER_KERNELS[iter_kernel] if isinstance(iter_kernel, str) else int(iter_kernel)
     return p
 
 

@@ -20,6 +20,7 @@ from tests._geom import dense_from_bricks, edge_crossings
 pytestmark = pytest.mark.gpu
 
 U_TOL = 1e-4
+KERNEL = {"form": "paired"}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,9 +31,18 @@ def _lib():
     tgv.lib()
 
 
+@pytest.fixture(autouse=True, params=["paired", "pipelined", "one_brick_per_cta"])
+def iter_kernel(request):
+    """Every parity test runs with each form of the fused iteration kernel."""
+    KERNEL["form"] = request.param
+    yield request.param
+    KERNEL["form"] = "paired"
+
+
 def gdomain(levels, nbins, **kw):
     if not isinstance(levels, (list, tuple)):
         levels = [levels]
+    kw.setdefault("iter_kernel", KERNEL["form"])
     return tgv.Domain(levels, nbins=nbins, stream=torch.cuda.current_stream().cuda_stream, **kw)
 
 
@@ -303,3 +313,30 @@ def test_device_pointer_io(sphere_scene, sphere_hist):
         dom.field(0, "u", out=out)
         host = dom.field(0, "u")
         np.testing.assert_array_equal(out.cpu().numpy(), host)
+
+
+def test_kernel_forms_agree_on_a_large_ragged_domain():
+    """Pipelined and one-brick-per-CTA forms on 6^3 bricks with holes and a frozen shell."""
+    rng = np.random.default_rng(77)
+    box = synth.dense_bricks(6)
+    keep = rng.random(len(box)) > 0.15
+    act = box[keep]
+    frz = box[~keep][:10]
+    fu = rng.uniform(-1, 1, (len(frz), 512)).astype(np.float32)
+    fv = rng.normal(0, 0.1, (len(frz), 3, 512)).astype(np.float32)
+    desc = synth.DomainDesc(np.zeros(3), 1.0, act, frozen=frz, frozen_u=fu, frozen_v=fv)
+    hist = synth.random_histograms(rng, desc.nvox, 10, max_count=15)
+    out = {}
+    forms = ("paired", "pipelined", "one_brick_per_cta")
+    for form in forms:
+        with gdomain(desc, 10, iter_kernel=form) as dom:
+            dom.set_histograms(0, hist)
+            dom.solve(0, 37)
+            out[form] = {f: dom.field(0, f) for f in ("u", "v", "p", "q", "ubar", "vbar")}
+    for form in forms[1:]:
+        for f in out["paired"]:
+            np.testing.assert_allclose(out["paired"][f], out[form][f], atol=2e-6, rtol=0)
+    orc = oracle.OracleLevel(desc, 10)
+    orc.hist[:] = hist
+    orc.iterate(37)
+    assert np.max(np.abs(out["paired"]["u"][:, 0] - orc.u)) <= U_TOL
