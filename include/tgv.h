@@ -84,7 +84,7 @@ enum { TGV_PINHOLE = 0, TGV_SPHERICAL = 1 };
  *            thread owns an x-adjacent voxel pair (default);
  * PIPELINED: the same pipeline with one voxel per thread;
  * ONE_BRICK_PER_CTA: one CTA per brick, plain loads.
- * Levels whose arrays reach 2^32 elements always use ONE_BRICK_PER_CTA. */
+ */
 enum { TGV_ITER_PIPELINED = 0, TGV_ITER_ONE_BRICK_PER_CTA = 1, TGV_ITER_PAIRED = 2 };
 
 typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
@@ -188,6 +188,21 @@ TGV_API tgv_status tgv_accumulate_depthmaps(tgv_domain* d, int32_t level, const 
  * synchronises the stream.  Errors: INVALID_ARG, STATE, CUDA. */
 TGV_API tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out);
 
+/* Same as tgv_solve, run as a CUDA graph: the first call with a given
+ * iteration count, starting ping-pong parity and work list launches its
+ * kernels one by one and captures them into a graph; later matching calls
+ * replay that graph with one launch.  Needs a non-NULL stream at creation
+ * (UNSUPPORTED otherwise).  Graphs are freed with the domain. */
+TGV_API tgv_status tgv_solve_graph(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out);
+
+/* Restricts later iterations and energy evaluations of a level to the listed
+ * active bricks (host or device int32 array of n distinct indices in [0,
+ * nbricks)); bricks = NULL or n < 0 restores "every active brick".  Bricks
+ * outside the list keep their state; none of them may be a face or edge
+ * neighbour of a listed brick (the intended use: one level holding several
+ * separated chunks, some of which are finished).  Errors: INVALID_ARG. */
+TGV_API tgv_status tgv_set_work_list(tgv_domain* d, int32_t level, const int32_t* bricks, int64_t n);
+
 /* Energy of Eq. 2 on the level (FP64 accumulation of FP32 per-voxel terms,
  * fixed-order deterministic reduction) and the value of the dual problem
  * with u in [-1, 1] and |v_a| <= box_v:
@@ -286,6 +301,69 @@ typedef struct {
 } tgv_state_view;
 
 TGV_API tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_params* prm, void* stream, double* out);
+
+/* ---------------------------------------------------------------------------
+ * Serving: chunk-solve requests with continuous batching.
+ *
+ * A request is one independent part of a domain (Sec. 4.3 treetop leaves:
+ * the parts are solved independently, their border cubes frozen, Sec. 4.5):
+ * a set of active bricks, its frozen shell and its histograms.  A server
+ * keeps every admitted request's state resident in one device arena whose
+ * capacity is fixed at creation (the HBM budget), and advances all running
+ * requests together: each fused iteration launch covers the work list of
+ * every running request, so requests that arrive while others are running
+ * join the next launch, and finished ones leave it.  A request's result is
+ * the same as solving it alone (no link ever leaves a request).
+ * All requests of a server share nbins and the other parameters.
+ * ------------------------------------------------------------------------- */
+typedef struct tgv_server tgv_server;
+
+typedef struct {
+    int64_t capacity_bricks;  /* active bricks the arena holds */
+    int64_t capacity_frozen;  /* frozen bricks the arena holds */
+    int64_t staging_bytes;    /* pinned host staging for inputs (<= 0: 256 MiB) */
+} tgv_server_cfg;
+
+/* Creates a server and allocates its arena on the current device.  stream:
+ * a non-NULL cudaStream_t for all of its work.  Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA. */
+TGV_API tgv_status tgv_server_create(const tgv_server_cfg* cfg, const tgv_params* prm, void* stream,
+                                     tgv_server** out);
+
+/* Admits a request: chunk = its active bricks and frozen shell (frozen_u /
+ * frozen_v as in tgv_level_desc; origin, h, radius unused), hist = uint32
+ * [voxel][nbins] counts (host or device; device memory must stay valid until
+ * the server's stream reaches this call; counts above 65535 are not
+ * allowed), `iterations` primal-dual iterations from u = v = p = q = 0.
+ * Returns a ticket.  Errors: BUDGET (not enough free arena space right now:
+ * retry after extracting finished requests), INVALID_ARG (a request larger
+ * than the whole arena, bad bricks), CUDA. */
+TGV_API tgv_status tgv_server_submit(tgv_server* s, const tgv_level_desc* chunk, const uint32_t* hist,
+                                     int32_t iterations, uint64_t* ticket);
+
+/* Queues up to max_iterations fused iterations over every running request,
+ * stopping early at the first iteration after which some request has run
+ * its count; *finished (nullable) receives how many requests finished.  Does
+ * not wait for the device. */
+TGV_API tgv_status tgv_server_step(tgv_server* s, int32_t max_iterations, int32_t* finished);
+
+/* *done = 1 once the request's iterations have all been queued. */
+TGV_API tgv_status tgv_server_poll(tgv_server* s, uint64_t ticket, int32_t* done);
+
+/* Copies a finished request's u (voxel order of its chunk, count = its
+ * active voxels) to u_out (host or device), waiting only for that request's
+ * work, and releases its arena space and ticket. */
+TGV_API tgv_status tgv_server_extract(tgv_server* s, uint64_t ticket, float* u_out, int64_t count);
+
+/* Free active-brick capacity, running requests, voxel-updates queued so far. */
+TGV_API int64_t tgv_server_free_bricks(const tgv_server* s);
+TGV_API int64_t tgv_server_running(const tgv_server* s);
+TGV_API int64_t tgv_server_voxel_updates(const tgv_server* s);
+
+/* Waits for all queued work of the server. */
+TGV_API tgv_status tgv_server_synchronize(tgv_server* s);
+
+TGV_API void tgv_server_destroy(tgv_server* s);
 
 TGV_API const char* tgv_status_string(tgv_status s);
 TGV_API const char* tgv_last_error(const tgv_domain* d);

@@ -6,6 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <unordered_map>
 
 #include "tgv_internal.cuh"
@@ -38,6 +41,28 @@ tgv_status tgv_check_device_error(tgv_domain* d)
         d->last_error = "a bounded device-side wait gave up (pipelined iteration kernel)";
         return TGV_ERR_TIMEOUT;
     }
+    return TGV_OK;
+}
+
+tgv_status tgv_kernel_setup(const void* kernel, int threads, size_t smem, int* per_sm)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TGV_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kernel, dev, threads, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return TGV_OK;
+    }
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return TGV_ERR_CUDA;
+    }
+    cache[key] = *per_sm;
     return TGV_OK;
 }
 
@@ -257,10 +282,17 @@ tgv_status dalloc(tgv_domain* d, void** p, size_t bytes)
     return TGV_OK;
 }
 
+void free_graphs(TgvLevel& L)
+{
+    for (auto& g : L.graphs) cudaGraphExecDestroy(g.exec);
+    L.graphs.clear();
+}
+
 void free_level(TgvLevel& L)
 {
+    free_graphs(L);
     void* ptrs[] = {L.u, L.ubar[0], L.ubar[1], L.v, L.vbar[0], L.vbar[1], L.p[0], L.p[1],
-                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev};
+                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev, L.work};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -292,6 +324,47 @@ void f32_to_storage(tgv_domain* d, const float* src, void* dst, int64_t n)
     case TGV_STORAGE_BF16: launch_f32_to_s<__nv_bfloat16>(d, src, dst, n); break;
     default: launch_f32_to_s<__half>(d, src, dst, n); break;
     }
+}
+
+// Allocates and zeroes every array of a level with nb active and nf frozen
+// bricks (neighbour table: all "none"; coordinates: zero).
+tgv_status alloc_level(tgv_domain* d, TgvLevel& L, int64_t nb, int64_t nf)
+{
+    L.nb = nb;
+    L.nf = nf;
+    const int64_t na = nb + nf;
+    const size_t sb = storage_bytes(d->prm.storage);
+    const int npairs = (d->prm.nbins + 1) / 2;
+    const size_t va = (size_t)na * TGV_BVOX, vn = (size_t)nb * TGV_BVOX;
+    tgv_status st = TGV_OK;
+    void** fl[] = {(void**)&L.u, (void**)&L.ubar[0], (void**)&L.ubar[1]};
+    for (void** p : fl)
+        if ((st = dalloc(d, p, va * 4)) != TGV_OK) return st;
+    void** vl[] = {&L.v, &L.vbar[0], &L.vbar[1]};
+    for (void** p : vl)
+        if ((st = dalloc(d, p, 3 * va * sb)) != TGV_OK) return st;
+    for (int k = 0; k < 2; ++k) {
+        if ((st = dalloc(d, &L.p[k], 3 * vn * sb)) != TGV_OK) return st;
+        if ((st = dalloc(d, &L.q[k], 6 * vn * sb)) != TGV_OK) return st;
+    }
+    if ((st = dalloc(d, (void**)&L.hist, (size_t)npairs * vn * 4)) != TGV_OK) return st;
+    if ((st = dalloc(d, (void**)&L.nbr, (size_t)nb * TGV_NNBR * 4)) != TGV_OK) return st;
+    if ((st = dalloc(d, (void**)&L.coords_dev, (size_t)na * 3 * 4)) != TGV_OK) return st;
+    cudaStream_t s = d->stream;
+    cudaError_t e = cudaMemsetAsync(L.u, 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[0], 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[1], 0, va * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.v, 0, 3 * va * sb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[0], 0, 3 * va * sb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[1], 0, 3 * va * sb, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(L.p[k], 0, 3 * vn * sb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.q[k], 0, 6 * vn * sb, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.hist, 0, (size_t)npairs * vn * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.nbr, 0xff, (size_t)nb * TGV_NNBR * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.coords_dev, 0, (size_t)na * 3 * 4, s);
+    return tgv_cuda_check(d, e, "level allocation");
 }
 
 tgv_status build_level(tgv_domain* d, const tgv_level_desc& desc, TgvLevel& L)
@@ -328,37 +401,12 @@ tgv_status build_level(tgv_domain* d, const tgv_level_desc& desc, TgvLevel& L)
             nbr[(size_t)i * TGV_NNBR + s] = it == index.end() ? -1 : it->second;
         }
     const size_t sb = storage_bytes(d->prm.storage);
-    const int npairs = (d->prm.nbins + 1) / 2;
-    const size_t va = (size_t)na * TGV_BVOX, vn = (size_t)nb * TGV_BVOX;
-    tgv_status st = TGV_OK;
-    void** fl[] = {(void**)&L.u, (void**)&L.ubar[0], (void**)&L.ubar[1]};
-    for (void** p : fl)
-        if ((st = dalloc(d, p, va * 4)) != TGV_OK) return st;
-    void** vl[] = {&L.v, &L.vbar[0], &L.vbar[1]};
-    for (void** p : vl)
-        if ((st = dalloc(d, p, 3 * va * sb)) != TGV_OK) return st;
-    for (int k = 0; k < 2; ++k) {
-        if ((st = dalloc(d, &L.p[k], 3 * vn * sb)) != TGV_OK) return st;
-        if ((st = dalloc(d, &L.q[k], 6 * vn * sb)) != TGV_OK) return st;
-    }
-    if ((st = dalloc(d, (void**)&L.hist, (size_t)npairs * vn * 4)) != TGV_OK) return st;
-    if ((st = dalloc(d, (void**)&L.nbr, nbr.size() * 4)) != TGV_OK) return st;
-    if ((st = dalloc(d, (void**)&L.coords_dev, L.coords.size() * 4)) != TGV_OK) return st;
+    const size_t vn = (size_t)nb * TGV_BVOX;
+    tgv_status st = alloc_level(d, L, nb, nf);
+    if (st != TGV_OK) return st;
     cudaStream_t s = d->stream;
     cudaError_t e = cudaSuccess;
-    e = cudaMemsetAsync(L.u, 0, va * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[0], 0, va * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.ubar[1], 0, va * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.v, 0, 3 * va * sb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[0], 0, 3 * va * sb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.vbar[1], 0, 3 * va * sb, s);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMemsetAsync(L.p[k], 0, 3 * vn * sb, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(L.q[k], 0, 6 * vn * sb, s);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.hist, 0, (size_t)npairs * vn * 4, s);
-    if (e == cudaSuccess && !nbr.empty())
-        e = cudaMemcpyAsync(L.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, s);
+    if (!nbr.empty()) e = cudaMemcpyAsync(L.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !L.coords.empty())
         e = cudaMemcpyAsync(L.coords_dev, L.coords.data(), L.coords.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are about to go away
@@ -385,6 +433,42 @@ tgv_status build_level(tgv_domain* d, const tgv_level_desc& desc, TgvLevel& L)
 }
 
 }  // namespace
+
+// ---- helpers used by the serving engine (tgv_server.cu)
+tgv_status tgv_create_arena(const tgv_params* prm, cudaStream_t stream, int64_t cap_active, int64_t cap_frozen,
+                            tgv_domain** out)
+{
+    *out = nullptr;
+    tgv_domain* d = new (std::nothrow) tgv_domain();
+    if (!d) return TGV_ERR_OUT_OF_MEMORY;
+    d->prm = *prm;
+    d->stream = stream;
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device);
+    tgv_status st = tgv_cuda_check(d, e, "device query");
+    if (st == TGV_OK) st = dalloc(d, (void**)&d->red_out, 4 * sizeof(double));
+    if (st == TGV_OK) st = dalloc(d, (void**)&d->err, sizeof(int));
+    if (st == TGV_OK) st = tgv_cuda_check(d, cudaMemsetAsync(d->err, 0, sizeof(int), d->stream), "error flag");
+    d->levels.resize(1);
+    if (st == TGV_OK) st = alloc_level(d, d->levels[0], cap_active, cap_frozen);
+    if (st == TGV_OK) st = tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "arena initialisation");
+    if (st != TGV_OK) {
+        tgv_destroy_domain(d);
+        return st;
+    }
+    *out = d;
+    return TGV_OK;
+}
+
+void tgv_launch_f32_to_storage(tgv_domain* d, const float* src, void* dst, int64_t n) { f32_to_storage(d, src, dst, n); }
+
+void tgv_launch_hist_pack(tgv_domain* d, uint32_t* dst, const uint32_t* src, int64_t nvox, unsigned int* maxc)
+{
+    const int npairs = (d->prm.nbins + 1) / 2;
+    hist_pack_kernel<<<grid1(nvox * npairs, 256, d->sm_count), 256, 0, d->stream>>>(dst, src, nvox, d->prm.nbins,
+                                                                                  npairs, maxc);
+    d->launches++;
+}
 
 // ========================================================================= C-ABI
 extern "C" {
@@ -750,6 +834,103 @@ tgv_status tgv_prolong(tgv_domain* d, int32_t from_level)
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);  // `parent` is a host temporary
     return tgv_cuda_check(d, e, "prolong");
+}
+
+tgv_status tgv_set_work_list(tgv_domain* d, int32_t level, const int32_t* bricks, int64_t n)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    if (!bricks || n < 0) {  // back to every active brick
+        L->work_gen++;
+        if (L->work) {
+            cudaError_t e = cudaStreamSynchronize(d->stream);  // queued launches may read the old list
+            if (e != cudaSuccess) return tgv_cuda_check(d, e, "work list sync");
+            cudaFree(L->work);
+            d->bytes -= L->work_cap * 4;
+        }
+        L->work = nullptr;
+        L->nwork = L->work_cap = 0;
+        return TGV_OK;
+    }
+    std::vector<int32_t> host((size_t)n);
+    cudaError_t e = cudaMemcpy(host.data(), bricks, (size_t)n * 4, cudaMemcpyDefault);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "work list read");
+    std::vector<uint8_t> seen((size_t)L->nb, 0);
+    for (int32_t b : host) {
+        if (b < 0 || b >= L->nb) return tgv_fail(d, TGV_ERR_INVALID_ARG, "work list entry is not an active brick");
+        if (seen[(size_t)b]++) return tgv_fail(d, TGV_ERR_INVALID_ARG, "work list repeats a brick");
+    }
+    if (n > L->work_cap) {
+        e = cudaStreamSynchronize(d->stream);
+        if (e != cudaSuccess) return tgv_cuda_check(d, e, "work list sync");
+        if (L->work) {
+            cudaFree(L->work);
+            d->bytes -= L->work_cap * 4;
+            L->work = nullptr;
+            L->work_cap = 0;
+        }
+        if ((st = dalloc(d, (void**)&L->work, (size_t)std::max<int64_t>(n, 1) * 4)) != TGV_OK) return st;
+        L->work_cap = std::max<int64_t>(n, 1);
+    }
+    e = cudaMemcpyAsync(L->work, host.data(), (size_t)n * 4, cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);  // `host` is a temporary
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "work list upload");
+    L->nwork = n;
+    L->work_gen++;
+    return TGV_OK;
+}
+
+tgv_status tgv_solve_graph(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    if (iterations < 0) return tgv_fail(d, TGV_ERR_INVALID_ARG, "iterations must be >= 0");
+    if (!d->stream) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "graph capture needs a non-default stream");
+    if (iterations > 0 && tgv_work_items(*L) > 0) {
+        const int parity = L->cur;
+        TgvLevel::Graph* hit = nullptr;
+        for (auto& gr : L->graphs)
+            if (gr.iters == iterations && gr.parity == parity && gr.gen == L->work_gen) hit = &gr;
+        if (hit) {
+            cudaError_t e = cudaGraphLaunch(hit->exec, d->stream);
+            if (e != cudaSuccess) return tgv_cuda_check(d, e, "graph launch");
+            d->launches += iterations;
+            L->cur ^= iterations & 1;
+        } else {
+            // This call runs its iterations with plain launches (which also caches every
+            // kernel's launch attributes); a graph of the same launches is captured for
+            // the next call with the same count, starting parity and work list.
+            if ((st = tgv_launch_iterations(d, *L, iterations)) != TGV_OK) return st;
+            const int after = L->cur;
+            const int64_t launches = d->launches;
+            L->cur = parity;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                L->cur = after;
+                return tgv_cuda_check(d, e, "begin capture");
+            }
+            st = tgv_launch_iterations(d, *L, iterations);
+            e = cudaStreamEndCapture(d->stream, &graph);
+            L->cur = after;  // capture recorded the launches without running them
+            d->launches = launches;
+            if (st != TGV_OK) return st;
+            if (e != cudaSuccess) return tgv_cuda_check(d, e, "end capture");
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return tgv_cuda_check(d, e, "graph instantiate");
+            L->graphs.push_back({iterations, parity, L->work_gen, exec});
+        }
+    }
+    if (energy_gap_out) return tgv_launch_energy(d, *L, energy_gap_out);
+    return TGV_OK;
 }
 
 tgv_status tgv_synchronize(tgv_domain* d)

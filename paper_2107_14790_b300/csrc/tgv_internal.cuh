@@ -76,6 +76,16 @@ struct TgvLevel {
     uint32_t* hist = nullptr;
     int32_t* nbr = nullptr;
     int32_t* coords_dev = nullptr;  // 3*(nb+nf) brick coordinates
+    int32_t* work = nullptr;   // optional list of active bricks to update (device); nullptr = all
+    int64_t nwork = 0;
+    int64_t work_cap = 0;
+    uint64_t work_gen = 0;     // bumped whenever the work list changes (invalidates cached graphs)
+    struct Graph {
+        int iters, parity;
+        uint64_t gen;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
     int cur = 0;               // ping-pong copy holding the current ubar/vbar/p/q
     uint64_t max_votes = 0;    // upper bound on any voxel's total count
 };
@@ -95,7 +105,9 @@ struct IterArgs {
     S* q_out;
     const uint32_t* hist;
     const int32_t* nbr;
-    int64_t nb;    // active bricks
+    const int32_t* work;  // work item -> active brick (nullptr: item i is brick i)
+    int64_t nitems;       // work items of this launch
+    int64_t nb;    // active bricks (indices >= nb are frozen)
     int64_t nall;  // active + frozen bricks (stride of the in-place fields' brick index)
     int nbins, npairs, clamp_u;
     float alpha1, alpha0, tau, sigma, taulam;
@@ -125,11 +137,19 @@ struct tgv_domain {
     int* err = nullptr;          // device flag: 1 after a bounded device-side wait gave up
 };
 
+// Sets the kernel's dynamic shared memory limit and returns its CTAs per SM
+// (cached per kernel, block size and shared memory size; safe to call while a
+// stream is being captured once the first call has happened outside capture).
+tgv_status tgv_kernel_setup(const void* kernel, int threads, size_t smem, int* per_sm);
+
 // helpers implemented in tgv_domain.cu
 tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg);
 tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what);
 tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes);
 void tgv_bin_centres(const tgv_params& prm, float* c);
+
+// Number of bricks one iteration updates.
+inline int64_t tgv_work_items(const TgvLevel& L) { return L.work ? L.nwork : L.nb; }
 
 // Iteration arguments for the current ping-pong copy of a level.
 template <typename S>
@@ -149,6 +169,8 @@ inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
     A.q_out = (S*)L.q[o];
     A.hist = L.hist;
     A.nbr = L.nbr;
+    A.work = L.work;
+    A.nitems = L.work ? L.nwork : L.nb;
     A.nb = L.nb;
     A.nall = L.nb + L.nf;
     A.nbins = d->prm.nbins;
@@ -162,6 +184,12 @@ inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
     tgv_bin_centres(d->prm, A.c);
     return A;
 }
+
+// serving-engine helpers implemented in tgv_domain.cu
+tgv_status tgv_create_arena(const tgv_params* prm, cudaStream_t stream, int64_t cap_active, int64_t cap_frozen,
+                            tgv_domain** out);
+void tgv_launch_f32_to_storage(tgv_domain* d, const float* src, void* dst, int64_t n);
+void tgv_launch_hist_pack(tgv_domain* d, uint32_t* dst, const uint32_t* src, int64_t nvox, unsigned int* maxc);
 
 // launchers implemented in tgv_solve.cu / tgv_iter_pipe.cu / tgv_hist.cu
 tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters);

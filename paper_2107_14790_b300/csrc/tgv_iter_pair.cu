@@ -16,9 +16,8 @@
 // the x faces, pairs on the y and z faces), and their inputs are loaded into
 // registers before the CTA waits for its stage.
 //
-// Element offsets are 32-bit (selected only when every array of the level
-// has fewer than 2^32 elements); the bin count is a template parameter for 8,
-// 10 and 12 bins (0 = read at run time).  Every mbarrier wait is bounded
+// The bin count is a template parameter for 8, 10 and 12 bins (0 = read at
+// run time).  Every mbarrier wait is bounded
 // (about a second); a CTA that gives up sets the domain's error flag, waits
 // (bounded) for its copies in flight and returns.
 #include <math.h>
@@ -269,13 +268,13 @@ struct PairCta {
         unsigned char* st = stage(s);
         uint64_t* b = bar() + s;
         mbar_arrive_expect_tx(b, P.tx_bytes);
-        bulk_copy_g2s(st + O_U, A.u + brick * TGV_BVOX, 2048, b);
-        bulk_copy_g2s(st + O_UB, A.ubar_in + brick * TGV_BVOX, 2048, b);
-        bulk_copy_g2s(st + O_V, A.v + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_VB, A.vbar_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_P, A.p_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_Q, A.q_in + brick * 6 * TGV_BVOX, 6 * 512 * SB, b);
-        bulk_copy_g2s(st + O_H, A.hist + brick * (uint32_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, b);
+        bulk_copy_g2s(st + O_U, A.u + (size_t)brick * TGV_BVOX, 2048, b);
+        bulk_copy_g2s(st + O_UB, A.ubar_in + (size_t)brick * TGV_BVOX, 2048, b);
+        bulk_copy_g2s(st + O_V, A.v + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_VB, A.vbar_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SB, b);
+        bulk_copy_g2s(st + O_H, A.hist + brick * (size_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, b);
     }
 
     // ---- global loads a brick's phase A needs besides its stage (own boundary neighbours, halo inputs)
@@ -290,20 +289,20 @@ struct PairCta {
             vbb_x[c] = 0.0f;
             vbb_y[c] = vbb_z[c] = make_float2(0, 0);
         }
-        if (j == 3 && n_px >= 0) ubf_x = A.ubar_in[(uint32_t)n_px * TGV_BVOX + l0 + 1 - 7];
-        if (y == 7 && n_py >= 0) ubf_y = ldf2(A.ubar_in + (uint32_t)n_py * TGV_BVOX + l0 - 56);
-        if (z == 7 && n_pz >= 0) ubf_z = ldf2(A.ubar_in + (uint32_t)n_pz * TGV_BVOX + l0 - 448);
+        if (j == 3 && n_px >= 0) ubf_x = A.ubar_in[(size_t)n_px * TGV_BVOX + l0 + 1 - 7];
+        if (y == 7 && n_py >= 0) ubf_y = ldf2(A.ubar_in + (size_t)n_py * TGV_BVOX + l0 - 56);
+        if (z == 7 && n_pz >= 0) ubf_z = ldf2(A.ubar_in + (size_t)n_pz * TGV_BVOX + l0 - 448);
         if (j == 0 && n_mx >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_x[c] = ld_s(A.vbar_in + ((uint32_t)n_mx * 3 + c) * TGV_BVOX + l0 + 7);
+            for (int c = 0; c < 3; ++c) vbb_x[c] = ld_s(A.vbar_in + ((size_t)n_mx * 3 + c) * TGV_BVOX + l0 + 7);
         }
         if (y == 0 && n_my >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_y[c] = PS::ld(A.vbar_in + ((uint32_t)n_my * 3 + c) * TGV_BVOX + l0 + 56);
+            for (int c = 0; c < 3; ++c) vbb_y[c] = PS::ld(A.vbar_in + ((size_t)n_my * 3 + c) * TGV_BVOX + l0 + 56);
         }
         if (z == 0 && n_mz >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(A.vbar_in + ((uint32_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
+            for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(A.vbar_in + ((size_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
         }
         // halo inputs.  p tasks: h[0..1] ubar(h0,h1), h[2..3] forward along the first face
         // axis, h[4..5] along the second, h[6..11] vbar (3 x pair), h[12..17] p (3 x pair).
@@ -316,7 +315,7 @@ struct PairCta {
             if (hn >= nbk) hn = -1;  // frozen: no dual variables there
         }
         if (hn < 0) return;
-        const uint32_t nb0 = (uint32_t)hn * TGV_BVOX;
+        const uint32_t nb0 = (size_t)hn * TGV_BVOX;
         if (task == 0) {  // -x face single: (7, hy, hz)
             const int hy = tk & 7, hz = tk >> 3;
             const uint32_t lh = 7 + 8 * hy + 64 * hz;
@@ -325,20 +324,20 @@ struct PairCta {
                 h[2] = A.ubar_in[nb0 + lh + 8];
                 hm |= 1u;
             } else if (nrow[NB_MX_PY] >= 0) {
-                h[2] = A.ubar_in[(uint32_t)nrow[NB_MX_PY] * TGV_BVOX + lh - 56];
+                h[2] = A.ubar_in[(size_t)nrow[NB_MX_PY] * TGV_BVOX + lh - 56];
                 hm |= 1u;
             }
             if (hz < 7) {
                 h[4] = A.ubar_in[nb0 + lh + 64];
                 hm |= 2u;
             } else if (nrow[NB_MX_PZ] >= 0) {
-                h[4] = A.ubar_in[(uint32_t)nrow[NB_MX_PZ] * TGV_BVOX + lh - 448];
+                h[4] = A.ubar_in[(size_t)nrow[NB_MX_PZ] * TGV_BVOX + lh - 448];
                 hm |= 2u;
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
-                h[12 + 2 * c] = ld_s(A.p_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[12 + 2 * c] = ld_s(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
             }
         } else if (task == 1 || task == 2) {  // -y / -z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 1) or y (task 2)
@@ -352,7 +351,7 @@ struct PairCta {
             } else {
                 const int e = nrow[task == 1 ? NB_MY_PX : NB_MZ_PX];
                 if (e >= 0) {
-                    h[2] = A.ubar_in[(uint32_t)e * TGV_BVOX + lh + 1 - 7];
+                    h[2] = A.ubar_in[(size_t)e * TGV_BVOX + lh + 1 - 7];
                     hm |= 1u;
                 }
             }
@@ -365,7 +364,7 @@ struct PairCta {
             } else {
                 const int e = nrow[task == 1 ? NB_MY_PZ : NB_MZ_PY];
                 if (e >= 0) {
-                    u2 = ldf2(A.ubar_in + (uint32_t)e * TGV_BVOX + lh - 7 * ostr);
+                    u2 = ldf2(A.ubar_in + (size_t)e * TGV_BVOX + lh - 7 * ostr);
                     h[4] = u2.x;
                     h[5] = u2.y;
                     hm |= 2u;
@@ -373,10 +372,10 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
                 h[6 + 2 * c] = w.x;
                 h[7 + 2 * c] = w.y;
-                w = PS::ld(A.p_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                w = PS::ld(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
                 h[12 + 2 * c] = w.x;
                 h[13 + 2 * c] = w.y;
             }
@@ -384,47 +383,47 @@ struct PairCta {
             const int hy = tk & 7, hz = tk >> 3;
             const uint32_t lh = 8 * hy + 64 * hz;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+            for (int c = 0; c < 3; ++c) h[2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
             if (hy > 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 8);
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 8);
                 hm |= 1u;
             } else if (nrow[NB_MY_PX] >= 0) {
-                const uint32_t e = (uint32_t)nrow[NB_MY_PX];
+                const size_t e = (size_t)nrow[NB_MY_PX];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 56);
                 hm |= 1u;
             }
             if (hz > 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 64);
+                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 64);
                 hm |= 2u;
             } else if (nrow[NB_MZ_PX] >= 0) {
-                const uint32_t e = (uint32_t)nrow[NB_MZ_PX];
+                const size_t e = (size_t)nrow[NB_MZ_PX];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 448);
                 hm |= 2u;
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_s(A.q_in + ((uint32_t)hn * 6 + c) * TGV_BVOX + lh);
+            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_s(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh);
         } else {  // task 4 / 5: +y / +z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 4) or y (task 5)
             const uint32_t lh = task == 4 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh);
+                const float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
                 h[2 * c] = w.x;
                 h[2 * c + 1] = w.y;
             }
             if (hj > 0) {  // backward along x of the pair's first voxel
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - 1);
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 1);
                 hm |= 1u;
             } else {
                 const int e = nrow[task == 4 ? NB_MX_PY : NB_MX_PZ];
                 if (e >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7);
+                    for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7);
                     hm |= 1u;
                 }
             }
@@ -432,7 +431,7 @@ struct PairCta {
             if (hw > 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 w = PS::ld(A.vbar_in + ((uint32_t)hn * 3 + c) * TGV_BVOX + lh - ostr);
+                    const float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - ostr);
                     h[12 + 2 * c] = w.x;
                     h[13 + 2 * c] = w.y;
                 }
@@ -442,7 +441,7 @@ struct PairCta {
                 if (e >= 0) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float2 w = PS::ld(A.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7 * ostr);
+                        const float2 w = PS::ld(A.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7 * ostr);
                         h[12 + 2 * c] = w.x;
                         h[13 + 2 * c] = w.y;
                     }
@@ -451,7 +450,7 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const float2 w = PS::ld(A.q_in + ((uint32_t)hn * 6 + c) * TGV_BVOX + lh);
+                const float2 w = PS::ld(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh);
                 h[18 + 2 * c] = w.x;
                 h[19 + 2 * c] = w.y;
             }
@@ -691,12 +690,12 @@ struct PairCta {
             una = fminf(1.0f, fmaxf(-1.0f, una));
             unb = fminf(1.0f, fmaxf(-1.0f, unb));
         }
-        const uint32_t vi = b * TGV_BVOX + l0;
+        const size_t vi = (size_t)b * TGV_BVOX + l0;
         stf2(A.u + vi, make_float2(una, unb));
         stf2(A.ubar_out + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const uint32_t oi = (b * 3 + c) * TGV_BVOX + l0;
+            const size_t oi = ((size_t)b * 3 + c) * TGV_BVOX + l0;
             const float2 v0 = PS::ld(sv + c * 512 + l0);
             const float2 v1 = make_float2(v0.x + A.tau * (pn0[c] + d2a[c]), v0.y + A.tau * (pn1[c] + d2b[c]));
             PS::st(A.v + oi, v1);
@@ -704,7 +703,7 @@ struct PairCta {
             PS::st(A.p_out + oi, make_float2(pn0[c], pn1[c]));
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) PS::st(A.q_out + (b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
+        for (int c = 0; c < 6; ++c) PS::st(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
     }
 };
 
@@ -717,8 +716,10 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
     extern __shared__ __align__(128) unsigned char smem[];
     PairCta<S, NB> C(P, smem);
     const uint32_t G = gridDim.x;
-    const uint32_t nb = (uint32_t)C.nbk;
-    uint32_t b = blockIdx.x;
+    const uint32_t nit = (uint32_t)P.it.nitems;
+    const int32_t* work = P.it.work;
+    auto brick = [&](uint32_t i) -> uint32_t { return work ? (uint32_t)work[i] : i; };
+    uint32_t it = blockIdx.x;  // work item in hand
     uint64_t* bar = C.bar();
     const int t = C.t;
 
@@ -728,13 +729,13 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
         fence_mbar_init();
     }
     if (t < TGV_NNBR) {
-        C.nbr_row(0)[t] = P.it.nbr[b * TGV_NNBR + t];
-        if (b + G < nb) C.nbr_row(1)[t] = P.it.nbr[(b + G) * TGV_NNBR + t];
+        C.nbr_row(0)[t] = P.it.nbr[brick(it) * TGV_NNBR + t];
+        if (it + G < nit) C.nbr_row(1)[t] = P.it.nbr[brick(it + G) * TGV_NNBR + t];
     }
     __syncthreads();
     if (t == 0) {
-        C.issue(0, b);
-        if (b + G < nb) C.issue(1, b + G);
+        C.issue(0, brick(it));
+        if (it + G < nit) C.issue(1, brick(it + G));
     }
     uint32_t parity = 0;
     bool bail = false;
@@ -752,31 +753,31 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
         __syncthreads();
     }
     while (!bail) {
-        const uint32_t bn = b + G;
+        const uint32_t itn = it + G;
         const int ns = s ^ 1;
         uint32_t next_links = 0;
-        if (bn < nb) C.load_inputs(C.nbr_row(ns));
-        // the row of brick b is no longer read: reuse it for brick bn + G
-        if (t < TGV_NNBR && bn + G < nb) C.nbr_row(s)[t] = P.it.nbr[(bn + G) * TGV_NNBR + t];
-        C.phase_b(s, b, links);
-        if (bn < nb) {
+        if (itn < nit) C.load_inputs(C.nbr_row(ns));
+        // the row of the brick in hand is no longer read: reuse it for item itn + G
+        if (t < TGV_NNBR && itn + G < nit) C.nbr_row(s)[t] = P.it.nbr[brick(itn + G) * TGV_NNBR + t];
+        C.phase_b(s, brick(it), links);
+        if (itn < nit) {
             const bool ok = mbar_wait_bounded(&bar[ns], (parity >> ns) & 1u, P.wait_budget);
             if (__syncthreads_or(!ok)) {
                 bail = true;
-                b = bn;
+                it = itn;
                 s = ns;
                 break;
             }
             parity ^= 1u << ns;
             next_links = C.phase_a(ns, C.nbr_row(ns));
         }
-        __syncthreads();  // stage s and the phase A results of bn are settled
-        if (t == 0 && b + 2 * G < nb) {
+        __syncthreads();  // stage s and the phase A results of item itn are settled
+        if (t == 0 && it + 2 * G < nit) {
             fence_proxy_async_smem();
-            C.issue(s, b + 2 * G);
+            C.issue(s, brick(it + 2 * G));
         }
-        if (bn >= nb) break;
-        b = bn;
+        if (itn >= nit) break;
+        it = itn;
         s = ns;
         links = next_links;
     }
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
         atomicExch(P.err, 1);
         // the stage being waited for (and, in the prologue, the second one) may still receive data
         mbar_wait_bounded(&bar[s], (parity >> s) & 1u, P.wait_budget);
-        if (b + G < nb) mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, P.wait_budget);
+        if (it + G < nit) mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, P.wait_budget);
     }
 }
 
@@ -811,14 +812,12 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     off += 2 * 8;
     const size_t smem = off;
     auto kern = tgv_iter_pair_kernel<S, NB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pair kernel smem attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pair kernel occupancy");
-    if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "paired iteration kernel does not fit on an SM");
+    tgv_status st = tgv_kernel_setup((const void*)kern, kThreads, smem, &per_sm);
+    if (st != TGV_OK) return tgv_fail(d, st, "pair kernel setup (shared memory attribute / occupancy) failed");
+    if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "pair iteration kernel does not fit on an SM");
     int64_t grid = (int64_t)per_sm * d->sm_count;
-    if (grid > L.nb) grid = L.nb;
+    if (grid > tgv_work_items(L)) grid = tgv_work_items(L);
     P.err = d->err;
     P.wait_budget = 2000000000LL;  // about one second at 2 GHz
     P.stage_bytes = stage;
@@ -847,7 +846,7 @@ tgv_status launch_pair_bins(tgv_domain* d, TgvLevel& L, int iters)
 
 tgv_status tgv_launch_iterations_pair(tgv_domain* d, TgvLevel& L, int iters)
 {
-    if (L.nb == 0 || iters == 0) return TGV_OK;
+    if (tgv_work_items(L) == 0 || iters == 0) return TGV_OK;
     switch (d->prm.storage) {
     case TGV_STORAGE_FP32: return launch_pair_bins<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_pair_bins<__nv_bfloat16>(d, L, iters);

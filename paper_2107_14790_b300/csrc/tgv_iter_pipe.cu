@@ -10,9 +10,8 @@
 // and one edge line of ubar / vbar) are loaded into registers before the CTA
 // waits for its stage, so their latency overlaps the stage's.
 //
-// Element offsets are 32-bit (the launcher only selects this kernel when every
-// array of the level has fewer than 2^32 elements); the bin count is a
-// template parameter for the common 8, 10 and 12 bins (0 = read at run time).
+// The bin count is a template parameter for the common 8, 10 and 12 bins
+// (0 = read at run time).
 //
 // Every mbarrier wait is bounded (about a second); a CTA that gives up sets
 // the domain's error flag, waits (bounded) for its copies still in flight and
@@ -47,7 +46,7 @@ __device__ __forceinline__ void halo_p_load(const IterArgs<S>& P, const int* nro
     constexpr int B1 = FaceAxes<A>::B1, B2 = FaceAxes<A>::B2;
     const int c1 = k & 7, c2 = k >> 3;
     const uint32_t lh = 7 * kStride(A) + c1 * kStride(B1) + c2 * kStride(B2);
-    const uint32_t nb0 = n * TGV_BVOX;
+    const size_t nb0 = (size_t)n * TGV_BVOX;
     hr[0] = P.ubar_in[nb0 + lh];
     if (c1 < 7) {
         hr[1] = P.ubar_in[nb0 + lh + kStride(B1)];
@@ -55,7 +54,7 @@ __device__ __forceinline__ void halo_p_load(const IterArgs<S>& P, const int* nro
     } else {
         const int e = nrow[nb_edge(A, B1)];
         if (e >= 0) {
-            hr[1] = P.ubar_in[(uint32_t)e * TGV_BVOX + lh - 7 * kStride(B1)];
+            hr[1] = P.ubar_in[(size_t)e * TGV_BVOX + lh - 7 * kStride(B1)];
             hmask |= 1u;
         }
     }
@@ -65,14 +64,14 @@ __device__ __forceinline__ void halo_p_load(const IterArgs<S>& P, const int* nro
     } else {
         const int e = nrow[nb_edge(A, B2)];
         if (e >= 0) {
-            hr[2] = P.ubar_in[(uint32_t)e * TGV_BVOX + lh - 7 * kStride(B2)];
+            hr[2] = P.ubar_in[(size_t)e * TGV_BVOX + lh - 7 * kStride(B2)];
             hmask |= 2u;
         }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        hr[3 + c] = ld_s(P.vbar_in + (n * 3 + c) * TGV_BVOX + lh);
-        hr[6 + c] = ld_s(P.p_in + (n * 3 + c) * TGV_BVOX + lh);
+        hr[3 + c] = ld_s(P.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + lh);
+        hr[6 + c] = ld_s(P.p_in + ((size_t)n * 3 + c) * TGV_BVOX + lh);
     }
 }
 
@@ -110,35 +109,35 @@ __device__ __forceinline__ void halo_q_load(const IterArgs<S>& P, const int* nro
     const int c1 = k & 7, c2 = k >> 3;
     const uint32_t lh = c1 * kStride(B1) + c2 * kStride(B2);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) hr[c] = ld_s(P.vbar_in + (n * 3 + c) * TGV_BVOX + lh);
+    for (int c = 0; c < 3; ++c) hr[c] = ld_s(P.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + lh);
     if (c1 > 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hr[3 + c] = ld_s(P.vbar_in + (n * 3 + c) * TGV_BVOX + lh - kStride(B1));
+        for (int c = 0; c < 3; ++c) hr[3 + c] = ld_s(P.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + lh - kStride(B1));
         hmask |= 1u;
     } else {
         const int e = nrow[nb_edge(B1, A)];  // offset +1 along A, -1 along B1
         if (e >= 0) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                hr[3 + c] = ld_s(P.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7 * kStride(B1));
+                hr[3 + c] = ld_s(P.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7 * kStride(B1));
             hmask |= 1u;
         }
     }
     if (c2 > 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hr[6 + c] = ld_s(P.vbar_in + (n * 3 + c) * TGV_BVOX + lh - kStride(B2));
+        for (int c = 0; c < 3; ++c) hr[6 + c] = ld_s(P.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + lh - kStride(B2));
         hmask |= 2u;
     } else {
         const int e = nrow[nb_edge(B2, A)];
         if (e >= 0) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                hr[6 + c] = ld_s(P.vbar_in + ((uint32_t)e * 3 + c) * TGV_BVOX + lh + 7 * kStride(B2));
+                hr[6 + c] = ld_s(P.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7 * kStride(B2));
             hmask |= 2u;
         }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) hr[9 + c] = ld_s(P.q_in + (n * 6 + c) * TGV_BVOX + lh);
+    for (int c = 0; c < 6; ++c) hr[9 + c] = ld_s(P.q_in + ((size_t)n * 6 + c) * TGV_BVOX + lh);
 }
 
 template <typename S, int A>
@@ -200,7 +199,10 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
     const int crd[3] = {x, y, z};
     const uint32_t G = gridDim.x;
     const uint32_t nbk = (uint32_t)A.nb;
-    uint32_t b = blockIdx.x;
+    const uint32_t nit = (uint32_t)A.nitems;
+    const int32_t* work = A.work;
+    auto brick = [&](uint32_t i) -> uint32_t { return work ? (uint32_t)work[i] : i; };
+    uint32_t it = blockIdx.x;
     uint64_t* bar = (uint64_t*)(smem + P.off_bar);
     int* s_nbr = (int*)(smem + P.off_nbr);
     float* hal_p = (float*)(smem + P.off_hp);
@@ -210,13 +212,13 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
     auto issue = [&](int s, uint32_t brick) {
         unsigned char* st = smem + (size_t)s * P.stage_bytes;
         mbar_arrive_expect_tx(&bar[s], P.tx_bytes);
-        bulk_copy_g2s(st + O_U, A.u + brick * TGV_BVOX, 2048, &bar[s]);
-        bulk_copy_g2s(st + O_UB, A.ubar_in + brick * TGV_BVOX, 2048, &bar[s]);
-        bulk_copy_g2s(st + O_V, A.v + brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_VB, A.vbar_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_P, A.p_in + brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_Q, A.q_in + brick * 6 * TGV_BVOX, 6 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_H, A.hist + brick * (uint32_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, &bar[s]);
+        bulk_copy_g2s(st + O_U, A.u + (size_t)brick * TGV_BVOX, 2048, &bar[s]);
+        bulk_copy_g2s(st + O_UB, A.ubar_in + (size_t)brick * TGV_BVOX, 2048, &bar[s]);
+        bulk_copy_g2s(st + O_V, A.v + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
+        bulk_copy_g2s(st + O_VB, A.vbar_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
+        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
+        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SB, &bar[s]);
+        bulk_copy_g2s(st + O_H, A.hist + brick * (size_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, &bar[s]);
     };
 
     if (t == 0) {
@@ -224,11 +226,11 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
+    if (t < TGV_NNBR) s_nbr[t] = A.nbr[brick(it) * TGV_NNBR + t];
     __syncthreads();
     if (t == 0) {
-        issue(0, b);
-        if (b + G < nbk) issue(1, b + G);
+        issue(0, brick(it));
+        if (it + G < nit) issue(1, brick(it + G));
     }
 
     uint32_t parity = 0;  // bit s: parity of the next phase of stage s
@@ -238,7 +240,8 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
     const bool ptask = t < 192, qtask = t >= 192 && t < 384;
     const int ha = ptask ? (t >> 6) : ((t - 192) >> 6);
     const int hk = t & 63;
-    for (; b < nbk; b += G, s ^= 1) {
+    for (; it < nit; it += G, s ^= 1) {
+        const uint32_t b = brick(it);
         unsigned char* st = smem + (size_t)s * P.stage_bytes;
         const int* nrow = s_nbr + s * TGV_NNBR;
 
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
             if (crd[a] == 7) {
                 const int n = nrow[nb_plus(a)];
                 if (n >= 0) {
-                    ubf[a] = A.ubar_in[(uint32_t)n * TGV_BVOX + t - 7 * kStride(a)];
+                    ubf[a] = A.ubar_in[(size_t)n * TGV_BVOX + t - 7 * kStride(a)];
                     fmask |= 1u << a;
                 }
             } else {
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
                 if (n >= 0) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        vbb[a][c] = ld_s(A.vbar_in + ((uint32_t)n * 3 + c) * TGV_BVOX + t + 7 * kStride(a));
+                        vbb[a][c] = ld_s(A.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + t + 7 * kStride(a));
                     bmask |= 1u << a;
                 }
             } else {
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
             }
         }
         // neighbour row of the next brick of this CTA (its previous user finished at the last barrier)
-        if (t < TGV_NNBR && b + G < nbk) s_nbr[(s ^ 1) * TGV_NNBR + t] = A.nbr[(b + G) * TGV_NNBR + t];
+        if (t < TGV_NNBR && it + G < nit) s_nbr[(s ^ 1) * TGV_NNBR + t] = A.nbr[brick(it + G) * TGV_NNBR + t];
 
         // ---- wait for this brick's stage
         const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, P.wait_budget);
@@ -421,12 +424,12 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         un = fmaxf(un, ut - A.taulam * W);
         if (A.clamp_u) un = fminf(1.0f, fmaxf(-1.0f, un));
 
-        const uint32_t vi = b * TGV_BVOX + t;
+        const size_t vi = (size_t)b * TGV_BVOX + t;
         A.u[vi] = un;
         A.ubar_out[vi] = 2.0f * un - u0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const uint32_t oi = (b * 3 + c) * TGV_BVOX + t;
+            const size_t oi = ((size_t)b * 3 + c) * TGV_BVOX + t;
             const float v0 = ld_s(sv + c * 512 + t);
             const float v1 = v0 + A.tau * (pn[c] + div2[c]);
             st_s(A.v + oi, v1);
@@ -434,20 +437,20 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
             st_s(A.p_out + oi, pn[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) st_s(A.q_out + (b * 6 + c) * TGV_BVOX + t, qn[c]);
+        for (int c = 0; c < 6; ++c) st_s(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + t, qn[c]);
 
         // ---- every thread is done with stage s: refill it with brick b + 2G
         __syncthreads();
-        if (t == 0 && b + 2 * G < nbk) {
+        if (t == 0 && it + 2 * G < nit) {
             fence_proxy_async_smem();
-            issue(s, b + 2 * G);
+            issue(s, brick(it + 2 * G));
         }
     }
     if (bail && t == 0) {
         atomicExch(P.err, 1);
         // copies may still be landing in either stage: wait for them (bounded) before leaving
         for (int k = 0; k < 2; ++k) {
-            if (b + k * G < nbk) mbar_wait_bounded(&bar[s ^ k], (parity >> (s ^ k)) & 1u, P.wait_budget);
+            if (it + k * G < nit) mbar_wait_bounded(&bar[s ^ k], (parity >> (s ^ k)) & 1u, P.wait_budget);
         }
     }
 }
@@ -482,14 +485,12 @@ tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
     off += 2 * 8;
     const size_t smem = off;
     auto kern = tgv_iter_pipe_kernel<S, NB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pipe kernel smem attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TGV_BVOX, smem);
-    if (e != cudaSuccess) return tgv_cuda_check(d, e, "pipe kernel occupancy");
-    if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "pipelined iteration kernel does not fit on an SM");
+    tgv_status st = tgv_kernel_setup((const void*)kern, TGV_BVOX, smem, &per_sm);
+    if (st != TGV_OK) return tgv_fail(d, st, "pipe kernel setup (shared memory attribute / occupancy) failed");
+    if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "pipe iteration kernel does not fit on an SM");
     int64_t grid = (int64_t)per_sm * d->sm_count;
-    if (grid > L.nb) grid = L.nb;
+    if (grid > tgv_work_items(L)) grid = tgv_work_items(L);
     P.err = d->err;
     P.wait_budget = 2000000000LL;  // about one second at 2 GHz
     P.stage_bytes = stage;
@@ -516,12 +517,12 @@ tgv_status launch_pipe_bins(tgv_domain* d, TgvLevel& L, int iters)
 
 }  // namespace
 
-// True when every array of the level can be indexed with 32-bit element offsets.
-bool tgv_pipe_supports(const TgvLevel& L) { return (L.nb + L.nf) * (int64_t)8 * TGV_BVOX < ((int64_t)1 << 32); }
+// The pipelined kernels index with 64-bit offsets: every level qualifies.
+bool tgv_pipe_supports(const TgvLevel& L) { return L.nb + L.nf < ((int64_t)1 << 31); }
 
 tgv_status tgv_launch_iterations_pipe(tgv_domain* d, TgvLevel& L, int iters)
 {
-    if (L.nb == 0 || iters == 0) return TGV_OK;
+    if (tgv_work_items(L) == 0 || iters == 0) return TGV_OK;
     switch (d->prm.storage) {
     case TGV_STORAGE_FP32: return launch_pipe_bins<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_pipe_bins<__nv_bfloat16>(d, L, iters);

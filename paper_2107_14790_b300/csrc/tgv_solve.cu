@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
     __shared__ float s_q[6][TGV_BVOX + 192];
     __shared__ int s_nbr[TGV_NNBR];
 
-    const int64_t b = blockIdx.x;
+    const int64_t b = A.work ? (int64_t)A.work[blockIdx.x] : (int64_t)blockIdx.x;
     const int t = threadIdx.x;
     const int x = t & 7, y = (t >> 3) & 7, z = t >> 6;
     const int crd[3] = {x, y, z};
@@ -287,6 +287,7 @@ struct EnergyArgs {
     const S* q;
     const uint32_t* hist;
     const int32_t* nbr;
+    const int32_t* work;  // item -> brick (nullptr: identity)
     int64_t nb, nall;
     int nbins, npairs;
     float alpha1, alpha0, lambda, box_v;
@@ -342,7 +343,8 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
 {
     __shared__ int32_t s_nbr[TGV_NNBR];
     __shared__ double s_red[3][16];
-    const int64_t b = blockIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t b = A.work ? (int64_t)A.work[item] : item;
     const int t = threadIdx.x;
     const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
     const int strd[3] = {1, 8, 64};
@@ -440,33 +442,34 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
     }
     float l1 = fabsf(p[0] + div2[0]) + fabsf(p[1] + div2[1]) + fabsf(p[2] + div2[2]);
 
-    double en = (double)A.alpha1 * (double)sqrtf(gmv2) + (double)A.alpha0 * (double)sqrtf(ef2) +
-                (double)(A.lambda * du_own);
-    double du = (double)k0 - (double)best - (double)A.box_v * (double)l1;
-    double vm = (double)vmax;
-
-    en = warp_sum(en);
-    du = warp_sum(du);
-    vm = warp_max(vm);
+    // per-voxel terms in FP32; warps reduce in FP32 (tree of 32: relative error
+    // below 5 ulp), warps and blocks in FP64, all in a fixed order
+    float en = A.alpha1 * sqrtf(gmv2) + A.alpha0 * sqrtf(ef2) + A.lambda * du_own;
+    float du = k0 - best - A.box_v * l1;
+    float vm = vmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        en += __shfl_down_sync(0xffffffffu, en, o);
+        du += __shfl_down_sync(0xffffffffu, du, o);
+        vm = fmaxf(vm, __shfl_down_sync(0xffffffffu, vm, o));
+    }
     const int w = t >> 5, lane = t & 31;
     if (lane == 0) {
-        s_red[0][w] = en;
-        s_red[1][w] = du;
-        s_red[2][w] = vm;
+        s_red[0][w] = (double)en;
+        s_red[1][w] = (double)du;
+        s_red[2][w] = (double)vm;
     }
     __syncthreads();
-    if (w == 0) {
-        en = lane < 16 ? s_red[0][lane] : 0.0;
-        du = lane < 16 ? s_red[1][lane] : 0.0;
-        vm = lane < 16 ? s_red[2][lane] : 0.0;
-        en = warp_sum(en);
-        du = warp_sum(du);
-        vm = warp_max(vm);
-        if (lane == 0) {
-            A.partial[3 * b + 0] = en;
-            A.partial[3 * b + 1] = du;
-            A.partial[3 * b + 2] = vm;
+    if (t == 0) {
+        double se = 0.0, sd = 0.0, sm = 0.0;
+        for (int k = 0; k < TGV_BVOX / 32; ++k) {
+            se += s_red[0][k];
+            sd += s_red[1][k];
+            sm = fmax(sm, s_red[2][k]);
         }
+        A.partial[3 * item + 0] = se;
+        A.partial[3 * item + 1] = sd;
+        A.partial[3 * item + 2] = sm;
     }
 }
 
@@ -516,7 +519,7 @@ static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
 {
     for (int it = 0; it < iters; ++it) {
         IterArgs<S> A = tgv_make_iter_args<S>(d, L);
-        tgv_iter_kernel<S><<<(unsigned)L.nb, TGV_BVOX, 0, d->stream>>>(A);
+        tgv_iter_kernel<S><<<(unsigned)A.nitems, TGV_BVOX, 0, d->stream>>>(A);
         d->launches++;
         L.cur ^= 1;
     }
@@ -525,7 +528,7 @@ static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
 
 tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters)
 {
-    if (L.nb == 0 || iters == 0) return TGV_OK;
+    if (tgv_work_items(L) == 0 || iters == 0) return TGV_OK;
     if (d->prm.iter_kernel == TGV_ITER_PAIRED && tgv_pipe_supports(L)) return tgv_launch_iterations_pair(d, L, iters);
     if (d->prm.iter_kernel == TGV_ITER_PIPELINED && tgv_pipe_supports(L)) return tgv_launch_iterations_pipe(d, L, iters);
     switch (d->prm.storage) {
@@ -539,7 +542,8 @@ tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters)
 template <typename S>
 static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
 {
-    tgv_status st = tgv_scratch(d, d->red, sizeof(double) * 3 * (size_t)L.nb);
+    const int64_t nitems = tgv_work_items(L);
+    tgv_status st = tgv_scratch(d, d->red, sizeof(double) * 3 * (size_t)nitems);
     if (st != TGV_OK) return st;
     EnergyArgs<S> A;
     A.u = L.u;
@@ -548,6 +552,7 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     A.q = (const S*)L.q[L.cur];
     A.hist = L.hist;
     A.nbr = L.nbr;
+    A.work = L.work;
     A.nb = L.nb;
     A.nall = L.nb + L.nf;
     A.nbins = d->prm.nbins;
@@ -558,8 +563,8 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     A.box_v = d->prm.box_v;
     tgv_bin_centres(d->prm, A.c);
     A.partial = (double*)d->red.ptr;
-    tgv_energy_kernel<S><<<(unsigned)L.nb, TGV_BVOX, 0, d->stream>>>(A);
-    tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, L.nb, d->prm.box_v, d->red_out);
+    tgv_energy_kernel<S><<<(unsigned)nitems, TGV_BVOX, 0, d->stream>>>(A);
+    tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, nitems, d->prm.box_v, d->red_out);
     d->launches += 2;
     st = tgv_cuda_check(d, cudaGetLastError(), "tgv_energy_kernel launch");
     if (st != TGV_OK) return st;
@@ -573,7 +578,7 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
 
 tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)
 {
-    if (L.nb == 0) {
+    if (tgv_work_items(L) == 0) {
         for (int k = 0; k < 4; ++k) host_out[k] = k == 3 ? 1.0 : 0.0;
         return TGV_OK;
     }
@@ -599,6 +604,7 @@ static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_param
     A.q = (const S*)s.q;
     A.hist = s.hist;
     A.nbr = s.nbr;
+    A.work = nullptr;
     A.nb = s.nbricks;
     A.nall = s.nall;
     A.nbins = prm.nbins;

@@ -57,6 +57,11 @@ class tgv_state_view(ctypes.Structure):
                 ("hist", ctypes.c_void_p), ("nbr", ctypes.c_void_p)]
 
 
+class tgv_server_cfg(ctypes.Structure):
+    _fields_ = [("capacity_bricks", ctypes.c_int64), ("capacity_frozen", ctypes.c_int64),
+                ("staging_bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -88,6 +93,18 @@ def lib() -> ctypes.CDLL:
         "tgv_level_voxels": (i64, [P, i32]),
         "tgv_launch_count": (i64, [P]),
         "tgv_energy_noalloc": (i32, [P, P, P, P]),
+        "tgv_solve_graph": (i32, [P, i32, i32, P]),
+        "tgv_set_work_list": (i32, [P, i32, P, i64]),
+        "tgv_server_create": (i32, [P, P, P, P]),
+        "tgv_server_submit": (i32, [P, P, P, i32, P]),
+        "tgv_server_step": (i32, [P, i32, P]),
+        "tgv_server_poll": (i32, [P, ctypes.c_uint64, P]),
+        "tgv_server_extract": (i32, [P, ctypes.c_uint64, P, i64]),
+        "tgv_server_free_bricks": (i64, [P]),
+        "tgv_server_running": (i64, [P]),
+        "tgv_server_voxel_updates": (i64, [P]),
+        "tgv_server_synchronize": (i32, [P]),
+        "tgv_server_destroy": (None, [P]),
         "tgv_status_string": (ctypes.c_char_p, [i32]),
         "tgv_last_error": (ctypes.c_char_p, [P]),
     }
@@ -151,27 +168,30 @@ def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, st
 
 
 # ------------------------------------------------------------------------------------ C entry points
+def _fill_desc(d: tgv_level_desc, lv, keep: list):
+    bc = _host(lv.bricks, np.int32).reshape(-1, 3)
+    fr = getattr(lv, "frozen", None)
+    fc = _host(fr, np.int32).reshape(-1, 3) if fr is not None else np.zeros((0, 3), np.int32)
+    fu = getattr(lv, "frozen_u", None)
+    fv = getattr(lv, "frozen_v", None)
+    fu = _host(fu, np.float32) if (fu is not None and len(fc)) else None
+    fv = _host(fv, np.float32) if (fv is not None and len(fc)) else None
+    keep += [bc, fc, fu, fv]
+    for a in range(3):
+        d.origin[a] = float(np.asarray(lv.origin)[a])
+    d.h = float(lv.h)
+    d.radius = float(getattr(lv, "radius", 0.0) or 0.0)
+    d.nbricks, d.brick_coords = bc.shape[0], _ptr(bc)
+    d.nfrozen, d.frozen_coords = fc.shape[0], _ptr(fc) if len(fc) else None
+    d.frozen_u, d.frozen_v = _ptr(fu), _ptr(fv)
+
+
 def tgv_create_domain(levels, params: tgv_params, stream: int = 0):
     """levels: objects with origin, h, radius, bricks, frozen, frozen_u, frozen_v (synth.DomainDesc)."""
     keep = []
     descs = (tgv_level_desc * len(levels))()
     for k, lv in enumerate(levels):
-        bc = _host(lv.bricks, np.int32).reshape(-1, 3)
-        fr = getattr(lv, "frozen", None)
-        fc = _host(fr, np.int32).reshape(-1, 3) if fr is not None else np.zeros((0, 3), np.int32)
-        fu = getattr(lv, "frozen_u", None)
-        fv = getattr(lv, "frozen_v", None)
-        fu = _host(fu, np.float32) if (fu is not None and len(fc)) else None
-        fv = _host(fv, np.float32) if (fv is not None and len(fc)) else None
-        keep += [bc, fc, fu, fv]
-        d = descs[k]
-        for a in range(3):
-            d.origin[a] = float(np.asarray(lv.origin)[a])
-        d.h = float(lv.h)
-        d.radius = float(getattr(lv, "radius", 0.0) or 0.0)
-        d.nbricks, d.brick_coords = bc.shape[0], _ptr(bc)
-        d.nfrozen, d.frozen_coords = fc.shape[0], _ptr(fc) if len(fc) else None
-        d.frozen_u, d.frozen_v = _ptr(fu), _ptr(fv)
+        _fill_desc(descs[k], lv, keep)
     out = ctypes.c_void_p()
     st = lib().tgv_create_domain(descs, len(levels), ctypes.byref(params), ctypes.c_void_p(stream or 0),
                                  ctypes.byref(out))
@@ -205,6 +225,21 @@ def tgv_solve(d, level: int, iterations: int, energy: bool = False):
     out = np.zeros(4) if energy else None
     _check(d, lib().tgv_solve(d, level, iterations, _ptr(out)))
     return out
+
+
+def tgv_solve_graph(d, level: int, iterations: int, energy: bool = False):
+    out = np.zeros(4) if energy else None
+    _check(d, lib().tgv_solve_graph(d, level, iterations, _ptr(out)))
+    return out
+
+
+def tgv_set_work_list(d, level: int, bricks=None):
+    """bricks: None (every active brick) or a host/device int32 array of brick indices."""
+    if bricks is None:
+        _check(d, lib().tgv_set_work_list(d, level, None, -1))
+        return
+    b = bricks if hasattr(bricks, "data_ptr") else _host(bricks, np.int32)
+    _check(d, lib().tgv_set_work_list(d, level, _ptr(b), int(b.shape[0])))
 
 
 def tgv_energy(d, level: int) -> np.ndarray:
@@ -323,6 +358,12 @@ class Domain:
     def energy(self, level=0):
         return tgv_energy(self.handle, level)
 
+    def solve_graph(self, level, iterations, energy=False):
+        return tgv_solve_graph(self.handle, level, iterations, energy)
+
+    def set_work_list(self, level, bricks=None):
+        tgv_set_work_list(self.handle, level, bricks)
+
     def field(self, level, name, out=None):
         return tgv_extract_field(self.handle, level, name, out)
 
@@ -354,3 +395,122 @@ class Domain:
     @property
     def nbytes(self):
         return tgv_domain_bytes(self.handle)
+
+
+# ------------------------------------------------------------------------------------ serving
+def tgv_server_create(capacity_bricks: int, capacity_frozen: int, params: tgv_params, stream: int,
+                      staging_bytes: int = 0):
+    cfg = tgv_server_cfg(int(capacity_bricks), int(capacity_frozen), int(staging_bytes))
+    out = ctypes.c_void_p()
+    _check(None, lib().tgv_server_create(ctypes.byref(cfg), ctypes.byref(params), ctypes.c_void_p(stream),
+                                         ctypes.byref(out)))
+    return out
+
+
+def tgv_server_submit(s, chunk, hist, iterations: int) -> int:
+    """chunk: DomainDesc-like (bricks, frozen, frozen_u, frozen_v); hist: (nvox, nbins) uint32 host/device."""
+    keep = []
+    d = tgv_level_desc()
+    _fill_desc(d, chunk, keep)
+    h = hist if hasattr(hist, "data_ptr") else _host(hist, np.uint32)
+    t = ctypes.c_uint64()
+    st = lib().tgv_server_submit(s, ctypes.byref(d), _ptr(h), int(iterations), ctypes.byref(t))
+    _check(None, st)
+    return int(t.value)
+
+
+def tgv_server_step(s, max_iterations: int) -> int:
+    f = ctypes.c_int32()
+    _check(None, lib().tgv_server_step(s, int(max_iterations), ctypes.byref(f)))
+    return int(f.value)
+
+
+def tgv_server_poll(s, ticket: int) -> bool:
+    f = ctypes.c_int32()
+    _check(None, lib().tgv_server_poll(s, ctypes.c_uint64(ticket), ctypes.byref(f)))
+    return bool(f.value)
+
+
+def tgv_server_extract(s, ticket: int, nvox: int, out=None):
+    if out is None:
+        out = np.empty(nvox, np.float32)
+    _check(None, lib().tgv_server_extract(s, ctypes.c_uint64(ticket), _ptr(out), int(nvox)))
+    return out
+
+
+def tgv_server_free_bricks(s) -> int:
+    return int(lib().tgv_server_free_bricks(s))
+
+
+def tgv_server_running(s) -> int:
+    return int(lib().tgv_server_running(s))
+
+
+def tgv_server_voxel_updates(s) -> int:
+    return int(lib().tgv_server_voxel_updates(s))
+
+
+def tgv_server_synchronize(s):
+    _check(None, lib().tgv_server_synchronize(s))
+
+
+def tgv_server_destroy(s):
+    lib().tgv_server_destroy(s)
+
+
+class Server:
+    """Owns one tgv_server handle; methods forward to the C entry points."""
+
+    def __init__(self, capacity_bricks, capacity_frozen, nbins=8, storage="fp32", stream: int = 0,
+                 staging_bytes: int = 0, **kw):
+        self.params = make_params(nbins=nbins, storage=storage, **kw)
+        self.handle = tgv_server_create(capacity_bricks, capacity_frozen, self.params, stream, staging_bytes)
+        self.nvox = {}
+
+    def close(self):
+        if self.handle:
+            tgv_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, chunk, hist, iterations):
+        t = tgv_server_submit(self.handle, chunk, hist, iterations)
+        self.nvox[t] = 512 * int(np.asarray(chunk.bricks).reshape(-1, 3).shape[0])
+        return t
+
+    def step(self, max_iterations):
+        return tgv_server_step(self.handle, max_iterations)
+
+    def done(self, ticket):
+        return tgv_server_poll(self.handle, ticket)
+
+    def extract(self, ticket, out=None):
+        u = tgv_server_extract(self.handle, ticket, self.nvox[ticket], out)
+        del self.nvox[ticket]
+        return u
+
+    @property
+    def running(self):
+        return tgv_server_running(self.handle)
+
+    @property
+    def free_bricks(self):
+        return tgv_server_free_bricks(self.handle)
+
+    @property
+    def voxel_updates(self):
+        return tgv_server_voxel_updates(self.handle)
+
+    def synchronize(self):
+        tgv_server_synchronize(self.handle)

@@ -1,0 +1,174 @@
+"""Batched and served forms: many independent chunks (Sec. 4.3 parts with frozen borders,
+Sec. 4.5) advanced by shared launches give exactly the results of solving each alone.
+
+* union level: chunks placed far apart in one level; one launch per iteration covers all;
+* work list: finished chunks leave the launches, the others continue;
+* CUDA graph replay of a run of iterations;
+* server: requests admitted under a fixed arena budget, joining and leaving the running
+  set (continuous batching); each result equals the request solved alone, bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2107_14790_b300 import tgv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2107_14790_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    tgv.lib()
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def chunks(seed, n, lo, hi, nbins=10):
+    return synth.chunk_workload(seed=seed, nchunks=n, min_vox=lo * 512, max_vox=hi * 512, nbins_range=(nbins, nbins))
+
+
+def union_desc(specs, spacing=4096):
+    """All chunks in one level, chunk c shifted by c * spacing bricks along x (never adjacent)."""
+    act, frz, fu, fv, ranges = [], [], [], [], []
+    o = 0
+    for c, sp in enumerate(specs):
+        shift = np.array([c * spacing, 0, 0], np.int32)
+        act.append(sp.domain.bricks + shift)
+        ranges.append((o, o + sp.domain.nbricks))
+        o += sp.domain.nbricks
+        if sp.domain.frozen is not None:
+            frz.append(sp.domain.frozen + shift)
+            fu.append(sp.domain.frozen_u)
+            fv.append(sp.domain.frozen_v)
+    desc = synth.DomainDesc(np.zeros(3), specs[0].domain.h, np.concatenate(act),
+                            frozen=np.concatenate(frz) if frz else None,
+                            frozen_u=np.concatenate(fu) if fu else None, frozen_v=np.concatenate(fv) if fv else None)
+    hist = np.concatenate([sp.hist for sp in specs])
+    return desc, hist, ranges
+
+
+def solve_alone(sp, iters, **kw):
+    with tgv.Domain([sp.domain], nbins=sp.nbins, stream=stream(), **kw) as dom:
+        dom.set_histograms(0, sp.hist)
+        dom.solve(0, iters)
+        return dom.field(0, "u")[:, 0].copy()
+
+
+def test_union_level_equals_each_chunk_alone():
+    specs = chunks(41, 3, 8, 40)
+    desc, hist, ranges = union_desc(specs)
+    with tgv.Domain([desc], nbins=10, stream=stream()) as dom:
+        dom.set_histograms(0, hist)
+        dom.solve(0, 30)
+        u = dom.field(0, "u")[:, 0]
+    for sp, (a, b) in zip(specs, ranges):
+        np.testing.assert_array_equal(u[512 * a:512 * b], solve_alone(sp, 30))
+
+
+def test_work_list_freezes_finished_chunks():
+    specs = chunks(42, 2, 10, 30)
+    desc, hist, ranges = union_desc(specs)
+    with tgv.Domain([desc], nbins=10, stream=stream()) as dom:
+        dom.set_histograms(0, hist)
+        dom.solve(0, 10)
+        a1, b1 = ranges[1]
+        dom.set_work_list(0, np.arange(a1, b1, dtype=np.int32))
+        dom.solve(0, 12)
+        e_list = dom.energy(0)
+        u = dom.field(0, "u")[:, 0]
+        with pytest.raises(tgv.TgvError):
+            dom.set_work_list(0, np.array([a1, a1], np.int32))  # repeated brick
+        dom.set_work_list(0, None)
+    a0, b0 = ranges[0]
+    np.testing.assert_array_equal(u[512 * a0:512 * b0], solve_alone(specs[0], 10))
+    np.testing.assert_array_equal(u[512 * a1:512 * b1], solve_alone(specs[1], 22))
+    with tgv.Domain([specs[1].domain], nbins=10, stream=stream()) as dom:
+        dom.set_histograms(0, specs[1].hist)
+        dom.solve(0, 22)
+        e_alone = dom.energy(0)
+    for k in range(3):
+        assert abs(e_list[k] - e_alone[k]) <= 1e-12 * abs(e_alone[0])
+
+
+@pytest.mark.parametrize("form", ["paired", "pipelined", "one_brick_per_cta"])
+def test_graph_replay_equals_plain_launches(form):
+    sp = chunks(43, 1, 20, 20)[0]
+    s = torch.cuda.Stream()
+    outs = []
+    for use_graph in (False, True):
+        with tgv.Domain([sp.domain], nbins=10, stream=s.cuda_stream, iter_kernel=form) as dom:
+            dom.set_histograms(0, sp.hist)
+            for _ in range(3):
+                if use_graph:
+                    dom.solve_graph(0, 8)
+                else:
+                    dom.solve(0, 8)
+            outs.append({f: dom.field(0, f) for f in ("u", "v", "p", "q")})
+    for f in outs[0]:
+        np.testing.assert_array_equal(outs[0][f], outs[1][f])
+
+
+def test_server_results_equal_solo_runs_under_continuous_batching():
+    specs = chunks(44, 6, 6, 48)
+    iters = [17, 40, 25, 9, 33, 21]
+    cap = sum(sp.domain.nbricks for sp in specs[:4])  # not all six fit at once
+    capf = sum(sp.domain.nfrozen for sp in specs)
+    s = torch.cuda.Stream()
+    results = {}
+    with tgv.Server(cap, capf, nbins=10, stream=s.cuda_stream) as srv:
+        pending = list(range(6))
+        tickets = {}
+        rounds = 0
+        while pending or tickets:
+            # admit what fits (device histograms for odd requests, host for even)
+            while pending:
+                k = pending[0]
+                h = specs[k].hist if k % 2 == 0 else torch.from_numpy(specs[k].hist.astype(np.int32)).cuda()
+                try:
+                    tickets[srv.submit(specs[k].domain, h, iters[k])] = k
+                    pending.pop(0)
+                except tgv.TgvError as e:
+                    assert e.status == 3  # budget: wait for running requests
+                    break
+            srv.step(5)
+            for t in [t for t in tickets if srv.done(t)]:
+                results[tickets.pop(t)] = srv.extract(t)
+            rounds += 1
+            assert rounds < 200
+        assert srv.running == 0 and srv.free_bricks == cap
+    for k, sp in enumerate(specs):
+        np.testing.assert_array_equal(results[k], solve_alone(sp, iters[k]))
+    # and the smallest against the oracle
+    k = int(np.argmin([sp.domain.nbricks for sp in specs]))
+    orc = oracle.OracleLevel(specs[k].domain, 10)
+    orc.hist[:] = specs[k].hist
+    orc.iterate(iters[k])
+    assert np.max(np.abs(results[k] - orc.u)) <= 1e-4
+
+
+def test_server_admission_limits():
+    specs = chunks(45, 2, 20, 20)
+    s = torch.cuda.Stream()
+    with tgv.Server(specs[0].domain.nbricks, 4 * specs[0].domain.nfrozen, nbins=10, stream=s.cuda_stream) as srv:
+        t0 = srv.submit(specs[0].domain, specs[0].hist, 5)
+        with pytest.raises(tgv.TgvError) as e:
+            srv.submit(specs[1].domain, specs[1].hist, 5)
+        assert e.value.status == 3
+        bad = specs[1].hist.copy()
+        bad[0, 0] = 70000
+        with pytest.raises(tgv.TgvError):
+            srv.submit(specs[1].domain, bad, 5)
+        while not srv.done(t0):
+            srv.step(100)
+        srv.extract(t0)
+        t1 = srv.submit(specs[1].domain, specs[1].hist, 5)
+        srv.step(100)
+        assert srv.done(t1)
+        np.testing.assert_array_equal(srv.extract(t1), solve_alone(specs[1], 5))
