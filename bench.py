@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--iter-kernel", default="paired", choices=["paired", "pipelined", "one_brick_per_cta"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving"],
+                    help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
+                         "300 iterations; serving: Poisson stream of 2000 chunk-solve requests")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM budget of all arenas")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="profiling case: N^3 dense domain, seeded random 10-bin histograms, "
                          "warm-up + 4 fused iterations + one energy/gap (no depth maps)")
@@ -353,10 +358,161 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": n, "voxels": desc.nvox, "energy": list(map(float, e))}))
 
 
+def _oracle_u(spec, iters):
+    import oracle
+    lvl = oracle.OracleLevel(spec.domain, spec.nbins)
+    h = spec.hist
+    lvl.hist[:] = h.cpu().numpy() if hasattr(h, "cpu") else h
+    lvl.iterate(iters)
+    return lvl.u
+
+
+def run_batched(args):
+    """256 uneven chunks (32^3..192^3 voxels, frozen one-brick shell, 10 bins, 300 iterations):
+    one union level advanced by graph-replayed fused launches, FP32 and BF16 storage, against
+    the plain form (each chunk its own domain, solved one after the other, FP32)."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import build, tgv
+    from paper_2107_14790_b300.batching import union_level
+    build.build()
+    torch.cuda.set_device(0)
+    iters = 300
+    t_gen = time.perf_counter()
+    specs = synth.chunk_workload(1004, 256, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="torch", device="cuda")
+    U = union_level([sp.domain for sp in specs])
+    hist = torch.cat([sp.hist for sp in specs])
+    t_gen = time.perf_counter() - t_gen
+    nvox = int(hist.shape[0])
+    stream = torch.cuda.Stream()
+    out = {}
+    sample = sorted(range(len(specs)), key=lambda k: specs[k].domain.nbricks)[:3]
+    ref = {k: _oracle_u(specs[k], iters) for k in sample}
+    for storage in ("fp32", "bf16", "fp16"):
+        dom = tgv.Domain([U], nbins=10, storage=storage, stream=stream.cuda_stream)
+        dom.set_histograms(0, hist)
+        dom.solve_graph(0, iters)  # first call: plain launches, captures the graph
+        dom.reset(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = dom.launches
+        e0.record(stream)
+        dom.solve_graph(0, iters)
+        e1.record(stream)
+        dom.synchronize()
+        ms = e0.elapsed_time(e1)
+        u = dom.field(0, "u")[:, 0]
+        err = max(float(np.max(np.abs(u[512 * U.ranges[k][0]:512 * U.ranges[k][1]] - ref[k]))) for k in sample)
+        bpv = algorithmic_bytes_per_voxel(10, storage)
+        out[storage] = {"voxel_updates_per_s": nvox * iters / (ms / 1e3), "ms": ms, "launches": dom.launches - l0,
+                        "achieved_gbs": nvox * bpv / (ms / 1e3 / iters) / 1e9, "u_err_inf_vs_fp64_oracle": err}
+        dom.close()
+    # plain form: every chunk alone, FP32
+    doms = []
+    for sp in specs:
+        d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)
+        d.set_histograms(0, sp.hist)
+        doms.append(d)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for d in doms:
+        tgv.tgv_solve(d.handle, 0, iters, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    for d in doms:
+        d.close()
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+    best = out["bf16"]["voxel_updates_per_s"]
+    return {"metric": "batched chunk solve: voxel-updates/s (256 chunks 32^3..192^3, 300 iterations)",
+            "value": best, "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32-math/bf16-storage",
+            "data": "synthetic (seeded chunk scenes)",
+            "config": {"workload": "batched-256-chunks-32^3..192^3-10bins-300it", "chunks": len(specs),
+                       "voxels": nvox, "generation_s": t_gen},
+            "batched": out,
+            "plain_fp32": {"voxel_updates_per_s": nvox * iters / (ms_plain / 1e3), "ms": ms_plain},
+            "speedup_batched_bf16_over_plain_fp32": best / (nvox * iters / (ms_plain / 1e3)),
+            "roofline": {"bound": "hbm", "achieved": out["fp32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": out["fp32"]["achieved_gbs"] / peak, "kernel": "tgv_iter_pair_kernel (fp32)"},
+            "accuracy_sample": f"3 smallest chunks vs FP64 oracle after {iters} iterations"}
+
+
+def run_serving(args):
+    """Poisson stream of chunk-solve requests (16k..8M voxels, 8..12 bins, 200..600 iterations)
+    through one server per bin count, arenas sized from the HBM budget."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import build, tgv
+    from paper_2107_14790_b300.batching import Request, RequestStream
+    build.build()
+    torch.cuda.set_device(0)
+    nreq = args.requests
+    specs = synth.chunk_workload(1005, nreq, 16 * 1024, 8 * 1024 * 1024, (8, 12), (200, 600), rate=1.0, hist="none")
+    bins = sorted({sp.nbins for sp in specs})
+    budget = args.budget_gb * 1e9
+    streams = {n: torch.cuda.Stream() for n in bins}
+
+    def brick_bytes(n):
+        npairs = (n + 1) // 2
+        return 512 * (4 + 8 + 12 + 24 + 24 + 48 + 4 * npairs) + 48, 512 * (4 + 8 + 12 + 24)
+
+    servers = {}
+    for n in bins:
+        ba, bf = brick_bytes(n)
+        share = budget / len(bins)
+        cap = int(share / (ba + bf))
+        servers[n] = tgv.Server(cap, cap, nbins=n, stream=streams[n].cuda_stream, staging_bytes=64 << 20)
+
+    def make(sp):
+        return lambda: synth.chunk_histogram(sp, "cuda")
+
+    def requests(k0, k1, scale):
+        return [Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, specs[k].arrival * scale, make(specs[k]))
+                for k in range(k0, k1)]
+
+    # saturated throughput: a block of requests all arriving at once
+    nsat = min(200, nreq)
+    warm = RequestStream(servers, streams).run([Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, 0.0,
+                                                        make(specs[k])) for k in range(min(16, nreq))])
+    sat = RequestStream(servers, streams).run([Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, 0.0,
+                                                       make(specs[k])) for k in range(nsat)])
+    sat_rate = nsat / sat.makespan
+    # the stream at 0.8x the saturated rate (unit-rate arrival times scaled)
+    rate = 0.8 * sat_rate
+    main = RequestStream(servers, streams).run(requests(0, nreq, 1.0 / rate))
+    over = RequestStream(servers, streams).run(requests(0, min(nreq, 400), 1.0 / (2.0 * sat_rate)))
+    for s_ in servers.values():
+        s_.close()
+    p = lambda a, q: float(np.percentile(a, q))
+    vu_main = main.voxel_updates
+    return {"metric": "chunk-solve serving: p50/p99 latency and voxel-updates/s (Poisson arrivals, 0.8x saturated rate)",
+            "value": vu_main / main.makespan, "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic (seeded chunk requests)",
+            "config": {"workload": "serving-2000-requests-16k..8M-voxels-8..12bins-200..600it",
+                       "requests": nreq, "budget_gb": args.budget_gb, "servers": len(servers),
+                       "round_iterations": 10},
+            "latency_s": {"p50": p(main.latencies, 50), "p99": p(main.latencies, 99),
+                          "mean": float(main.latencies.mean()), "max": float(main.latencies.max())},
+            "queue_wait_s": {"p50": p(main.wait, 50), "p99": p(main.wait, 99)},
+            "arrival_rate_per_s": rate, "saturated_rate_per_s": sat_rate,
+            "saturated_voxel_updates_per_s": sat.voxel_updates / sat.makespan,
+            "makespan_s": main.makespan, "max_running": main.max_running,
+            "overload_2x": {"requests": over.completed, "p50": p(over.latencies, 50), "p99": p(over.latencies, 99),
+                            "voxel_updates_per_s": over.voxel_updates / over.makespan}}
+
+
 def main():
     args = parse()
     if args.profile:
         run_profile_case(args)
+        return
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args)), flush=True)
+        return
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args)), flush=True)
         return
     cfg = SMALL if args.small else WORKLOAD
     if args.impl == "reference":

@@ -360,6 +360,9 @@ TGV_API int64_t tgv_server_free_bricks(const tgv_server* s);
 TGV_API int64_t tgv_server_running(const tgv_server* s);
 TGV_API int64_t tgv_server_voxel_updates(const tgv_server* s);
 
+/* Message of the last failure on the server. */
+TGV_API const char* tgv_server_last_error(const tgv_server* s);
+
 /* Waits for all queued work of the server. */
 TGV_API tgv_status tgv_server_synchronize(tgv_server* s);
 

@@ -1,0 +1,193 @@
+"""Host orchestration of the batched and served forms (no arithmetic of the method).
+
+* `union_level`: several independent chunks (Sec. 4.3 parts, each with its
+  frozen border, Sec. 4.5) placed far apart in one brick level, so one launch
+  of the fused iteration advances all of them;
+* `RequestStream`: a request loop over `tgv.Server` objects (one per bin
+  count) with arrival times, FIFO admission under the servers' fixed arena
+  budget, rounds of `step` iterations and per-request latency.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import tgv
+
+
+
+@dataclass
+class UnionLevel:
+    origin: np.ndarray
+    h: float
+    bricks: np.ndarray
+    frozen: Optional[np.ndarray]
+    frozen_u: Optional[np.ndarray]
+    frozen_v: Optional[np.ndarray]
+    ranges: List[tuple]  # active-brick range [a, b) of each chunk
+    radius: float = 0.0
+
+
+def union_level(domains: Sequence) -> UnionLevel:
+    """One level holding every chunk of `domains` (DomainDesc-like): the chunks are laid
+    side by side along x with a gap of two bricks between their extents (frozen shells
+    included), so no face or edge link crosses chunks."""
+    act, frz, fu, fv, ranges = [], [], [], [], []
+    o = 0
+    x_next = -(1 << 18)
+    for c, dm in enumerate(domains):
+        b = np.asarray(dm.bricks, np.int32).reshape(-1, 3)
+        allb = b if getattr(dm, "frozen", None) is None or not len(dm.frozen) else \
+            np.concatenate([b, np.asarray(dm.frozen, np.int32).reshape(-1, 3)])
+        lo, hi = int(allb[:, 0].min()), int(allb[:, 0].max())
+        shift = np.array([x_next - lo, 0, 0], np.int32)
+        x_next += hi - lo + 3
+        act.append(b + shift)
+        ranges.append((o, o + b.shape[0]))
+        o += b.shape[0]
+        if getattr(dm, "frozen", None) is not None and len(dm.frozen):
+            f = np.asarray(dm.frozen, np.int32).reshape(-1, 3)
+            frz.append(f + shift)
+            fu.append(np.asarray(dm.frozen_u, np.float32).reshape(-1, 512) if dm.frozen_u is not None
+                      else np.zeros((f.shape[0], 512), np.float32))
+            fv.append(np.asarray(dm.frozen_v, np.float32).reshape(-1, 3, 512) if dm.frozen_v is not None
+                      else np.zeros((f.shape[0], 3, 512), np.float32))
+    if x_next >= (1 << 19):
+        raise ValueError("chunks do not fit the brick coordinate range of one level")
+    return UnionLevel(np.asarray(domains[0].origin, np.float64), float(domains[0].h), np.concatenate(act),
+                      np.concatenate(frz) if frz else None, np.concatenate(fu) if fu else None,
+                      np.concatenate(fv) if fv else None, ranges)
+
+
+@dataclass
+class Request:
+    rid: int
+    chunk: object          # DomainDesc-like
+    nbins: int
+    iterations: int
+    arrival: float         # seconds after the stream starts
+    make_hist: Callable    # () -> (nvox, nbins) counts (host or device); called at admission
+    hist: object = None
+    ticket: int = 0
+    admitted: float = -1.0
+    finished: float = -1.0
+    u: object = None
+
+
+@dataclass
+class StreamResult:
+    latencies: np.ndarray
+    wait: np.ndarray
+    makespan: float
+    voxel_updates: int
+    completed: int
+    max_running: int
+    rounds: int
+    requests: List[Request] = field(default_factory=list)
+
+
+class RequestStream:
+    """Runs requests through one server per bin count.
+
+    Each round: admit arrived requests in arrival order while their server has
+    room (BUDGET leaves a request queued), queue `round_iters` iterations on
+    every server with running requests, then extract the requests the
+    previous round finished.  Two rounds are kept in flight so the host work
+    of one overlaps the device work of the other.
+    """
+
+    def __init__(self, servers: Dict[int, "tgv.Server"], streams: Dict[int, object], round_iters: int = 10,
+                 keep_results: bool = False):
+        self.servers = servers
+        self.streams = streams
+        self.round_iters = int(round_iters)
+        self.keep = keep_results
+
+    def run(self, requests: List[Request], clock=time.perf_counter) -> StreamResult:
+        import torch
+
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        vu0 = sum(srv.voxel_updates for srv in self.servers.values())
+        pending = deque()
+        running: Dict[int, Request] = {}
+        nxt = 0
+        done = 0
+        rounds = 0
+        max_running = 0
+        t0 = clock()
+        in_flight = []  # events of the previous round, with the tickets that round finished
+        finishing = set()
+        while done < len(reqs):
+            now = clock() - t0
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                pending.append(reqs[nxt])
+                nxt += 1
+            # admission, first come first served per server
+            blocked = set()
+            keep = deque()
+            while pending:
+                r = pending.popleft()
+                if r.nbins in blocked:
+                    keep.append(r)
+                    continue
+                if r.hist is None:
+                    r.hist = r.make_hist()
+                try:
+                    r.ticket = self.servers[r.nbins].submit(r.chunk, r.hist, r.iterations)
+                    r.admitted = clock() - t0
+                    running[(r.nbins, r.ticket)] = r
+                except tgv.TgvError as e:
+                    if e.status != 3:
+                        raise
+                    blocked.add(r.nbins)
+                    keep.append(r)
+            pending = keep
+            max_running = max(max_running, len(running))
+            # one round of iterations on every busy server
+            finished_now = []
+            events = []
+            for n, srv in self.servers.items():
+                if srv.running == 0:
+                    continue
+                srv.step(self.round_iters)
+                ev = torch.cuda.Event()
+                ev.record(self.streams[n])
+                events.append(ev)
+            for key in running:
+                if key not in finishing and self.servers[key[0]].done(key[1]):
+                    finished_now.append(key)
+                    finishing.add(key)
+            # finish the previous round on the host while this one runs
+            for ev in in_flight_events(in_flight):
+                ev.synchronize()
+            for key in flush(in_flight):
+                finishing.discard(key)
+                r = running.pop(key)
+                u = self.servers[key[0]].extract(key[1])
+                r.finished = clock() - t0
+                r.hist = None
+                if self.keep:
+                    r.u = u
+                done += 1
+            in_flight = [(events, finished_now)]
+            rounds += 1
+            if not running and not pending and not finished_now and nxt < len(reqs):
+                time.sleep(max(0.0, reqs[nxt].arrival - (clock() - t0)))
+        lat = np.array([r.finished - r.arrival for r in reqs])
+        wait = np.array([r.admitted - r.arrival for r in reqs])
+        vu = sum(srv.voxel_updates for srv in self.servers.values()) - vu0
+        return StreamResult(lat, wait, clock() - t0, vu, done, max_running, rounds, reqs if self.keep else [])
+
+
+def in_flight_events(in_flight):
+    for events, _ in in_flight:
+        yield from events
+
+
+def flush(in_flight):
+    for _, keys in in_flight:
+        yield from keys

@@ -57,7 +57,13 @@ tgv_status tgv_kernel_setup(const void* kernel, int threads, size_t smem, int* p
         *per_sm = it->second;
         return TGV_OK;
     }
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    // The limit is raised to the device maximum (not to `smem`): the same kernel may be
+    // launched with different shared-memory sizes, and a lower limit set for one
+    // size would make launches with a larger one fail.
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        (size_t)optin < smem ||
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return TGV_ERR_CUDA;

@@ -487,6 +487,8 @@ tgv_status tgv_server_extract(tgv_server* s, uint64_t ticket, float* u_out, int6
 
 int64_t tgv_server_free_bricks(const tgv_server* s) { return s ? s->act.free_total() : 0; }
 
+const char* tgv_server_last_error(const tgv_server* s) { return s && s->dom ? s->dom->last_error.c_str() : "null server"; }
+
 int64_t tgv_server_running(const tgv_server* s) { return s ? s->running : 0; }
 
 int64_t tgv_server_voxel_updates(const tgv_server* s) { return s ? s->voxel_updates : 0; }

@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "tgv_server_running": (i64, [P]),
         "tgv_server_voxel_updates": (i64, [P]),
         "tgv_server_synchronize": (i32, [P]),
+        "tgv_server_last_error": (ctypes.c_char_p, [P]),
         "tgv_server_destroy": (None, [P]),
         "tgv_status_string": (ctypes.c_char_p, [i32]),
         "tgv_last_error": (ctypes.c_char_p, [P]),
@@ -122,9 +123,12 @@ def exported_symbols() -> Sequence[str]:
     return [n for n in dir(_lib) if n.startswith("tgv_")]
 
 
-def _check(d, status: int):
+def _check(d, status: int, server=None):
     if status != TGV_OK:
-        msg = lib().tgv_last_error(d).decode() if d else ""
+        if server is not None:
+            msg = lib().tgv_server_last_error(server).decode()
+        else:
+            msg = lib().tgv_last_error(d).decode() if d else ""
         raise TgvError(status, msg)
 
 
@@ -415,26 +419,26 @@ def tgv_server_submit(s, chunk, hist, iterations: int) -> int:
     h = hist if hasattr(hist, "data_ptr") else _host(hist, np.uint32)
     t = ctypes.c_uint64()
     st = lib().tgv_server_submit(s, ctypes.byref(d), _ptr(h), int(iterations), ctypes.byref(t))
-    _check(None, st)
+    _check(None, st, server=s)
     return int(t.value)
 
 
 def tgv_server_step(s, max_iterations: int) -> int:
     f = ctypes.c_int32()
-    _check(None, lib().tgv_server_step(s, int(max_iterations), ctypes.byref(f)))
+    _check(None, lib().tgv_server_step(s, int(max_iterations), ctypes.byref(f)), server=s)
     return int(f.value)
 
 
 def tgv_server_poll(s, ticket: int) -> bool:
     f = ctypes.c_int32()
-    _check(None, lib().tgv_server_poll(s, ctypes.c_uint64(ticket), ctypes.byref(f)))
+    _check(None, lib().tgv_server_poll(s, ctypes.c_uint64(ticket), ctypes.byref(f)), server=s)
     return bool(f.value)
 
 
 def tgv_server_extract(s, ticket: int, nvox: int, out=None):
     if out is None:
         out = np.empty(nvox, np.float32)
-    _check(None, lib().tgv_server_extract(s, ctypes.c_uint64(ticket), _ptr(out), int(nvox)))
+    _check(None, lib().tgv_server_extract(s, ctypes.c_uint64(ticket), _ptr(out), int(nvox)), server=s)
     return out
 
 
@@ -450,8 +454,12 @@ def tgv_server_voxel_updates(s) -> int:
     return int(lib().tgv_server_voxel_updates(s))
 
 
+def tgv_server_last_error(s) -> str:
+    return lib().tgv_server_last_error(s).decode()
+
+
 def tgv_server_synchronize(s):
-    _check(None, lib().tgv_server_synchronize(s))
+    _check(None, lib().tgv_server_synchronize(s), server=s)
 
 
 def tgv_server_destroy(s):

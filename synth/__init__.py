@@ -22,6 +22,8 @@ from .scenes import (  # noqa: F401
     plane_depth,
     random_histograms,
     chunk_workload,
+    chunk_histogram,
+    synthetic_votes_torch,
     ChunkSpec,
     CONFIG_SEEDS,
 )

@@ -353,10 +353,11 @@ def random_histograms(rng: np.random.Generator, nvox: int, nbins: int, max_count
 class ChunkSpec:
     """One chunk-solve request: a box of bricks with a frozen one-brick face shell."""
     domain: DomainDesc
-    hist: np.ndarray   # (nvox, nbins) uint32
+    hist: object       # (nvox, nbins) counts: uint32 numpy, int32 torch, or None
     nbins: int
     iterations: int
     arrival: float = 0.0
+    meta: dict = field(default_factory=dict)
 
 
 def _box_dims(nb: int, rng) -> tuple:
@@ -376,21 +377,65 @@ def _synthetic_votes(s_vox: np.ndarray, nbins: int, rng, views: int) -> np.ndarr
     observations are uniform outliers.
     """
     nv = s_vox.shape[0]
-    out = np.zeros((nv, nbins), np.uint32)
+    flat = np.zeros(nv * nbins, np.int64)
     seen = s_vox > -9.0
     centre = (nbins - 1) / 2.0 + s_vox * (nbins - 1) / 6.0
+    base = np.arange(nv, dtype=np.int64) * nbins
     for _ in range(views):
         b = np.rint(centre + rng.normal(0.0, 1.0, size=nv))
         outl = rng.random(nv) < 0.05
         b[outl] = rng.integers(0, nbins, size=int(outl.sum()))
         b = np.clip(b, 0, nbins - 1).astype(np.int64)
-        np.add.at(out, (np.nonzero(seen)[0], b[seen]), 1)
-    return out
+        flat += np.bincount((base + b)[seen], minlength=nv * nbins)
+    return flat.reshape(nv, nbins).astype(np.uint32)
+
+
+def synthetic_votes_torch(s_vox, nbins: int, seed: int, views: int = 12):
+    """Same statistical vote model as _synthetic_votes, drawn with torch on s_vox's device.
+
+    Returns int32 counts (nvox, nbins) on that device.
+    """
+    torch = _torch()
+    dev = s_vox.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    nv = s_vox.shape[0]
+    out = torch.zeros(nv * nbins, dtype=torch.int32, device=dev)
+    seen = s_vox > -9.0
+    centre = (nbins - 1) / 2.0 + s_vox * ((nbins - 1) / 6.0)
+    base = torch.arange(nv, device=dev, dtype=torch.int64) * nbins
+    ones = seen.to(torch.int32)
+    for _ in range(views):
+        b = torch.round(centre + torch.randn(nv, generator=gen, device=dev, dtype=centre.dtype))
+        outl = torch.rand(nv, generator=gen, device=dev) < 0.05
+        b = torch.where(outl, torch.randint(0, nbins, (nv,), generator=gen, device=dev).to(b.dtype), b)
+        b = b.clamp(0, nbins - 1).to(torch.int64)
+        out.index_add_(0, base + b, ones)
+    return out.view(nv, nbins)
+
+
+def chunk_heights(terrain: "Terrain", bricks: np.ndarray, h: float, device=None):
+    """Height above the terrain surface, in voxels, of every voxel of `bricks` (brick order)."""
+    if device is None:
+        li = np.arange(512)
+        lx, ly, lz = li % 8, (li // 8) % 8, li // 64
+        gx = (bricks[:, 0:1] * 8 + lx[None, :] + 0.5) * h
+        gy = (bricks[:, 1:2] * 8 + ly[None, :] + 0.5) * h
+        gz = (bricks[:, 2:3] * 8 + lz[None, :] + 0.5) * h
+        return ((gz - terrain.height(gx, gy)) / h).reshape(-1)
+    torch = _torch()
+    bt = torch.as_tensor(bricks, dtype=torch.float64, device=device)
+    li = torch.arange(512, device=device)
+    lx, ly, lz = (li % 8).double(), ((li // 8) % 8).double(), (li // 64).double()
+    gx = (bt[:, 0:1] * 8 + lx[None, :] + 0.5) * h
+    gy = (bt[:, 1:2] * 8 + ly[None, :] + 0.5) * h
+    gz = (bt[:, 2:3] * 8 + lz[None, :] + 0.5) * h
+    return ((gz - terrain.height(gx, gy, xp=torch)) / h).reshape(-1)
 
 
 def chunk_workload(seed: int, nchunks: int, min_vox: int, max_vox: int, nbins_range=(10, 10),
                    iters_range=(300, 300), rate: float = 0.0, max_total_vox: Optional[int] = None,
-                   views: int = 12) -> List[ChunkSpec]:
+                   views: int = 12, hist: str = "numpy", device=None) -> List[ChunkSpec]:
     """Chunks cut from an unbounded terrain-style scene (sum of 6 sinusoids).
 
     Active voxel count log-uniform in [min_vox, max_vox], rounded to whole
@@ -398,6 +443,8 @@ def chunk_workload(seed: int, nchunks: int, min_vox: int, max_vox: int, nbins_ra
     its frozen halo is every brick face-adjacent to the box, carrying
     u = clip(s/3, -1, 1) (s = height above the surface in voxels) and v = 0.
     `rate` > 0 draws Poisson arrival times (requests/s).
+    hist: "numpy" (host counts now), "torch" (int32 counts on `device` now) or
+    "none" (hist = None; draw later with chunk_histogram(spec)).
     """
     rng = np.random.default_rng(seed)
     terrain = make_terrain(rng, nbox=0)
@@ -437,13 +484,27 @@ def chunk_workload(seed: int, nchunks: int, min_vox: int, max_vox: int, nbins_ra
             gz = (bc[:, 2:3] * 8 + lz[None, :] + 0.5) * h
             return (gz - terrain.height(gx, gy)) / h  # (nb, 512) voxel units
 
-        s_act = heights(bricks).reshape(-1)
-        hist = _synthetic_votes(s_act, nbins, rng, views)
+        vote_seed = int(rng.integers(0, 2**31 - 1))
+        if hist == "numpy":
+            hst = _synthetic_votes(heights(bricks).reshape(-1), nbins, np.random.default_rng(vote_seed), views)
+        elif hist == "torch":
+            hst = synthetic_votes_torch(chunk_heights(terrain, bricks, h, device), nbins, vote_seed, views)
+        else:
+            hst = None
         fu = np.clip(heights(frozen) / 3.0, -1.0, 1.0).astype(np.float32) if len(frozen) else None
         fv = np.zeros((len(frozen), 3, 512), np.float32) if len(frozen) else None
         dom = DomainDesc(origin=np.zeros(3), h=h, bricks=bricks,
                          frozen=frozen if len(frozen) else None, frozen_u=fu, frozen_v=fv)
         if rate > 0:
             t_arr += rng.exponential(1.0 / rate)
-        specs.append(ChunkSpec(dom, hist, nbins, iters, t_arr))
+        sp = ChunkSpec(dom, hst, nbins, iters, t_arr)
+        sp.meta = dict(terrain=terrain, vote_seed=vote_seed, views=views)
+        specs.append(sp)
     return specs
+
+
+def chunk_histogram(spec: "ChunkSpec", device):
+    """Draws the counts of a chunk made with hist="none" (int32 (nvox, nbins) on `device`)."""
+    m = spec.meta
+    return synthetic_votes_torch(chunk_heights(m["terrain"], spec.domain.bricks, spec.domain.h, device), spec.nbins,
+                                 m["vote_seed"], m["views"])

@@ -172,3 +172,26 @@ def test_server_admission_limits():
         srv.step(100)
         assert srv.done(t1)
         np.testing.assert_array_equal(srv.extract(t1), solve_alone(specs[1], 5))
+
+
+def test_request_stream_with_arrivals_matches_solo_runs():
+    """A small Poisson stream through one server per bin count: admission under the
+    budget, rounds of iterations, extraction; every result equals its solo run."""
+    from paper_2107_14790_b300.batching import Request, RequestStream
+    specs = synth.chunk_workload(46, 10, 8 * 512, 40 * 512, (8, 11), (10, 40), rate=200.0)
+    bins = sorted({sp.nbins for sp in specs})
+    assert len(bins) >= 3  # mixes the compile-time (8, 10) and run-time bin-count kernels
+    streams = {n: torch.cuda.Stream() for n in bins}
+    cap = 120
+    servers = {n: tgv.Server(cap, 4 * cap, nbins=n, stream=streams[n].cuda_stream) for n in bins}
+    reqs = [Request(k, sp.domain, sp.nbins, sp.iterations, sp.arrival, (lambda sp=sp: sp.hist))
+            for k, sp in enumerate(specs)]
+    res = RequestStream(servers, streams, round_iters=7, keep_results=True).run(reqs)
+    assert res.completed == len(specs)
+    assert np.all(res.latencies > 0) and np.all(res.wait >= 0)
+    assert res.voxel_updates == sum(sp.domain.nvox * sp.iterations for sp in specs)
+    for r in res.requests:
+        np.testing.assert_array_equal(r.u, solve_alone(specs[r.rid], specs[r.rid].iterations))
+    for srv in servers.values():
+        assert srv.running == 0 and srv.free_bricks == cap
+        srv.close()
