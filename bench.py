@@ -372,14 +372,23 @@ def run_batched(args):
     one union level advanced by graph-replayed fused launches, FP32 and BF16 storage, against
     the plain form (each chunk its own domain, solved one after the other, FP32)."""
     import torch
+    import torch.distributed as tdist
     import synth
     from paper_2107_14790_b300 import build, tgv
     from paper_2107_14790_b300.batching import union_level
+    from paper_2107_14790_b300.multigpu import reduce_scalar, shard
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     build.build()
-    torch.cuda.set_device(0)
     iters = 300
     t_gen = time.perf_counter()
-    specs = synth.chunk_workload(1004, 256, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="torch", device="cuda")
+    geo = synth.chunk_workload(1004, 256, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="none")
+    mine = shard([g.domain.nvox for g in geo], rank, world)  # each rank solves its own chunks
+    specs = [geo[k] for k in mine]
+    for sp in specs:
+        sp.hist = synth.chunk_histogram(sp, f"cuda:{local}")
     U = union_level([sp.domain for sp in specs])
     hist = torch.cat([sp.hist for sp in specs])
     t_gen = time.perf_counter() - t_gen
@@ -400,11 +409,12 @@ def run_batched(args):
         dom.solve_graph(0, iters)
         e1.record(stream)
         dom.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = reduce_scalar(e0.elapsed_time(e1), "max")
         u = dom.field(0, "u")[:, 0]
         err = max(float(np.max(np.abs(u[512 * U.ranges[k][0]:512 * U.ranges[k][1]] - ref[k]))) for k in sample)
         bpv = algorithmic_bytes_per_voxel(10, storage)
-        out[storage] = {"voxel_updates_per_s": nvox * iters / (ms / 1e3), "ms": ms, "launches": dom.launches - l0,
+        tot = reduce_scalar(nvox, "sum")
+        out[storage] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms, "launches": dom.launches - l0,
                         "achieved_gbs": nvox * bpv / (ms / 1e3 / iters) / 1e9, "u_err_inf_vs_fp64_oracle": err}
         dom.close()
     # plain form: every chunk alone, FP32
@@ -420,20 +430,26 @@ def run_batched(args):
         tgv.tgv_solve(d.handle, 0, iters, False)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_plain = e0.elapsed_time(e1)
+    ms_plain = reduce_scalar(e0.elapsed_time(e1), "max")
+    nvox = int(reduce_scalar(nvox, "sum"))
     for d in doms:
         d.close()
     peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
-    best = out["bf16"]["voxel_updates_per_s"]
+    best = out["fp16"]["voxel_updates_per_s"]
+    if world > 1:
+        tdist.destroy_process_group()
+    if rank != 0:
+        return None
     return {"metric": "batched chunk solve: voxel-updates/s (256 chunks 32^3..192^3, 300 iterations)",
-            "value": best, "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32-math/bf16-storage",
+            "value": best, "unit": "voxel-updates/s", "n_gpus": world, "scaling": "weak" if world == 1 else "strong",
+            "higher_is_better": True, "dtype": "f32-math/fp16-storage",
             "data": "synthetic (seeded chunk scenes)",
             "config": {"workload": "batched-256-chunks-32^3..192^3-10bins-300it", "chunks": len(specs),
                        "voxels": nvox, "generation_s": t_gen},
             "batched": out,
             "plain_fp32": {"voxel_updates_per_s": nvox * iters / (ms_plain / 1e3), "ms": ms_plain},
-            "speedup_batched_bf16_over_plain_fp32": best / (nvox * iters / (ms_plain / 1e3)),
+            "speedup_batched_fp16_over_plain_fp32": best / (nvox * iters / (ms_plain / 1e3)),
             "roofline": {"bound": "hbm", "achieved": out["fp32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": out["fp32"]["achieved_gbs"] / peak, "kernel": "tgv_iter_pair_kernel (fp32)"},
             "accuracy_sample": f"3 smallest chunks vs FP64 oracle after {iters} iterations"}
@@ -456,14 +472,16 @@ def run_serving(args):
 
     def brick_bytes(n):
         npairs = (n + 1) // 2
-        return 512 * (4 + 8 + 12 + 24 + 24 + 48 + 4 * npairs) + 48, 512 * (4 + 8 + 12 + 24)
+        sb = 4 if args.storage == "fp32" else 2
+        return 512 * (4 + 8 + (3 + 6 + 6 + 12) * sb + 4 * npairs) + 48, 512 * (4 + 8 + 9 * sb)
 
     servers = {}
     for n in bins:
         ba, bf = brick_bytes(n)
         share = budget / len(bins)
         cap = int(share / (ba + bf))
-        servers[n] = tgv.Server(cap, cap, nbins=n, stream=streams[n].cuda_stream, staging_bytes=64 << 20)
+        servers[n] = tgv.Server(cap, cap, nbins=n, storage=args.storage, stream=streams[n].cuda_stream,
+                                staging_bytes=64 << 20)
 
     def make(sp):
         return lambda: synth.chunk_histogram(sp, "cuda")
@@ -489,7 +507,8 @@ def run_serving(args):
     vu_main = main.voxel_updates
     return {"metric": "chunk-solve serving: p50/p99 latency and voxel-updates/s (Poisson arrivals, 0.8x saturated rate)",
             "value": vu_main / main.makespan, "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic (seeded chunk requests)",
+            "dtype": "f32" if args.storage == "fp32" else f"f32-math/{args.storage}-storage",
+            "data": "synthetic (seeded chunk requests)",
             "config": {"workload": "serving-2000-requests-16k..8M-voxels-8..12bins-200..600it",
                        "requests": nreq, "budget_gb": args.budget_gb, "servers": len(servers),
                        "round_iterations": 10},
@@ -509,7 +528,9 @@ def main():
         run_profile_case(args)
         return
     if args.workload == "batched":
-        print(json.dumps(run_batched(args)), flush=True)
+        res = run_batched(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
         return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)

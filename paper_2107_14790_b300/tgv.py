@@ -331,9 +331,17 @@ class Domain:
     """Owns one tgv_domain handle; methods forward to the C entry points."""
 
     def __init__(self, levels, nbins=8, storage="fp32", stream: int = 0, **kw):
+        """iter_kernel="auto" asks the autotuner (cached per size class) for the kernel form."""
         self.nbins = int(nbins)
-        self.params = make_params(nbins=nbins, storage=storage, **kw)
         self.levels = list(levels)
+        self.use_graph = False
+        if kw.get("iter_kernel") == "auto":
+            from . import autotune
+            nvox = max(512 * int(np.asarray(lv.bricks).reshape(-1, 3).shape[0]) for lv in self.levels)
+            rec = autotune.choose(storage, nbins, nvox)
+            kw["iter_kernel"] = rec["iter_kernel"] if rec else "paired"
+            self.use_graph = bool(rec and rec.get("graph"))
+        self.params = make_params(nbins=nbins, storage=storage, **kw)
         self.handle = tgv_create_domain(self.levels, self.params, stream)
 
     def close(self):
@@ -357,6 +365,8 @@ class Domain:
         tgv_accumulate_depthmaps(self.handle, level, cams, depth, votes)
 
     def solve(self, level, iterations, energy=False):
+        if self.use_graph:
+            return tgv_solve_graph(self.handle, level, iterations, energy)
         return tgv_solve(self.handle, level, iterations, energy)
 
     def energy(self, level=0):

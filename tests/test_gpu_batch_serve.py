@@ -195,3 +195,21 @@ def test_request_stream_with_arrivals_matches_solo_runs():
     for srv in servers.values():
         assert srv.running == 0 and srv.free_bricks == cap
         srv.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
+    from paper_2107_14790_b300 import autotune
+    monkeypatch.setenv("TGV_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(autotune, "SIZE_CLASSES", [(1 << 16, 16), (1 << 62, 24)])
+    rec = autotune.tune("fp32", 10, 0)
+    assert rec["iter_kernel"] in autotune.FORMS and len(rec["candidates"]) == 6
+    assert rec["us_per_iteration"] == min(rec["candidates"].values())
+    assert autotune.choose("fp32", 10, 1000, allow_tuning=False) == rec  # cached
+    # a domain built with the tuned choice gives the same result as any fixed form
+    sp = chunks(47, 1, 8, 8)[0]
+    with tgv.Domain([sp.domain], nbins=10, stream=torch.cuda.Stream().cuda_stream, iter_kernel="auto") as dom:
+        dom.set_histograms(0, sp.hist)
+        dom.solve(0, 9)
+        dom.solve(0, 9)
+        u = dom.field(0, "u")[:, 0]
+    np.testing.assert_array_equal(u, solve_alone(sp, 18, iter_kernel=rec["iter_kernel"]))
