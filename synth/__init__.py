@@ -24,6 +24,7 @@ from .scenes import (  # noqa: F401
     chunk_workload,
     chunk_histogram,
     synthetic_votes_torch,
+    multilevel_scene,
     ChunkSpec,
     CONFIG_SEEDS,
 )

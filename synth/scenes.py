@@ -508,3 +508,229 @@ def chunk_histogram(spec: "ChunkSpec", device):
     m = spec.meta
     return synthetic_votes_torch(chunk_heights(m["terrain"], spec.domain.bricks, spec.domain.h, device), spec.nbins,
                                  m["vote_seed"], m["views"])
+
+
+# --------------------------------------------------------------------------- multi-level scene
+@dataclass
+class Blob:
+    """Union of ellipsoids (centre, rotation, semi-axes) and tori (centre, axis, R, r)."""
+    ell_c: np.ndarray  # (ne, 3)
+    ell_q: np.ndarray  # (ne, 3, 3) columns = local axes
+    ell_a: np.ndarray  # (ne, 3)
+    tor_c: np.ndarray  # (nt, 3)
+    tor_n: np.ndarray  # (nt, 3)
+    tor_R: np.ndarray  # (nt,)
+    tor_r: np.ndarray  # (nt,)
+
+    @property
+    def bound(self):
+        lo = np.minimum((self.ell_c - self.ell_a.max(1, keepdims=True)).min(0),
+                        (self.tor_c - (self.tor_R + self.tor_r)[:, None]).min(0))
+        hi = np.maximum((self.ell_c + self.ell_a.max(1, keepdims=True)).max(0),
+                        (self.tor_c + (self.tor_R + self.tor_r)[:, None]).max(0))
+        return lo, hi
+
+    def sdf(self, p, xp=np):
+        """Approximate signed distance (exact for the tori, the usual scaled-sphere bound for ellipsoids)."""
+        d = None
+        for k in range(self.ell_c.shape[0]):
+            q = (p - self.ell_c[k]) @ self.ell_q[k] if xp is np else (p - xp.as_tensor(self.ell_c[k], device=p.device)) @ xp.as_tensor(self.ell_q[k], device=p.device)
+            a = self.ell_a[k]
+            a_t = a if xp is np else xp.as_tensor(a, device=p.device)
+            k0 = (((q / a_t) ** 2).sum(-1)) ** 0.5
+            k1 = (((q / a_t ** 2) ** 2).sum(-1)) ** 0.5
+            e = k0 * (k0 - 1.0) / (k1 + 1e-12)
+            d = e if d is None else (xp.minimum(d, e))
+        for k in range(self.tor_c.shape[0]):
+            c = self.tor_c[k] if xp is np else xp.as_tensor(self.tor_c[k], device=p.device)
+            n = self.tor_n[k] if xp is np else xp.as_tensor(self.tor_n[k], device=p.device)
+            x = p - c
+            h = (x * n).sum(-1)
+            perp = ((x * x).sum(-1) - h * h).clip(0) ** 0.5 if xp is np else (((x * x).sum(-1) - h * h).clamp(min=0)) ** 0.5
+            e = ((perp - self.tor_R[k]) ** 2 + h * h) ** 0.5 - self.tor_r[k]
+            d = xp.minimum(d, e)
+        return d
+
+
+def make_blob(rng: np.random.Generator, centre: np.ndarray, radius: float) -> Blob:
+    def rot():
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        return q
+    ne, nt = 5, 3
+    ell_c = centre + rng.uniform(-0.35, 0.35, size=(ne, 3)) * radius
+    ell_q = np.stack([rot() for _ in range(ne)])
+    ell_a = rng.uniform(0.25, 0.6, size=(ne, 3)) * radius
+    tor_c = centre + rng.uniform(-0.3, 0.3, size=(nt, 3)) * radius
+    tor_n = rng.normal(size=(nt, 3))
+    tor_n /= np.linalg.norm(tor_n, axis=1, keepdims=True)
+    tor_R = rng.uniform(0.3, 0.5, size=nt) * radius
+    tor_r = rng.uniform(0.06, 0.12, size=nt) * radius
+    return Blob(ell_c, ell_q, ell_a, tor_c, tor_n, tor_R, tor_r)
+
+
+def _blob_hits_torch(blob: Blob, C, d, step_floor: float, device):
+    """First hit parameter of rays C + t d with the blob (inf where none)."""
+    torch = _torch()
+    n = d.shape[0]
+    inf = torch.full((n,), float("inf"), dtype=torch.float64, device=device)
+    t_best = inf.clone()
+    for k in range(blob.ell_c.shape[0]):  # ellipsoids: unit-sphere intersection in local frame
+        Q = torch.as_tensor(blob.ell_q[k], dtype=torch.float64, device=device)
+        a = torch.as_tensor(blob.ell_a[k], dtype=torch.float64, device=device)
+        c = torch.as_tensor(blob.ell_c[k], dtype=torch.float64, device=device)
+        o2 = ((C - c) @ Q) / a
+        d2 = (d @ Q) / a
+        A = (d2 * d2).sum(-1)
+        B = (o2 * d2).sum(-1)
+        Cc = (o2 * o2).sum(-1) - 1.0
+        disc = B * B - A * Cc
+        ok = disc >= 0
+        t = (-B - torch.sqrt(disc.clamp(min=0))) / A
+        t = torch.where(ok & (t > 0), t, inf)
+        t_best = torch.minimum(t_best, t)
+    # tori: sphere tracing of the exact distance, started at the bounding sphere
+    for k in range(blob.tor_c.shape[0]):
+        c = torch.as_tensor(blob.tor_c[k], dtype=torch.float64, device=device)
+        nrm = torch.as_tensor(blob.tor_n[k], dtype=torch.float64, device=device)
+        R, r = float(blob.tor_R[k]), float(blob.tor_r[k])
+        dn = torch.sqrt((d * d).sum(-1))
+        oc = C - c
+        bb = (oc * d).sum(-1) / dn
+        cc = (oc * oc).sum(-1) - (R + r) ** 2
+        disc = bb * bb - cc
+        t = torch.where(disc > 0, (-bb - torch.sqrt(disc.clamp(min=0))).clamp(min=0) / dn, inf)
+        idx = torch.nonzero(torch.isfinite(t)).squeeze(1)
+        tt = t[idx]
+        hit = torch.zeros(idx.shape[0], dtype=torch.bool, device=device)
+        for _ in range(200):
+            p = C[idx] + tt[:, None] * d[idx]
+            x = p - c
+            h = (x * nrm).sum(-1)
+            perp = torch.sqrt(((x * x).sum(-1) - h * h).clamp(min=0))
+            sd = torch.sqrt((perp - R) ** 2 + h * h) - r
+            hit = hit | (sd < 1e-7)
+            tt = torch.where(hit, tt, tt + sd / dn[idx])
+            if bool(hit.all()):
+                break
+        far = (~hit) | (tt > t_best[idx])
+        t_best[idx] = torch.where(far, t_best[idx], tt)
+    return t_best
+
+
+def multilevel_scene(seed: int = CONFIG_SEEDS[3], n0: int = 1024, blob_radius_vox: float = 56.0,
+                     nmaps_aerial: int = 192, nmaps_ring: int = 64, res: int = 1024, nbins: int = 10,
+                     iterations: int = 200, noise_vox: float = 0.3, footprint: float = 0.75, device=None) -> dict:
+    """Sparse three-level brick domain: terrain at level 0 (voxel h0 = 1/n0 over the unit
+    square), a statue-like blob (5 ellipsoids + 3 tori, radius `blob_radius_vox` level-0
+    voxels) floating above it refined to level 2 (h0/4), and a level-1 (h0/2) transition
+    shell around the blob.  Active bricks of a level: brick centres within the band
+    |signed distance| <= eta + brick half-diagonal (+ a 2-brick dilation on level 1); the
+    frozen shell of levels 1 and 2: bricks face-adjacent to the level's active bricks.
+    Level 0 covers the central `footprint` x `footprint` part of the unit square.
+    Maps: `nmaps_aerial` over the terrain (nadir and oblique) and `nmaps_ring` on two rings
+    around the blob, all res x res; z-depth noise N(0, (noise_vox * h_level)^2) with h of the
+    finest level the map sees.
+    """
+    torch = _torch()
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    rng = np.random.default_rng(seed)
+    terrain = make_terrain(rng, nbox=0)
+    h0 = 1.0 / n0
+    hs = [h0, h0 / 2, h0 / 4]
+    top = terrain.base + float(np.sum(terrain.amp))
+    bc = np.array([0.5, 0.5, top + 1.6 * blob_radius_vox * h0])
+    blob = make_blob(rng, bc, blob_radius_vox * h0)
+    blo, bhi = blob.bound
+
+    def brick_centres(bricks, h):
+        return (bricks.astype(np.float64) * 8 + 4.0) * h
+
+    def terrain_sd(p):
+        """Vertical offset over the local slope: (z - H) / sqrt(1 + |grad H|^2)."""
+        gz = terrain.height(p[:, 0], p[:, 1])
+        e = 1e-5
+        gx = (terrain.height(p[:, 0] + e, p[:, 1]) - terrain.height(p[:, 0] - e, p[:, 1])) / (2 * e)
+        gy = (terrain.height(p[:, 0], p[:, 1] + e) - terrain.height(p[:, 0], p[:, 1] - e)) / (2 * e)
+        return (p[:, 2] - gz) / np.sqrt(1.0 + gx * gx + gy * gy)
+
+    # level 0: terrain band over the unit square, plus the blob band at the coarse level
+    nb0 = n0 // 8
+    f0 = int(round(nb0 * (1.0 - footprint) / 2.0))
+    nbf = nb0 - 2 * f0
+    band0 = (9.0 + 4.0 * np.sqrt(3.0)) * h0
+    zlo = int(np.floor((terrain.base - float(np.sum(terrain.amp)) - band0) / (8 * h0))) - 1
+    zhi = int(np.ceil((bhi[2] + band0) / (8 * h0))) + 1
+    cand = dense_bricks(nbf, nbf, zhi - zlo, offset=(f0, f0, zlo))
+    cc = brick_centres(cand, h0)
+    sd = np.minimum(np.abs(terrain_sd(cc)), np.abs(blob.sdf(cc)))
+    lv0 = cand[sd <= band0]
+    levels = [lv0]
+    # levels 1 and 2: bricks in the blob's bounding box (dilated) near the blob surface
+    for l, dil in ((1, 2), (2, 0)):
+        h = hs[l]
+        band = (9.0 + 4.0 * np.sqrt(3.0)) * h + dil * 8 * h
+        lo = np.floor((blo - band) / (8 * h)).astype(int) - 1
+        hi = np.ceil((bhi + band) / (8 * h)).astype(int) + 1
+        cand = dense_bricks(*(hi - lo), offset=tuple(lo))
+        cc = brick_centres(cand, h)
+        levels.append(cand[np.abs(blob.sdf(cc)) <= band])
+    descs = []
+    for l, act in enumerate(levels):
+        frozen = None
+        if l > 0:
+            s = {tuple(x) for x in act.tolist()}
+            fro = set()
+            for x in s:
+                for dd in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    y = (x[0] + dd[0], x[1] + dd[1], x[2] + dd[2])
+                    if y not in s:
+                        fro.add(y)
+            frozen = np.array(sorted(fro), np.int32).reshape(-1, 3)
+        descs.append(DomainDesc(np.zeros(3), hs[l], act.astype(np.int32), frozen=frozen))
+    # cameras
+    cams: List[Camera] = []
+    fxa = pinhole_intrinsics(res, res, 40.0)
+    na = nmaps_aerial
+    side = int(np.ceil(np.sqrt(max(1, na // 3))))
+    for k in range(na):
+        if k % 3 == 0:  # nadir on a grid
+            g = k // 3
+            gx, gy = g % side, (g // side) % side
+            C = np.array([(gx + 0.5) / side, (gy + 0.5) / side, 1.5])
+            cams.append(Camera(*fxa, look_at(C, C - np.array([0, 0, 1.0]), up=(0, 1, 0)), C, res, res))
+        else:  # oblique, 40 degrees, azimuth cycling
+            az = 2 * np.pi * rng.random()
+            T = np.array([rng.uniform(0.1, 0.9), rng.uniform(0.1, 0.9), terrain.base])
+            off = 1.2 * np.tan(np.radians(40.0))
+            C = T + np.array([-np.cos(az) * off, -np.sin(az) * off, 1.2])
+            cams.append(Camera(*fxa, look_at(C, T), C, res, res))
+    fxr = pinhole_intrinsics(res, res, 35.0)
+    rb = float(np.max(bhi - blo))
+    for k in range(nmaps_ring):
+        az = 2 * np.pi * k / max(1, nmaps_ring // 2)
+        el = np.radians(25.0 if k % 2 == 0 else 55.0)
+        dist = 2.2 * rb
+        C = bc + dist * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        cams.append(Camera(*fxr, look_at(C, bc), C, res, res))
+    # ray casting: terrain and blob, nearest hit
+    depths = []
+    for k0 in range(0, len(cams), 16):
+        batch = cams[k0:k0 + 16]
+        t_ter = _terrain_depth_torch(terrain, batch, step=hs[0], device=device)
+        d = torch.cat([torch.as_tensor(c.ray_directions().reshape(-1, 3), dtype=torch.float64) for c in batch]).to(device)
+        C = torch.cat([torch.as_tensor(np.asarray(c.C, np.float64)[None, :].repeat(c.width * c.height, 0))
+                       for c in batch]).to(device)
+        t_blob = _blob_hits_torch(blob, C, d, hs[2], device).cpu().numpy()
+        o = 0
+        for c, tt in zip(batch, t_ter):
+            tb = t_blob[o:o + c.width * c.height].reshape(c.height, c.width)
+            o += c.width * c.height
+            t = np.where(np.isnan(tt), tb, np.minimum(np.nan_to_num(tt, nan=np.inf), tb))
+            t = np.where(np.isfinite(t), t, np.nan)
+            valid = np.isfinite(t)
+            t = t + rng.normal(0.0, noise_vox * hs[2], size=t.shape)
+            t[~valid] = np.nan
+            depths.append(t.astype(np.float32))
+    return dict(levels=descs, cameras=cams, depths=depths, nbins=nbins, iterations=iterations,
+                terrain=terrain, blob=blob, h=hs, seed=seed)
