@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="64^3 sphere case instead of the 256^3 terrain")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--iter-kernel", default="paired", choices=["paired", "pipelined", "one_brick_per_cta"])
+    ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel"],
@@ -162,7 +163,7 @@ def run_ours(args, cfg):
         depth_dev = depth_host.to(f"cuda:{local}", non_blocking=True)
     stream.synchronize()
     dom = tgv.Domain([sc.domain], nbins=nbins, storage=args.storage, stream=stream.cuda_stream,
-                     iter_kernel=args.iter_kernel)
+                     iter_kernel=args.iter_kernel, x_run=args.x_run)
     nvox = dom.voxels(0)
     iters, ce = cfg["iterations"], cfg["check_every"]
     blocks = [ce] * (iters // ce) + ([iters % ce] if iters % ce else [])
@@ -349,7 +350,7 @@ def run_profile_case(args):
     hist = synth.random_histograms(np.random.default_rng(7), desc.nvox, 10, max_count=20)
     stream = torch.cuda.Stream()
     dom = tgv.Domain([desc], nbins=10, storage=args.storage, stream=stream.cuda_stream,
-                     iter_kernel=args.iter_kernel)
+                     iter_kernel=args.iter_kernel, x_run=args.x_run)
     dom.set_histograms(0, hist)
     tgv.tgv_solve(dom.handle, 0, 6, False)
     tgv.tgv_solve(dom.handle, 0, 4, False)

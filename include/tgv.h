@@ -93,7 +93,7 @@ typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
  * Defaults (tgv_default_params): nbins 8 (Alg. 1), alpha1 1, alpha0 2, lambda 1,
  * tau = sigma = 0.2 (tau*sigma*24 < 1: ||K||^2 <= 24 for the forward/backward
  * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2,
- * paired iteration kernel. */
+ * paired iteration kernel, x_run 0 (automatic). */
 typedef struct {
     int32_t nbins;       /* histogram bins, 2..16 */
     float alpha1;        /* weight of |grad u - v| */
@@ -106,6 +106,10 @@ typedef struct {
     int32_t centres;     /* TGV_CENTRES_* */
     float box_v;         /* bound B_v on |v_a| used by the duality gap */
     int32_t iter_kernel; /* TGV_ITER_* form of the fused iteration kernel */
+    int32_t x_run;       /* PAIRED form: work items per run, 0..64.  A CTA takes runs of
+                          * consecutive items, so x-neighbouring bricks pass their face
+                          * duals through shared memory; results do not depend on it.
+                          * 0 = chosen from the item and SM counts, 1 = no runs. */
 } tgv_params;
 
 /* One level of a domain (all arrays host memory, copied at creation).
@@ -252,6 +256,22 @@ TGV_API int64_t tgv_level_voxels(const tgv_domain* d, int32_t level);
 
 /* Number of kernels this library launched on the domain so far. */
 TGV_API int64_t tgv_launch_count(const tgv_domain* d);
+
+/* Run length the paired iteration kernel chooses when tgv_params.x_run is 0
+ * (host only; no device work).  The iteration is Eq. 2-3 whatever the choice;
+ * it only sets how many consecutive work items a CTA takes in a row, trading
+ * x-face halo work saved by hand-overs against load balance and the L2 reuse
+ * of neighbours' face layers (a cost model over the level's links).
+ *  nbr:   host, nbricks x 12 neighbour rows in the library's layout (faces +x,
+ *         -x, +y, -y, +z, -z, then the six mixed-sign edges; -1 none, >= nbricks
+ *         frozen), as built for the level;
+ *  work:  host list of nwork distinct active bricks, or NULL for all bricks in order;
+ *  slots: resident CTAs of the kernel (CTAs per SM x SMs), > 0;
+ *  storage: TGV_STORAGE_*.
+ * Writes 1..16 to *run_length.  TGV_ERR_INVALID_ARG on bad sizes or a work
+ * list entry that is out of range or repeated. */
+TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nbricks, const int32_t* work, int64_t nwork,
+                                       int64_t slots, int32_t storage, int32_t* run_length);
 
 /* ---------------------------------------------------------------------------
  * Energy / gap without any allocation.

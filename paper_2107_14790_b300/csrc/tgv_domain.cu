@@ -417,6 +417,7 @@ tgv_status build_level(tgv_domain* d, const tgv_level_desc& desc, TgvLevel& L)
         e = cudaMemcpyAsync(L.coords_dev, L.coords.data(), L.coords.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are about to go away
     if ((st = tgv_cuda_check(d, e, "level initialisation")) != TGV_OK) return st;
+    L.nbr_host = std::move(nbr);
     // frozen values (set B): constant u and v, mirrored into both ping-pong copies
     if (nf > 0 && desc.frozen_u) {
         const size_t n = (size_t)nf * TGV_BVOX;
@@ -457,6 +458,7 @@ tgv_status tgv_create_arena(const tgv_params* prm, cudaStream_t stream, int64_t 
     if (st == TGV_OK) st = tgv_cuda_check(d, cudaMemsetAsync(d->err, 0, sizeof(int), d->stream), "error flag");
     d->levels.resize(1);
     if (st == TGV_OK) st = alloc_level(d, d->levels[0], cap_active, cap_frozen);
+    if (st == TGV_OK) d->levels[0].nbr_host.assign((size_t)cap_active * TGV_NNBR, -1);
     if (st == TGV_OK) st = tgv_cuda_check(d, cudaStreamSynchronize(d->stream), "arena initialisation");
     if (st != TGV_OK) {
         tgv_destroy_domain(d);
@@ -510,6 +512,7 @@ tgv_status tgv_default_params(tgv_params* out)
     out->centres = TGV_CENTRES_ENDPOINTS;
     out->box_v = 2.0f;
     out->iter_kernel = TGV_ITER_PAIRED;
+    out->x_run = 0;
     return TGV_OK;
 }
 
@@ -525,6 +528,7 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
     if (prm->iter_kernel != TGV_ITER_PIPELINED && prm->iter_kernel != TGV_ITER_ONE_BRICK_PER_CTA &&
         prm->iter_kernel != TGV_ITER_PAIRED)
         return TGV_ERR_INVALID_ARG;
+    if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
     if (!(prm->alpha1 > 0.0f) || !(prm->alpha0 > 0.0f) || !(prm->lambda >= 0.0f) || !(prm->tau > 0.0f) ||
         !(prm->sigma > 0.0f) || !(prm->box_v > 0.0f))
         return TGV_ERR_INVALID_ARG;
@@ -859,6 +863,7 @@ tgv_status tgv_set_work_list(tgv_domain* d, int32_t level, const int32_t* bricks
         }
         L->work = nullptr;
         L->nwork = L->work_cap = 0;
+        L->work_host.clear();
         return TGV_OK;
     }
     std::vector<int32_t> host((size_t)n);
@@ -886,6 +891,7 @@ tgv_status tgv_set_work_list(tgv_domain* d, int32_t level, const int32_t* bricks
     if (e != cudaSuccess) return tgv_cuda_check(d, e, "work list upload");
     L->nwork = n;
     L->work_gen++;
+    L->work_host = std::move(host);
     return TGV_OK;
 }
 

@@ -88,6 +88,12 @@ struct TgvLevel {
     std::vector<Graph> graphs;
     int cur = 0;               // ping-pong copy holding the current ubar/vbar/p/q
     uint64_t max_votes = 0;    // upper bound on any voxel's total count
+    // host copies of nbr (nb rows) and of the work list, for the paired kernel's run-length choice
+    std::vector<int32_t> nbr_host;
+    std::vector<int32_t> work_host;
+    int xrun = 0;              // cached automatic run length, valid for (xrun_gen, xrun_slots)
+    uint64_t xrun_gen = 0;
+    int64_t xrun_slots = 0;
 };
 
 // Arguments of one fused primal-dual iteration over the active bricks of a level.

@@ -1,26 +1,41 @@
 // Pipelined, paired form of the fused TGV primal-dual iteration (the
 // arithmetic of tgv_iter_kernel in tgv_solve.cu: Eq. 2-3, Sec. 3.2).
 //
-// Persistent CTAs of 256 threads walk the active bricks with a grid stride;
-// each thread owns the x-adjacent voxel pair (2j, 2j+1) of one row of the
-// brick in hand, so shared-memory and global accesses are 64-bit (two FP32 or
-// two 16-bit values) and the x-neighbour inside the pair comes from registers.
-// Each brick's whole state -- u, ubar, v, vbar, p, q and the packed
-// histogram, contiguous per brick -- arrives in shared memory through seven
-// cp.async.bulk copies completed on an mbarrier, double-buffered: while brick
-// i is computed, brick i + grid is in flight.
+// Persistent CTAs of 256 threads; each thread owns the x-adjacent voxel pair
+// (2j, 2j+1) of one row of the brick in hand, so shared-memory and global
+// accesses are 64-bit (two FP32 or two 16-bit values) and the x-neighbour
+// inside the pair comes from registers.  Each brick's whole state -- u, ubar,
+// v, vbar, p, q and the packed histogram, contiguous per brick -- arrives in
+// shared memory through seven cp.async.bulk copies completed on an mbarrier,
+// double-buffered: while one brick is computed, the next is in flight.
 //
-// Halo duals (new p on the three -face layers, new q on the three +face
-// layers, which neighbouring bricks own) are recomputed here; the 384 halo
-// voxels split into exactly one warp-uniform task per thread (single voxels on
-// the x faces, pairs on the y and z faces), and their inputs are loaded into
-// registers before the CTA waits for its stage.
+// Work items are taken in runs of R consecutive items (run r by CTA r mod
+// grid).  Consecutive items of a run are usually x-neighbouring bricks, and
+// then the two x-face halos pass between them on chip instead of being
+// recomputed from scattered (stride-8) global loads:
+//   * the new p_x on the x = 7 layer of brick i is what brick i+1 needs on its
+//     -x face: phase A of brick i writes it straight into brick i+1's halo slot;
+//   * brick i needs the new q on the x = 0 layer of brick i+1, which only
+//     phase A of brick i+1 produces, after phase B of brick i: the v update of
+//     brick i's x = 7 voxels leaves the +x term out (it is added last), parks
+//     the partial sum, and phase A of brick i+1 completes and stores it.
+// The dual updates use explicitly rounded arithmetic, so a dual recomputed as
+// a halo equals the owner's bit for bit and results do not depend on R, the
+// grid size or the order of the work items.
+//
+// The other halo duals (new p on the -y/-z face layers, new q on the +y/+z
+// layers, and the x faces when the neighbour is not the adjacent item) are
+// recomputed here; the 384 halo voxels split into exactly one warp-uniform task
+// per thread (single voxels on the x faces, pairs on the y and z faces), and
+// their inputs are loaded into registers before the CTA waits for its stage.
 //
 // The bin count is a template parameter for 8, 10 and 12 bins (0 = read at
-// run time).  Every mbarrier wait is bounded
-// (about a second); a CTA that gives up sets the domain's error flag, waits
-// (bounded) for its copies in flight and returns.
+// run time).  Every mbarrier wait is bounded (about a second); a CTA that
+// gives up sets the domain's error flag, waits (bounded) for its copies in
+// flight and returns.
 #include <math.h>
+
+#include <vector>
 
 #include "tgv_async.cuh"
 #include "tgv_internal.cuh"
@@ -56,65 +71,47 @@ __device__ __forceinline__ void stf2(float* p, float2 v) { *(float2*)p = v; }
 
 __device__ __forceinline__ int qidx(int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); }
 
-// p <- proj(p_old + sigma (g - vb)) and q <- proj(q_old + sigma E) for one voxel
-__device__ __forceinline__ void dual_update(const float g[3], const float vb[3], const float dm[3][3], float pn[3],
-                                            float qn[6], float sigma, float alpha1, float a1sq, float alpha0,
-                                            float a0sq)
+// Dual updates of one voxel, every operation rounded explicitly (no contraction
+// choices left to the compiler): the owner of a voxel and a neighbour that
+// recomputes it as a halo get the same bits from the same inputs.
+// p <- proj_{|.| <= alpha1}(p + sigma (g - vb)),  g = grad ubar, vb = vbar
+__device__ __forceinline__ void upd_p(float p[3], const float g[3], const float vb[3], float sigma, float alpha1,
+                                      float a1sq)
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) pn[c] += sigma * (g[c] - vb[c]);
-    const float pn2 = pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2];
-    if (pn2 > a1sq) {
-        const float s = alpha1 * rsqrtf(pn2);
-        pn[0] *= s;
-        pn[1] *= s;
-        pn[2] *= s;
-    }
-    qn[0] += sigma * dm[0][0];
-    qn[1] += sigma * dm[1][1];
-    qn[2] += sigma * dm[2][2];
-    qn[3] += sigma * (0.5f * (dm[0][1] + dm[1][0]));
-    qn[4] += sigma * (0.5f * (dm[0][2] + dm[2][0]));
-    qn[5] += sigma * (0.5f * (dm[1][2] + dm[2][1]));
-    const float qn2 = qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + 2.0f * (qn[3] * qn[3] + qn[4] * qn[4] + qn[5] * qn[5]);
-    if (qn2 > a0sq) {
-        const float s = alpha0 * rsqrtf(qn2);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) qn[c] *= s;
-    }
-}
-
-__device__ __forceinline__ void proj_p(float p[3], float alpha1, float a1sq)
-{
-    const float n2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    for (int c = 0; c < 3; ++c) p[c] = __fmaf_rn(sigma, __fsub_rn(g[c], vb[c]), p[c]);
+    const float n2 = __fmaf_rn(p[2], p[2], __fmaf_rn(p[1], p[1], __fmul_rn(p[0], p[0])));
     if (n2 > a1sq) {
-        const float s = alpha1 * rsqrtf(n2);
-        p[0] *= s;
-        p[1] *= s;
-        p[2] *= s;
-    }
-}
-
-__device__ __forceinline__ void proj_q(float q[6], float alpha0, float a0sq)
-{
-    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 2.0f * (q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
-    if (n2 > a0sq) {
-        const float s = alpha0 * rsqrtf(n2);
+        const float s = __fmul_rn(alpha1, rsqrtf(n2));
 #pragma unroll
-        for (int c = 0; c < 6; ++c) q[c] *= s;
+        for (int c = 0; c < 3; ++c) p[c] = __fmul_rn(p[c], s);
     }
 }
 
-__device__ __forceinline__ void sym6(const float dm[3][3], float e[6])
+// q <- proj_{|.|_F <= alpha0}(q + sigma E(vbar)); dm[a][c] = backward difference of vbar_c along a
+__device__ __forceinline__ void upd_q(float q[6], const float dm[3][3], float sigma, float alpha0, float a0sq)
 {
-    e[0] = dm[0][0];
-    e[1] = dm[1][1];
-    e[2] = dm[2][2];
-    e[3] = 0.5f * (dm[0][1] + dm[1][0]);
-    e[4] = 0.5f * (dm[0][2] + dm[2][0]);
-    e[5] = 0.5f * (dm[1][2] + dm[2][1]);
+    q[0] = __fmaf_rn(sigma, dm[0][0], q[0]);
+    q[1] = __fmaf_rn(sigma, dm[1][1], q[1]);
+    q[2] = __fmaf_rn(sigma, dm[2][2], q[2]);
+    q[3] = __fmaf_rn(sigma, __fmul_rn(0.5f, __fadd_rn(dm[0][1], dm[1][0])), q[3]);
+    q[4] = __fmaf_rn(sigma, __fmul_rn(0.5f, __fadd_rn(dm[0][2], dm[2][0])), q[4]);
+    q[5] = __fmaf_rn(sigma, __fmul_rn(0.5f, __fadd_rn(dm[1][2], dm[2][1])), q[5]);
+    const float off = __fmaf_rn(q[5], q[5], __fmaf_rn(q[4], q[4], __fmul_rn(q[3], q[3])));
+    const float n2 = __fmaf_rn(2.0f, off, __fmaf_rn(q[2], q[2], __fmaf_rn(q[1], q[1], __fmul_rn(q[0], q[0]))));
+    if (n2 > a0sq) {
+        const float s = __fmul_rn(alpha0, rsqrtf(n2));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] = __fmul_rn(q[c], s);
+    }
 }
 
+// v <- v + tau (p + div2 q) and its over-relaxation 2 v_new - v_old
+__device__ __forceinline__ float vnew(float v0, float p, float d2, float tau)
+{
+    return __fmaf_rn(tau, __fadd_rn(p, d2), v0);
+}
+__device__ __forceinline__ float vbar_of(float v1, float v0) { return __fsub_rn(__fmul_rn(2.0f, v1), v0); }
 
 // new p for the halo pair (2hj, 7, hw) / (2hj, hw, 7) on the -AX face (AX = 1: y, 2: z)
 template <int AX>
@@ -132,14 +129,10 @@ __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const f
     gb[AX] = own.y - h[1];
     ga[OA] = (hm & 2u) ? h[4] - h[0] : 0.0f;
     gb[OA] = (hm & 2u) ? h[5] - h[1] : 0.0f;
-    float pa[3], pb[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        pa[c] = h[12 + 2 * c] + sigma * (ga[c] - h[6 + 2 * c]);
-        pb[c] = h[13 + 2 * c] + sigma * (gb[c] - h[7 + 2 * c]);
-    }
-    proj_p(pa, alpha1, a1sq);
-    proj_p(pb, alpha1, a1sq);
+    float pa[3] = {h[12], h[14], h[16]}, pb[3] = {h[13], h[15], h[17]};
+    const float va[3] = {h[6], h[8], h[10]}, vb[3] = {h[7], h[9], h[11]};
+    upd_p(pa, ga, va, sigma, alpha1, a1sq);
+    upd_p(pb, gb, vb, sigma, alpha1, a1sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
     for (int c = 0; c < 3; ++c) stf2(hal_p + c * 192 + AX * 64 + fi, make_float2(pa[c], pb[c]));
@@ -166,15 +159,13 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
         dmb[OA][c] = (hm & 2u) ? vbv - h[13 + 2 * c] : 0.0f;
     }
     float ea[6], eb[6];
-    sym6(dma, ea);
-    sym6(dmb, eb);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        ea[c] = h[18 + 2 * c] + sigma * ea[c];
-        eb[c] = h[19 + 2 * c] + sigma * eb[c];
+        ea[c] = h[18 + 2 * c];
+        eb[c] = h[19 + 2 * c];
     }
-    proj_q(ea, alpha0, a0sq);
-    proj_q(eb, alpha0, a0sq);
+    upd_q(ea, dma, sigma, alpha0, a0sq);
+    upd_q(eb, dmb, sigma, alpha0, a0sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
     for (int c = 0; c < 6; ++c) stf2(hal_q + c * 192 + AX * 64 + fi, make_float2(ea[c], eb[c]));
@@ -190,6 +181,7 @@ struct PairArgs {
     uint32_t stage_bytes, tx_bytes;
     uint32_t pn_bytes;                 // bytes of one own-new-dual buffer (0 when it aliases the stage)
     uint32_t off_pn, off_hal, off_nbr, off_bar;
+    uint32_t xrun;                     // work items per run (>= 1)
 };
 
 // Per-thread view of one CTA: thread t owns the voxel pair (2j, y, z), (2j+1, y, z).
@@ -203,6 +195,12 @@ struct PairArgs {
 //   [224,256) new q, +z face, pair (2j, y, 0), (2j+1, y, 0)
 // Halo arrays of a stage: hal_p[c][a*64 + face index] (3 x 192 floats), then
 // hal_q[c][a*64 + face index] (6 x 192); face index y+8z (a = x), x+8z (a = y), x+8y (a = z).
+// Within a run ("hand-over" from brick i to the adjacent item i+1, its +x neighbour):
+//   * task 0 of brick i+1 is skipped: phase A of brick i writes hal_p[0][y+8z] of
+//     brick i+1's stage from its own new p;
+//   * task 3 of brick i is skipped: phase B of brick i parks the partial div2 q sum of
+//     its x = 7 voxels in hal_q[qidx(0,c)][y+8z] of its own stage (the slots task 3
+//     would have filled); phase A of brick i+1 adds its new q and stores v, vbar.
 template <typename S, int NB>
 struct PairCta {
     using PS = Pair<S>;
@@ -278,7 +276,9 @@ struct PairCta {
     }
 
     // ---- global loads a brick's phase A needs besides its stage (own boundary neighbours, halo inputs)
-    __device__ __forceinline__ void load_inputs(const int* nrow)
+    // skip0 / skip3: the -x p halo comes from the previous item, the +x q halo is
+    // replaced by the hand-over to the next item (see above)
+    __device__ __forceinline__ void load_inputs(const int* nrow, bool skip0, bool skip3)
     {
         const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
         const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
@@ -313,6 +313,7 @@ struct PairCta {
             const int a = task % 3;
             hn = task < 3 ? nrow[nb_minus(a)] : nrow[nb_plus(a)];
             if (hn >= nbk) hn = -1;  // frozen: no dual variables there
+            if ((task == 0 && skip0) || (task == 3 && skip3)) hn = -1;
         }
         if (hn < 0) return;
         const uint32_t nb0 = (size_t)hn * TGV_BVOX;
@@ -459,7 +460,10 @@ struct PairCta {
 
     // ---- phase A of the brick in stage s: new p, q at the own pair (into pn_own / qn_own)
     // and the halo duals (into hal_p / hal_q).  Returns the link bits phase B needs.
-    __device__ __forceinline__ uint32_t phase_a(int s, const int* nrow)
+    // from_prev: this brick is the +x neighbour and run successor of brick bprev, whose
+    // phase B parked the partial v update of its x = 7 voxels (completed here);
+    // to_next: the next item is this brick's +x neighbour (its -x halo p is written here).
+    __device__ __forceinline__ uint32_t phase_a(int s, const int* nrow, bool from_prev, bool to_next, uint32_t bprev)
     {
         const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
         const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
@@ -506,8 +510,10 @@ struct PairCta {
                 dm0[2][c] = bz ? vb0[c] - wz.x : 0.0f;
                 dm1[2][c] = bz ? vb1[c] - wz.y : 0.0f;
             }
-            dual_update(g0, vb0, dm0, pn0, qn0, sigma, alpha1, a1sq, alpha0, a0sq);
-            dual_update(g1, vb1, dm1, pn1, qn1, sigma, alpha1, a1sq, alpha0, a0sq);
+            upd_p(pn0, g0, vb0, sigma, alpha1, a1sq);
+            upd_p(pn1, g1, vb1, sigma, alpha1, a1sq);
+            upd_q(qn0, dm0, sigma, alpha0, a0sq);
+            upd_q(qn1, dm1, sigma, alpha0, a0sq);
         }
         // own old p / q were read above by this thread only; overwrite in place (FP32) or store
         float* pno = pn_own(s);
@@ -516,6 +522,27 @@ struct PairCta {
         for (int c = 0; c < 3; ++c) stf2(pno + c * 512 + l0, make_float2(pn0[c], pn1[c]));
 #pragma unroll
         for (int c = 0; c < 6; ++c) stf2(qno + c * 512 + l0, make_float2(qn0[c], qn1[c]));
+        // hand-over along the run
+        if (to_next && j == 3) hal_p(s ^ 1)[y + 8 * z] = pn1[0];
+        if (from_prev && j == 0) {
+            // brick bprev's voxel (7, y, z): its partial div2 q, its new p and old v are
+            // still in the other stage; add the x-forward term (this voxel's new q)
+            const int ps = s ^ 1;
+            const float* hq_prev = hal_q(ps);
+            const float* pn_prev = pn_own(ps);
+            const S* sv_prev = (const S*)(stage(ps) + O_V);
+            const uint32_t l7 = 7 + 8 * y + 64 * z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int qc = qidx(0, c);
+                const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qn0[qc]);
+                const float v0 = ld_s(sv_prev + c * 512 + l7);
+                const float v1 = vnew(v0, pn_prev[c * 512 + l7], d2, A.tau);
+                const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l7;
+                st_s(A.v + oi, v1);
+                st_s(A.vbar_out + oi, vbar_of(v1, v0));
+            }
+        }
 
         // halo duals
         float* hp = hal_p(s);
@@ -523,12 +550,11 @@ struct PairCta {
         if (hn >= 0) {
             if (task == 0) {  // p at (7, hy, hz) of the -x brick
                 const int hy = tk & 7, hz = tk >> 3;
-                float g[3] = {sub[8 * hy + 64 * hz] - h[0], (hm & 1u) ? h[2] - h[0] : 0.0f,
-                              (hm & 2u) ? h[4] - h[0] : 0.0f};
-                float pp[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) pp[c] = h[12 + 2 * c] + sigma * (g[c] - h[6 + 2 * c]);
-                proj_p(pp, alpha1, a1sq);
+                const float g[3] = {sub[8 * hy + 64 * hz] - h[0], (hm & 1u) ? h[2] - h[0] : 0.0f,
+                                    (hm & 2u) ? h[4] - h[0] : 0.0f};
+                float pp[3] = {h[12], h[14], h[16]};
+                const float vv[3] = {h[6], h[8], h[10]};
+                upd_p(pp, g, vv, sigma, alpha1, a1sq);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hp[c * 192 + tk] = pp[c];
             } else if (task == 1) {
@@ -546,10 +572,9 @@ struct PairCta {
                     dm[2][c] = (hm & 2u) ? h[2 * c] - h[12 + 2 * c] : 0.0f;
                 }
                 float e[6];
-                sym6(dm, e);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) e[c] = h[18 + 2 * c] + sigma * e[c];
-                proj_q(e, alpha0, a0sq);
+                for (int c = 0; c < 6; ++c) e[c] = h[18 + 2 * c];
+                upd_q(e, dm, sigma, alpha0, a0sq);
 #pragma unroll
                 for (int c = 0; c < 6; ++c) hq[c * 192 + tk] = e[c];
             } else if (task == 4) {
@@ -570,8 +595,10 @@ struct PairCta {
         return L;
     }
 
-    // ---- phase B of brick b in stage s: divergences, prox, over-relaxation, global stores
-    __device__ __forceinline__ void phase_b(int s, uint32_t b, uint32_t L) const
+    // ---- phase B of brick b in stage s: divergences, prox, over-relaxation, global stores.
+    // to_next: the next item is b's +x neighbour; the v update of the x = 7 voxels is
+    // parked without its x-forward div2 q term and completed by that item's phase A.
+    __device__ __forceinline__ void phase_b(int s, uint32_t b, uint32_t L, bool to_next) const
     {
         unsigned char* st = stage(s);
         const float* su = (const float*)(st + O_U);
@@ -598,6 +625,7 @@ struct PairCta {
         float d2a[3] = {0, 0, 0}, d2b[3] = {0, 0, 0};
         // x: voxel 0: forward = voxel 1, backward = (x0-1) or the -x brick;
         //    voxel 1: backward = voxel 0, forward = (x0+2) or the +x brick
+        // (voxel 1's x-forward div2 q term is added last, after y and z)
         d1a += pn0[0];
         if (L & 2u) d1a -= j > 0 ? pno[l0 - 1] : hp[y + 8 * z];
         if (L & 4u) d1b += pn1[0];
@@ -607,7 +635,6 @@ struct PairCta {
             const int qc = qidx(0, c);
             d2a[c] += qn1[qc];
             if (L & 1u) d2a[c] -= qn0[qc];
-            if (L & 8u) d2b[c] += j < 3 ? qno[qc * 512 + l0 + 2] : hq[qc * 192 + y + 8 * z];
             d2b[c] -= qn1[qc];
         }
         // y
@@ -693,13 +720,23 @@ struct PairCta {
         const size_t vi = (size_t)b * TGV_BVOX + l0;
         stf2(A.u + vi, make_float2(una, unb));
         stf2(A.ubar_out + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
+        const bool park = to_next && j == 3;  // uniform per warp row group; implies L & 8
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t oi = ((size_t)b * 3 + c) * TGV_BVOX + l0;
             const float2 v0 = PS::ld(sv + c * 512 + l0);
-            const float2 v1 = make_float2(v0.x + A.tau * (pn0[c] + d2a[c]), v0.y + A.tau * (pn1[c] + d2b[c]));
-            PS::st(A.v + oi, v1);
-            PS::st(A.vbar_out + oi, make_float2(2.0f * v1.x - v0.x, 2.0f * v1.y - v0.y));
+            const float v1a = vnew(v0.x, pn0[c], d2a[c], A.tau);
+            if (park) {
+                hal_q(s)[qidx(0, c) * 192 + y + 8 * z] = d2b[c];
+                st_s(A.v + oi, v1a);
+                st_s(A.vbar_out + oi, vbar_of(v1a, v0.x));
+            } else {
+                if (L & 8u) d2b[c] = __fadd_rn(d2b[c], j < 3 ? qno[qidx(0, c) * 512 + l0 + 2]
+                                                             : hq[qidx(0, c) * 192 + y + 8 * z]);
+                const float v1b = vnew(v0.y, pn1[c], d2b[c], A.tau);
+                PS::st(A.v + oi, make_float2(v1a, v1b));
+                PS::st(A.vbar_out + oi, make_float2(vbar_of(v1a, v0.x), vbar_of(v1b, v0.y)));
+            }
             PS::st(A.p_out + oi, make_float2(pn0[c], pn1[c]));
         }
 #pragma unroll
@@ -707,41 +744,58 @@ struct PairCta {
     }
 };
 
-// Software-pipelined over bricks: in one barrier interval a CTA finishes brick
-// b (phase B) and starts brick b + grid (its halo loads are issued first, so
-// their latency overlaps phase B; then phase A once its stage has landed).
+// Software-pipelined over the CTA's items (runs r = blockIdx.x + m * grid of R
+// consecutive items each): in one barrier interval a CTA finishes item i (phase
+// B) and starts the next item (its halo loads are issued first, so their
+// latency overlaps phase B; then phase A once its stage has landed).
 template <typename S, int NB>
 __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairArgs<S> P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     PairCta<S, NB> C(P, smem);
     const uint32_t G = gridDim.x;
+    const uint32_t R = P.xrun;
     const uint32_t nit = (uint32_t)P.it.nitems;
     const int32_t* work = P.it.work;
+    const int* nbr = P.it.nbr;
     auto brick = [&](uint32_t i) -> uint32_t { return work ? (uint32_t)work[i] : i; };
-    uint32_t it = blockIdx.x;  // work item in hand
+    // the CTA's item after i: i + 1 inside a run, else the start of its next run
+    auto next = [&](uint32_t i) -> uint32_t { return (i + 1) % R ? i + 1 : i + 1 + (G - 1) * R; };
+    uint32_t it = blockIdx.x * R;  // item in hand
+    if (it >= nit) return;
     uint64_t* bar = C.bar();
     const int t = C.t;
 
+    uint32_t itn = next(it);
+    uint32_t bcur = brick(it), bnext = itn < nit ? brick(itn) : 0u;
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     if (t < TGV_NNBR) {
-        C.nbr_row(0)[t] = P.it.nbr[brick(it) * TGV_NNBR + t];
-        if (it + G < nit) C.nbr_row(1)[t] = P.it.nbr[brick(it + G) * TGV_NNBR + t];
+        C.nbr_row(0)[t] = nbr[(size_t)bcur * TGV_NNBR + t];
+        if (itn < nit) C.nbr_row(1)[t] = nbr[(size_t)bnext * TGV_NNBR + t];
     }
     __syncthreads();
+    uint32_t pending = 0;  // stages with copies in flight (thread 0's view)
     if (t == 0) {
-        C.issue(0, brick(it));
-        if (it + G < nit) C.issue(1, brick(it + G));
+        C.issue(0, bcur);
+        pending = 1u;
+        if (itn < nit) {
+            C.issue(1, bnext);
+            pending |= 2u;
+        }
     }
     uint32_t parity = 0;
     bool bail = false;
     int s = 0;
-    // prologue: phase A of the first brick
-    C.load_inputs(C.nbr_row(0));
+    // hand-over from the item in hand to the next one: the next item follows in the
+    // same run and is this brick's +x neighbour (links are symmetric, so the next
+    // brick's -x neighbour is this one)
+    bool to_next = itn == it + 1 && itn < nit && C.nbr_row(0)[NB_PX] == (int)bnext;
+    // prologue: phase A of the first item
+    C.load_inputs(C.nbr_row(0), false, to_next);
     {
         const bool ok = mbar_wait_bounded(&bar[0], 0, P.wait_budget);
         if (__syncthreads_or(!ok)) bail = true;
@@ -749,47 +803,131 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
     uint32_t links = 0;
     if (!bail) {
         parity ^= 1u;
-        links = C.phase_a(0, C.nbr_row(0));
+        pending &= ~1u;
+        links = C.phase_a(0, C.nbr_row(0), false, to_next, 0u);
         __syncthreads();
     }
     while (!bail) {
-        const uint32_t itn = it + G;
         const int ns = s ^ 1;
+        const uint32_t itnn = itn < nit ? next(itn) : nit;
+        const uint32_t bnn = itnn < nit ? brick(itnn) : 0u;
+        bool next_to_next = false;
         uint32_t next_links = 0;
-        if (itn < nit) C.load_inputs(C.nbr_row(ns));
-        // the row of the brick in hand is no longer read: reuse it for item itn + G
-        if (t < TGV_NNBR && itn + G < nit) C.nbr_row(s)[t] = P.it.nbr[brick(itn + G) * TGV_NNBR + t];
-        C.phase_b(s, brick(it), links);
+        if (itn < nit) {
+            next_to_next = itnn == itn + 1 && itnn < nit && C.nbr_row(ns)[NB_PX] == (int)bnn;
+            C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
+        }
+        // the row of the item in hand is no longer read: reuse it for item itnn
+        if (t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
+        C.phase_b(s, bcur, links, to_next);
         if (itn < nit) {
             const bool ok = mbar_wait_bounded(&bar[ns], (parity >> ns) & 1u, P.wait_budget);
             if (__syncthreads_or(!ok)) {
                 bail = true;
-                it = itn;
-                s = ns;
                 break;
             }
             parity ^= 1u << ns;
-            next_links = C.phase_a(ns, C.nbr_row(ns));
+            pending &= ~(1u << ns);
+            next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
         }
-        __syncthreads();  // stage s and the phase A results of item itn are settled
-        if (t == 0 && it + 2 * G < nit) {
+        __syncthreads();  // stage s, the phase A results of item itn and the hand-over are settled
+        if (t == 0 && itnn < nit) {
             fence_proxy_async_smem();
-            C.issue(s, brick(it + 2 * G));
+            C.issue(s, bnn);
+            pending |= 1u << s;
         }
         if (itn >= nit) break;
         it = itn;
+        itn = itnn;
         s = ns;
         links = next_links;
+        bcur = bnext;
+        bnext = bnn;
+        to_next = next_to_next;
     }
     if (bail && t == 0) {
         atomicExch(P.err, 1);
-        // the stage being waited for (and, in the prologue, the second one) may still receive data
-        mbar_wait_bounded(&bar[s], (parity >> s) & 1u, P.wait_budget);
-        if (it + G < nit) mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, P.wait_budget);
+        // copies still in flight land before the CTA's shared memory is released
+        for (int k = 0; k < 2; ++k)
+            if (pending & (1u << k)) mbar_wait_bounded(&bar[k], (parity >> k) & 1u, P.wait_budget);
     }
 }
 
 namespace {
+
+// Items per run, chosen on the host from the level's links (cached per work list
+// and grid).  Estimated time of the slowest CTA for run length R:
+//   (items it takes) x (1 - f_int x interior + missed halo bytes / item bytes)
+// * interior: share of items with hand-overs on both x faces, which skip both
+//   x-face halo tasks (the slowest warps of phase A); f_int = 0.12 measured on
+//   dense blocks;
+// * missed halo bytes: item i is processed at step T(i) = (i / (G R)) R + i % R
+//   (G CTAs).  A halo read of the neighbour j hits L2 only when the neighbour's
+//   own stream is close in time: |T(j) - T(i)| x G items, with ~80 KB of traffic
+//   each, within the ~64 MB of L2 that keeps such data.  A miss costs the
+//   neighbour's face layer from DRAM: ~8 KB on a y face (rows of 32 B fetched in
+//   longer lines), ~2 KB on a z face, ~16 KB on an x face (a column touches
+//   every row of the neighbour's fields); 16-bit storage about 5/8 of that.
+// Runs that do not divide the row length of a dense block put y neighbours
+// several steps apart and lose to shorter ones.  Candidates 1..16 (divisors of
+// typical row lengths), ties to the shorter run.
+// 16-bit storage takes no runs: its x-face columns cost half the sectors, the
+// split stores of the x = 6 / x = 7 voxels cost more L2 write sectors, and runs
+// measured slower (dense 256^3: 607 us per launch without runs, 637 us with 16).
+int pair_run_length(const int32_t* nbr, int64_t nb, const int32_t* work, int64_t n, int64_t slots, uint32_t sb)
+{
+    if (n <= 1 || slots <= 0 || sb != 4) return 1;
+    const bool wl = work != nullptr;
+    std::vector<int32_t> item_of;
+    if (wl) {
+        item_of.assign((size_t)nb, -1);
+        for (int64_t i = 0; i < n; ++i) item_of[(size_t)work[i]] = (int32_t)i;
+    }
+    auto brick = [&](int64_t i) -> int32_t { return wl ? work[i] : (int32_t)i; };
+    auto item = [&](int32_t b) -> int64_t { return wl ? item_of[(size_t)b] : (int64_t)b; };
+    const double item_bytes = (16.0 + 30.0 * sb) * 512.0;
+    const double window = 64.0e6 / item_bytes;
+    const double scale = sb == 4 ? 1.0 : 0.625;
+    const double miss_bytes[3] = {16384.0 * scale, 8192.0 * scale, 2048.0 * scale};  // x, y, z faces
+    // sample about 2048 items; the stride is prime to 2 and 3, so samples fall at
+    // every position of a run for every candidate length
+    int64_t stride = n > 2048 ? n / 2048 : 1;
+    while (stride > 1 && (stride % 2 == 0 || stride % 3 == 0)) ++stride;
+    static const int kCand[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    int best = 1;
+    double best_t = 0.0;
+    for (int R : kCand) {
+        const int64_t nruns = (n + R - 1) / R;
+        const int64_t G = nruns < slots ? nruns : slots;
+        const double per_cta = (double)((nruns + G - 1) / G) * R;
+        auto T = [&](int64_t i) -> int64_t { return (i / (G * R)) * R + i % R; };
+        double extra = 0.0;
+        int64_t interior = 0, cnt = 0;
+        for (int64_t i = 0; i < n; i += stride) {
+            ++cnt;
+            const int32_t* row = nbr + (size_t)brick(i) * TGV_NNBR;
+            const bool from_prev = R > 1 && i % R != 0 && row[NB_MX] == brick(i - 1);
+            const bool to_next = R > 1 && (i + 1) % R != 0 && i + 1 < n && row[NB_PX] == brick(i + 1);
+            interior += from_prev && to_next;
+            const int64_t Ti = T(i);
+            for (int k = 0; k < 6; ++k) {
+                const int32_t nbk = row[k];
+                if (nbk < 0 || nbk >= nb) continue;
+                if ((k == NB_MX && from_prev) || (k == NB_PX && to_next)) continue;
+                const int64_t j = item(nbk);
+                if (j < 0) continue;  // not updated here: its halo reads miss for every R alike
+                const int64_t dT = T(j) > Ti ? T(j) - Ti : Ti - T(j);
+                if ((double)(dT * G) > window) extra += miss_bytes[k / 2];
+            }
+        }
+        const double t = per_cta * (1.0 - 0.12 * (double)interior / cnt + extra / cnt / item_bytes);
+        if (R == 1 || t < best_t) {
+            best = R;
+            best_t = t;
+        }
+    }
+    return best;
+}
 
 template <typename S, int NB>
 tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
@@ -816,8 +954,21 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     tgv_status st = tgv_kernel_setup((const void*)kern, kThreads, smem, &per_sm);
     if (st != TGV_OK) return tgv_fail(d, st, "pair kernel setup (shared memory attribute / occupancy) failed");
     if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "pair iteration kernel does not fit on an SM");
-    int64_t grid = (int64_t)per_sm * d->sm_count;
-    if (grid > tgv_work_items(L)) grid = tgv_work_items(L);
+    const int64_t nitems = tgv_work_items(L);
+    const int64_t slots = (int64_t)per_sm * d->sm_count;
+    if (d->prm.x_run == 0 && (L.xrun == 0 || L.xrun_gen != L.work_gen || L.xrun_slots != slots)) {
+        const bool host_ok = (int64_t)L.nbr_host.size() >= L.nb * TGV_NNBR &&
+                             (!L.work || (int64_t)L.work_host.size() == nitems);
+        L.xrun = host_ok ? pair_run_length(L.nbr_host.data(), L.nb, L.work ? L.work_host.data() : nullptr, nitems,
+                                           slots, SB)
+                         : 1;
+        L.xrun_gen = L.work_gen;
+        L.xrun_slots = slots;
+    }
+    const int R = d->prm.x_run > 0 ? d->prm.x_run : L.xrun;
+    const int64_t nruns = (nitems + R - 1) / R;
+    const int64_t grid = nruns < slots ? nruns : slots;
+    P.xrun = (uint32_t)R;
     P.err = d->err;
     P.wait_budget = 2000000000LL;  // about one second at 2 GHz
     P.stage_bytes = stage;
@@ -853,4 +1004,19 @@ tgv_status tgv_launch_iterations_pair(tgv_domain* d, TgvLevel& L, int iters)
     case TGV_STORAGE_FP16: return launch_pair_bins<__half>(d, L, iters);
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
+}
+
+extern "C" TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nbricks, const int32_t* work, int64_t nwork,
+                                          int64_t slots, int32_t storage, int32_t* run_length)
+{
+    if (!nbr || nbricks <= 0 || slots <= 0 || !run_length || (work && nwork < 0)) return TGV_ERR_INVALID_ARG;
+    if (storage < TGV_STORAGE_FP32 || storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    const int64_t n = work ? nwork : nbricks;
+    if (work) {
+        std::vector<uint8_t> seen((size_t)nbricks, 0);
+        for (int64_t i = 0; i < nwork; ++i)
+            if (work[i] < 0 || work[i] >= nbricks || seen[(size_t)work[i]]++) return TGV_ERR_INVALID_ARG;
+    }
+    *run_length = pair_run_length(nbr, nbricks, work, n, slots, storage == TGV_STORAGE_FP32 ? 4u : 2u);
+    return TGV_OK;
 }

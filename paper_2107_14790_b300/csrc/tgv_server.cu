@@ -204,6 +204,7 @@ tgv_status tgv_server_create(const tgv_server_cfg* cfg, const tgv_params* prm, v
     if (cfg->capacity_bricks <= 0 || cfg->capacity_frozen < 0) return TGV_ERR_INVALID_ARG;
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
     if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
     tgv_server* s = new (std::nothrow) tgv_server();
     if (!s) return TGV_ERR_OUT_OF_MEMORY;
     s->cap_active = cfg->capacity_bricks;
@@ -294,6 +295,7 @@ tgv_status tgv_server_submit(tgv_server* s, const tgv_level_desc* chunk, const u
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(L.nbr + r.a0 * TGV_NNBR, rows, (size_t)nb * TGV_NNBR * 4,
                                                   cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) std::copy(rows, rows + nb * TGV_NNBR, L.nbr_host.begin() + r.a0 * TGV_NNBR);
         if (e == cudaSuccess) s->ring.busy_until(st);
     }
     // 2. active state: zero in both ping-pong copies
@@ -428,6 +430,7 @@ tgv_status tgv_server_step(tgv_server* s, int32_t max_iterations, int32_t* finis
         s->ring.busy_until(d->stream);
         L.nwork = n;
         L.work_gen++;
+        L.work_host.assign(w, w + n);
         s->work_dirty = false;
     }
     tgv_status st = tgv_launch_iterations(d, L, k);

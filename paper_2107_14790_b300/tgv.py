@@ -35,7 +35,8 @@ class tgv_params(ctypes.Structure):
     _fields_ = [("nbins", ctypes.c_int32), ("alpha1", ctypes.c_float), ("alpha0", ctypes.c_float),
                 ("lam", ctypes.c_float), ("tau", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("clamp_u", ctypes.c_int32), ("centres", ctypes.c_int32),
-                ("box_v", ctypes.c_float), ("iter_kernel", ctypes.c_int32)]
+                ("box_v", ctypes.c_float), ("iter_kernel", ctypes.c_int32),
+                ("x_run", ctypes.c_int32)]
 
 
 class tgv_level_desc(ctypes.Structure):
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "tgv_domain_bytes": (i64, [P]),
         "tgv_level_voxels": (i64, [P, i32]),
         "tgv_launch_count": (i64, [P]),
+        "tgv_pair_run_length": (i32, [P, i64, P, i64, i64, i32, P]),
         "tgv_energy_noalloc": (i32, [P, P, P, P]),
         "tgv_solve_graph": (i32, [P, i32, i32, P]),
         "tgv_set_work_list": (i32, [P, i32, P, i64]),
@@ -161,13 +163,14 @@ ITER_KERNELS = {"pipelined": 0, "one_brick_per_cta": 1, "paired": 2}
 
 
 def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, storage="fp32", clamp_u=True,
-                centres=0, box_v=2.0, iter_kernel="paired") -> tgv_params:
+                centres=0, box_v=2.0, iter_kernel="paired", x_run=0) -> tgv_params:
     p = tgv_params()
     _check(None, lib().tgv_default_params(ctypes.byref(p)))
     p.nbins, p.alpha1, p.alpha0, p.lam, p.tau, p.sigma = int(nbins), alpha1, alpha0, lam, tau, sigma
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.clamp_u, p.centres, p.box_v = int(bool(clamp_u)), int(centres), box_v
     p.iter_kernel = ITER_KERNELS[iter_kernel] if isinstance(iter_kernel, str) else int(iter_kernel)
+    p.x_run = int(x_run)
     return p
 
 
@@ -324,6 +327,19 @@ def tgv_level_voxels(d, level: int) -> int:
 
 def tgv_launch_count(d) -> int:
     return int(lib().tgv_launch_count(d))
+
+
+def tgv_pair_run_length(nbr: np.ndarray, work=None, slots: int = 296, storage="fp32") -> int:
+    """Run length the paired kernel picks for a level with neighbour rows `nbr`
+    ((nbricks, 12) int32, library layout) and an optional work list (host only)."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1, 12)
+    w = None if work is None else np.ascontiguousarray(work, dtype=np.int32)
+    out = ctypes.c_int32(0)
+    _check(None, lib().tgv_pair_run_length(nbr.ctypes.data, nbr.shape[0], None if w is None else w.ctypes.data,
+                                           0 if w is None else w.size, int(slots),
+                                           STORAGE[storage] if isinstance(storage, str) else int(storage),
+                                           ctypes.byref(out)))
+    return int(out.value)
 
 
 # ------------------------------------------------------------------------------------ convenience
