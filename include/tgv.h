@@ -131,11 +131,24 @@ typedef struct {
     const float* frozen_v;
 } tgv_level_desc;
 
-/* Pinhole camera (Sec. 3.1 depth maps).  Camera frame Xc = R (X - C), R
- * row-major with rows = right, down, forward; pixel x = fx Xc/Zc + cx,
- * y = fy Yc/Zc + cy; pixel (i, j) covers [i, i+1) x [j, j+1).  Depth maps
- * hold the camera-frame z-depth of the observed point; NaN, inf and values
- * <= 0 mark pixels without a sample.  model must be TGV_PINHOLE. */
+/* Depth-map camera (Sec. 3.1 depth maps, Sec. 3.4 LIDAR scans).  Frame
+ * Xc = R (X - C), R row-major; pixel (i, j) covers [i, i+1) x [j, j+1).
+ * NaN, inf and values <= 0 in a map mark pixels without a sample.
+ *  TGV_PINHOLE: rows of R = right, down, forward; x = fx Xc/Zc + cx,
+ *    y = fy Yc/Zc + cy (Zc > 0); maps hold the camera-frame z-depth of the
+ *    observed point; a = depth - Zc; projected voxel diameter fx 2r / Zc.
+ *  TGV_SPHERICAL (a LIDAR scan as a spherical depth map): rows of R = the
+ *    scanner's x, y, z (z up); range rho = |Xc|, azimuth phi = atan2(Yc, Xc)
+ *    in (-pi, pi], elevation theta = atan2(Zc, |(Xc, Yc)|) in [-pi/2, pi/2];
+ *    x = fx phi + cx, y = cy - fy theta (fx, fy pixels per radian: a full
+ *    scan of W x H has fx = W / (2 pi), cx = W / 2, fy = H / pi, cy = H / 2);
+ *    maps hold the range of the observed point; a = depth - rho; projected
+ *    voxel diameter fx 2r / rho.  The angles are evaluated in FP32 with one
+ *    rounding per operation by the arctangent polynomial of Abramowitz &
+ *    Stegun 4.4.49 (|error| <= 2e-8 rad on [0, 1]) after reducing the ratio
+ *    min/max of the two arguments to [0, 1]; the exact step order is listed
+ *    in tgv_hist.cu, so the pixel decision is reproducible bit for bit.
+ * Votes: 1 per map, or 5 for noise-free LIDAR scans (Sec. 3.4). */
 typedef struct {
     double fx, fy, cx, cy;
     double R[9];
@@ -163,8 +176,9 @@ TGV_API void tgv_destroy_domain(tgv_domain* d);
  * (1, or 5 for noise-free LIDAR) to bin
  *   floor(((clamp(a/delta, -1, 1) + 1)/2) * nbins)   (clamped to nbins-1)
  * of every voxel whose centre projects to a valid pixel at its level of
- * detail and has a = depth - Zc >= -eta, with delta = 6r, eta = 3 delta
- * (Sec. 3.1).  The decision is taken in FP32 with one rounding per operation.
+ * detail and has a >= -eta (a = depth minus the voxel's z-depth, or range for
+ * a spherical map), with delta = 6r, eta = 3 delta (Sec. 3.1).  The decision
+ * is taken in FP32 with one rounding per operation.
  * depth_dev: device pointer, height rows of pitch_elems floats.
  * Errors: INVALID_ARG (level, camera, pitch < width, NULL), BUDGET (a voxel
  * count could pass 65535: counts are stored as 16-bit integers), CUDA. */

@@ -61,6 +61,7 @@ def lib():
             "orc_energy": (None, [i64, P, P, P, P, P, i32, P, i32, f64, P, P, P, P, P]),
             "orc_prolong": (i64, [i64, P, P, P, i64, P, P, P]),
             "orc_max_threads": (i32, []),
+            "orc_atan2_as": (ctypes.c_float, [ctypes.c_float, ctypes.c_float]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -107,6 +108,11 @@ def pyramid_levels(depth: np.ndarray):
 def voxel_radius(desc) -> float:
     r = float(getattr(desc, "radius", 0.0) or 0.0)
     return r if r > 0 else float(desc.h) / 2.0
+
+
+def atan2_as(y: float, x: float) -> float:
+    """The FP32 arctangent of the spherical projection (A&S 4.4.49, explicit rounding)."""
+    return float(lib().orc_atan2_as(float(y), float(x)))
 
 
 def vote_list(idx3: np.ndarray, origin, h: float, r: float, cam, depth: np.ndarray, nbins: int) -> np.ndarray:

@@ -115,12 +115,23 @@ void orc_build_pyramid(const float* depth, int W, int H, int64_t pitch, float* p
 /*   bin = min(bin, n-1)   (reading: Alg. 1 gives bin = n at a' = +1)         */
 /* Camera parameters arrive as FP64 and are rounded once to FP32.            */
 /* Returns 1 and sets *bin when the map votes for the voxel, else 0.         */
+/*                                                                          */
+/* Spherical maps (LIDAR scans, Sec. 3.4), reading: the frame rows are the   */
+/* scanner's x, y, z; the map stores the range of the observed point, and    */
+/* the "distance" of Alg. 1 is the voxel centre's range rho = |Xc|:          */
+/*   s2 = Xc*Xc + Yc*Yc;  rho = sqrt(s2 + Zc*Zc)  (requires rho > 0)         */
+/*   azimuth phi = atan2(Yc, Xc), elevation theta = atan2(Zc, sqrt(s2))      */
+/*   x = fx*phi + cx,  y = cy - fy*theta,  fp = (fx*(2r))/rho,  a = depth-rho */
+/* with atan2 taken in FP32 by the arctangent polynomial of Abramowitz and   */
+/* Stegun 4.4.49 (orc_atan2_as below), so both sides decide identically.     */
 /* ======================================================================== */
 typedef struct {
     float fx, fy, cx, cy, R[9], C[3];
     int W, H;
+    int spherical;
 } orc_cam32;
 
+/* cam: 17 doubles (fx, fy, cx, cy, R row-major, C, model: 0 pinhole, 1 spherical) */
 static orc_cam32 orc_cam_from_f64(const double* cam, int W, int H)
 {
     orc_cam32 c;
@@ -132,7 +143,33 @@ static orc_cam32 orc_cam_from_f64(const double* cam, int W, int H)
     for (int k = 0; k < 3; ++k) c.C[k] = (float)cam[13 + k];
     c.W = W;
     c.H = H;
+    c.spherical = cam[16] == 1.0;
     return c;
+}
+
+/* atan2(y, x) in FP32 (every operation rounded to float, no contraction):
+ * t = min(|x|,|y|) / max(|x|,|y|) in [0, 1]; arctan t by A&S 4.4.49,
+ *   arctan t ~ t (1 + a2 t^2 + a4 t^4 + ... + a16 t^16),  |error| <= 2e-8,
+ * the bracket evaluated by Horner in s = t^2 from a16 down to the constant 1;
+ * then the octant: |y| > |x| -> pi/2 - r; x < 0 -> pi - r; y < 0 -> -r.
+ * atan2(0, 0) = 0. */
+float orc_atan2_as(float y, float x)
+{
+    static const float a[8] = {-0.3333314528f, 0.1999355085f, -0.1420889944f, 0.1065626393f,
+                               -0.0752896400f, 0.0429096138f, -0.0161657367f, 0.0028662257f};
+    float ax = fabsf(x), ay = fabsf(y);
+    float big = ax > ay ? ax : ay, small = ax > ay ? ay : ax;
+    if (big == 0.0f) return 0.0f;
+    float t = small / big;
+    float s = t * t;
+    float p = a[7];
+    for (int k = 6; k >= 0; --k) p = p * s + a[k];
+    p = p * s + 1.0f;
+    float r = t * p;
+    if (ay > ax) r = 1.5707963267948966f - r;
+    if (x < 0.0f) r = 3.14159265358979323846f - r;
+    if (y < 0.0f) r = -r;
+    return r;
 }
 
 static int orc_vote_f32(const orc_cam32* cam, const float* pyr, int nlev, const int32_t* dims,
@@ -153,11 +190,25 @@ static int orc_vote_f32(const orc_cam32* cam, const float* pyr, int nlev, const 
     yc = yc + R[5] * d[2];
     float zc = R[6] * d[0] + R[7] * d[1];
     zc = zc + R[8] * d[2];
-    if (!(zc > 0.0f)) return 0;
-    float px = (cam->fx * xc) / zc + cam->cx;
-    float py = (cam->fy * yc) / zc + cam->cy;
     float diam = r * 2.0f;
-    float fp = (cam->fx * diam) / zc;
+    float px, py, fp, dist;
+    if (!cam->spherical) {
+        if (!(zc > 0.0f)) return 0;
+        px = (cam->fx * xc) / zc + cam->cx;
+        py = (cam->fy * yc) / zc + cam->cy;
+        fp = (cam->fx * diam) / zc;
+        dist = zc;
+    } else {
+        float s2 = xc * xc + yc * yc;
+        float rho = sqrtf(s2 + zc * zc);
+        if (!(rho > 0.0f)) return 0;
+        float phi = orc_atan2_as(yc, xc);
+        float theta = orc_atan2_as(zc, sqrtf(s2));
+        px = cam->fx * phi + cam->cx;
+        py = cam->cy - cam->fy * theta;
+        fp = (cam->fx * diam) / rho;
+        dist = rho;
+    }
     int L = 0;
     float p2 = 2.0f;
     while (L + 1 < nlev && p2 <= fp) {
@@ -172,7 +223,7 @@ static int orc_vote_f32(const orc_cam32* cam, const float* pyr, int nlev, const 
     int i = (int)floorf(xl), j = (int)floorf(yl);
     float depth = pyr[offs[L] + (int64_t)j * wl + i];
     if (isnan(depth)) return 0;
-    float a = depth - zc;
+    float a = depth - dist;
     float delta = 6.0f * r;
     float eta = 3.0f * delta;
     if (a < -eta) return 0;
@@ -200,8 +251,18 @@ static int orc_vote_f64(const double* cam, int L32, const float* pyr, const int3
     double xc = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
     double yc = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
     double zc = R[6] * d[0] + R[7] * d[1] + R[8] * d[2];
-    if (!(zc > 0.0)) return 0;
-    double px = cam[0] * xc / zc + cam[2], py = cam[1] * yc / zc + cam[3];
+    double px, py, dist;
+    if (cam[16] != 1.0) {
+        if (!(zc > 0.0)) return 0;
+        px = cam[0] * xc / zc + cam[2];
+        py = cam[1] * yc / zc + cam[3];
+        dist = zc;
+    } else {
+        dist = sqrt(xc * xc + yc * yc + zc * zc);
+        if (!(dist > 0.0)) return 0;
+        px = cam[0] * atan2(yc, xc) + cam[2];
+        py = cam[3] - cam[1] * atan2(zc, sqrt(xc * xc + yc * yc));
+    }
     int L = L32; /* use the FP32 LOD so the diagnostic isolates binning */
     double xl = ldexp(px, -L), yl = ldexp(py, -L);
     int wl = dims[2 * L], hl = dims[2 * L + 1];
@@ -209,7 +270,7 @@ static int orc_vote_f64(const double* cam, int L32, const float* pyr, const int3
     int i = (int)floor(xl), j = (int)floor(yl);
     float depth = pyr[offs[L] + (int64_t)j * wl + i];
     if (isnan(depth)) return 0;
-    double a = (double)depth - zc;
+    double a = (double)depth - dist;
     double delta = 6.0 * r, eta = 3.0 * delta;
     if (a < -eta) return 0;
     double ac = fmax(-1.0, fmin(1.0, a / delta));
@@ -230,7 +291,15 @@ static int orc_lod_f32(const orc_cam32* cam, int nlev, const float o[3], float h
     }
     float zc = cam->R[6] * d[0] + cam->R[7] * d[1];
     zc = zc + cam->R[8] * d[2];
-    float fp = (cam->fx * (r * 2.0f)) / zc;
+    float dist = zc;
+    if (cam->spherical) {
+        float xc = cam->R[0] * d[0] + cam->R[1] * d[1];
+        xc = xc + cam->R[2] * d[2];
+        float yc = cam->R[3] * d[0] + cam->R[4] * d[1];
+        yc = yc + cam->R[5] * d[2];
+        dist = sqrtf((xc * xc + yc * yc) + zc * zc);
+    }
+    float fp = (cam->fx * (r * 2.0f)) / dist;
     int L = 0;
     float p2 = 2.0f;
     while (L + 1 < nlev && p2 <= fp) {
@@ -245,7 +314,7 @@ static int orc_lod_f32(const orc_cam32* cam, int nlev, const float o[3], float h
  *   bricks[3*b+a]: brick coordinates; voxel (i,j,k) of brick b has global index
  *   8*brick + (i,j,k) and flat id b*512 + i + 8 j + 64 k.
  *   hist: uint32 [nvox][nbins], incremented by `vote` in place.
- *   cam: 16 doubles (fx, fy, cx, cy, R row-major, C).
+ *   cam: 17 doubles (fx, fy, cx, cy, R row-major, C, model 0 pinhole / 1 spherical).
  *   r: voxel radius (Sec. 3.3, Eq. 5; reading: r = h/2 on a dense level).
  * Returns the number of votes cast; *ndiff64 (nullable) receives the number of
  * voxels where the FP64 decision differs from the FP32 one.
@@ -281,7 +350,7 @@ int64_t orc_accumulate(int64_t nbricks, const int32_t* bricks, const double* ori
                     for (int a = 0; a < 3; ++a) d[a] = origin[a] + ((double)idx[a] + 0.5) * h - cam[13 + a];
                     zc_test = cam[10] * d[0] + cam[11] * d[1] + cam[12] * d[2];
                 }
-                if (zc_test > 0.0) {
+                if (zc_test > 0.0 || cam[16] == 1.0) {
                     int L = orc_lod_f32(&c32, nlev, o32, h32, r32, idx);
                     ok64 = orc_vote_f64(cam, L, pyr, dims, offs, origin, h, r, idx, nbins, &bin64);
                 }

@@ -587,7 +587,7 @@ tgv_status tgv_accumulate_depthmaps(tgv_domain* d, int32_t level, const tgv_came
     for (int m = 0; m < nmaps; ++m) {
         const tgv_camera& c = cams[m];
         if (c.width != W || c.height != H) return tgv_fail(d, TGV_ERR_INVALID_ARG, "maps of one batch differ in size");
-        if (c.model != TGV_PINHOLE) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "only pinhole cameras are built");
+        if (c.model != TGV_PINHOLE && c.model != TGV_SPHERICAL) return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown camera model");
         bool ok = isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy) && c.fx > 0 && c.fy > 0;
         for (int k = 0; k < 9; ++k) ok = ok && isfinite(c.R[k]);
         for (int k = 0; k < 3; ++k) ok = ok && isfinite(c.C[k]);

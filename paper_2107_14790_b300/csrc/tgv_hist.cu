@@ -6,6 +6,9 @@
 // Lmax = floor(log2(max(W, H))).  One launch per level covers every map of a
 // batch.
 //
+// Cameras: pinhole maps (z-depth) and spherical maps (LIDAR scans, range), see
+// tgv_camera.
+//
 // Histograms: one CTA per active brick, one thread per voxel; each thread
 // evaluates Alg. 1 for every map of the batch (gather form: the voxel's own
 // projection selects the map's level of detail and pixel), counts its votes
@@ -26,15 +29,46 @@ namespace {
 // FP32 camera of one map (parameters rounded once from FP64).
 // Decision for a voxel with global index idx (per axis):
 //   X = o + ((float)idx + 0.5) * h;  d = X - C
-//   Xc = (R0 d0 + R1 d1) + R2 d2 (likewise Yc, Zc);  requires Zc > 0
-//   x = (fx Xc)/Zc + cx;  y = (fy Yc)/Zc + cy;  diameter fp = (fx (2r))/Zc
+//   Xc = (R0 d0 + R1 d1) + R2 d2 (likewise Yc, Zc)
+//   pinhole:   requires Zc > 0;  x = (fx Xc)/Zc + cx;  y = (fy Yc)/Zc + cy;
+//              diameter fp = (fx (2r))/Zc;  distance dist = Zc
+//   spherical: s2 = Xc Xc + Yc Yc;  rho = sqrt(s2 + Zc Zc), requires rho > 0;
+//              phi = atan2p(Yc, Xc);  theta = atan2p(Zc, sqrt(s2));
+//              x = fx phi + cx;  y = cy - fy theta;  fp = (fx (2r))/rho;  dist = rho
 //   LOD l = largest l <= Lmax with 2^l <= max(1, fp)
 //   pixel (floor(x 2^-l), floor(y 2^-l)) inside level l, depth valid
-//   a = depth - Zc;  a >= -eta;  bin = min(floor(((clamp(a/delta) + 1)/2) n), n-1)
+//   a = depth - dist;  a >= -eta;  bin = min(floor(((clamp(a/delta) + 1)/2) n), n-1)
 struct Alg1Cam {
     float fx, fy, cx, cy, R[9], C[3];
     uint32_t vote;
+    int model;  // TGV_PINHOLE / TGV_SPHERICAL
 };
+
+// atan2 for the spherical projection: the arctangent polynomial of Abramowitz &
+// Stegun 4.4.49 (Hastings; |error| <= 2e-8 on [0, 1]) on t = min/max of |y|, |x|,
+// Horner from the highest power, then the octant is restored:
+//   |y| > |x|: pi/2 - r;  x < 0: pi - r;  y < 0: -r.   atan2p(0, 0) = 0.
+__device__ __forceinline__ float atan2p(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    if (mx == 0.0f) return 0.0f;
+    const float t = __fdiv_rn(mn, mx);
+    const float s = __fmul_rn(t, t);
+    float p = 0.0028662257f;
+    p = __fadd_rn(__fmul_rn(p, s), -0.0161657367f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.0429096138f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.0752896400f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.1065626393f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.1420889944f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.1999355085f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.3333314528f);
+    p = __fadd_rn(__fmul_rn(p, s), 1.0f);
+    float r = __fmul_rn(t, p);
+    if (ay > ax) r = __fsub_rn(1.5707963267948966f, r);
+    if (x < 0.0f) r = __fsub_rn(3.14159265358979323846f, r);
+    return y < 0.0f ? -r : r;
+}
 
 struct PyrLayout {
     int nlev;
@@ -98,12 +132,26 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
     const float d1 = __fsub_rn(X[1], c.C[1]);
     const float d2 = __fsub_rn(X[2], c.C[2]);
     const float zc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[6], d0), __fmul_rn(c.R[7], d1)), __fmul_rn(c.R[8], d2));
-    if (!(zc > 0.0f)) return -1;
+    if (c.model == TGV_PINHOLE && !(zc > 0.0f)) return -1;
     const float xc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], d0), __fmul_rn(c.R[1], d1)), __fmul_rn(c.R[2], d2));
     const float yc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[3], d0), __fmul_rn(c.R[4], d1)), __fmul_rn(c.R[5], d2));
-    const float px = __fadd_rn(__fdiv_rn(__fmul_rn(c.fx, xc), zc), c.cx);
-    const float py = __fadd_rn(__fdiv_rn(__fmul_rn(c.fy, yc), zc), c.cy);
-    const float fp = __fdiv_rn(__fmul_rn(c.fx, diam), zc);
+    float px, py, fp, dist;
+    if (c.model == TGV_PINHOLE) {
+        px = __fadd_rn(__fdiv_rn(__fmul_rn(c.fx, xc), zc), c.cx);
+        py = __fadd_rn(__fdiv_rn(__fmul_rn(c.fy, yc), zc), c.cy);
+        fp = __fdiv_rn(__fmul_rn(c.fx, diam), zc);
+        dist = zc;
+    } else {
+        const float s2 = __fadd_rn(__fmul_rn(xc, xc), __fmul_rn(yc, yc));
+        const float rho = __fsqrt_rn(__fadd_rn(s2, __fmul_rn(zc, zc)));
+        if (!(rho > 0.0f)) return -1;
+        const float phi = atan2p(yc, xc);
+        const float theta = atan2p(zc, __fsqrt_rn(s2));
+        px = __fadd_rn(__fmul_rn(c.fx, phi), c.cx);
+        py = __fsub_rn(c.cy, __fmul_rn(c.fy, theta));
+        fp = __fdiv_rn(__fmul_rn(c.fx, diam), rho);
+        dist = rho;
+    }
     int l = 0;
     float p2 = 2.0f;
     while (l + 1 < L.nlev && p2 <= fp) {
@@ -118,7 +166,7 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
     const int i = (int)xl, j = (int)yl;  // truncation == floor for non-negative values
     const float depth = __ldg(pyr + L.off[l] + (int64_t)j * wl + i);
     if (isnan(depth)) return -1;
-    const float a = __fsub_rn(depth, zc);
+    const float a = __fsub_rn(depth, dist);
     if (a < -eta) return -1;
     float ac = __fdiv_rn(a, delta);
     ac = fminf(1.0f, ac);
@@ -240,6 +288,7 @@ tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& Lv, const tgv_camera* 
             for (int k = 0; k < 9; ++k) g.R[k] = (float)c.R[k];
             for (int k = 0; k < 3; ++k) g.C[k] = (float)c.C[k];
             g.vote = votes ? votes[m0 + m] : 1u;
+            g.model = c.model;
         }
         A.coords = Lv.coords_dev;
         hist_accumulate_kernel<<<(unsigned)Lv.nb, TGV_BVOX, 0, d->stream>>>(A);

@@ -155,7 +155,7 @@ def make_camera(cam) -> tgv_camera:
         c.R[k] = float(R[k])
     for k in range(3):
         c.C[k] = float(C[k])
-    c.width, c.height, c.model = int(cam.width), int(cam.height), 0
+    c.width, c.height, c.model = int(cam.width), int(cam.height), int(getattr(cam, "model", 0))
     return c
 
 

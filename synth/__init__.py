@@ -18,7 +18,10 @@ from .scenes import (  # noqa: F401
     look_at,
     pinhole_intrinsics,
     sphere_scene,
+    lidar_sphere_scene,
+    spherical_scanner,
     terrain_scene,
+    terrain_lidar_scans,
     plane_depth,
     random_histograms,
     chunk_workload,

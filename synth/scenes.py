@@ -2,11 +2,14 @@
 
 Conventions shared with the C-ABI (``include/tgv.h``):
 
-* Camera frame: ``Xc = R (X - C)``; pixel ``x = fx*Xc/Zc + cx``, ``y = fy*Yc/Zc + cy``;
-  pixel (i, j) covers ``[i, i+1) x [j, j+1)``; the rows of R are the camera's
-  right, down and forward axes in world coordinates.
-* Depth maps store the camera-frame z-depth ``Zc`` of the observed surface
-  point (float32, row-major, NaN where the ray hits nothing).
+* Camera frame: ``Xc = R (X - C)``; pixel (i, j) covers ``[i, i+1) x [j, j+1)``.
+  Pinhole (model 0): ``x = fx*Xc/Zc + cx``, ``y = fy*Yc/Zc + cy``; the rows of R
+  are the camera's right, down and forward axes in world coordinates; depth
+  maps store the camera-frame z-depth ``Zc`` of the observed surface point.
+  Spherical (model 1, LIDAR scans): the rows of R are the scanner's x, y, z
+  (z up); ``x = fx*azimuth + cx``, ``y = cy - fy*elevation``; maps store the
+  range ``|Xc|`` of the observed point.
+* Depth maps are float32, row-major, NaN where the ray hits nothing.
 * A domain level is a list of 8^3 bricks given by integer brick coordinates;
   voxel (i, j, k) of brick (bx, by, bz) is the global voxel
   (8*bx+i, 8*by+j, 8*bz+k) whose centre is ``origin + (idx + 0.5) * h``.
@@ -31,28 +34,42 @@ class Camera:
     fy: float
     cx: float
     cy: float
-    R: np.ndarray  # (3, 3) float64, rows = right, down, forward
+    R: np.ndarray  # (3, 3) float64, rows = right, down, forward (pinhole) / x, y, z (spherical)
     C: np.ndarray  # (3,) float64, camera centre
     width: int
     height: int
+    model: int = 0  # 0 pinhole (z-depth maps), 1 spherical (LIDAR scan, range maps)
 
     def as_array(self) -> np.ndarray:
-        """16 doubles: fx, fy, cx, cy, R (row-major), C."""
+        """17 doubles: fx, fy, cx, cy, R (row-major), C, model."""
         return np.concatenate([[self.fx, self.fy, self.cx, self.cy],
                                np.asarray(self.R, np.float64).reshape(9),
-                               np.asarray(self.C, np.float64).reshape(3)]).astype(np.float64)
+                               np.asarray(self.C, np.float64).reshape(3), [float(self.model)]]).astype(np.float64)
 
     def ray_directions(self):
-        """World direction per pixel centre, scaled so its camera-frame z is 1.
+        """World direction per pixel centre.
 
-        Returns (H, W, 3) float64; a point at parameter t along the ray has
-        camera z-depth t.
+        Pinhole: scaled so its camera-frame z is 1 (a point at parameter t along
+        the ray has z-depth t).  Spherical: unit length (parameter t = range).
+        Returns (H, W, 3) float64.
         """
         i = np.arange(self.width, dtype=np.float64) + 0.5
         j = np.arange(self.height, dtype=np.float64) + 0.5
-        xx, yy = np.meshgrid((i - self.cx) / self.fx, (j - self.cy) / self.fy)
-        dc = np.stack([xx, yy, np.ones_like(xx)], axis=-1)
+        if self.model == 1:
+            az, el = np.meshgrid((i - self.cx) / self.fx, (self.cy - j) / self.fy)
+            dc = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=-1)
+        else:
+            xx, yy = np.meshgrid((i - self.cx) / self.fx, (j - self.cy) / self.fy)
+            dc = np.stack([xx, yy, np.ones_like(xx)], axis=-1)
         return dc @ np.asarray(self.R, np.float64)  # (dc @ R) == (R^T dc^T)^T
+
+
+def spherical_scanner(C, width: int, height: int, R=None) -> Camera:
+    """A full 360 x 180 degree LIDAR scan as a spherical depth map of width x height
+    pixels (equal angular steps), scanner axes R (default: the world axes)."""
+    R = np.eye(3) if R is None else np.asarray(R, np.float64)
+    return Camera(width / (2.0 * math.pi), height / math.pi, width / 2.0, height / 2.0, R,
+                  np.asarray(C, np.float64), int(width), int(height), model=1)
 
 
 def look_at(C, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
@@ -165,6 +182,31 @@ def sphere_scene(seed: int = CONFIG_SEEDS[1], n: int = 64, nmaps: int = 16, res:
     nb = n // BRICK
     dom = DomainDesc(origin=np.zeros(3), h=1.0 / n, bricks=dense_bricks(nb))
     return Scene("sphere", dom, cams, depths, nbins, iterations, votes=[1] * nmaps,
+                 meta=dict(centre=centre, radius=radius, seed=seed))
+
+
+def lidar_sphere_scene(seed: int = CONFIG_SEEDS[1] + 100, n: int = 64, nscans: int = 4, width: int = 512,
+                       height: int = 256, radius: float = 0.35, ring: float = 1.0, noise_frac: float = 0.001,
+                       nbins: int = 8, iterations: int = 200) -> Scene:
+    """The sphere of `sphere_scene` scanned by `nscans` spherical LIDAR scanners on a
+    ring of radius `ring` about its centre (elevation alternating +10 / -10 degrees,
+    scanner axes = world axes), full 360 x 180 degree range maps of width x height
+    plus N(0, (noise_frac*radius)^2); vote 5 per scan (Sec. 3.4)."""
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.5, 0.5, 0.5])
+    cams, depths = [], []
+    for k in range(nscans):
+        az = 2.0 * math.pi * (k + 0.25) / nscans
+        el = math.radians(10.0 if k % 2 == 0 else -10.0)
+        C = centre + ring * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        cam = spherical_scanner(C, width, height)
+        t = _sphere_hit(cam, centre, radius)
+        t = t + rng.normal(0.0, noise_frac * radius, size=t.shape)
+        cams.append(cam)
+        depths.append(t.astype(np.float32))
+    nb = n // BRICK
+    dom = DomainDesc(origin=np.zeros(3), h=1.0 / n, bricks=dense_bricks(nb))
+    return Scene("lidar-sphere", dom, cams, depths, nbins, iterations, votes=[5] * nscans,
                  meta=dict(centre=centre, radius=radius, seed=seed))
 
 
@@ -337,6 +379,36 @@ def terrain_scene(seed: int = CONFIG_SEEDS[2], n: int = 256, nmaps: int = 64, re
     dom = DomainDesc(origin=np.zeros(3), h=h, bricks=dense_bricks(n // BRICK))
     return Scene("terrain", dom, cams, depths, nbins, iterations, votes=[1] * len(cams),
                  meta=dict(seed=seed, terrain=terrain))
+
+
+def terrain_lidar_scans(terrain: "Terrain", nscans: int = 16, width: int = 2048, height: int = 1024,
+                        h: float = 1.0 / 256, mast: float = 0.02, noise_vox: float = 0.1, seed: int = 1102,
+                        device=None):
+    """Ground LIDAR scans of a terrain (the terrestrial scans of the paper's mixed
+    datasets): `nscans` scanners on a square grid over the central 0.8 x 0.8 of the
+    unit square, `mast` above the ground (moved off any building footprint), full
+    360 x 180 degree range maps of width x height, noise N(0, (noise_vox*h)^2).
+    Returns (cameras, range maps)."""
+    torch = _torch()
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    rng = np.random.default_rng(seed)
+    g = int(round(math.sqrt(nscans)))
+    cams = []
+    for k in range(nscans):
+        x, y = 0.1 + 0.8 * ((k % g) + 0.5) / g, 0.1 + 0.8 * ((k // g) + 0.5) / g
+        for _ in range(64):  # step off building footprints
+            inside = [(b[0] <= x <= b[1] and b[2] <= y <= b[3]) for b in terrain.boxes]
+            if not any(inside):
+                break
+            x, y = x + 0.013, y + 0.007
+        z = float(terrain.height(np.array([x]), np.array([y]))[0]) + mast
+        cams.append(spherical_scanner(np.array([x, y, z]), width, height))
+    depths = []
+    for t in _terrain_depth_torch(terrain, cams, step=h / 4, device=device):
+        t = t + rng.normal(0.0, noise_vox * h, size=t.shape)
+        depths.append(t.astype(np.float32))
+    return cams, depths
 
 
 # --------------------------------------------------------------------------- histograms

@@ -160,3 +160,103 @@ def test_sphere_band_bins_follow_signed_distance(sphere_scene):
     assert deep_in.sum() > 4000  # ball of radius 22.4 - 12 voxels: about 4700 voxels
     assert lvl.hist[deep_in].sum() == 0  # deeper than eta = 9 voxels: never observed
     assert math.isclose(sc.domain.h, 1 / 64)
+
+
+# --- spherical (LIDAR) maps: scanner at the origin, world axes, 64 x 32 full scan --------
+import math as _m
+
+
+def _scan(W=64, H=32):
+    return synth.spherical_scanner(np.zeros(3), W, H)
+
+
+S_ORIGIN = np.array([-1.0 / 128] * 3)  # voxel (i, j, k) centre = (i, j, k) / 64 exactly
+
+
+def _sbins(idx, depth, nbins=8):
+    return list(oracle.vote_list(np.asarray(idx, np.int64), S_ORIGIN, H_VOX, R_VOX, _scan(), depth, nbins))
+
+
+def test_atan2_polynomial_against_the_library():
+    """A&S 4.4.49 plus octant reduction, in FP32: within 4e-7 rad of atan2 over a grid
+    spanning all octants and magnitudes; exact on the axes; odd in y."""
+    vals = np.concatenate([-np.logspace(-3, 3, 25), [0.0], np.logspace(-3, 3, 25)]).astype(np.float32)
+    worst = 0.0
+    for y in vals:
+        for x in vals:
+            a = oracle.atan2_as(y, x)
+            if x == 0 and y == 0:
+                assert a == 0.0
+                continue
+            worst = max(worst, abs(a - _m.atan2(float(y), float(x))))
+            assert oracle.atan2_as(-y, x) == -a or y == 0
+    assert worst <= 4e-7, worst
+    assert oracle.atan2_as(0.0, 1.0) == 0.0
+    assert oracle.atan2_as(1.0, 0.0) == float(np.float32(_m.pi / 2))
+    assert oracle.atan2_as(0.0, -1.0) == float(np.float32(_m.pi))
+
+
+def test_spherical_bins_by_range_along_an_axis():
+    """Along +x the angles are exactly 0: pixel (32, 16); a = depth - range.  With a
+    constant range map of 1 the voxel at range k/64 has a/delta = (64-k)/3."""
+    depth = np.ones((32, 64), np.float32)
+    cases = {60: 7, 61: 7, 62: 6, 63: 5, 64: 4, 65: 2, 66: 1, 67: 0,
+             73: 0,    # a = -eta exactly still votes
+             74: -1,   # a < -eta
+             0: -1}    # range 0: no direction
+    got = _sbins([(k, 0, 0) for k in cases], depth)
+    assert got == list(cases.values())
+    only = np.full((32, 64), np.nan, np.float32)
+    only[16, 32] = 1.0  # the single pixel the +x axis maps to
+    assert _sbins([(64, 0, 0), (65, 0, 0)], only) == [4, 2]
+
+
+def test_spherical_bins_depend_on_range_not_direction():
+    """Voxels at equal range in different directions (away from the poles and the
+    azimuth seam) take the same bin from a constant range map."""
+    depth = np.ones((32, 64), np.float32)
+    # range exactly 1 on the axes; 65/64 on the 39-52-65 diagonals (a/delta = -1/3)
+    pts = [(64, 0, 0), (0, 64, 0), (0, -64, 0), (39, 52, 0), (-39, 52, 0), (39, -52, 0), (-39, -52, 0), (52, 0, 39)]
+    want = [4, 4, 4, 2, 2, 2, 2, 2]
+    assert _sbins(pts, depth) == want
+
+
+def test_spherical_pixel_follows_the_library_angles():
+    """Each voxel votes only where its pixel (from numpy's arctan2 in FP64) holds the
+    single valid sample; voxels within 1e-4 pixel of a pixel edge are skipped."""
+    rng = np.random.default_rng(5)
+    cam = _scan(256, 128)
+    checked = 0
+    for _ in range(60):
+        idx = rng.integers(-60, 61, size=3)
+        c = idx / 64.0
+        rho = float(np.linalg.norm(c))
+        if rho < 0.5:
+            continue
+        x = cam.fx * _m.atan2(c[1], c[0]) + cam.cx
+        y = cam.cy - cam.fy * _m.atan2(c[2], _m.hypot(c[0], c[1]))
+        if min(abs(x - round(x)), abs(y - round(y))) < 1e-4 or not (0 <= x < 256 and 0 <= y < 128):
+            continue
+        fp = cam.fx * H_VOX / rho
+        assert fp < 2.0  # level of detail 0
+        depth = np.full((128, 256), np.nan, np.float32)
+        depth[int(_m.floor(y)), int(_m.floor(x))] = rho + 0.25 * 3 / 64  # a = delta / 4
+        got = oracle.vote_list(idx[None, :].astype(np.int64), S_ORIGIN, H_VOX, R_VOX, cam, depth, 8)
+        assert got[0] == 5, (idx, x, y)
+        checked += 1
+    assert checked > 30
+
+
+def test_spherical_level_of_detail_uses_the_pyramid():
+    """At range 1/16 the projected diameter is 16/(2 pi) = 2.55 pixels: level 1, pixel
+    (16, 8), the minimum of level-0 pixels (32..33, 16..17); at range 1, level 0."""
+    depth = np.full((32, 64), np.nan, np.float32)
+    depth[17, 33] = 1.0
+    assert _sbins([(4, 0, 0), (64, 0, 0)], depth) == [7, -1]
+
+
+def test_spherical_votes_of_five():
+    sc = synth.lidar_sphere_scene(n=32, nscans=2, width=128, height=64)
+    lvl = oracle.OracleLevel(sc.domain, sc.nbins)
+    votes = sum(lvl.accumulate(c, d, 5) for c, d in zip(sc.cameras, sc.depths))
+    assert votes > 0 and int(lvl.hist.sum()) == 5 * votes and np.all(lvl.hist % 5 == 0)
