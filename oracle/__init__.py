@@ -62,6 +62,8 @@ def lib():
             "orc_prolong": (i64, [i64, P, P, P, i64, P, P, P]),
             "orc_max_threads": (i32, []),
             "orc_atan2_as": (ctypes.c_float, [ctypes.c_float, ctypes.c_float]),
+            "orc_mesh": (i64, [i64, P, i64, P, P, P, f64, P, P, P]),
+            "orc_mc_triangulate": (i32, [i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -108,6 +110,36 @@ def pyramid_levels(depth: np.ndarray):
 def voxel_radius(desc) -> float:
     r = float(getattr(desc, "radius", 0.0) or 0.0)
     return r if r > 0 else float(desc.h) / 2.0
+
+
+def mesh(desc, u: np.ndarray):
+    """Marching cubes (Sec. 4.6) of the FP32 indicator `u` ((nb + nf) * 512 values:
+    active bricks, then frozen) on the level `desc`: (vertices (nv, 3) float32,
+    triangles (nt, 3) int32), vertices by increasing edge id, triangles by cell."""
+    b = _c(desc.bricks, np.int32).reshape(-1, 3)
+    f = _c(desc.frozen, np.int32).reshape(-1, 3) if getattr(desc, "frozen", None) is not None else \
+        np.zeros((0, 3), np.int32)
+    u32 = _c(u, np.float32).reshape(-1)
+    if u32.size != 512 * (b.shape[0] + f.shape[0]):
+        raise ValueError("u must hold (nb + nf) * 512 values")
+    o = _c(desc.origin, np.float64)
+    nv = np.zeros(1, np.int64)
+    nt = lib().orc_mesh(b.shape[0], _p(b), f.shape[0], _p(f), _p(u32), _p(o), float(desc.h), _p(nv), None, None)
+    if nt < 0:
+        raise ValueError("duplicate brick")
+    verts = np.zeros((int(nv[0]), 3), np.float32)
+    tris = np.zeros((int(nt), 3), np.int32)
+    lib().orc_mesh(b.shape[0], _p(b), f.shape[0], _p(f), _p(u32), _p(o), float(desc.h), _p(nv), _p(verts), _p(tris))
+    return verts, tris
+
+
+def triangulate_min_area(P: np.ndarray) -> np.ndarray:
+    """The marching-cubes polygon triangulation (FP32 dynamic programming) of the
+    polygon P ((k, 3), 3 <= k <= 12): (k - 2, 3) polygon-local vertex indices."""
+    P32 = _c(P, np.float32).reshape(-1, 3)
+    out = np.zeros((max(1, P32.shape[0] - 2), 3), np.int32)
+    n = lib().orc_mc_triangulate(P32.shape[0], _p(P32), None, _p(out))
+    return out[:n]
 
 
 def atan2_as(y: float, x: float) -> float:

@@ -805,3 +805,434 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ======================================================================== */
+/* Marching cubes on a brick level (Sec. 4.6): for every cube whose corners   */
+/* take indicator values of different sign, the points where u crosses zero  */
+/* along its edges, joined into closed polygons and triangulated by dynamic  */
+/* programming that minimises the total area (after Bloomenthal 1988).       */
+/*                                                                          */
+/* Readings (the paper gives no more detail):                                */
+/*  - a cube ("cell") has 8 voxel centres as corners; the cell with lower    */
+/*    corner voxel g is extracted when g lies in an active brick and all 8   */
+/*    corners exist (active or frozen bricks);                               */
+/*  - corner c = dx + 2 dy + 4 dz is inside when u < 0 (u = -1 interior);    */
+/*  - an edge from voxel p to p + e_a crosses when exactly one end is inside; */
+/*    its point is at t = u_p / (u_p - u_q) along the edge; coordinates      */
+/*    o + ((g + 0.5) + t) h on axis a, o + (g + 0.5) h on the others, all in */
+/*    FP32 with one rounding per operation;                                  */
+/*  - each face of the cell, corners counter-clockwise seen from outside the */
+/*    cell, joins a crossing where the boundary enters the inside region to  */
+/*    the next crossing where it leaves; on a face with four crossings the   */
+/*    face sum ((u_a + u_b) + (u_c + u_d)) over its corners in cell order    */
+/*    decides: >= 0 joins each entry to the next exit (inside corners apart),*/
+/*    < 0 to the previous exit (inside corners connected).  The two cells    */
+/*    sharing a face see the same corners in the same order and decide alike;*/
+/*  - segments run entry -> exit, so every polygon is counter-clockwise seen */
+/*    from the outside region (u >= 0) and triangle normals point there;     */
+/*  - a polygon P0..P(k-1) (P0 = its crossing on the cell edge of lowest     */
+/*    index 4a + (other two corner bits)) is triangulated by                 */
+/*      C[i][j] = min_{i<m<j} (C[i][m] + C[m][j]) + |(Pm - Pi) x (Pj - Pi)|  */
+/*    in FP32 (ties: smallest m), triangles emitted root first, then the     */
+/*    (i, m) side, then the (m, j) side, each as (Pi, Pm, Pj);               */
+/*  - a polygon with no triangulation free of chords along a cell face (one */
+/*    that carries the segments of several four-crossing faces) is fanned    */
+/*    around its centroid (FP32 sum in polygon order, divided by k), a vertex */
+/*    of the cell; at most one per cell, later ones take the unconstrained   */
+/*    triangulation;                                                         */
+/*  - vertices are numbered by increasing id: 4 slot(p) + a for the crossing */
+/*    on the edge from voxel p along axis a, 4 slot(g) + 3 for the centroid  */
+/*    of the cell with lower corner g; slot = brick * 512 + local and frozen */
+/*    brick f has brick index nb + f;                                        */
+/*    triangles come in increasing cell order (active brick, local index).   */
+/* ======================================================================== */
+#define ORC_MC_MAXV 12
+
+static const int orc_mc_face[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4},
+                                      {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+
+/* cell edge index of the edge between corners c0 and c1 (they differ in one bit) */
+static int orc_mc_edge(int c0, int c1)
+{
+    int lo = c0 < c1 ? c0 : c1, x = c0 ^ c1;
+    int a = x == 1 ? 0 : (x == 2 ? 1 : 2);
+    int bits[3] = {lo & 1, (lo >> 1) & 1, (lo >> 2) & 1};
+    int m = 0, s = 0;
+    for (int b = 0; b < 3; ++b)
+        if (b != a) m |= bits[b] << s++;
+    return 4 * a + m;
+}
+
+/* base corner and axis of cell edge e */
+static void orc_mc_edge_base(int e, int* base, int* axis)
+{
+    int a = e / 4, m = e % 4, bits[3] = {0, 0, 0}, s = 0;
+    for (int b = 0; b < 3; ++b)
+        if (b != a) bits[b] = (m >> s++) & 1;
+    *base = bits[0] + 2 * bits[1] + 4 * bits[2];
+    *axis = a;
+}
+
+static float orc_mc_area2(const float* P, int i, int m, int j)
+{
+    float e1[3], e2[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = P[3 * m + c] - P[3 * i + c];
+        e2[c] = P[3 * j + c] - P[3 * i + c];
+    }
+    float cx = e1[1] * e2[2] - e1[2] * e2[1];
+    float cy = e1[2] * e2[0] - e1[0] * e2[2];
+    float cz = e1[0] * e2[1] - e1[1] * e2[0];
+    float n2 = cx * cx + cy * cy;
+    n2 = n2 + cz * cz;
+    return sqrtf(n2);
+}
+
+/* 1 when cell edges e1 and e2 lie on a common face of the cell: a face fixes
+ * one coordinate bit f, and an edge of axis a with base corner b lies on the
+ * faces f != a with bit f of b as the fixed value. */
+static int orc_mc_share_face(int e1, int e2)
+{
+    int b1, a1, b2, a2;
+    orc_mc_edge_base(e1, &b1, &a1);
+    orc_mc_edge_base(e2, &b2, &a2);
+    for (int f = 0; f < 3; ++f)
+        if (f != a1 && f != a2 && ((b1 >> f) & 1) == ((b2 >> f) & 1)) return 1;
+    return 0;
+}
+
+/* Minimum-area triangulation of the polygon P[0..k-1] (3 floats per vertex) by
+ * dynamic programming over chords, FP32 with the operation order of
+ * orc_mc_area2: C[i][j] = min_{i<m<j} (C[i][m] + C[m][j]) + area2(i, m, j),
+ * ties to the smallest m; triangles (i, m, j) emitted root first, then the
+ * (i, m) side, then the (m, j) side.  Returns the number of triangles (k - 2).
+ * cell_edges (nullable): the cell edge of each vertex; a chord between two
+ * vertices on a common cell face is then not allowed (the neighbouring cell
+ * would place the opposite triangle in that face); returns -1 when every
+ * triangulation needs one. */
+int orc_mc_triangulate(int k, const float* P, const int* cell_edges, int* tri)
+{
+    float C[ORC_MC_MAXV][ORC_MC_MAXV];
+    int best[ORC_MC_MAXV][ORC_MC_MAXV];
+    if (k < 3 || k > ORC_MC_MAXV) return 0;
+    {
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                C[i][j] = 0.0f;
+                best[i][j] = j == i + 1 ? k : -1; /* polygon edges: valid, no triangle */
+            }
+        for (int len = 2; len < k; ++len)
+            for (int i = 0; i + len < k; ++i) {
+                int j = i + len;
+                if (cell_edges && len < k - 1 && orc_mc_share_face(cell_edges[i], cell_edges[j])) continue;
+                float bc = 0.0f;
+                int bm = -1;
+                for (int m = i + 1; m < j; ++m) {
+                    if (best[i][m] < 0 || best[m][j] < 0) continue;
+                    float c = (C[i][m] + C[m][j]) + orc_mc_area2(P, i, m, j);
+                    if (bm < 0 || c < bc) {
+                        bc = c;
+                        bm = m;
+                    }
+                }
+                C[i][j] = bc;
+                best[i][j] = bm;
+            }
+        if (best[0][k - 1] < 0) return -1;
+    }
+    int st[2 * ORC_MC_MAXV][2], sp = 0, nt = 0;
+    st[sp][0] = 0;
+    st[sp][1] = k - 1;
+    sp++;
+    while (sp > 0) {
+        sp--;
+        int i = st[sp][0], j = st[sp][1];
+        if (j - i < 2) continue;
+        int m = best[i][j];
+        tri[3 * nt + 0] = i;
+        tri[3 * nt + 1] = m;
+        tri[3 * nt + 2] = j;
+        nt++;
+        st[sp][0] = m; /* (m, j) below (i, m): (i, m) comes out first */
+        st[sp][1] = j;
+        sp++;
+        st[sp][0] = i;
+        st[sp][1] = m;
+        sp++;
+    }
+    return nt;
+}
+
+typedef struct {
+    const orc_bkey* t;
+    int64_t nall, nb;
+    const int32_t* bricks;
+    const int32_t* frozen;
+    const float* u;
+    float o[3], h;
+} orc_mc_ctx;
+
+/* slot of the voxel at global coordinates g, or -1 */
+static int64_t orc_mc_slot(const orc_mc_ctx* X, const int64_t g[3])
+{
+    int64_t bq[3], lq[3];
+    for (int c = 0; c < 3; ++c) {
+        bq[c] = g[c] >= 0 ? g[c] / ORC_BRICK : -((-g[c] + ORC_BRICK - 1) / ORC_BRICK);
+        lq[c] = g[c] - ORC_BRICK * bq[c];
+    }
+    int64_t pos = orc_find(X->t, X->nall, orc_key(bq[0], bq[1], bq[2]));
+    if (pos < 0) return -1;
+    int64_t id = X->t[pos].id, brick = id >= 0 ? id : X->nb + (-1 - id);
+    return brick * ORC_BVOX + lq[0] + 8 * lq[1] + 64 * lq[2];
+}
+
+static void orc_mc_slot_coords(const orc_mc_ctx* X, int64_t slot, int64_t g[3])
+{
+    int64_t b = slot / ORC_BVOX, v = slot % ORC_BVOX;
+    const int32_t* bc = b < X->nb ? X->bricks + 3 * b : X->frozen + 3 * (b - X->nb);
+    g[0] = (int64_t)ORC_BRICK * bc[0] + (v & 7);
+    g[1] = (int64_t)ORC_BRICK * bc[1] + ((v >> 3) & 7);
+    g[2] = (int64_t)ORC_BRICK * bc[2] + (v >> 6);
+}
+
+/* FP32 position of the zero crossing on edge id = 4 slot + axis (axis < 3) */
+static void orc_mc_vertex(const orc_mc_ctx* X, int64_t eid, float out[3])
+{
+    int64_t slot = eid / 4, g[3], gq[3];
+    int a = (int)(eid % 4);
+    orc_mc_slot_coords(X, slot, g);
+    for (int c = 0; c < 3; ++c) gq[c] = g[c] + (c == a);
+    float up = X->u[slot], uq = X->u[orc_mc_slot(X, gq)];
+    float t = up / (up - uq);
+    for (int c = 0; c < 3; ++c) {
+        float s = (float)g[c] + 0.5f;
+        if (c == a) s = s + t;
+        out[c] = X->o[c] + s * X->h;
+    }
+}
+
+typedef struct {
+    int64_t id;
+    float p[3];
+} orc_mc_centre;
+
+static int orc_mc_cmp64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int64_t orc_mc_rank(const int64_t* ids, int64_t n, int64_t id)
+{
+    int64_t lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (ids[mid] == id) return mid;
+        if (ids[mid] < id) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* One cell: its global edge ids of crossed edges (eid[12], -1 if not crossed),
+ * its polygons (loop vertex lists as cell edges) and the triangles of each.
+ * Returns the number of triangles, writes them as cell edge triples. */
+static int orc_mc_cell(const orc_mc_ctx* X, const int64_t g0[3], int64_t eid[13], int tri[ORC_MC_MAXV * 3],
+                       float centre[3], int* centre_used)
+{
+    *centre_used = 0;
+    int64_t slot[8];
+    float uc[8];
+    for (int c = 0; c < 8; ++c) {
+        int64_t g[3] = {g0[0] + (c & 1), g0[1] + ((c >> 1) & 1), g0[2] + (c >> 2)};
+        slot[c] = orc_mc_slot(X, g);
+        if (slot[c] < 0) return -1;
+        uc[c] = X->u[slot[c]];
+    }
+    int inside[8], any_in = 0, any_out = 0;
+    for (int c = 0; c < 8; ++c) {
+        inside[c] = uc[c] < 0.0f;
+        any_in |= inside[c];
+        any_out |= !inside[c];
+    }
+    for (int e = 0; e < 13; ++e) eid[e] = -1;
+    if (!any_in || !any_out) return 0;
+    for (int e = 0; e < 12; ++e) {
+        int base, a;
+        orc_mc_edge_base(e, &base, &a);
+        if (inside[base] != inside[base | (1 << a)]) eid[e] = 4 * slot[base] + a;
+    }
+    eid[12] = 4 * slot[0] + 3; /* the cell's centre vertex, used only by a fan */
+    /* next[e]: the segment starting at crossing e (where it is an entry) ends at next[e] */
+    int next[12];
+    for (int e = 0; e < 12; ++e) next[e] = -1;
+    for (int f = 0; f < 6; ++f) {
+        const int* k = orc_mc_face[f];
+        int ne = 0, pos_e[4], typ[4];
+        for (int m = 0; m < 4; ++m) {
+            int c0 = k[m], c1 = k[(m + 1) % 4];
+            typ[m] = inside[c0] == inside[c1] ? 0 : (inside[c0] ? 2 /* exit */ : 1 /* entry */);
+            pos_e[m] = orc_mc_edge(c0, c1);
+        }
+        for (int m = 0; m < 4; ++m) ne += typ[m] != 0;
+        if (ne == 0) continue;
+        int connected_inside = 0;
+        if (ne == 4) {
+            int s[4] = {k[0], k[1], k[2], k[3]};
+            /* corners in cell order */
+            for (int x = 0; x < 4; ++x)
+                for (int y = x + 1; y < 4; ++y)
+                    if (s[y] < s[x]) {
+                        int tmp = s[x];
+                        s[x] = s[y];
+                        s[y] = tmp;
+                    }
+            float sum = (uc[s[0]] + uc[s[1]]) + (uc[s[2]] + uc[s[3]]);
+            connected_inside = sum < 0.0f;
+        }
+        for (int m = 0; m < 4; ++m) {
+            if (typ[m] != 1) continue;
+            int p = -1;
+            if (!connected_inside) {
+                for (int d = 1; d < 4; ++d)
+                    if (typ[(m + d) % 4] == 2) {
+                        p = (m + d) % 4;
+                        break;
+                    }
+            } else {
+                for (int d = 1; d < 4; ++d)
+                    if (typ[(m + 4 - d) % 4] == 2) {
+                        p = (m + 4 - d) % 4;
+                        break;
+                    }
+            }
+            next[pos_e[m]] = pos_e[p];
+        }
+    }
+    int ntri = 0, done[12] = {0};
+    for (int e0 = 0; e0 < 12; ++e0) {
+        if (eid[e0] < 0 || done[e0]) continue;
+        int poly[ORC_MC_MAXV], k = 0, e = e0;
+        do {
+            poly[k++] = e;
+            done[e] = 1;
+            e = next[e];
+        } while (e != e0 && e >= 0 && k < ORC_MC_MAXV);
+        float P[3 * ORC_MC_MAXV];
+        for (int v = 0; v < k; ++v) orc_mc_vertex(X, eid[poly[v]], P + 3 * v);
+        int lt[3 * ORC_MC_MAXV];
+        int nt = orc_mc_triangulate(k, P, poly, lt);
+        if (nt < 0 && !*centre_used) {
+            /* fan around the polygon's centroid (vertex 12 of the cell) */
+            float c[3] = {0.0f, 0.0f, 0.0f};
+            for (int v = 0; v < k; ++v)
+                for (int q = 0; q < 3; ++q) c[q] = c[q] + P[3 * v + q];
+            for (int q = 0; q < 3; ++q) centre[q] = c[q] / (float)k;
+            *centre_used = 1;
+            for (int v = 0; v < k; ++v) {
+                tri[3 * ntri + 0] = poly[v];
+                tri[3 * ntri + 1] = poly[(v + 1) % k];
+                tri[3 * ntri + 2] = 12;
+                ntri++;
+            }
+            continue;
+        }
+        if (nt < 0) nt = orc_mc_triangulate(k, P, NULL, lt);
+        for (int q = 0; q < 3 * nt; ++q) tri[3 * ntri + q] = poly[lt[q]];
+        ntri += nt;
+    }
+    return ntri;
+}
+
+/*
+ * u: FP32 indicator of (nb + nf) * 512 voxels (active bricks, then frozen).
+ * First call with verts = tris = NULL: returns the triangle count and sets
+ * *nverts.  Second call with buffers of 3 * nverts floats and 3 * ntris int32
+ * fills them.  Returns -1 on a duplicate brick.
+ */
+int64_t orc_mesh(int64_t nb, const int32_t* bricks, int64_t nf, const int32_t* frozen, const float* u,
+                 const double* origin, double h, int64_t* nverts, float* verts, int32_t* tris)
+{
+    int64_t nall = nb + nf;
+    orc_bkey* t = (orc_bkey*)malloc(sizeof(orc_bkey) * (size_t)(nall > 0 ? nall : 1));
+    for (int64_t b = 0; b < nb; ++b) {
+        t[b].key = orc_key(bricks[3 * b], bricks[3 * b + 1], bricks[3 * b + 2]);
+        t[b].id = b;
+    }
+    for (int64_t f = 0; f < nf; ++f) {
+        t[nb + f].key = orc_key(frozen[3 * f], frozen[3 * f + 1], frozen[3 * f + 2]);
+        t[nb + f].id = -1 - f;
+    }
+    qsort(t, (size_t)nall, sizeof(orc_bkey), orc_cmp);
+    for (int64_t k = 1; k < nall; ++k)
+        if (t[k].key == t[k - 1].key) {
+            free(t);
+            return -1;
+        }
+    orc_mc_ctx X = {t, nall, nb, bricks, frozen, u, {(float)origin[0], (float)origin[1], (float)origin[2]}, (float)h};
+    /* pass 1: referenced edges and cell centres */
+    int64_t cap = 1024, ne = 0, ntri = 0, capc = 16, nc = 0;
+    int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    orc_mc_centre* cen = (orc_mc_centre*)malloc(sizeof(orc_mc_centre) * (size_t)capc);
+    for (int64_t b = 0; b < nb; ++b)
+        for (int v = 0; v < ORC_BVOX; ++v) {
+            int64_t g0[3] = {(int64_t)ORC_BRICK * bricks[3 * b] + (v & 7), (int64_t)ORC_BRICK * bricks[3 * b + 1] + ((v >> 3) & 7),
+                             (int64_t)ORC_BRICK * bricks[3 * b + 2] + (v >> 6)};
+            int64_t eid[13];
+            int tri[3 * ORC_MC_MAXV], cu;
+            float cp[3];
+            int n = orc_mc_cell(&X, g0, eid, tri, cp, &cu);
+            if (n <= 0) continue;
+            ntri += n;
+            for (int e = 0; e < 13; ++e)
+                if (eid[e] >= 0 && (e < 12 || cu)) {
+                    if (ne == cap) {
+                        cap *= 2;
+                        ids = (int64_t*)realloc(ids, sizeof(int64_t) * (size_t)cap);
+                    }
+                    ids[ne++] = eid[e];
+                }
+            if (cu) {
+                if (nc == capc) {
+                    capc *= 2;
+                    cen = (orc_mc_centre*)realloc(cen, sizeof(orc_mc_centre) * (size_t)capc);
+                }
+                cen[nc].id = eid[12];
+                for (int q = 0; q < 3; ++q) cen[nc].p[q] = cp[q];
+                nc++;
+            }
+        }
+    qsort(ids, (size_t)ne, sizeof(int64_t), orc_mc_cmp64);
+    int64_t nu = 0;
+    for (int64_t k = 0; k < ne; ++k)
+        if (k == 0 || ids[k] != ids[k - 1]) ids[nu++] = ids[k];
+    *nverts = nu;
+    if (verts)
+        for (int64_t k = 0; k < nu; ++k) {
+            if (ids[k] % 4 != 3) {
+                orc_mc_vertex(&X, ids[k], verts + 3 * k);
+                continue;
+            }
+            for (int64_t c = 0; c < nc; ++c)
+                if (cen[c].id == ids[k])
+                    for (int q = 0; q < 3; ++q) verts[3 * k + q] = cen[c].p[q];
+        }
+    if (tris) {
+        int64_t o = 0;
+        for (int64_t b = 0; b < nb; ++b)
+            for (int v = 0; v < ORC_BVOX; ++v) {
+                int64_t g0[3] = {(int64_t)ORC_BRICK * bricks[3 * b] + (v & 7),
+                                 (int64_t)ORC_BRICK * bricks[3 * b + 1] + ((v >> 3) & 7),
+                                 (int64_t)ORC_BRICK * bricks[3 * b + 2] + (v >> 6)};
+                int64_t eid[13];
+                int tri[3 * ORC_MC_MAXV], cu;
+                float cp[3];
+                int n = orc_mc_cell(&X, g0, eid, tri, cp, &cu);
+                for (int k = 0; k < 3 * n; ++k) tris[o++] = (int32_t)orc_mc_rank(ids, nu, eid[tri[k]]);
+            }
+    }
+    free(cen);
+    free(ids);
+    free(t);
+    return ntri;
+}
