@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
                          "300 iterations; serving: Poisson stream of 2000 chunk-solve requests")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
@@ -601,6 +601,54 @@ def run_lidar(args):
             "parity_sample": {"bricks": int(len(pick)), "mismatched_counts": mism}}
 
 
+def run_mesh(args):
+    """Marching cubes (Sec. 4.6) of the solved 256^3 terrain field (64 maps, 10 bins, 500
+    iterations): cells/s and triangles/s of the extraction (count pass, scans, write pass,
+    with the device-to-host copy of the mesh timed separately)."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import build, tgv
+    build.build()
+    torch.cuda.set_device(0)
+    sc = synth.terrain_scene(1002, 256, 64, 512, 10, 500, device="cuda")
+    stream = torch.cuda.Stream()
+    dom = tgv.Domain([sc.domain], nbins=10, stream=stream.cuda_stream)
+    dom.accumulate(0, sc.cameras, torch.from_numpy(np.stack(sc.depths)).cuda())
+    dom.solve(0, 500)
+    dom.synchronize()
+    import ctypes
+    cv, ct = ctypes.c_int64(0), ctypes.c_int64(0)
+    for _ in range(max(1, args.warmup)):
+        tgv._check(dom.handle, tgv.lib().tgv_extract_mesh(dom.handle, 0, ctypes.byref(cv), ctypes.byref(ct)))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        tgv._check(dom.handle, tgv.lib().tgv_extract_mesh(dom.handle, 0, ctypes.byref(cv), ctypes.byref(ct)))
+        times.append(time.perf_counter() - t0)
+    nv, nt = cv.value, ct.value
+    verts = np.zeros((nv, 3), np.float32)
+    tris = np.zeros((nt, 3), np.int32)
+    t0 = time.perf_counter()
+    tgv.tgv_copy_mesh(dom.handle, verts, tris)
+    t_copy = time.perf_counter() - t0
+    ncell = dom.voxels(0)
+    dom.close()
+    t = float(np.median(times))
+    # open surface (it leaves the domain), but every interior edge must have its reverse
+    key = lambda a, b: a.astype(np.int64) * (1 << 32) + b
+    e = np.concatenate([key(tris[:, 0], tris[:, 1]), key(tris[:, 1], tris[:, 2]), key(tris[:, 2], tris[:, 0])])
+    r = np.concatenate([key(tris[:, 1], tris[:, 0]), key(tris[:, 2], tris[:, 1]), key(tris[:, 0], tris[:, 2])])
+    dup = len(e) - len(np.unique(e))
+    unpaired = int(np.count_nonzero(~np.isin(e, r)))
+    return {"metric": "marching cubes: cells/s (zero level set of the solved field, Sec. 4.6)",
+            "value": ncell / t, "unit": "cells/s", "n_gpus": 1, "higher_is_better": True, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f32", "data": "synthetic (seeded terrain scene, 64 maps, 500 iterations)",
+            "config": {"workload": "dense-256^3-terrain-solved-500it-marching-cubes", "cells": ncell},
+            "extract_ms": t * 1e3, "copy_to_host_ms": t_copy * 1e3, "vertices": nv, "triangles": nt,
+            "triangles_per_s": nt / t, "repeated_directed_edges": dup, "edges_without_reverse": unpaired,
+            "note": "edges without a reverse lie on the domain boundary, where the surface is cut"}
+
+
 def run_serving(args):
     """Poisson stream of chunk-solve requests (16k..8M voxels, 8..12 bins, 200..600 iterations)
     through one server per bin count, arenas sized from the HBM budget."""
@@ -683,6 +731,9 @@ def main():
         return
     if args.workload == "multilevel":
         print(json.dumps(run_multilevel(args)), flush=True)
+        return
+    if args.workload == "mesh":
+        print(json.dumps(run_mesh(args)), flush=True)
         return
     if args.workload == "lidar":
         print(json.dumps(run_lidar(args)), flush=True)

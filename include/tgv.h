@@ -271,6 +271,38 @@ TGV_API int64_t tgv_level_voxels(const tgv_domain* d, int32_t level);
 /* Number of kernels this library launched on the domain so far. */
 TGV_API int64_t tgv_launch_count(const tgv_domain* d);
 
+/* Marching cubes (Sec. 4.6): the zero level set of level `level`'s u as a
+ * welded triangle mesh, kept in library-owned device memory until the next
+ * extraction or tgv_destroy_domain; writes its vertex and triangle counts.
+ *  Cells: cubes of 8 voxel centres, one per voxel g of an active brick (its
+ *  lower corner), extracted when all 8 corners exist (active or frozen bricks).
+ *  Corner inside when u < 0.  Vertices: the zero crossing on each edge with
+ *  ends of different sides, t = u_p / (u_p - u_q), world coordinates
+ *  origin + (idx + 0.5 (+ t along the edge)) h, FP32 with one rounding per
+ *  operation.  Per cell, each face joins the crossing where its boundary
+ *  (counter-clockwise seen from outside the cell) enters the inside region to
+ *  the next one where it leaves; with four crossings, the face sum
+ *  ((u_a + u_b) + (u_c + u_d)) of its corners in cell order picks the next
+ *  (>= 0) or the previous (< 0) exit, so both cells of a face agree.  The joins
+ *  form loops, counter-clockwise seen from u >= 0 (triangle normals point to
+ *  u >= 0), each triangulated by the minimum-area dynamic programme (FP32, ties
+ *  to the smallest split) without chords along a cell face; a loop with no such
+ *  triangulation is fanned around its centroid (one extra vertex per cell).
+ *  The mesh of a closed zero set inside the domain is closed and consistently
+ *  oriented.
+ *  Vertex order: increasing id (4 slot + axis for a crossing on the edge from
+ *  voxel slot along axis, 4 slot + 3 for a cell's centroid; slot = brick * 512
+ *  + local, frozen brick f at brick index nbricks + f); triangles in cell order.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 2^31 vertices or 2^32 ids),
+ * OUT_OF_MEMORY, CUDA.  Synchronises the stream. */
+TGV_API tgv_status tgv_extract_mesh(tgv_domain* d, int32_t level, int64_t* nverts, int64_t* ntris);
+
+/* Copies the last extracted mesh: verts = 3 * nverts floats (x, y, z),
+ * tris = 3 * ntris int32 vertex indices (host or device pointers).  The counts
+ * must equal those tgv_extract_mesh returned (INVALID_ARG otherwise; STATE if
+ * there is no mesh).  Synchronises the stream. */
+TGV_API tgv_status tgv_copy_mesh(tgv_domain* d, float* verts, int64_t nverts, int32_t* tris, int64_t ntris);
+
 /* Run length the paired iteration kernel chooses when tgv_params.x_run is 0
  * (host only; no device work).  The iteration is Eq. 2-3 whatever the choice;
  * it only sets how many consecutive work items a CTA takes in a row, trading

@@ -298,7 +298,7 @@ void free_level(TgvLevel& L)
 {
     free_graphs(L);
     void* ptrs[] = {L.u, L.ubar[0], L.ubar[1], L.v, L.vbar[0], L.vbar[1], L.p[0], L.p[1],
-                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev, L.work};
+                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev, L.work, L.up7};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -560,7 +560,8 @@ void tgv_destroy_domain(tgv_domain* d)
     DeviceGuard g(d->device);
     cudaStreamSynchronize(d->stream);
     for (TgvLevel& L : d->levels) free_level(L);
-    for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table})
+    for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table, &d->mesh_flags, &d->mesh_count, &d->mesh_scan,
+                          &d->mesh_v, &d->mesh_t})
         if (s->ptr) cudaFree(s->ptr);
     if (d->red_out) cudaFree(d->red_out);
     if (d->err) cudaFree(d->err);
@@ -664,6 +665,34 @@ tgv_status tgv_extract_field(tgv_domain* d, int32_t level, int32_t field, float*
     if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, (size_t)count * 4, cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     return tgv_cuda_check(d, e, "extract field");
+}
+
+tgv_status tgv_extract_mesh(tgv_domain* d, int32_t level, int64_t* nverts, int64_t* ntris)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    if (!nverts || !ntris) return tgv_fail(d, TGV_ERR_INVALID_ARG, "nverts and ntris must not be NULL");
+    DeviceGuard g(d->device);
+    TgvLevel* L;
+    if ((st = get_level(d, level, &L)) != TGV_OK) return st;
+    d->mesh_nv = d->mesh_nt = -1;
+    return tgv_mesh_extract(d, *L, nverts, ntris);
+}
+
+tgv_status tgv_copy_mesh(tgv_domain* d, float* verts, int64_t nverts, int32_t* tris, int64_t ntris)
+{
+    tgv_status st = check_domain(d);
+    if (st != TGV_OK) return st;
+    if (d->mesh_nv < 0) return tgv_fail(d, TGV_ERR_STATE, "no mesh extracted");
+    if (nverts != d->mesh_nv || ntris != d->mesh_nt || (nverts > 0 && !verts) || (ntris > 0 && !tris))
+        return tgv_fail(d, TGV_ERR_INVALID_ARG, "counts must be those of the last tgv_extract_mesh");
+    DeviceGuard g(d->device);
+    cudaError_t e = cudaSuccess;
+    if (nverts > 0) e = cudaMemcpyAsync(verts, d->mesh_v.ptr, (size_t)nverts * 12, cudaMemcpyDefault, d->stream);
+    if (e == cudaSuccess && ntris > 0)
+        e = cudaMemcpyAsync(tris, d->mesh_t.ptr, (size_t)ntris * 12, cudaMemcpyDefault, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "mesh copy");
 }
 
 tgv_status tgv_set_field(tgv_domain* d, int32_t level, int32_t field, const float* in, int64_t count)

@@ -91,6 +91,7 @@ struct TgvLevel {
     // host copies of nbr (nb rows) and of the work list, for the paired kernel's run-length choice
     std::vector<int32_t> nbr_host;
     std::vector<int32_t> work_host;
+    int32_t* up7 = nullptr;    // marching cubes: nb x 7 upper-neighbour bricks (built on first use)
     int xrun = 0;              // cached automatic run length, valid for (xrun_gen, xrun_slots)
     uint64_t xrun_gen = 0;
     int64_t xrun_slots = 0;
@@ -139,6 +140,8 @@ struct tgv_domain {
     TgvScratch red;     // per-block partial sums of the energy reduction
     TgvScratch tmp;     // staging for host <-> device field copies
     TgvScratch table;   // per-brick parent table of tgv_prolong
+    TgvScratch mesh_flags, mesh_count, mesh_scan, mesh_v, mesh_t;  // marching cubes
+    int64_t mesh_nv = -1, mesh_nt = -1;  // counts of the last extracted mesh (-1: none)
     double* red_out = nullptr;   // 4 doubles: final reduction result (device)
     int* err = nullptr;          // device flag: 1 after a bounded device-side wait gave up
 };
@@ -153,6 +156,9 @@ tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg);
 tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what);
 tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes);
 void tgv_bin_centres(const tgv_params& prm, float* c);
+
+// Marching cubes of level L into the domain's mesh buffers (synchronises).
+tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t* ntris);
 
 // Number of bricks one iteration updates.
 inline int64_t tgv_work_items(const TgvLevel& L) { return L.work ? L.nwork : L.nb; }

@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
         "tgv_level_voxels": (i64, [P, i32]),
         "tgv_launch_count": (i64, [P]),
         "tgv_pair_run_length": (i32, [P, i64, P, i64, i64, i32, P]),
+        "tgv_extract_mesh": (i32, [P, i32, P, P]),
+        "tgv_copy_mesh": (i32, [P, P, i64, P, i64]),
         "tgv_energy_noalloc": (i32, [P, P, P, P]),
         "tgv_solve_graph": (i32, [P, i32, i32, P]),
         "tgv_set_work_list": (i32, [P, i32, P, i64]),
@@ -329,6 +331,21 @@ def tgv_launch_count(d) -> int:
     return int(lib().tgv_launch_count(d))
 
 
+def tgv_copy_mesh(d, verts: np.ndarray, tris: np.ndarray):
+    """Copies the last extracted mesh into (nv, 3) float32 and (nt, 3) int32 host arrays."""
+    _check(d, lib().tgv_copy_mesh(d, verts.ctypes.data, verts.shape[0], tris.ctypes.data, tris.shape[0]))
+
+
+def tgv_extract_mesh(d, level: int):
+    """Marching cubes of the level's u: (vertices (nv, 3) float32, triangles (nt, 3) int32)."""
+    nv, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(d, lib().tgv_extract_mesh(d, level, ctypes.byref(nv), ctypes.byref(nt)))
+    verts = np.zeros((nv.value, 3), np.float32)
+    tris = np.zeros((nt.value, 3), np.int32)
+    tgv_copy_mesh(d, verts, tris)
+    return verts, tris
+
+
 def tgv_pair_run_length(nbr: np.ndarray, work=None, slots: int = 296, storage="fp32") -> int:
     """Run length the paired kernel picks for a level with neighbour rows `nbr`
     ((nbricks, 12) int32, library layout) and an optional work list (host only)."""
@@ -396,6 +413,9 @@ class Domain:
 
     def field(self, level, name, out=None):
         return tgv_extract_field(self.handle, level, name, out)
+
+    def mesh(self, level=0):
+        return tgv_extract_mesh(self.handle, level)
 
     def set_field(self, level, name, values):
         tgv_set_field(self.handle, level, name, values)
