@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
                          "300 iterations; serving: Poisson stream of 2000 chunk-solve requests")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
@@ -568,22 +568,25 @@ def run_lidar(args):
             tgv.tgv_energy(dom.handle, 0)
 
     ms_step = timed(step, args.steps)
-    # bit-exact check of 48 sampled bricks against the oracle (both kinds of maps)
     dom.reset(0, clear_hist=True)
     dom.accumulate(0, sc.cameras, photos)
     dom.accumulate(0, scans, lidar, votes5)
     h_gpu = dom.histograms(0)
     e = dom.energy(0)
     dom.close()
+    # CPU baseline: the oracle's Alg. 1 on 48 sampled bricks with all 80 maps (timed),
+    # whose counts also serve as a bit-exact check of the same bricks
     import oracle
     rng = np.random.default_rng(7)
     pick = np.sort(rng.choice(sc.domain.nbricks, 48, replace=False))
     sub = synth.DomainDesc(sc.domain.origin, sc.domain.h, sc.domain.bricks[pick])
     orc = oracle.OracleLevel(sub, 10)
-    for c, d in zip(sc.cameras, sc.depths):
-        orc.accumulate(c, d, 1)
+    t_cpu = time.perf_counter()
     for c, d in zip(scans, ranges):
         orc.accumulate(c, d, 5)
+    t_cpu = time.perf_counter() - t_cpu
+    for c, d in zip(sc.cameras, sc.depths):
+        orc.accumulate(c, d, 1)
     rows = (pick[:, None] * 512 + np.arange(512)[None, :]).ravel()
     mism = int(np.count_nonzero(h_gpu[rows] != orc.hist))
     lidar_pairs = nvox * len(scans)
@@ -598,7 +601,10 @@ def run_lidar(args):
             "votes_total": int(h_gpu.sum()), "step_ms": ms_step,
             "step_voxel_updates_per_s": nvox * 500 / (ms_step / 1e3),
             "energy_gap": {"energy": e[0], "gap": e[2], "certified": bool(e[3])},
-            "parity_sample": {"bricks": int(len(pick)), "mismatched_counts": mism}}
+            "cpu_baseline": {"value": 48 * 512 * len(scans) / t_cpu, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": "48 random bricks x 16 LIDAR scans (its pyramids included)"},
+            "parity_sample": {"bricks": int(len(pick)), "maps": len(scans) + len(sc.cameras),
+                              "mismatched_counts": mism}}
 
 
 def run_mesh(args):
@@ -647,6 +653,45 @@ def run_mesh(args):
             "extract_ms": t * 1e3, "copy_to_host_ms": t_copy * 1e3, "vertices": nv, "triangles": nt,
             "triangles_per_s": nt / t, "repeated_directed_edges": dup, "edges_without_reverse": unpaired,
             "note": "edges without a reverse lie on the domain boundary, where the surface is cut"}
+
+
+def run_octree(args):
+    """Brick domain from the 64 terrain maps (512^2) by Eq. 4 (depths 5..9 of the unit root
+    cube, band 1, 2:1 balance, frozen shells): samples/s of the whole build, timed as the
+    library call (it synchronises); the oracle's build of the same maps as CPU baseline and
+    as a bit-exact check of every level."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import build, tgv
+    build.build()
+    torch.cuda.set_device(0)
+    sc = synth.terrain_scene(1002, 256, 64, 512, 10, 500, device="cuda")
+    depth = torch.from_numpy(np.stack(sc.depths)).cuda()
+    stream = torch.cuda.Stream()
+    cfgs = (np.zeros(3), 1.0, 5, 9, 1)
+    for _ in range(max(1, args.warmup)):
+        tgv.tgv_octree_build(sc.cameras, depth, *cfgs, stream=stream.cuda_stream)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        levels, ns = tgv.tgv_octree_build(sc.cameras, depth, *cfgs, stream=stream.cuda_stream)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    import oracle
+    t_cpu = time.perf_counter()
+    ref, ns_ref = oracle.octree_build(sc.cameras, sc.depths, *cfgs)
+    t_cpu = time.perf_counter() - t_cpu
+    same = ns == ns_ref and all(np.array_equal(L.bricks, a) and np.array_equal(L.frozen, f)
+                                for L, (a, f) in zip(levels, ref))
+    return {"metric": "octree domain build: depth samples/s (Eq. 4, Sec. 4.1-4.2)", "value": ns / t,
+            "unit": "samples/s", "n_gpus": 1, "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32", "data": "synthetic (seeded terrain scene, 64 maps 512^2)",
+            "config": {"workload": "terrain-64x512^2-maps-octree-depths-5..9-band1", "samples": ns},
+            "build_ms": t * 1e3,
+            "levels": [{"depth": 5 + l, "active": L.nbricks, "frozen": L.nfrozen} for l, L in enumerate(levels)],
+            "cpu_baseline": {"value": ns_ref / t_cpu, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": "the whole build of the same maps"},
+            "identical_to_oracle": bool(same)}
 
 
 def run_serving(args):
@@ -731,6 +776,9 @@ def main():
         return
     if args.workload == "multilevel":
         print(json.dumps(run_multilevel(args)), flush=True)
+        return
+    if args.workload == "octree":
+        print(json.dumps(run_octree(args)), flush=True)
         return
     if args.workload == "mesh":
         print(json.dumps(run_mesh(args)), flush=True)

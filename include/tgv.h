@@ -303,6 +303,53 @@ TGV_API tgv_status tgv_extract_mesh(tgv_domain* d, int32_t level, int64_t* nvert
  * there is no mesh).  Synchronises the stream. */
 TGV_API tgv_status tgv_copy_mesh(tgv_domain* d, float* verts, int64_t nverts, int32_t* tris, int64_t ntris);
 
+/* ---------------------------------------------------------------------------
+ * Brick domains from depth maps (Sec. 3.3 Eq. 4, Sec. 4.1-4.2; in memory, one
+ * GPU).  Every valid pixel of a pinhole map is a sample: its z-depth
+ * unprojected to X, radius r = half the mean distance to the points of its
+ * valid 4-neighbours (left, right, up, down).  Eq. 4 puts it in the cube of
+ * depth d with 0.75 r <= r_root 2^-d < 1.5 r (r_root = root_edge / 2): the
+ * smallest d in [depth_min, depth_max] with r_root 2^-d < 1.5 r (depth_max if
+ * none), cube q = floor(((X - root_min) / root_edge) 2^d), samples outside the
+ * root dropped; all in FP32 with one rounding per operation (order in
+ * tgv_octree.cu).  Level l = d - depth_min: voxel edge root_edge / 2^d, origin
+ * root_min; active bricks = the occupied cubes' q >> 3, dilated `band` times
+ * by their 26 neighbours; then, finest first, level l-1 gains the parents
+ * (b >> 1) of level l's bricks dilated once (2:1 balance: each finer level is
+ * wrapped by a shell of the next coarser level); frozen bricks of level l > 0
+ * = the non-active 26-neighbours of its active bricks.  Neighbours stay inside
+ * the root.  Bricks are listed in Morton (Z-curve) order.  The levels feed
+ * tgv_create_domain for a coarse-to-fine solve (frozen values by tgv_prolong).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double root_min[3];
+    double root_edge;   /* root cube [root_min, root_min + root_edge)^3 */
+    int32_t depth_min;  /* >= 3 (one brick = 8 cubes per axis) */
+    int32_t depth_max;  /* depth_min..21 */
+    int32_t band;       /* dilation rings of the occupied bricks, 0..8 */
+} tgv_octree_cfg;
+
+typedef struct tgv_octree tgv_octree; /* opaque, library-owned (host memory) */
+
+/* Builds the levels from nmaps pinhole maps of one size (map m at depth_dev +
+ * m * map_stride_elems, rows of pitch_elems floats, device memory; cams on the
+ * host) on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (a spherical map),
+ * OUT_OF_MEMORY, BUDGET (the device hash set could not hold the bricks),
+ * CUDA.  Synchronises the stream. */
+TGV_API tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, int32_t nmaps,
+                                    const float* depth_dev, int64_t pitch_elems, int64_t map_stride_elems,
+                                    void* stream, tgv_octree** out);
+TGV_API int32_t tgv_octree_levels(const tgv_octree* o);
+/* Number of samples that fell inside the root. */
+TGV_API int64_t tgv_octree_samples(const tgv_octree* o);
+/* Counts, origin (3 doubles) and voxel edge of a level (any output may be NULL). */
+TGV_API tgv_status tgv_octree_level(const tgv_octree* o, int32_t level, int64_t* nactive, int64_t* nfrozen,
+                                    double* origin, double* h);
+/* Copies a level's brick coordinates (3 int32 per brick) into host arrays sized
+ * from tgv_octree_level. */
+TGV_API tgv_status tgv_octree_bricks(const tgv_octree* o, int32_t level, int32_t* active, int32_t* frozen);
+TGV_API void tgv_octree_destroy(tgv_octree* o);
+
 /* Run length the paired iteration kernel chooses when tgv_params.x_run is 0
  * (host only; no device work).  The iteration is Eq. 2-3 whatever the choice;
  * it only sets how many consecutive work items a CTA takes in a row, trading

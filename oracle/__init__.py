@@ -64,6 +64,8 @@ def lib():
             "orc_atan2_as": (ctypes.c_float, [ctypes.c_float, ctypes.c_float]),
             "orc_mesh": (i64, [i64, P, i64, P, P, P, f64, P, P, P]),
             "orc_mc_triangulate": (i32, [i32, P, P, P]),
+            "orc_octree_samples": (i64, [P, i32, i32, P, P, f64, i32, i32, P, P, P]),
+            "orc_octree_build": (i64, [i32, P, i32, i32, P, P, f64, i32, i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -140,6 +142,39 @@ def triangulate_min_area(P: np.ndarray) -> np.ndarray:
     out = np.zeros((max(1, P32.shape[0] - 2), 3), np.int32)
     n = lib().orc_mc_triangulate(P32.shape[0], _p(P32), None, _p(out))
     return out[:n]
+
+
+def octree_samples(cam, depth: np.ndarray, root_min, root_edge: float, dmin: int, dmax: int):
+    """Per pixel of one pinhole map: (depth d or -1, cube coords (H, W, 3), radius r)."""
+    d = _c(depth, np.float32)
+    H, W = d.shape
+    dd = np.empty((H, W), np.int32)
+    qq = np.zeros((H, W, 3), np.int64)
+    rr = np.zeros((H, W), np.float32)
+    lib().orc_octree_samples(_p(_c(cam.as_array(), np.float64)), W, H, _p(d), _p(_c(root_min, np.float64)),
+                             float(root_edge), int(dmin), int(dmax), _p(dd), _p(qq), _p(rr))
+    return dd, qq, rr
+
+
+def octree_build(cams, depths, root_min, root_edge: float, dmin: int, dmax: int, band: int = 1):
+    """Brick domain from pinhole depth maps (Eq. 4, Sec. 4.1-4.2): per level (active, frozen)
+    brick coordinate arrays in Morton order, and the sample count."""
+    dep = _c(np.stack(depths), np.float32)
+    nm, H, W = dep.shape
+    cam = _c(np.stack([c.as_array() for c in cams]), np.float64)
+    nlev = dmax - dmin + 1
+    counts = np.zeros(2 * nlev, np.int64)
+    rm = _c(root_min, np.float64)
+    lib().orc_octree_build(nm, _p(cam), W, H, _p(dep), _p(rm), float(root_edge), dmin, dmax, band, _p(counts), None)
+    out = np.zeros(3 * int(counts.sum()) + 3, np.int32)
+    ns = lib().orc_octree_build(nm, _p(cam), W, H, _p(dep), _p(rm), float(root_edge), dmin, dmax, band, _p(counts),
+                                _p(out))
+    levels, o = [], 0
+    for l in range(nlev):
+        a, f = int(counts[2 * l]), int(counts[2 * l + 1])
+        levels.append((out[3 * o:3 * (o + a)].reshape(-1, 3).copy(), out[3 * (o + a):3 * (o + a + f)].reshape(-1, 3).copy()))
+        o += a + f
+    return levels, int(ns)
 
 
 def atan2_as(y: float, x: float) -> float:

@@ -1236,3 +1236,250 @@ int64_t orc_mesh(int64_t nb, const int32_t* bricks, int64_t nf, const int32_t* f
     free(t);
     return ntri;
 }
+
+/* ======================================================================== */
+/* Octree domain from depth maps (Sec. 3.3 Eq. 4, Sec. 4.1-4.3), in memory.  */
+/*                                                                          */
+/* Readings (the paper's out-of-core files become arrays):                   */
+/*  - root cube [m, m + E)^3, radius r_root = E / 2;                         */
+/*  - sample of pixel (i, j) with valid z-depth z (pinhole map):             */
+/*      Pc = (((i + 0.5) - cx) / fx * z, ((j + 0.5) - cy) / fy * z, z)       */
+/*      X_a = C_a + ((R0a Pc0 + R1a Pc1) + R2a Pc2)    (R rows = camera axes) */
+/*    radius r = 0.5 * (sum of |X - X_n| over the valid 4-neighbours n, in   */
+/*    the order left, right, up, down) / their count; none valid: no sample;  */
+/*  - depth d (Eq. 4): the smallest d in [dmin, dmax] with                    */
+/*    r_root * 2^-d < 1.5 r (so 0.75 r <= r_root 2^-d above dmin), else dmax;*/
+/*  - cube q_a = floor(((X_a - m_a) / E) * 2^d), dropped outside [0, 2^d);    */
+/*  - all of it in FP32, one rounding per operation, parameters rounded once;*/
+/*  - level l = d - dmin has voxel edge E / 2^d, origin m; its bricks are the */
+/*    cubes' q >> 3, dilated `band` times by their 26 neighbours (inside the */
+/*    root); then, finest first, level l-1 gains the parents (b >> 1) of      */
+/*    level l's bricks, dilated once (2:1 balance: a finer level is wrapped  */
+/*    by a shell of the next coarser one);                                   */
+/*  - frozen bricks of level l > 0: the 26-neighbours of its active bricks   */
+/*    that are not active (inside the root);                                 */
+/*  - bricks of a level are listed in Morton (Z-curve) order of their coords.*/
+/* ======================================================================== */
+static uint64_t orc_spread3(uint64_t v)
+{
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+static uint64_t orc_morton(int64_t x, int64_t y, int64_t z)
+{
+    return orc_spread3((uint64_t)x) | (orc_spread3((uint64_t)y) << 1) | (orc_spread3((uint64_t)z) << 2);
+}
+
+/* One sample per valid pixel of one map: writes depth d (or -1) and cube coords. */
+int64_t orc_octree_samples(const double* cam, int W, int H, const float* depth, const double* root_min, double root_edge,
+                           int dmin, int dmax, int32_t* d_out, int64_t* q_out, float* r_out)
+{
+    float fx = (float)cam[0], fy = (float)cam[1], cx = (float)cam[2], cy = (float)cam[3];
+    float R[9], C[3], m[3];
+    for (int k = 0; k < 9; ++k) R[k] = (float)cam[4 + k];
+    for (int k = 0; k < 3; ++k) C[k] = (float)cam[13 + k];
+    for (int k = 0; k < 3; ++k) m[k] = (float)root_min[k];
+    float E = (float)root_edge, rroot = E * 0.5f;
+    float* X = (float*)malloc(sizeof(float) * 3 * (size_t)W * (size_t)H);
+    char* ok = (char*)malloc((size_t)W * (size_t)H);
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            int64_t p = (int64_t)j * W + i;
+            float z = depth[p];
+            ok[p] = isfinite(z) && z > 0.0f;
+            if (!ok[p]) continue;
+            float pc[3];
+            pc[0] = (((float)i + 0.5f) - cx) / fx * z;
+            pc[1] = (((float)j + 0.5f) - cy) / fy * z;
+            pc[2] = z;
+            for (int a = 0; a < 3; ++a) {
+                float s = R[0 + a] * pc[0] + R[3 + a] * pc[1];
+                s = s + R[6 + a] * pc[2];
+                X[3 * p + a] = C[a] + s;
+            }
+        }
+    int64_t n = 0;
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            int64_t p = (int64_t)j * W + i;
+            d_out[p] = -1;
+            if (!ok[p]) continue;
+            const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+            float sum = 0.0f;
+            int cnt = 0;
+            for (int k = 0; k < 4; ++k) {
+                int ii = i + di[k], jj = j + dj[k];
+                if (ii < 0 || ii >= W || jj < 0 || jj >= H) continue;
+                int64_t q = (int64_t)jj * W + ii;
+                if (!ok[q]) continue;
+                float e0 = X[3 * q] - X[3 * p], e1 = X[3 * q + 1] - X[3 * p + 1], e2 = X[3 * q + 2] - X[3 * p + 2];
+                float l2 = e0 * e0 + e1 * e1;
+                l2 = l2 + e2 * e2;
+                sum = sum + sqrtf(l2);
+                cnt++;
+            }
+            if (cnt == 0) continue;
+            float r = 0.5f * (sum / (float)cnt);
+            int d = dmin;
+            while (d < dmax && !(ldexpf(rroot, -d) < 1.5f * r)) d++;
+            int64_t q3[3];
+            int inside = 1;
+            for (int a = 0; a < 3; ++a) {
+                float s = (X[3 * p + a] - m[a]) / E;
+                float t = ldexpf(s, d);
+                if (!(t >= 0.0f && t < ldexpf(1.0f, d))) inside = 0;
+                q3[a] = inside ? (int64_t)floorf(t) : 0;
+            }
+            if (!inside) continue;
+            d_out[p] = d;
+            for (int a = 0; a < 3; ++a) q_out[3 * p + a] = q3[a];
+            if (r_out) r_out[p] = r;
+            n++;
+        }
+    free(X);
+    free(ok);
+    return n;
+}
+
+typedef struct {
+    uint64_t key;
+    int64_t c[3];
+} orc_obrick;
+
+static int orc_obrick_cmp(const void* a, const void* b)
+{
+    uint64_t x = ((const orc_obrick*)a)->key, y = ((const orc_obrick*)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* sorted unique brick set (Morton order) */
+typedef struct {
+    orc_obrick* v;
+    int64_t n, cap;
+} orc_bset;
+
+static void orc_bset_add(orc_bset* s, int64_t x, int64_t y, int64_t z)
+{
+    if (s->n == s->cap) {
+        s->cap = s->cap ? 2 * s->cap : 1024;
+        s->v = (orc_obrick*)realloc(s->v, sizeof(orc_obrick) * (size_t)s->cap);
+    }
+    s->v[s->n].key = orc_morton(x, y, z);
+    s->v[s->n].c[0] = x;
+    s->v[s->n].c[1] = y;
+    s->v[s->n].c[2] = z;
+    s->n++;
+}
+
+static void orc_bset_finish(orc_bset* s)
+{
+    qsort(s->v, (size_t)s->n, sizeof(orc_obrick), orc_obrick_cmp);
+    int64_t u = 0;
+    for (int64_t k = 0; k < s->n; ++k)
+        if (k == 0 || s->v[k].key != s->v[u - 1].key) s->v[u++] = s->v[k];
+    s->n = u;
+}
+
+static int orc_bset_has(const orc_bset* s, uint64_t key)
+{
+    int64_t lo = 0, hi = s->n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (s->v[mid].key == key) return 1;
+        if (s->v[mid].key < key) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return 0;
+}
+
+/* 26-dilation of s inside [0, nbr)^3 (bricks per axis at that level) */
+static orc_bset orc_bset_dilate(const orc_bset* s, int64_t nbr)
+{
+    orc_bset o = {0, 0, 0};
+    for (int64_t k = 0; k < s->n; ++k)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t x = s->v[k].c[0] + dx, y = s->v[k].c[1] + dy, z = s->v[k].c[2] + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= nbr || y >= nbr || z >= nbr) continue;
+                    orc_bset_add(&o, x, y, z);
+                }
+    orc_bset_finish(&o);
+    return o;
+}
+
+/*
+ * Whole build for nmaps maps of W x H (depth: nmaps * W * H floats, cams: 17
+ * doubles each).  Level l = d - dmin, nlev = dmax - dmin + 1.
+ * counts[2 * l] = active bricks, counts[2 * l + 1] = frozen bricks of level l.
+ * With out != NULL, writes for each level its active then frozen brick
+ * coordinates (3 int32 each), levels one after another.  Returns the number of
+ * samples.
+ */
+int64_t orc_octree_build(int nmaps, const double* cams, int W, int H, const float* depth, const double* root_min,
+                         double root_edge, int dmin, int dmax, int band, int64_t* counts, int32_t* out)
+{
+    int nlev = dmax - dmin + 1;
+    orc_bset* act = (orc_bset*)calloc((size_t)nlev, sizeof(orc_bset));
+    int32_t* dd = (int32_t*)malloc(sizeof(int32_t) * (size_t)W * (size_t)H);
+    int64_t* qq = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)W * (size_t)H);
+    int64_t ns = 0;
+    for (int k = 0; k < nmaps; ++k) {
+        ns += orc_octree_samples(cams + 17 * k, W, H, depth + (int64_t)k * W * H, root_min, root_edge, dmin, dmax, dd, qq,
+                                 NULL);
+        for (int64_t p = 0; p < (int64_t)W * H; ++p)
+            if (dd[p] >= 0) orc_bset_add(&act[dd[p] - dmin], qq[3 * p] >> 3, qq[3 * p + 1] >> 3, qq[3 * p + 2] >> 3);
+    }
+    free(dd);
+    free(qq);
+    for (int l = 0; l < nlev; ++l) {
+        orc_bset_finish(&act[l]);
+        int64_t nbr = ((int64_t)1 << (dmin + l)) >> 3;
+        if (nbr < 1) nbr = 1;
+        for (int b = 0; b < band; ++b) {
+            orc_bset o = orc_bset_dilate(&act[l], nbr);
+            free(act[l].v);
+            act[l] = o;
+        }
+    }
+    for (int l = nlev - 1; l >= 1; --l) {
+        orc_bset par = {0, 0, 0};
+        for (int64_t k = 0; k < act[l].n; ++k)
+            orc_bset_add(&par, act[l].v[k].c[0] >> 1, act[l].v[k].c[1] >> 1, act[l].v[k].c[2] >> 1);
+        orc_bset_finish(&par);
+        int64_t nbr = ((int64_t)1 << (dmin + l - 1)) >> 3;
+        if (nbr < 1) nbr = 1;
+        orc_bset dl = orc_bset_dilate(&par, nbr);
+        for (int64_t k = 0; k < dl.n; ++k) orc_bset_add(&act[l - 1], dl.v[k].c[0], dl.v[k].c[1], dl.v[k].c[2]);
+        orc_bset_finish(&act[l - 1]);
+        free(par.v);
+        free(dl.v);
+    }
+    int64_t o = 0;
+    for (int l = 0; l < nlev; ++l) {
+        int64_t nbr = ((int64_t)1 << (dmin + l)) >> 3;
+        if (nbr < 1) nbr = 1;
+        orc_bset frz = {0, 0, 0};
+        if (l > 0) {
+            orc_bset dl = orc_bset_dilate(&act[l], nbr);
+            for (int64_t k = 0; k < dl.n; ++k)
+                if (!orc_bset_has(&act[l], dl.v[k].key)) orc_bset_add(&frz, dl.v[k].c[0], dl.v[k].c[1], dl.v[k].c[2]);
+            free(dl.v);
+            orc_bset_finish(&frz);
+        }
+        counts[2 * l] = act[l].n;
+        counts[2 * l + 1] = frz.n;
+        if (out) {
+            for (int64_t k = 0; k < act[l].n; ++k)
+                for (int a = 0; a < 3; ++a) out[o++] = (int32_t)act[l].v[k].c[a];
+            for (int64_t k = 0; k < frz.n; ++k)
+                for (int a = 0; a < 3; ++a) out[o++] = (int32_t)frz.v[k].c[a];
+        }
+        free(frz.v);
+    }
+    for (int l = 0; l < nlev; ++l) free(act[l].v);
+    free(act);
+    return ns;
+}

@@ -95,6 +95,12 @@ def lib() -> ctypes.CDLL:
         "tgv_launch_count": (i64, [P]),
         "tgv_pair_run_length": (i32, [P, i64, P, i64, i64, i32, P]),
         "tgv_extract_mesh": (i32, [P, i32, P, P]),
+        "tgv_octree_build": (i32, [P, P, i32, P, i64, i64, P, P]),
+        "tgv_octree_levels": (i32, [P]),
+        "tgv_octree_samples": (i64, [P]),
+        "tgv_octree_level": (i32, [P, i32, P, P, P, P]),
+        "tgv_octree_bricks": (i32, [P, i32, P, P]),
+        "tgv_octree_destroy": (None, [P]),
         "tgv_copy_mesh": (i32, [P, P, i64, P, i64]),
         "tgv_energy_noalloc": (i32, [P, P, P, P]),
         "tgv_solve_graph": (i32, [P, i32, i32, P]),
@@ -344,6 +350,88 @@ def tgv_extract_mesh(d, level: int):
     tris = np.zeros((nt.value, 3), np.int32)
     tgv_copy_mesh(d, verts, tris)
     return verts, tris
+
+
+class tgv_octree_cfg(ctypes.Structure):
+    _fields_ = [("root_min", ctypes.c_double * 3), ("root_edge", ctypes.c_double), ("depth_min", ctypes.c_int32),
+                ("depth_max", ctypes.c_int32), ("band", ctypes.c_int32)]
+
+
+class OctreeLevel:
+    """One level built by tgv_octree_build, shaped like a level description
+    (origin, h, bricks, frozen) for tgv.Domain."""
+
+    def __init__(self, origin, h, bricks, frozen):
+        self.origin, self.h, self.bricks, self.frozen = np.asarray(origin), float(h), bricks, frozen
+        self.frozen_u = self.frozen_v = None
+        self.radius = 0.0
+
+    @property
+    def nbricks(self):
+        return int(self.bricks.shape[0])
+
+    @property
+    def nvox(self):
+        return 512 * self.nbricks
+
+    @property
+    def nfrozen(self):
+        return int(self.frozen.shape[0])
+
+
+def tgv_octree_levels(o) -> int:
+    return int(lib().tgv_octree_levels(o))
+
+
+def tgv_octree_samples(o) -> int:
+    return int(lib().tgv_octree_samples(o))
+
+
+def tgv_octree_level(o, level: int):
+    """(nactive, nfrozen, origin (3,), h) of one built level."""
+    na, nf, hh = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0)
+    org = (ctypes.c_double * 3)()
+    _check(None, lib().tgv_octree_level(o, level, ctypes.byref(na), ctypes.byref(nf), org, ctypes.byref(hh)))
+    return na.value, nf.value, np.array(org[:]), hh.value
+
+
+def tgv_octree_bricks(o, level: int):
+    """(active (na, 3), frozen (nf, 3)) int32 brick coordinates of one built level."""
+    na, nf, _, _ = tgv_octree_level(o, level)
+    act = np.zeros((na, 3), np.int32)
+    frz = np.zeros((nf, 3), np.int32)
+    _check(None, lib().tgv_octree_bricks(o, level, act.ctypes.data, frz.ctypes.data))
+    return act, frz
+
+
+def tgv_octree_destroy(o):
+    lib().tgv_octree_destroy(o)
+
+
+def tgv_octree_build(cams, depth, root_min, root_edge: float, depth_min: int, depth_max: int, band: int = 1,
+                     stream: int = 0):
+    """Brick levels from pinhole depth maps (CUDA tensor (nmaps, H, W)); returns
+    (list of OctreeLevel, number of samples)."""
+    if depth.dim() == 2:
+        depth = depth.unsqueeze(0)
+    nmaps = depth.shape[0]
+    cfg = tgv_octree_cfg()
+    for a in range(3):
+        cfg.root_min[a] = float(root_min[a])
+    cfg.root_edge, cfg.depth_min, cfg.depth_max, cfg.band = float(root_edge), int(depth_min), int(depth_max), int(band)
+    arr = (tgv_camera * nmaps)(*[make_camera(c) for c in cams])
+    h = ctypes.c_void_p()
+    _check(None, lib().tgv_octree_build(ctypes.byref(cfg), arr, nmaps, depth.data_ptr(), depth.stride(1),
+                                        depth.stride(0), ctypes.c_void_p(stream), ctypes.byref(h)))
+    try:
+        levels = []
+        for l in range(tgv_octree_levels(h)):
+            _, _, org, hh = tgv_octree_level(h, l)
+            act, frz = tgv_octree_bricks(h, l)
+            levels.append(OctreeLevel(org, hh, act, frz))
+        return levels, tgv_octree_samples(h)
+    finally:
+        tgv_octree_destroy(h)
 
 
 def tgv_pair_run_length(nbr: np.ndarray, work=None, slots: int = 296, storage="fp32") -> int:
