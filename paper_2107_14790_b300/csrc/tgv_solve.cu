@@ -338,42 +338,59 @@ __device__ __forceinline__ double warp_max(double v)
 
 }  // namespace
 
-template <typename S>
-__global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
+// One CTA (512 threads, one voxel each) per brick, three per SM (registers
+// capped at 40: a few spilled values cost less than the lost occupancy; measured
+// 706 us per 256^3 evaluation against 800 us at two CTAs per SM).  NB: bin count as a
+// compile-time constant (8, 10, 12), 0 = read at run time.  Own fields through
+// per-brick base pointers; neighbours in the same brick or across a face.
+template <typename S, int NB>
+__global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> A)
 {
+    constexpr int NBM = NB ? NB : TGV_MAX_BINS;
     __shared__ int32_t s_nbr[TGV_NNBR];
     __shared__ double s_red[3][16];
     const int64_t item = blockIdx.x;
     const int64_t b = A.work ? (int64_t)A.work[item] : item;
     const int t = threadIdx.x;
     const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
-    const int strd[3] = {1, 8, 64};
     if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
-    __syncthreads();
-
-    const int64_t vi = b * TGV_BVOX + t;
-    const float u = A.u[vi];
+    const int nbins = NB ? NB : A.nbins;
+    const float* ub = A.u + b * TGV_BVOX;
+    const S* vb = A.v + b * 3 * TGV_BVOX;
+    const S* pb = A.p + b * 3 * TGV_BVOX;
+    const S* qb = A.q + b * 6 * TGV_BVOX;
+    const float u = ub[t];
     float v[3], p[3], q[6];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        v[c] = ld_s(A.v + (b * 3 + c) * TGV_BVOX + t);
-        p[c] = ld_s(A.p + (b * 3 + c) * TGV_BVOX + t);
+        v[c] = ld_s(vb + c * TGV_BVOX + t);
+        p[c] = ld_s(pb + c * TGV_BVOX + t);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) q[c] = ld_s(A.q + (b * 6 + c) * TGV_BVOX + t);
+    for (int c = 0; c < 6; ++c) q[c] = ld_s(qb + c * TGV_BVOX + t);
+    __syncthreads();  // s_nbr
 
     float gmv2 = 0.0f, k0 = 0.0f, dm[3][3], dk[3][3], div1 = 0.0f, div2[3] = {0, 0, 0};
     float vmax = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        const int strd = a == 0 ? 1 : (a == 1 ? 8 : 64);
         vmax = fmaxf(vmax, fabsf(v[a]));
-        int64_t nf = 0, nbk = 0;
-        int lf = nbr_voxel(s_nbr, b, t, a, +1, crd[a], strd[a], &nf);
-        int lb = nbr_voxel(s_nbr, b, t, a, -1, crd[a], strd[a], &nbk);
+        // forward neighbour: brick nf (-1 none), local index lf
+        int64_t nf = b, nbk = b;
+        int lf = t + strd, lb = t - strd;
+        if (crd[a] == 7) {
+            nf = s_nbr[nb_plus(a)];
+            lf = t - 7 * strd;
+        }
+        if (crd[a] == 0) {
+            nbk = s_nbr[nb_minus(a)];
+            lb = t + 7 * strd;
+        }
         // forward gradient of u (frozen neighbours give their constant)
         float g = 0.0f;
-        if (lf >= 0) {
-            float un = A.u[nf * TGV_BVOX + lf];
+        if (nf >= 0) {
+            const float un = A.u[nf * TGV_BVOX + lf];
             g = un - u;
             if (nf >= A.nb) k0 += un * p[a];  // frozen constant paired with p
         }
@@ -385,21 +402,24 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
             dm[a][c] = 0.0f;
             dk[a][c] = 0.0f;
         }
-        if (lb >= 0) {
+        if (nbk >= 0) {
+            const S* vn = A.v + nbk * 3 * TGV_BVOX + lb;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float w = ld_s(A.v + (nbk * 3 + c) * TGV_BVOX + lb);
+                const float w = ld_s(vn + c * TGV_BVOX);
                 dm[a][c] = v[c] - w;
                 if (nbk >= A.nb) dk[a][c] = -w;  // frozen constant part of E(v)
             }
         }
         // div1 p and div2 q
-        if (lf >= 0) div1 += p[a];
-        if (lb >= 0 && nbk < A.nb) div1 -= ld_s(A.p + (nbk * 3 + a) * TGV_BVOX + lb);
+        if (nf >= 0) div1 += p[a];
+        if (nbk >= 0 && nbk < A.nb) div1 -= ld_s(A.p + (nbk * 3 + a) * TGV_BVOX + lb);
+        const bool qact = nf >= 0 && nf < A.nb;
+        const S* qn = A.q + (qact ? nf * 6 * TGV_BVOX + lf : 0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if (lf >= 0 && nf < A.nb) div2[c] += ld_s(A.q + (nf * 6 + qi(a, c)) * TGV_BVOX + lf);
-            if (lb >= 0) div2[c] -= q[qi(a, c)];
+            if (qact) div2[c] += ld_s(qn + qi(a, c) * TGV_BVOX);
+            if (nbk >= 0) div2[c] -= q[qi(a, c)];
         }
     }
     const float e[6] = {dm[0][0], dm[1][1], dm[2][2], 0.5f * (dm[0][1] + dm[1][0]), 0.5f * (dm[0][2] + dm[2][0]),
@@ -413,14 +433,17 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
     // maximum of w*u - data(u) over the breakpoints {-1, c_0..c_{n-1}, +1}.  With
     // prefix sums H_< , S_< (counts and count-weighted centres below bin k):
     //   data(c_k) = lambda (c_k (H_< - H_>) - (S_< - S_>)).
-    float hb[TGV_MAX_BINS];
+    uint32_t hw[(NBM + 1) / 2];
+    const uint32_t* hb0 = A.hist + (int64_t)b * ((nbins + 1) / 2) * TGV_BVOX + t;
+#pragma unroll
+    for (int k = 0; k < (NBM + 1) / 2; ++k) hw[k] = (NB || 2 * k < nbins) ? hb0[k * TGV_BVOX] : 0u;
+    float hb[NBM];
     float H = 0.0f, Sc = 0.0f, du_own = 0.0f;
 #pragma unroll
-    for (int k = 0; k < TGV_MAX_BINS; ++k) {
+    for (int k = 0; k < NBM; ++k) {
         hb[k] = 0.0f;
-        if (k < A.nbins) {
-            const uint32_t w = A.hist[((int64_t)b * A.npairs + (k >> 1)) * TGV_BVOX + t];
-            hb[k] = (float)((w >> ((k & 1) * 16)) & 0xffffu);
+        if (NB || k < nbins) {
+            hb[k] = (float)((hw[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
             H += hb[k];
             Sc += hb[k] * A.c[k];
             du_own += hb[k] * fabsf(u - A.c[k]);
@@ -430,11 +453,11 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
     {
         float Hlt = 0.0f, Slt = 0.0f;
 #pragma unroll
-        for (int k = 0; k < TGV_MAX_BINS; ++k) {
-            if (k < A.nbins) {
+        for (int k = 0; k < NBM; ++k) {
+            if (NB || k < nbins) {
                 const float Hgt = H - Hlt - hb[k], Sgt = Sc - Slt - hb[k] * A.c[k];
-                const float dk = A.lambda * (A.c[k] * (Hlt - Hgt) - (Slt - Sgt));
-                best = fmaxf(best, div1 * A.c[k] - dk);
+                const float dk2 = A.lambda * (A.c[k] * (Hlt - Hgt) - (Slt - Sgt));
+                best = fmaxf(best, div1 * A.c[k] - dk2);
                 Hlt += hb[k];
                 Slt += hb[k] * A.c[k];
             }
@@ -470,6 +493,17 @@ __global__ void __launch_bounds__(512) tgv_energy_kernel(const EnergyArgs<S> A)
         A.partial[3 * item + 0] = se;
         A.partial[3 * item + 1] = sd;
         A.partial[3 * item + 2] = sm;
+    }
+}
+
+template <typename S>
+static void launch_energy_kernel(const EnergyArgs<S>& A, int64_t nitems, cudaStream_t stream)
+{
+    switch (A.nbins) {
+    case 8: tgv_energy_kernel<S, 8><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
+    case 10: tgv_energy_kernel<S, 10><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
+    case 12: tgv_energy_kernel<S, 12><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
+    default: tgv_energy_kernel<S, 0><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
     }
 }
 
@@ -563,7 +597,7 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     A.box_v = d->prm.box_v;
     tgv_bin_centres(d->prm, A.c);
     A.partial = (double*)d->red.ptr;
-    tgv_energy_kernel<S><<<(unsigned)nitems, TGV_BVOX, 0, d->stream>>>(A);
+    launch_energy_kernel<S>(A, nitems, d->stream);
     tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, nitems, d->prm.box_v, d->red_out);
     d->launches += 2;
     st = tgv_cuda_check(d, cudaGetLastError(), "tgv_energy_kernel launch");
@@ -615,7 +649,7 @@ static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_param
     A.box_v = prm.box_v;
     tgv_bin_centres(prm, A.c);
     A.partial = partial;
-    tgv_energy_kernel<S><<<(unsigned)s.nbricks, TGV_BVOX, 0, stream>>>(A);
+    launch_energy_kernel<S>(A, s.nbricks, stream);
     tgv_reduce_partials<<<1, 1024, 0, stream>>>(partial, s.nbricks, prm.box_v, result);
     return cudaGetLastError();
 }
