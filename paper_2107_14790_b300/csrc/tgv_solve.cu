@@ -297,31 +297,6 @@ struct EnergyArgs {
 
 namespace {
 
-// value of a field component at the neighbour of voxel t along axis a (dir +1/-1);
-// returns false for "none".  Frozen bricks are in the same arrays.
-__device__ __forceinline__ int nbr_voxel(const int32_t* s_nbr, int64_t b, int t, int a, int dir, int crd_a,
-                                         int strd_a, int64_t* nbrick)
-{
-    if (dir > 0) {
-        if (crd_a < 7) {
-            *nbrick = b;
-            return t + strd_a;
-        }
-        int n = s_nbr[nb_plus(a)];
-        if (n < 0) return -1;
-        *nbrick = n;
-        return t - 7 * strd_a;
-    }
-    if (crd_a > 0) {
-        *nbrick = b;
-        return t - strd_a;
-    }
-    int n = s_nbr[nb_minus(a)];
-    if (n < 0) return -1;
-    *nbrick = n;
-    return t + 7 * strd_a;
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
