@@ -304,6 +304,46 @@ TGV_API tgv_status tgv_extract_mesh(tgv_domain* d, int32_t level, int64_t* nvert
 TGV_API tgv_status tgv_copy_mesh(tgv_domain* d, float* verts, int64_t nverts, int32_t* tris, int64_t ntris);
 
 /* ---------------------------------------------------------------------------
+ * Joint solve of all levels of a domain on their composite grid (Sec. 3.3: in
+ * a 2:1-balanced octree a cube has up to four neighbours over a face; Eq. 2-3,
+ * Sec. 3.2), instead of one level after another with frozen shells.
+ * Leaves: voxels of level l in an active brick whose 8 children are not in an
+ * active brick of level l+1 (levels nested 2:1, as tgv_octree_build makes
+ * them).  Every difference is a unit index step, as on a single level; for
+ * leaf x and axis a the +a neighbours are the same-level leaf x + e_a, else
+ * the coarser leaf containing that position, else the 4 children of the
+ * refined voxel there on the face next to x, else none (likewise -a):
+ *   (G_a u)(x) = mean(u over +a neighbours) - u(x),
+ *   (B_a w)(x) = w(x) - mean(w over -a neighbours)   (0 without neighbours),
+ *   E(v)_ab = (B_a v_b + B_b v_a) / 2, div1 = -sum_a G_a^T,
+ *   (div2 q)_b = -sum_a B_a^T q_ab (exact negative adjoints);
+ * the Chambolle-Pock iteration of tgv_solve with the domain's parameters, each
+ * leaf using the histogram of its own level; outer boundaries Neumann (frozen
+ * bricks are not used).  State in FP32 whatever the domain's storage; u and
+ * ubar start from the levels' u, v, vbar, p, q from 0.  Leaf order: level by
+ * level, brick order, local voxel index.
+ * ------------------------------------------------------------------------- */
+typedef struct tgv_composite tgv_composite; /* opaque, library-owned */
+
+/* Builds the composite of every level of d (host lists + device state; the
+ * histograms must be accumulated).  Keeps a reference to d (destroy the
+ * composite first).  Errors: INVALID_ARG (levels not 2:1 nested), STATE,
+ * OUT_OF_MEMORY, UNSUPPORTED (2^31 leaves), CUDA.  Synchronises. */
+TGV_API tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out);
+/* `iterations` joint iterations (two kernels each) on d's stream. */
+TGV_API tgv_status tgv_composite_solve(tgv_composite* c, int32_t iterations);
+TGV_API int64_t tgv_composite_leaves(const tgv_composite* c);
+/* Leaves of one level (-1 for a bad level). */
+TGV_API int64_t tgv_composite_level_leaves(const tgv_composite* c, int32_t level);
+/* Copies u of every leaf (count = leaves, host or device).  Synchronises. */
+TGV_API tgv_status tgv_composite_extract(tgv_composite* c, float* u_out, int64_t count);
+/* Writes each leaf's u into its level's u (refined voxels keep theirs), so
+ * tgv_extract_field / tgv_extract_mesh see the joint result.  Synchronises. */
+TGV_API tgv_status tgv_composite_scatter(tgv_composite* c);
+TGV_API int64_t tgv_composite_launch_count(const tgv_composite* c);
+TGV_API void tgv_composite_destroy(tgv_composite* c);
+
+/* ---------------------------------------------------------------------------
  * Brick domains from depth maps (Sec. 3.3 Eq. 4, Sec. 4.1-4.2; in memory, one
  * GPU).  Every valid pixel of a pinhole map is a sample: its z-depth
  * unprojected to X, radius r = half the mean distance to the points of its

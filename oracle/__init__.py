@@ -177,6 +177,19 @@ def octree_build(cams, depths, root_min, root_edge: float, dmin: int, dmax: int,
     return levels, int(ns)
 
 
+def prox_many(ut: np.ndarray, hist: np.ndarray, tau: float, lam: float, centres: int = 0) -> np.ndarray:
+    """The histogram prox of many voxels at once (T7 read from Eq. 2's data term): the
+    median of the 2n + 1 values {c_b} and {ut - tau lam W_i}, W_i = sum_{b<i} h_b - sum_{b>=i} h_b."""
+    h = np.asarray(hist, np.float64)
+    n = h.shape[1]
+    b = np.arange(n)
+    c = -1.0 + 2.0 * b / (n - 1) if centres == 0 else -1.0 + (2.0 * b + 1.0) / n
+    cum = np.concatenate([np.zeros((h.shape[0], 1)), np.cumsum(h, 1)], 1)  # sum_{b<i}
+    W = cum - (cum[:, -1:] - cum)                                            # i = 0..n
+    vals = np.concatenate([np.broadcast_to(c, h.shape), ut[:, None] - tau * lam * W], 1)
+    return np.median(vals, axis=1)
+
+
 def atan2_as(y: float, x: float) -> float:
     """The FP32 arctangent of the spherical projection (A&S 4.4.49, explicit rounding)."""
     return float(lib().orc_atan2_as(float(y), float(x)))

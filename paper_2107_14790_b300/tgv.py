@@ -96,6 +96,14 @@ def lib() -> ctypes.CDLL:
         "tgv_pair_run_length": (i32, [P, i64, P, i64, i64, i32, P]),
         "tgv_extract_mesh": (i32, [P, i32, P, P]),
         "tgv_octree_build": (i32, [P, P, i32, P, i64, i64, P, P]),
+        "tgv_composite_create": (i32, [P, P]),
+        "tgv_composite_solve": (i32, [P, i32]),
+        "tgv_composite_leaves": (i64, [P]),
+        "tgv_composite_level_leaves": (i64, [P, i32]),
+        "tgv_composite_extract": (i32, [P, P, i64]),
+        "tgv_composite_scatter": (i32, [P]),
+        "tgv_composite_launch_count": (i64, [P]),
+        "tgv_composite_destroy": (None, [P]),
         "tgv_octree_levels": (i32, [P]),
         "tgv_octree_samples": (i64, [P]),
         "tgv_octree_level": (i32, [P, i32, P, P, P, P]),
@@ -350,6 +358,81 @@ def tgv_extract_mesh(d, level: int):
     tris = np.zeros((nt.value, 3), np.int32)
     tgv_copy_mesh(d, verts, tris)
     return verts, tris
+
+
+def tgv_composite_create(d):
+    h = ctypes.c_void_p()
+    _check(d, lib().tgv_composite_create(d, ctypes.byref(h)))
+    return h
+
+
+def tgv_composite_solve(c, d, iterations: int):
+    _check(d, lib().tgv_composite_solve(c, int(iterations)))
+
+
+def tgv_composite_leaves(c) -> int:
+    return int(lib().tgv_composite_leaves(c))
+
+
+def tgv_composite_level_leaves(c, level: int) -> int:
+    return int(lib().tgv_composite_level_leaves(c, level))
+
+
+def tgv_composite_extract(c, d) -> np.ndarray:
+    out = np.zeros(tgv_composite_leaves(c), np.float32)
+    _check(d, lib().tgv_composite_extract(c, out.ctypes.data, out.size))
+    return out
+
+
+def tgv_composite_scatter(c, d):
+    _check(d, lib().tgv_composite_scatter(c))
+
+
+def tgv_composite_launch_count(c) -> int:
+    return int(lib().tgv_composite_launch_count(c))
+
+
+def tgv_composite_destroy(c):
+    lib().tgv_composite_destroy(c)
+
+
+class Composite:
+    """Joint solve of every level of a Domain on their composite grid."""
+
+    def __init__(self, dom: "Domain"):
+        self.dom = dom
+        self.handle = tgv_composite_create(dom.handle)
+
+    @property
+    def leaves(self):
+        return tgv_composite_leaves(self.handle)
+
+    def level_leaves(self, level):
+        return tgv_composite_level_leaves(self.handle, level)
+
+    def solve(self, iterations):
+        tgv_composite_solve(self.handle, self.dom.handle, iterations)
+
+    def u(self):
+        return tgv_composite_extract(self.handle, self.dom.handle)
+
+    def scatter(self):
+        tgv_composite_scatter(self.handle, self.dom.handle)
+
+    @property
+    def launches(self):
+        return tgv_composite_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            tgv_composite_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class tgv_octree_cfg(ctypes.Structure):
