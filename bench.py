@@ -758,7 +758,7 @@ def run_composite(args):
             "ms_per_100_iterations": ms, "build_s": t_build,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "algorithmic_bytes_per_leaf": bpl,
-                         "note": "state bytes only; the neighbour and reverse lists add up to 192 B per leaf"},
+                         "note": "state bytes only; regular leaves add 24 B of neighbour ids, leaves at 2:1 faces 192 B of lists"},
             "cpu_baseline": {"value": small.n * 5 / t_cpu, "unit": "leaf-updates/s", "cores": 1, "kind": "oracle",
                              "sample": f"composite of the two coarsest levels ({small.n} leaves), 5 iterations"}}
 

@@ -15,7 +15,8 @@
 // level all of this is the iteration of tgv_iter_kernel without frozen bricks.
 //
 // State per leaf in FP32 (u, ubar, v, vbar, p, q and the packed histogram of its
-// level); one iteration = a dual kernel (p, q from ubar, vbar and the neighbour
+// level).  Regular leaves (one same-level neighbour or none per side) carry six
+// neighbour ids; leaves at 2:1 faces carry the full lists.  One iteration = a dual kernel (p, q from ubar, vbar and the neighbour
 // lists) and a primal kernel (divergences through the reverse lists, prox,
 // clamp, v update, over-relaxation), one thread per leaf.
 #include <math.h>
@@ -33,7 +34,9 @@ struct tgv_composite {
     std::vector<std::vector<int32_t>> leaf_slot;  // per level: slot (brick * 512 + local) of each leaf
     float *u = nullptr, *ubar = nullptr, *v = nullptr, *vbar = nullptr, *p = nullptr, *q = nullptr;
     uint32_t* hist = nullptr;                     // [n][npairs]
-    int32_t* lists = nullptr;                     // [n][4 kinds][3 axes][4]: fwd, bwd, rev fwd, rev bwd
+    int32_t* nb6 = nullptr;                       // [n][6]: +x +y +z -x -y -z neighbour of a regular leaf
+    int32_t* lists = nullptr;                     // [irregular][4 kinds][3 axes][4]: fwd, bwd, rev fwd, rev bwd
+    int64_t nirr = 0;
     int64_t launches = 0;
 };
 
@@ -45,18 +48,22 @@ constexpr uint32_t kQuarter = 0x80000000u;  // reverse-list weight 1/4 (else 1)
 struct CompArgs {
     float *u, *ubar, *v, *vbar, *p, *q;
     const uint32_t* hist;
-    const int32_t* lists;
+    const int32_t* nb6;    // regular leaf: six neighbour ids (-1 none); irregular: nb6[0] = -2 - index
+    const int32_t* lists;  // full lists of the irregular leaves
     int64_t n;
     int nbins, npairs, clamp_u;
     float alpha1, alpha0, tau, sigma, taulam;
     float c[TGV_MAX_BINS];
 };
 
-__device__ __forceinline__ const int32_t* list_of(const CompArgs& A, int64_t x, int kind, int a)
+__device__ __forceinline__ const int32_t* list_of(const CompArgs& A, int64_t irr, int kind, int a)
 {
-    return A.lists + ((x * 4 + kind) * 3 + a) * kList;
+    return A.lists + ((irr * 4 + kind) * 3 + a) * kList;
 }
 
+// Most leaves are regular: one same-level neighbour (or none) on every side,
+// so their reverse lists are the mirrored neighbours with weight 1 and six ids
+// describe them.  Leaves at 2:1 faces keep the full lists.
 __global__ void comp_dual_kernel(const CompArgs A)
 {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,8 +71,17 @@ __global__ void comp_dual_kernel(const CompArgs A)
     const float ub = A.ubar[x];
     float vb[3], g[3], dm[3][3];
     for (int c = 0; c < 3; ++c) vb[c] = A.vbar[3 * x + c];
+    const int32_t m0 = A.nb6[6 * x];
+    if (m0 > -2) {
+        for (int a = 0; a < 3; ++a) {
+            const int32_t f = A.nb6[6 * x + a], bk = A.nb6[6 * x + 3 + a];
+            g[a] = f >= 0 ? A.ubar[f] - ub : 0.0f;
+            for (int c = 0; c < 3; ++c) dm[a][c] = bk >= 0 ? vb[c] - A.vbar[3 * (int64_t)bk + c] : 0.0f;
+        }
+    } else {
+    const int64_t irr = -2 - (int64_t)m0;
     for (int a = 0; a < 3; ++a) {
-        const int32_t* f = list_of(A, x, 0, a);
+        const int32_t* f = list_of(A, irr, 0, a);
         int cnt = 0;
         float s = 0.0f;
         for (int k = 0; k < kList; ++k)
@@ -74,7 +90,7 @@ __global__ void comp_dual_kernel(const CompArgs A)
                 ++cnt;
             }
         g[a] = cnt ? (cnt == 1 ? s : 0.25f * s) - ub : 0.0f;
-        const int32_t* bl = list_of(A, x, 1, a);
+        const int32_t* bl = list_of(A, irr, 1, a);
         float w[3] = {0.0f, 0.0f, 0.0f};
         cnt = 0;
         for (int k = 0; k < kList; ++k)
@@ -83,6 +99,7 @@ __global__ void comp_dual_kernel(const CompArgs A)
                 ++cnt;
             }
         for (int c = 0; c < 3; ++c) dm[a][c] = cnt ? vb[c] - (cnt == 1 ? w[c] : 0.25f * w[c]) : 0.0f;
+    }
     }
     float pn[3], qn[6];
     for (int c = 0; c < 3; ++c) pn[c] = A.p[3 * x + c] + A.sigma * (g[c] - vb[c]);
@@ -110,10 +127,24 @@ __global__ void comp_primal_kernel(const CompArgs A)
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.n) return;
     float d1 = 0.0f, d2[3] = {0.0f, 0.0f, 0.0f};
+    const int32_t m0 = A.nb6[6 * x];
+    if (m0 > -2) {
+        for (int a = 0; a < 3; ++a) {
+            const int32_t f = A.nb6[6 * x + a], bk = A.nb6[6 * x + 3 + a];
+            if (f >= 0) d1 += A.p[3 * x + a];
+            if (bk >= 0) d1 -= A.p[3 * (int64_t)bk + a];
+            for (int b = 0; b < 3; ++b) {
+                const int qc = qidx_c(a, b);
+                if (bk >= 0) d2[b] -= A.q[6 * x + qc];
+                if (f >= 0) d2[b] += A.q[6 * (int64_t)f + qc];
+            }
+        }
+    } else {
+    const int64_t irr = -2 - (int64_t)m0;
     for (int a = 0; a < 3; ++a) {
         // div1 = sum_a ([x has +a neighbours] p_a(x) - sum over reverse +a list of w p_a(r))
-        if (list_of(A, x, 0, a)[0] >= 0) d1 += A.p[3 * x + a];
-        const int32_t* rf = list_of(A, x, 2, a);
+        if (list_of(A, irr, 0, a)[0] >= 0) d1 += A.p[3 * x + a];
+        const int32_t* rf = list_of(A, irr, 2, a);
         for (int k = 0; k < kList; ++k)
             if (rf[k] != -1) {
                 const int64_t r = rf[k] & 0x7fffffff;
@@ -121,8 +152,8 @@ __global__ void comp_primal_kernel(const CompArgs A)
                 d1 -= w * A.p[3 * r + a];
             }
         // (div2 q)_b = sum_a (-[x has -a neighbours] q_ab(x) + sum over reverse -a list of w q_ab(r))
-        const bool hb = list_of(A, x, 1, a)[0] >= 0;
-        const int32_t* rb = list_of(A, x, 3, a);
+        const bool hb = list_of(A, irr, 1, a)[0] >= 0;
+        const int32_t* rb = list_of(A, irr, 3, a);
         for (int b = 0; b < 3; ++b) {
             const int qc = qidx_c(a, b);
             if (hb) d2[b] -= A.q[6 * x + qc];
@@ -133,6 +164,7 @@ __global__ void comp_primal_kernel(const CompArgs A)
                     d2[b] += w * A.q[6 * r + qc];
                 }
         }
+    }
     }
     const float u0 = A.u[x];
     const float ut = u0 + A.tau * d1;
@@ -204,7 +236,7 @@ unsigned grid_of(int64_t n, int sms) { return (unsigned)std::max<int64_t>(1, std
 void free_comp(tgv_composite* c)
 {
     for (void* p : {(void*)c->u, (void*)c->ubar, (void*)c->v, (void*)c->vbar, (void*)c->p, (void*)c->q, (void*)c->hist,
-                    (void*)c->lists})
+                    (void*)c->lists, (void*)c->nb6})
         if (p) cudaFree(p);
 }
 
@@ -322,6 +354,32 @@ tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out)
                 }
             }
     if (!ok) return tgv_fail(d, TGV_ERR_INVALID_ARG, "a leaf has more than four neighbours over a face");
+    // regular leaves: at most one neighbour per side and mirrored reverse lists of weight 1
+    std::vector<int32_t> nb6((size_t)n * 6, -1), irr_lists;
+    int64_t nirr = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        const int32_t* L0 = &lists[(size_t)x * 4 * 3 * kList];
+        bool regular = true;
+        for (int a = 0; a < 3 && regular; ++a) {
+            const int32_t* f = L0 + (0 * 3 + a) * kList;
+            const int32_t* bk = L0 + (1 * 3 + a) * kList;
+            const int32_t* rf = L0 + (2 * 3 + a) * kList;
+            const int32_t* rb = L0 + (3 * 3 + a) * kList;
+            regular = f[1] < 0 && bk[1] < 0 && rf[1] == -1 && rb[1] == -1 && rf[0] == bk[0] && rb[0] == f[0];
+        }
+        if (regular) {
+            for (int a = 0; a < 3; ++a) {
+                nb6[(size_t)x * 6 + a] = L0[(0 * 3 + a) * kList];
+                nb6[(size_t)x * 6 + 3 + a] = L0[(1 * 3 + a) * kList];
+            }
+        } else {
+            nb6[(size_t)x * 6] = (int32_t)(-2 - nirr);
+            irr_lists.insert(irr_lists.end(), L0, L0 + 4 * 3 * kList);
+            ++nirr;
+        }
+    }
+    c->nirr = nirr;
+    std::vector<int32_t>().swap(lists);
     const int npairs = (d->prm.nbins + 1) / 2;
     cudaStream_t st = d->stream;
     auto alloc = [&](void** p, size_t bytes) {
@@ -335,11 +393,14 @@ tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out)
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     if (!alloc((void**)&c->u, nn * 4) || !alloc((void**)&c->ubar, nn * 4) || !alloc((void**)&c->v, nn * 12) ||
         !alloc((void**)&c->vbar, nn * 12) || !alloc((void**)&c->p, nn * 12) || !alloc((void**)&c->q, nn * 24) ||
-        !alloc((void**)&c->hist, nn * npairs * 4) || !alloc((void**)&c->lists, lists.size() * 4 + 16)) {
+        !alloc((void**)&c->hist, nn * npairs * 4) || !alloc((void**)&c->lists, irr_lists.size() * 4 + 16) ||
+        !alloc((void**)&c->nb6, nb6.size() * 4)) {
         free_comp(c.get());
         return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite allocation failed");
     }
-    cudaError_t e = cudaMemcpyAsync(c->lists, lists.data(), lists.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(c->nb6, nb6.data(), nb6.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !irr_lists.empty())
+        e = cudaMemcpyAsync(c->lists, irr_lists.data(), irr_lists.size() * 4, cudaMemcpyHostToDevice, st);
     for (void* p : {(void*)c->v, (void*)c->vbar, (void*)c->p, (void*)c->q}) {
         const size_t bytes = p == c->q ? nn * 24 : nn * 12;
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, st);
@@ -384,6 +445,7 @@ tgv_status tgv_composite_solve(tgv_composite* c, int32_t iterations)
     A.q = c->q;
     A.hist = c->hist;
     A.lists = c->lists;
+    A.nb6 = c->nb6;
     A.n = c->n;
     A.nbins = d->prm.nbins;
     A.npairs = (d->prm.nbins + 1) / 2;
