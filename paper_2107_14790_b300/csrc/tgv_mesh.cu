@@ -476,7 +476,10 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
     tgv_status st = build_up7(d, L);
     if (st != TGV_OK) return st;
     const int64_t ncell = L.nb * TGV_BVOX, nids = 4 * (L.nb + L.nf) * TGV_BVOX;
-    if (ncell == 0) return TGV_OK;
+    if (ncell == 0) {
+        d->mesh_nv = d->mesh_nt = 0;
+        return TGV_OK;
+    }
     if (nids >= ((int64_t)1 << 32) - 1 || ncell >= ((int64_t)1 << 32) - 1)
         return tgv_fail(d, TGV_ERR_UNSUPPORTED, "level too large for 32-bit mesh indices");
     if ((st = tgv_scratch(d, d->mesh_flags, sizeof(uint32_t) * (size_t)nids)) != TGV_OK) return st;

@@ -86,6 +86,11 @@ def test_empty_and_state_errors():
         dom.set_field(0, "u", np.ones((d.nvox, 1), np.float32))
         V, T = dom.mesh(0)
         assert V.shape == (0, 3) and T.shape == (0, 3)
+    # a level without active bricks extracts an empty mesh too
+    d2 = synth.DomainDesc(np.zeros(3), 1.0 / 16, np.zeros((0, 3), np.int32))
+    with tgv.Domain([d, d2], nbins=8, stream=torch.cuda.current_stream().cuda_stream) as dom:
+        V, T = dom.mesh(1)
+        assert V.shape == (0, 3) and T.shape == (0, 3)
 
 
 def test_solved_sphere_mesh(sphere_scene):
