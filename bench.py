@@ -149,9 +149,9 @@ def run_ours(args, cfg):
     from paper_2107_14790_b300 import build, tgv
 
     rank, world, local = dist_env()
-    if world > 1:
-        tdist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     build.build()
     tgv.lib()
     stream = torch.cuda.Stream()
@@ -381,9 +381,9 @@ def run_batched(args):
     from paper_2107_14790_b300.batching import union_level
     from paper_2107_14790_b300.multigpu import reduce_scalar, shard
     rank, world, local = dist_env()
-    if world > 1:
-        tdist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     build.build()
     iters = 300
     t_gen = time.perf_counter()
