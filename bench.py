@@ -238,12 +238,8 @@ def run_ours(args, cfg):
         "value": value, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else f"f32-math/{args.storage}-storage",
-        "data": "synthetic (seeded terrain scene, ray-cast depth maps)",
-        "config": {"workload": cfg["workload"], "voxels": nvox, "maps": cfg["nmaps"], "map_res": cfg["res"],
-                   "nbins": nbins, "iterations": iters, "energy_every": ce, "storage": args.storage,
-                   "l2": ("inputs larger than L2 (state %.2f GB)" if dom.nbytes > 126e6 else
-                          "state fits in L2 (%.2f GB): a parity case, not a roofline case") % (dom.nbytes / 1e9),
-                   "parallelism": f"independent instance per GPU x{world}"},
+        "data": scene_note(cfg),
+        "config": arm_config(cfg, args, nvox, dom.nbytes, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "kernel": {"paired": "tgv_iter_pair_kernel", "pipelined": "tgv_iter_pipe_kernel",
@@ -301,6 +297,21 @@ def oracle_sample(cfg, sc, bricks_per_axis=8, iters=100):
     return lvl.n * iters / dt, dt, f"{k}^3 bricks ({lvl.n} voxels) at the domain centre, all {len(sc.cameras)} maps, {iters} iterations + energy"
 
 
+def scene_note(cfg):
+    kind = "sphere" if cfg["n"] == 64 else "terrain"
+    return f"synthetic (seeded {kind} scene, ray-cast depth maps)"
+
+
+def arm_config(cfg, args, nvox, nbytes, world):
+    """The workload description both arms print."""
+    return {"workload": cfg["workload"], "voxels": nvox, "maps": cfg["nmaps"], "map_res": cfg["res"],
+            "nbins": cfg["nbins"], "iterations": cfg["iterations"], "energy_every": cfg["check_every"],
+            "storage": args.storage,
+            "l2": ("inputs larger than L2 (state %.2f GB)" if nbytes > 126e6 else
+                   "state fits in L2 (%.2f GB): a parity case, not a roofline case") % (nbytes / 1e9),
+            "parallelism": f"independent instance per GPU x{world}"}
+
+
 def cpu_baseline(cfg, sc):
     import oracle
     ups, dt, note = oracle_sample(cfg, sc)
@@ -334,8 +345,9 @@ def run_reference(args, cfg):
     return {"impl": "reference", "metric": "TGV voxel-updates/s (histograms + 500 fused primal-dual iterations + energy/gap)",
             "value": value, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded terrain scene, ray-cast depth maps)",
-            "config": {"workload": cfg["workload"], "sample": note},
+            "vs_baseline": None, "dtype": "f64", "data": scene_note(cfg),
+            "config": arm_config(cfg, args, sc.domain.nvox, sc.domain.nvox * (140 if args.storage == "fp32" else 92),
+                                 world),
             "cpu_baseline": {"value": value, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle",
                              "sample": note},
             "e2e": {"value": value, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
