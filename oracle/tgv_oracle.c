@@ -8,8 +8,7 @@
  * no code, header, table or helper with that library.
  *
  * Plain, slow, obviously correct loops.  Each function names the passage it
- * follows.  Where the paper is silent, the reading taken is stated inline and
- * listed in DESIGN.md ("readings").
+ * follows.  Where the paper is silent, the reading taken is stated inline.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC
  *   -ffp-contract=off is required: the histogram decision (Alg. 1) is taken in
