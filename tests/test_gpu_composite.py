@@ -102,3 +102,21 @@ def test_levels_that_are_not_nested_are_rejected():
     with tgv.Domain([coarse, fine, finer], nbins=8, stream=stream()) as dom:
         with pytest.raises(tgv.TgvError):
             tgv.Composite(dom)
+
+
+def test_frozen_bricks_of_the_levels_are_ignored(sphere_scene):
+    """Octree levels carry frozen shells for the level-by-level solve; the joint solve
+    uses the active bricks only, so it equals the solve of the same levels without them."""
+    sc = sphere_scene
+    dep = torch.from_numpy(np.stack(sc.depths)).cuda()
+    lv, _ = tgv.tgv_octree_build(sc.cameras, dep, np.array([-0.5, -0.5, -0.5]), 2.0, 5, 6, 1, stream=stream())
+    bare = [synth.DomainDesc(L.origin, L.h, L.bricks) for L in lv]
+    outs = []
+    for levels in (lv, bare):
+        with tgv.Domain(levels, nbins=8, stream=stream()) as dom:
+            for l in range(len(levels)):
+                dom.accumulate(l, sc.cameras, dep)
+            with tgv.Composite(dom) as comp:
+                comp.solve(15)
+                outs.append(comp.u())
+    np.testing.assert_array_equal(outs[0], outs[1])

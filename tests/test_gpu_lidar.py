@@ -89,3 +89,22 @@ def test_unknown_camera_model_is_rejected(lidar):
     with dom_of(sc.domain, sc.nbins) as dom:
         with pytest.raises(tgv.TgvError):
             dom.accumulate(0, [cam], dev(sc.depths[:1]), [5])
+
+
+def test_pinhole_and_spherical_maps_in_one_batch(lidar):
+    """One accumulate call may mix camera models (maps of one size)."""
+    sc = lidar
+    W, H = sc.cameras[0].width, sc.cameras[0].height
+    fx, fy, cx, cy = synth.pinhole_intrinsics(W, H, 60.0)
+    ph = synth.Camera(fx, fy, cx, cy, synth.look_at(np.array([0.5, -0.9, 0.5]), np.array([0.5, 0.5, 0.5])),
+                      np.array([0.5, -0.9, 0.5]), W, H)
+    dep = np.full((H, W), 1.4, np.float32)
+    cams = [sc.cameras[0], ph, sc.cameras[1]]
+    deps = [sc.depths[0], dep, sc.depths[1]]
+    votes = [5, 1, 5]
+    orc = oracle.OracleLevel(sc.domain, sc.nbins)
+    for c, d, v in zip(cams, deps, votes):
+        orc.accumulate(c, d, v)
+    with dom_of(sc.domain, sc.nbins) as dom:
+        dom.accumulate(0, cams, dev(deps), votes)
+        np.testing.assert_array_equal(dom.histograms(0), orc.hist)

@@ -80,3 +80,10 @@ def test_invalid_configs_and_spherical_maps(sphere_scene):
     with pytest.raises(tgv.TgvError) as e:
         tgv.tgv_octree_build([scan], torch.ones((1, 64, 128), device="cuda"), np.zeros(3), 1.0, 3, 6, 1)
     assert e.value.status == 7
+
+
+def test_maps_without_samples_give_empty_levels(sphere_scene):
+    sc = sphere_scene
+    nan = torch.full((2, sc.depths[0].shape[0], sc.depths[0].shape[1]), float("nan"), device="cuda")
+    lv, ns = tgv.tgv_octree_build(sc.cameras[:2], nan, np.zeros(3), 1.0, 3, 6, 1)
+    assert ns == 0 and all(L.nbricks == 0 and L.nfrozen == 0 for L in lv)
