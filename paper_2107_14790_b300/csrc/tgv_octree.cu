@@ -13,13 +13,15 @@
 // GPU: one pass unprojects a batch of maps, a second computes radius, depth and
 // brick key (level << 57 | Morton code of the brick) and inserts the key into a
 // device hash set (open addressing, bounded linear probing; a full table is
-// detected and the build retried with a larger one).  The unique keys (far fewer
-// than the samples) go to the host, which sorts them and forms the levels:
-// dilation by `band` rings of 26-neighbours, the 2:1 balance (finest first,
-// level l-1 gains the parents b >> 1 of level l's bricks dilated once, so every
-// finer level is wrapped by a shell of the next coarser one), and the frozen
-// shell of each level above the coarsest (26-neighbours of its active bricks
-// that are not active).  Bricks of a level are listed in Morton order.
+// detected and the build retried with a larger one).  The levels are formed from
+// the unique keys in a second device hash set, with no host pass over the keys:
+// dilation by `band` rings of 26-neighbours (all levels at once), the 2:1 balance
+// (finest first, level l-1 gains the parents b >> 1 of level l's bricks dilated
+// once, so every finer level is wrapped by a shell of the next coarser one), and
+// the frozen shell of each level above the coarsest (26-neighbours of its active
+// bricks that are not active) in a third set.  A stable LSD radix sort on the
+// device orders both sets by (level, Morton code); the host only splits the
+// sorted keys into levels and decodes the coordinates.
 #include <math.h>
 
 #include <algorithm>
@@ -75,6 +77,41 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z)
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
+}
+
+constexpr int kLevelShift = 57;
+constexpr uint64_t kMortonMask = ((uint64_t)1 << kLevelShift) - 1;
+
+// ---- device hash sets of 64-bit keys (open addressing, linear probing bounded by
+// kMaxProbe; a key never moves once written, so a slot reads either empty or final)
+__device__ __forceinline__ bool set_insert(uint64_t* table, uint64_t cap, uint64_t key)
+{
+    uint64_t h = mix64(key) & (cap - 1);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        const uint64_t cur = table[h];
+        if (cur == key) return true;
+        if (cur == kEmpty) {
+            const uint64_t prev = atomicCAS((unsigned long long*)&table[h], (unsigned long long)kEmpty,
+                                            (unsigned long long)key);
+            if (prev == kEmpty || prev == key) return true;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    return false;
+}
+
+// membership in a set that no thread modifies meanwhile: every key present sits
+// within kMaxProbe slots of its home (its insertion reported failure otherwise)
+__device__ __forceinline__ bool set_contains(const uint64_t* table, uint64_t cap, uint64_t key)
+{
+    uint64_t h = mix64(key) & (cap - 1);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        const uint64_t cur = table[h];
+        if (cur == key) return true;
+        if (cur == kEmpty) return false;
+        h = (h + 1) & (cap - 1);
+    }
+    return false;
 }
 
 struct OctCam {
@@ -160,70 +197,188 @@ __global__ void oct_key_kernel(const OctArgs A)
         }
         if (!inside) continue;
         ++mine;
-        const uint64_t key = ((uint64_t)(d - A.dmin) << 57) | morton3(q[0] >> 3, q[1] >> 3, q[2] >> 3);
-        uint64_t h = mix64(key) & (A.cap - 1);
-        bool done = false;
-        for (int probe = 0; probe < kMaxProbe && !done; ++probe) {
-            const uint64_t cur = A.table[h];
-            if (cur == key) {
-                done = true;
-            } else if (cur == kEmpty) {
-                const uint64_t prev = atomicCAS((unsigned long long*)&A.table[h], (unsigned long long)kEmpty,
-                                                (unsigned long long)key);
-                if (prev == kEmpty || prev == key) done = true;
-                else h = (h + 1) & (A.cap - 1);
-            } else {
-                h = (h + 1) & (A.cap - 1);
-            }
-        }
-        if (!done) ++fails;
+        const uint64_t key = ((uint64_t)(d - A.dmin) << kLevelShift) | morton3(q[0] >> 3, q[1] >> 3, q[2] >> 3);
+        if (!set_insert(A.table, A.cap, key)) ++fails;
     }
     if (mine) atomicAdd(&A.counters[0], mine);
     if (fails) atomicAdd(&A.counters[1], fails);
 }
 
-__global__ void oct_compact_kernel(const uint64_t* table, uint64_t cap, uint64_t* out, unsigned long long* n)
+// the keys of a set (of one level, or all with level < 0) to a list; *n counts them
+__global__ void oct_compact_kernel(const uint64_t* table, uint64_t cap, int level, uint64_t* out,
+                                   unsigned long long* n)
 {
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = table[k];
-        if (v != kEmpty) out[atomicAdd(n, 1ull)] = v;
+        if (v != kEmpty && (level < 0 || (int)(v >> kLevelShift) == level)) out[atomicAdd(n, 1ull)] = v;
     }
 }
 
-// ---- host set operations on sorted Morton keys of one level
-using Keys = std::vector<uint64_t>;
+struct LevelDims {
+    int64_t per_axis[32];  // bricks per axis of each level
+};
 
-void sort_unique(Keys& k)
-{
-    std::sort(k.begin(), k.end());
-    k.erase(std::unique(k.begin(), k.end()), k.end());
-}
+enum NeighbourMode { kSelf = 0, kRing = 1, kParentRing = 2, kShell = 3 };
 
-Keys dilate(const Keys& s, int64_t nbr)
+// For each key of `list` (*n of them), inserts into `dst`:
+//   kSelf        the key itself;
+//   kRing        its 27-neighbourhood (itself included) at its level;
+//   kParentRing  the 27-neighbourhood of its parent b >> 1 one level coarser;
+//   kShell       its 26 neighbours that `act` does not hold (levels above 0 only).
+// Neighbours outside the level's cube are dropped.  Failed insertions are counted.
+__global__ void oct_neighbour_kernel(const uint64_t* list, const unsigned long long* n, uint64_t* dst,
+                                     uint64_t cap, const uint64_t* act, uint64_t act_cap, const LevelDims D,
+                                     int mode, unsigned long long* fails)
 {
-    Keys o;
-    o.reserve(s.size() * 27);
-    for (uint64_t key : s) {
-        const int64_t x = (int64_t)compact3(key), y = (int64_t)compact3(key >> 1), z = (int64_t)compact3(key >> 2);
+    const uint64_t count = *n;
+    unsigned long long bad = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = list[i];
+        int l = (int)(key >> kLevelShift);
+        if (mode == kSelf) {
+            if (!set_insert(dst, cap, key)) ++bad;
+            continue;
+        }
+        const uint64_t m = key & kMortonMask;
+        int64_t x = (int64_t)compact3(m), y = (int64_t)compact3(m >> 1), z = (int64_t)compact3(m >> 2);
+        if (mode == kParentRing) {
+            if (l == 0) continue;
+            --l;
+            x >>= 1;
+            y >>= 1;
+            z >>= 1;
+        }
+        if (mode == kShell && l == 0) continue;
+        const int64_t P = D.per_axis[l];
+        const uint64_t tag = (uint64_t)l << kLevelShift;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
+                    if (mode == kShell && dx == 0 && dy == 0 && dz == 0) continue;
                     const int64_t a = x + dx, b = y + dy, c = z + dz;
-                    if (a < 0 || b < 0 || c < 0 || a >= nbr || b >= nbr || c >= nbr) continue;
-                    o.push_back(morton3((uint64_t)a, (uint64_t)b, (uint64_t)c));
+                    if (a < 0 || b < 0 || c < 0 || a >= P || b >= P || c >= P) continue;
+                    const uint64_t nk = tag | morton3((uint64_t)a, (uint64_t)b, (uint64_t)c);
+                    if (mode == kShell && set_contains(act, act_cap, nk)) continue;
+                    if (!set_insert(dst, cap, nk)) ++bad;
                 }
     }
-    sort_unique(o);
-    return o;
+    if (bad) atomicAdd(fails, bad);
 }
 
-void decode(const Keys& k, std::vector<int32_t>& out)
+// ---- stable LSD radix sort of 64-bit keys, 8-bit digits, tiles of 1024 keys
+constexpr int kRsThreads = 256, kRsTile = 1024;
+
+// digit counts of each tile, digit-major: hist[digit * tiles + tile]
+__global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint64_t* keys, int64_t n, int shift,
+                                                               uint32_t* hist, int64_t tiles)
 {
-    out.resize(3 * k.size());
-    for (size_t i = 0; i < k.size(); ++i) {
-        out[3 * i] = (int32_t)compact3(k[i]);
-        out[3 * i + 1] = (int32_t)compact3(k[i] >> 1);
-        out[3 * i + 2] = (int32_t)compact3(k[i] >> 2);
+    __shared__ uint32_t s[256];
+    s[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int k = threadIdx.x; k < kRsTile; k += kRsThreads) {
+        const int64_t i = base + k;
+        if (i < n) atomicAdd(&s[(keys[i] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = s[threadIdx.x];
+}
+
+// exclusive prefix sum of m counts in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t* a, int64_t m)
+{
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < m; base += 1024) {
+        const int64_t i = base + t;
+        const uint32_t v = i < m ? a[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        if (i < m) a[i] = carry + (w ? wsum[w - 1] : 0u) + x - v;
+        carry += wsum[31];
+        __syncthreads();  // wsum is rewritten by the next chunk
+    }
+}
+
+// each tile's keys to their slots: the tile's first slot of the digit plus the key's
+// rank among the tile's earlier keys of that digit (ranks in index order: stable)
+__global__ void __launch_bounds__(kRsThreads) rs_scatter_kernel(const uint64_t* in, uint64_t* out, int64_t n,
+                                                                  int shift, const uint32_t* offs, int64_t tiles)
+{
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_cnt[kRsThreads / 32][256];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    s_run[t] = offs[(int64_t)t * tiles + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsTile / kRsThreads; ++r) {
+#pragma unroll
+        for (int k = 0; k < kRsThreads / 32; ++k) s_cnt[k][t] = 0;
+        __syncthreads();
+        const int64_t i = base + r * kRsThreads + t;
+        const bool valid = i < n;
+        const uint64_t key = valid ? in[i] : 0;
+        const uint32_t dg = valid ? (uint32_t)((key >> shift) & 0xff) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) s_cnt[w][dg] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = 0;  // digit t: counts of the earlier warps
+#pragma unroll
+        for (int k = 0; k < kRsThreads / 32; ++k) {
+            const uint32_t c = s_cnt[k][t];
+            s_cnt[k][t] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (valid) out[s_run[dg] + s_cnt[w][dg] + rank] = key;
+        __syncthreads();
+        s_run[t] += acc;
+    }
+}
+
+// sorts n keys by the 8-bit digits at `shifts` (least significant first); `tmp`
+// holds n keys, `hist` 256 * ceil(n / 1024) counts
+cudaError_t radix_sort(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, const std::vector<int>& shifts,
+                       cudaStream_t s)
+{
+    if (n <= 1) return cudaSuccess;
+    const int64_t tiles = (n + kRsTile - 1) / kRsTile;
+    uint64_t *a = keys, *b = tmp;
+    for (int sh : shifts) {
+        rs_hist_kernel<<<(unsigned)tiles, kRsThreads, 0, s>>>(a, n, sh, hist, tiles);
+        rs_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
+        rs_scatter_kernel<<<(unsigned)tiles, kRsThreads, 0, s>>>(a, b, n, sh, hist, tiles);
+        std::swap(a, b);
+    }
+    if (a != keys) return cudaMemcpyAsync(keys, a, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+void decode(const uint64_t* k, size_t n, std::vector<int32_t>& out)
+{
+    out.resize(3 * n);
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t m = k[i] & kMortonMask;
+        out[3 * i] = (int32_t)compact3(m);
+        out[3 * i + 1] = (int32_t)compact3(m >> 1);
+        out[3 * i + 2] = (int32_t)compact3(m >> 2);
     }
 }
 
@@ -277,7 +432,6 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
         return TGV_ERR_OUT_OF_MEMORY;
     }
     uint64_t cap = (uint64_t)1 << 20;
-    Keys keys;
     unsigned long long hc[2] = {0, 0};
     for (int attempt = 0; attempt < 6; ++attempt) {
         if (table.p) cudaFree(table.p);
@@ -328,54 +482,123 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
         cap <<= 2;  // a probe sequence ran out: retry with a table four times larger
         if (attempt == 5) return TGV_ERR_BUDGET;
     }
-    // unique keys to the host
+    // unique sample keys to a list on the device
     unsigned long long nu = 0;
     if (cudaMalloc(&uniq.p, sizeof(uint64_t) * cap) != cudaSuccess) {
         cudaGetLastError();
         return TGV_ERR_OUT_OF_MEMORY;
     }
-    e = cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-        oct_compact_kernel<<<(unsigned)std::min<uint64_t>((cap + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(
-            (const uint64_t*)table.p, cap, (uint64_t*)uniq.p, (unsigned long long*)cnt.p);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nu, cnt.p, sizeof(nu), cudaMemcpyDeviceToHost, s);
+    const unsigned sgrid = (unsigned)sms * 8;
+    auto compact = [&](const void* tab, uint64_t c, int level, void* list, unsigned long long* n) -> cudaError_t {
+        cudaError_t r = cudaMemsetAsync(n, 0, sizeof(unsigned long long), s);
+        if (r != cudaSuccess) return r;
+        oct_compact_kernel<<<(unsigned)std::min<uint64_t>((c + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(
+            (const uint64_t*)tab, c, level, (uint64_t*)list, n);
+        return cudaGetLastError();
+    };
+    unsigned long long* dcnt = (unsigned long long*)cnt.p;
+    e = compact(table.p, cap, -1, uniq.p, dcnt);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nu, dcnt, sizeof(nu), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) {
-        keys.resize(nu);
-        if (nu) e = cudaMemcpy(keys.data(), uniq.p, sizeof(uint64_t) * nu, cudaMemcpyDeviceToHost);
-    }
     if (e != cudaSuccess) return TGV_ERR_CUDA;
-    // levels
-    std::vector<Keys> act(nlev);
-    for (uint64_t k : keys) act[k >> 57].push_back(k & ((((uint64_t)1) << 57) - 1));
-    auto per_axis = [&](int l) -> int64_t { return std::max<int64_t>(((int64_t)1 << (cfg->depth_min + l)) >> 3, 1); };
-    for (int l = 0; l < nlev; ++l) {
-        sort_unique(act[l]);
-        for (int b = 0; b < cfg->band; ++b) act[l] = dilate(act[l], per_axis(l));
+    cudaFree(table.p);
+    table.p = nullptr;
+
+    LevelDims D;
+    for (int l = 0; l < 32; ++l)
+        D.per_axis[l] = l < nlev ? std::max<int64_t>(((int64_t)1 << (cfg->depth_min + l)) >> 3, 1) : 1;
+    // level sets: active (act) and frozen shells (frz), with their key lists
+    DevBuf act, frz, lst, lst2, tmp, hist, sc;
+    unsigned long long hs[3] = {0, 0, 0};  // failed insertions, active keys, frozen keys
+    if (cudaMalloc(&sc.p, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return TGV_ERR_OUT_OF_MEMORY;
     }
-    for (int l = nlev - 1; l >= 1; --l) {
-        Keys par;
-        par.reserve(act[l].size());
-        for (uint64_t k : act[l]) par.push_back(morton3(compact3(k) >> 1, compact3(k >> 1) >> 1, compact3(k >> 2) >> 1));
-        sort_unique(par);
-        Keys dl = dilate(par, per_axis(l - 1));
-        act[l - 1].insert(act[l - 1].end(), dl.begin(), dl.end());
-        sort_unique(act[l - 1]);
+    unsigned long long* dsc = (unsigned long long*)sc.p;
+    uint64_t cap2 = (uint64_t)1 << 20;
+    while (cap2 < 64 * (uint64_t)nu) cap2 <<= 1;
+    for (int attempt = 0; nu > 0; ++attempt) {
+        for (DevBuf* b : {&act, &frz, &lst, &lst2, &tmp, &hist}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+        }
+        const size_t kb = sizeof(uint64_t) * cap2;
+        if (cudaMalloc(&act.p, kb) != cudaSuccess || cudaMalloc(&frz.p, kb) != cudaSuccess ||
+            cudaMalloc(&lst.p, kb) != cudaSuccess || cudaMalloc(&lst2.p, kb) != cudaSuccess ||
+            cudaMalloc(&tmp.p, kb) != cudaSuccess ||
+            cudaMalloc(&hist.p, sizeof(uint32_t) * 256 * (cap2 / kRsTile + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return TGV_ERR_OUT_OF_MEMORY;
+        }
+        uint64_t *A = (uint64_t*)act.p, *F = (uint64_t*)frz.p, *L1 = (uint64_t*)lst.p, *L2 = (uint64_t*)lst2.p;
+        e = cudaMemsetAsync(A, 0xff, kb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F, 0xff, kb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dsc, 0, 3 * sizeof(unsigned long long), s);
+        auto expand = [&](const uint64_t* list, const unsigned long long* n, uint64_t* dst, const uint64_t* in,
+                          int mode) {
+            if (e != cudaSuccess) return;
+            oct_neighbour_kernel<<<sgrid, 256, 0, s>>>(list, n, dst, cap2, in, cap2, D, mode, dsc);
+            e = cudaGetLastError();
+        };
+        auto list_of = [&](const uint64_t* tab, int level, uint64_t* list, unsigned long long* n) {
+            if (e == cudaSuccess) e = compact(tab, cap2, level, list, n);
+        };
+        // the sample bricks, then `band` rings of neighbours on every level at once
+        expand((const uint64_t*)uniq.p, dcnt, A, nullptr, kSelf);
+        for (int b = 0; b < cfg->band; ++b) {
+            list_of(A, -1, L1, dsc + 1);
+            expand(L1, dsc + 1, A, nullptr, kRing);
+        }
+        // 2:1 balance, finest level first (level l-1 sees level l's final bricks)
+        for (int l = nlev - 1; l >= 1; --l) {
+            list_of(A, l, L1, dsc + 1);
+            expand(L1, dsc + 1, A, nullptr, kParentRing);
+        }
+        // frozen shells from the final active bricks of all levels
+        list_of(A, -1, L1, dsc + 1);
+        expand(L1, dsc + 1, F, A, kShell);
+        list_of(F, -1, L2, dsc + 2);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, dsc, sizeof(hs), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return TGV_ERR_CUDA;
+        if (hs[0] == 0) break;
+        if (attempt == 5) return TGV_ERR_BUDGET;
+        cap2 <<= 2;  // a probe sequence ran out: redo the level sets in a larger table
+    }
+    // order both sets by (level, Morton code): the Morton digits of the finest level,
+    // then the level digit
+    std::vector<int> shifts;
+    for (int sh = 0; sh < 3 * (cfg->depth_max - 3); sh += 8) shifts.push_back(sh);
+    shifts.push_back(kLevelShift);
+    std::vector<uint64_t> ka(hs[1]), kf(hs[2]);
+    if (nu > 0) {
+        e = radix_sort((uint64_t*)lst.p, (uint64_t*)tmp.p, (uint32_t*)hist.p, (int64_t)hs[1], shifts, s);
+        if (e == cudaSuccess)
+            e = radix_sort((uint64_t*)lst2.p, (uint64_t*)tmp.p, (uint32_t*)hist.p, (int64_t)hs[2], shifts, s);
+        if (e == cudaSuccess && hs[1])
+            e = cudaMemcpyAsync(ka.data(), lst.p, sizeof(uint64_t) * hs[1], cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && hs[2])
+            e = cudaMemcpyAsync(kf.data(), lst2.p, sizeof(uint64_t) * hs[2], cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return TGV_ERR_CUDA;
     }
     tgv_octree* o = new (std::nothrow) tgv_octree();
     if (!o) return TGV_ERR_OUT_OF_MEMORY;
     o->samples = (int64_t)hc[0];
     o->levels.resize(nlev);
-    for (int l = 0; l < nlev; ++l) {
-        Keys frz;
-        if (l > 0) {
-            Keys dl = dilate(act[l], per_axis(l));
-            std::set_difference(dl.begin(), dl.end(), act[l].begin(), act[l].end(), std::back_inserter(frz));
+    // split the sorted keys into their levels
+    auto split = [&](const std::vector<uint64_t>& k, bool frozen) {
+        size_t i = 0;
+        for (int l = 0; l < nlev; ++l) {
+            size_t j = i;
+            while (j < k.size() && (int)(k[j] >> kLevelShift) == l) ++j;
+            decode(k.data() + i, j - i, frozen ? o->levels[l].frozen : o->levels[l].active);
+            i = j;
         }
-        decode(act[l], o->levels[l].active);
-        decode(frz, o->levels[l].frozen);
+    };
+    split(ka, false);
+    split(kf, true);
+    for (int l = 0; l < nlev; ++l) {
         const double h = cfg->root_edge / (double)((int64_t)1 << (cfg->depth_min + l));
         for (int a = 0; a < 3; ++a) o->levels[l].origin[a] = cfg->root_min[a];
         o->levels[l].h = h;

@@ -288,7 +288,7 @@ struct EnergyArgs {
     const uint32_t* hist;
     const int32_t* nbr;
     const int32_t* work;  // item -> brick (nullptr: identity)
-    int64_t nb, nall;
+    int64_t nb, nall, nitems;
     int nbins, npairs;
     float alpha1, alpha0, lambda, box_v;
     float c[TGV_MAX_BINS];
@@ -324,10 +324,13 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
     constexpr int NBM = NB ? NB : TGV_MAX_BINS;
     __shared__ int32_t s_nbr[TGV_NNBR];
     __shared__ double s_red[3][16];
-    const int64_t item = blockIdx.x;
-    const int64_t b = A.work ? (int64_t)A.work[item] : item;
     const int t = threadIdx.x;
     const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    // per-warp running sums over the CTA's bricks (FP64, in brick order)
+    double acc_en = 0.0, acc_du = 0.0, acc_vm = 0.0;
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+    const int64_t b = A.work ? (int64_t)A.work[item] : item;
+    __syncthreads();  // the previous brick's neighbour row is no longer read
     if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
     const int nbins = NB ? NB : A.nbins;
     const float* ub = A.u + b * TGV_BVOX;
@@ -451,11 +454,15 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
         du += __shfl_down_sync(0xffffffffu, du, o);
         vm = fmaxf(vm, __shfl_down_sync(0xffffffffu, vm, o));
     }
+    acc_en += (double)en;
+    acc_du += (double)du;
+    acc_vm = fmax(acc_vm, (double)vm);
+    }
     const int w = t >> 5, lane = t & 31;
     if (lane == 0) {
-        s_red[0][w] = (double)en;
-        s_red[1][w] = (double)du;
-        s_red[2][w] = (double)vm;
+        s_red[0][w] = acc_en;
+        s_red[1][w] = acc_du;
+        s_red[2][w] = acc_vm;
     }
     __syncthreads();
     if (t == 0) {
@@ -465,21 +472,37 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
             sd += s_red[1][k];
             sm = fmax(sm, s_red[2][k]);
         }
-        A.partial[3 * item + 0] = se;
-        A.partial[3 * item + 1] = sd;
-        A.partial[3 * item + 2] = sm;
+        A.partial[3 * blockIdx.x + 0] = se;
+        A.partial[3 * blockIdx.x + 1] = sd;
+        A.partial[3 * blockIdx.x + 2] = sm;
     }
 }
 
-template <typename S>
-static void launch_energy_kernel(const EnergyArgs<S>& A, int64_t nitems, cudaStream_t stream)
+// CTAs of the persistent energy kernel: three per SM (capped by the bricks)
+static int64_t energy_grid(int64_t nitems)
 {
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    const int64_t g = 3 * (int64_t)(sms[dev] > 0 ? sms[dev] : 1);
+    return nitems < g ? nitems : g;
+}
+
+// launches the energy kernel; returns its grid (the number of partials)
+template <typename S>
+static int64_t launch_energy_kernel(EnergyArgs<S> A, int64_t nitems, cudaStream_t stream)
+{
+    const int64_t grid = energy_grid(nitems);
+    A.nitems = nitems;
     switch (A.nbins) {
-    case 8: tgv_energy_kernel<S, 8><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
-    case 10: tgv_energy_kernel<S, 10><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
-    case 12: tgv_energy_kernel<S, 12><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
-    default: tgv_energy_kernel<S, 0><<<(unsigned)nitems, TGV_BVOX, 0, stream>>>(A); break;
+    case 8: tgv_energy_kernel<S, 8><<<(unsigned)grid, TGV_BVOX, 0, stream>>>(A); break;
+    case 10: tgv_energy_kernel<S, 10><<<(unsigned)grid, TGV_BVOX, 0, stream>>>(A); break;
+    case 12: tgv_energy_kernel<S, 12><<<(unsigned)grid, TGV_BVOX, 0, stream>>>(A); break;
+    default: tgv_energy_kernel<S, 0><<<(unsigned)grid, TGV_BVOX, 0, stream>>>(A); break;
     }
+    return grid;
 }
 
 // One block sums the per-block partials in a fixed order.
@@ -572,8 +595,8 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     A.box_v = d->prm.box_v;
     tgv_bin_centres(d->prm, A.c);
     A.partial = (double*)d->red.ptr;
-    launch_energy_kernel<S>(A, nitems, d->stream);
-    tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, nitems, d->prm.box_v, d->red_out);
+    const int64_t parts = launch_energy_kernel<S>(A, nitems, d->stream);
+    tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, parts, d->prm.box_v, d->red_out);
     d->launches += 2;
     st = tgv_cuda_check(d, cudaGetLastError(), "tgv_energy_kernel launch");
     if (st != TGV_OK) return st;
@@ -624,8 +647,8 @@ static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_param
     A.box_v = prm.box_v;
     tgv_bin_centres(prm, A.c);
     A.partial = partial;
-    launch_energy_kernel<S>(A, s.nbricks, stream);
-    tgv_reduce_partials<<<1, 1024, 0, stream>>>(partial, s.nbricks, prm.box_v, result);
+    const int64_t parts = launch_energy_kernel<S>(A, s.nbricks, stream);
+    tgv_reduce_partials<<<1, 1024, 0, stream>>>(partial, parts, prm.box_v, result);
     return cudaGetLastError();
 }
 
