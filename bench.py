@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree", "composite"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree", "composite",
+                             "histforms"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
                          "300 iterations; serving: Poisson stream of 2000 chunk-solve requests")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
@@ -542,6 +543,52 @@ def run_multilevel(args):
                              "scaled-down scene in tests/test_gpu_multilevel.py"}
 
 
+def run_histforms(args):
+    """The two forms of the histogram kernel on the 256^3 terrain's 64 aerial maps 512^2:
+    gather (one thread per voxel, every map) and scatter (one thread per pyramid pixel,
+    atomic votes).  Same counts bit for bit (checked here on the whole domain); the time
+    of one accumulate call of all 64 maps (pyramids included), CUDA events."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import build, tgv
+    build.build()
+    torch.cuda.set_device(0)
+    sc = synth.terrain_scene(1002, 256, 64, 512, 10, 500, device="cuda")
+    photos = torch.from_numpy(np.stack(sc.depths)).cuda()
+    stream = torch.cuda.Stream()
+    out = {}
+    hists = {}
+    for form in ("gather", "scatter"):
+        dom = tgv.Domain([sc.domain], nbins=10, stream=stream.cuda_stream, hist_form=form)
+        nvox = dom.voxels(0)
+        for _ in range(max(1, args.warmup)):
+            dom.reset(0, clear_hist=True)
+            dom.accumulate(0, sc.cameras, photos)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(args.steps):
+            dom.reset(0, clear_hist=True)
+            e0.record(stream)
+            dom.accumulate(0, sc.cameras, photos)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        hists[form] = dom.histograms(0)
+        dom.close()
+        med = float(np.median(ms))
+        out[form] = {"ms": med, "pairs_per_s": nvox * len(sc.cameras) / (med / 1e3)}
+    same = bool(np.array_equal(hists["gather"], hists["scatter"]))
+    return {"metric": "histograms: (voxel, map) pairs/s (Alg. 1), gather vs scatter form",
+            "value": out["scatter"]["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic (seeded terrain, 64 aerial maps 512^2)",
+            "config": {"workload": "dense-256^3-terrain-64x512^2-maps-10bins-histograms", "voxels": nvox,
+                       "maps": len(sc.cameras)},
+            "gather": out["gather"], "scatter": out["scatter"],
+            "scatter_over_gather": out["scatter"]["pairs_per_s"] / out["gather"]["pairs_per_s"],
+            "votes_total": int(hists["gather"].sum()), "identical_counts": same}
+
+
 def run_lidar(args):
     """Ground LIDAR scans (spherical range maps, vote 5) of the 256^3 terrain next to its 64
     aerial photos (pinhole z-depth maps, vote 1): histogram throughput of each map kind, then
@@ -869,6 +916,9 @@ def main():
         return
     if args.workload == "lidar":
         print(json.dumps(run_lidar(args)), flush=True)
+        return
+    if args.workload == "histforms":
+        print(json.dumps(run_histforms(args)), flush=True)
         return
     cfg = SMALL if args.small else WORKLOAD
     if args.impl == "reference":

@@ -87,13 +87,24 @@ enum { TGV_PINHOLE = 0, TGV_SPHERICAL = 1 };
  */
 enum { TGV_ITER_PIPELINED = 0, TGV_ITER_ONE_BRICK_PER_CTA = 1, TGV_ITER_PAIRED = 2 };
 
+/* Form of the histogram kernel of tgv_accumulate_depthmap(s) (identical counts):
+ * GATHER:  one thread per voxel evaluates Alg. 1 for every map of a launch and
+ *          adds its votes to its own words once (default);
+ * SCATTER: one thread per depth-pyramid pixel walks the voxels its frustum can
+ *          own (within the pixel's level-of-detail depth window and up to its
+ *          depth + eta), repeats each voxel's Alg. 1 decision and adds the vote
+ *          with an atomic when the decision picks this pixel.  Pinhole maps only
+ *          (TGV_ERR_UNSUPPORTED otherwise); the bounding box of a level's active
+ *          bricks is indexed densely (at most 2^28 brick cells). */
+enum { TGV_HIST_GATHER = 0, TGV_HIST_SCATTER = 1 };
+
 typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
 
 /* Solver parameters (Eq. 2 with the primal-dual step sizes of Sec. 3.2).
  * Defaults (tgv_default_params): nbins 8 (Alg. 1), alpha1 1, alpha0 2, lambda 1,
  * tau = sigma = 0.2 (tau*sigma*24 < 1: ||K||^2 <= 24 for the forward/backward
  * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2,
- * paired iteration kernel, x_run 0 (automatic). */
+ * paired iteration kernel, x_run 0 (automatic), gather-form histograms. */
 typedef struct {
     int32_t nbins;       /* histogram bins, 2..16 */
     float alpha1;        /* weight of |grad u - v| */
@@ -110,6 +121,7 @@ typedef struct {
                           * consecutive items, so x-neighbouring bricks pass their face
                           * duals through shared memory; results do not depend on it.
                           * 0 = chosen from the item and SM counts, 1 = no runs. */
+    int32_t hist_form;   /* TGV_HIST_* form of the histogram kernel */
 } tgv_params;
 
 /* One level of a domain (all arrays host memory, copied at creation).

@@ -298,7 +298,7 @@ void free_level(TgvLevel& L)
 {
     free_graphs(L);
     void* ptrs[] = {L.u, L.ubar[0], L.ubar[1], L.v, L.vbar[0], L.vbar[1], L.p[0], L.p[1],
-                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev, L.work, L.up7};
+                    L.q[0], L.q[1], L.hist, L.nbr, L.coords_dev, L.work, L.up7, L.bgrid};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -513,6 +513,7 @@ tgv_status tgv_default_params(tgv_params* out)
     out->box_v = 2.0f;
     out->iter_kernel = TGV_ITER_PAIRED;
     out->x_run = 0;
+    out->hist_form = TGV_HIST_GATHER;
     return TGV_OK;
 }
 
@@ -529,6 +530,7 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
         prm->iter_kernel != TGV_ITER_PAIRED)
         return TGV_ERR_INVALID_ARG;
     if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
+    if (prm->hist_form != TGV_HIST_GATHER && prm->hist_form != TGV_HIST_SCATTER) return TGV_ERR_INVALID_ARG;
     if (!(prm->alpha1 > 0.0f) || !(prm->alpha0 > 0.0f) || !(prm->lambda >= 0.0f) || !(prm->tau > 0.0f) ||
         !(prm->sigma > 0.0f) || !(prm->box_v > 0.0f))
         return TGV_ERR_INVALID_ARG;

@@ -20,6 +20,9 @@
 // contracted into FMAs).
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "tgv_internal.cuh"
 
 #define TGV_MAX_LEVELS 16
@@ -125,17 +128,19 @@ __global__ void pyr_down_kernel(float* __restrict__ pyr, int64_t size, int nmaps
     }
 }
 
-__device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, const float* __restrict__ pyr,
-                                        const float X[3], float diam, float delta, float eta, int nbins)
+// Alg. 1 up to the depth read: LOD level l and pixel (i, j) of the voxel centre X,
+// and its distance to the camera.  false: not projected into the map.
+__device__ __forceinline__ bool alg1_pixel(const Alg1Cam& c, const PyrLayout& L, const float X[3], float diam,
+                                           int& l, int& i, int& j, float& dist)
 {
     const float d0 = __fsub_rn(X[0], c.C[0]);
     const float d1 = __fsub_rn(X[1], c.C[1]);
     const float d2 = __fsub_rn(X[2], c.C[2]);
     const float zc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[6], d0), __fmul_rn(c.R[7], d1)), __fmul_rn(c.R[8], d2));
-    if (c.model == TGV_PINHOLE && !(zc > 0.0f)) return -1;
+    if (c.model == TGV_PINHOLE && !(zc > 0.0f)) return false;
     const float xc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], d0), __fmul_rn(c.R[1], d1)), __fmul_rn(c.R[2], d2));
     const float yc = __fadd_rn(__fadd_rn(__fmul_rn(c.R[3], d0), __fmul_rn(c.R[4], d1)), __fmul_rn(c.R[5], d2));
-    float px, py, fp, dist;
+    float px, py, fp;
     if (c.model == TGV_PINHOLE) {
         px = __fadd_rn(__fdiv_rn(__fmul_rn(c.fx, xc), zc), c.cx);
         py = __fadd_rn(__fdiv_rn(__fmul_rn(c.fy, yc), zc), c.cy);
@@ -144,7 +149,7 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
     } else {
         const float s2 = __fadd_rn(__fmul_rn(xc, xc), __fmul_rn(yc, yc));
         const float rho = __fsqrt_rn(__fadd_rn(s2, __fmul_rn(zc, zc)));
-        if (!(rho > 0.0f)) return -1;
+        if (!(rho > 0.0f)) return false;
         const float phi = atan2p(yc, xc);
         const float theta = atan2p(zc, __fsqrt_rn(s2));
         px = __fadd_rn(__fmul_rn(c.fx, phi), c.cx);
@@ -152,7 +157,7 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
         fp = __fdiv_rn(__fmul_rn(c.fx, diam), rho);
         dist = rho;
     }
-    int l = 0;
+    l = 0;
     float p2 = 2.0f;
     while (l + 1 < L.nlev && p2 <= fp) {
         ++l;
@@ -160,11 +165,17 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
     }
     const float scale = __int_as_float((127 - l) << 23);  // exactly 2^-l
     const float xl = __fmul_rn(px, scale), yl = __fmul_rn(py, scale);
-    const int wl = L.w[l], hl = L.h[l];
-    if (!(xl >= 0.0f && xl < (float)wl)) return -1;
-    if (!(yl >= 0.0f && yl < (float)hl)) return -1;
-    const int i = (int)xl, j = (int)yl;  // truncation == floor for non-negative values
-    const float depth = __ldg(pyr + L.off[l] + (int64_t)j * wl + i);
+    if (!(xl >= 0.0f && xl < (float)L.w[l])) return false;
+    if (!(yl >= 0.0f && yl < (float)L.h[l])) return false;
+    i = (int)xl;  // truncation == floor for non-negative values
+    j = (int)yl;
+    return true;
+}
+
+// Alg. 1 after the depth read: the bin of a = depth - dist, or -1 (no sample, or
+// occluded beyond eta)
+__device__ __forceinline__ int alg1_bin_of(float depth, float dist, float delta, float eta, int nbins)
+{
     if (isnan(depth)) return -1;
     const float a = __fsub_rn(depth, dist);
     if (a < -eta) return -1;
@@ -176,6 +187,16 @@ __device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, co
     const float t3 = __fmul_rn(t2, (float)nbins);
     int bin = (int)floorf(t3);
     return bin > nbins - 1 ? nbins - 1 : bin;
+}
+
+__device__ __forceinline__ int alg1_bin(const Alg1Cam& c, const PyrLayout& L, const float* __restrict__ pyr,
+                                        const float X[3], float diam, float delta, float eta, int nbins)
+{
+    int l, i, j;
+    float dist;
+    if (!alg1_pixel(c, L, X, diam, l, i, j, dist)) return -1;
+    const float depth = __ldg(pyr + L.off[l] + (int64_t)j * L.w[l] + i);
+    return alg1_bin_of(depth, dist, delta, eta, nbins);
 }
 
 __global__ void __launch_bounds__(512) hist_accumulate_kernel(const AccArgs A)
@@ -216,6 +237,193 @@ __global__ void __launch_bounds__(512) hist_accumulate_kernel(const AccArgs A)
     }
 }
 
+// ---- scatter form: one thread per pyramid pixel (map m, level l, pixel (i, j))
+//
+// The voxels whose Alg. 1 decision lands on (l, i, j) have their centres inside
+// the pixel's frustum (the cone from the camera centre through the level-0 square
+// [i 2^l, (i+1) 2^l) x [j 2^l, (j+1) 2^l)), at camera depths zc where the LOD is l
+// (2^l <= fx 2r / zc < 2^(l+1), open at the first and last level) and not beyond
+// the pixel's depth + eta.  The thread walks the voxel-centre planes across the
+// dominant axis of the pixel's central ray inside that depth window; in each
+// plane the frustum's cross-section is the quadrilateral of its four corner rays,
+// whose bounding box (plus a margin far above FP32 rounding) holds every
+// candidate.  A pixel whose corner rays run too close to the planes (the widest
+// pixels of the coarsest levels, whose depth window lies next to the camera)
+// takes the bounding box of the whole window instead.  Each candidate repeats the
+// decision of the gather form (same FP32 operations); the voxel is counted only
+// if the decision picks this level and pixel, so every (voxel, map) pair is
+// counted once, as in the gather form, and the integer counts are identical.
+struct ScatArgs {
+    uint32_t* hist;
+    const int32_t* grid;  // active brick index per brick cell of the bounding box, -1 none
+    int gmin[3], gdim[3];
+    const float* pyr;
+    int nmaps, nbins, npairs;
+    float o[3], h, r;
+    PyrLayout L;
+    float zdom[TGV_MAPS_PER_LAUNCH][2];  // camera depth range of the voxel centres' box
+    Alg1Cam cam[TGV_MAPS_PER_LAUNCH];
+};
+
+// world direction of the ray through level-0 pixel coordinates (px, py), zc = 1
+__device__ __forceinline__ void pix_dir(const Alg1Cam& c, float px, float py, float d[3])
+{
+    const float xn = (px - c.cx) / c.fx, yn = (py - c.cy) / c.fy;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = c.R[a] * xn + c.R[3 + a] * yn + c.R[6 + a];
+}
+
+__global__ void __launch_bounds__(256) hist_scatter_kernel(const ScatArgs A)
+{
+    const int64_t per_map = A.L.size;
+    const float diam = __fmul_rn(A.r, 2.0f);
+    const float delta = __fmul_rn(6.0f, A.r);
+    const float eta = __fmul_rn(3.0f, delta);
+    const float mg = 0.05f * A.h;  // geometric margin, in world units
+    int vlo[3], vhi[3];            // voxel index range of the box
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vlo[a] = 8 * A.gmin[a];
+        vhi[a] = 8 * (A.gmin[a] + A.gdim[a]) - 1;
+    }
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < per_map * A.nmaps;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(g / per_map);
+        const int64_t k = g - (int64_t)m * per_map;
+        const float D = A.pyr[g];
+        if (isnan(D)) continue;
+        int l = 0;
+        while (l + 1 < A.L.nlev && A.L.off[l + 1] <= k) ++l;
+        const int64_t kk = k - A.L.off[l];
+        const int pj = (int)(kk / A.L.w[l]), pi = (int)(kk - (int64_t)pj * A.L.w[l]);
+        const Alg1Cam& c = A.cam[m];
+        // depth window
+        const float F = c.fx * diam;
+        float zlo = l + 1 < A.L.nlev ? F * __int_as_float((127 - l - 1) << 23) : 0.0f;
+        float zhi = l > 0 ? F * __int_as_float((127 - l) << 23) : INFINITY;
+        zlo = fmaxf(fmaxf(zlo * (1.0f - 1e-4f), A.zdom[m][0]), 0.0f);
+        zhi = fminf(fminf(zhi * (1.0f + 1e-4f), (D + eta) * (1.0f + 1e-4f) + mg), A.zdom[m][1]);
+        if (!(zlo < zhi)) continue;
+        // corner rays of the pixel and its central ray
+        const float s = __int_as_float((127 + l) << 23);
+        float dq[4][3], dc[3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pix_dir(c, (pi + (q & 1)) * s, (pj + (q >> 1)) * s, dq[q]);
+        pix_dir(c, (pi + 0.5f) * s, (pj + 0.5f) * s, dc);
+        int ax = 0;
+        if (fabsf(dc[1]) > fabsf(dc[ax])) ax = 1;
+        if (fabsf(dc[2]) > fabsf(dc[ax])) ax = 2;
+        bool well = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float n = sqrtf(dq[q][0] * dq[q][0] + dq[q][1] * dq[q][1] + dq[q][2] * dq[q][2]);
+            well = well && (dq[q][ax] > 0.0f) == (dc[ax] > 0.0f) && fabsf(dq[q][ax]) >= 0.25f * n;
+        }
+        auto visit = [&](int gx, int gy, int gz) {
+            const int gidx[3] = {gx, gy, gz};
+            int cell = 0;
+#pragma unroll
+            for (int a = 2; a >= 0; --a) {
+                const int bc = (gidx[a] >> 3) - A.gmin[a];
+                if (bc < 0 || bc >= A.gdim[a]) return;
+                cell = cell * A.gdim[a] + bc;
+            }
+            const int32_t b = A.grid[cell];
+            if (b < 0) return;
+            float X[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                X[a] = __fadd_rn(A.o[a], __fmul_rn(__fadd_rn(__int2float_rn(gidx[a]), 0.5f), A.h));
+            int l2, i2, j2;
+            float dist;
+            if (!alg1_pixel(c, A.L, X, diam, l2, i2, j2, dist)) return;
+            if (l2 != l || i2 != pi || j2 != pj) return;
+            const int bin = alg1_bin_of(D, dist, delta, eta, A.nbins);
+            if (bin < 0) return;
+            const int loc = (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
+            atomicAdd(A.hist + ((int64_t)b * A.npairs + (bin >> 1)) * TGV_BVOX + loc, c.vote << ((bin & 1) * 16));
+        };
+        auto lo_idx = [&](float x, int a) { return (int)ceilf((x - mg - A.o[a]) / A.h - 0.5f); };
+        auto hi_idx = [&](float x, int a) { return (int)floorf((x + mg - A.o[a]) / A.h - 0.5f); };
+        if (well) {
+            // planes of voxel centres across axis ax within the window; b1, b2 are the
+            // other two axes (components picked into registers, no indexed arrays)
+            const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+            auto pick = [](const float* v, int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); };
+            float da[4], d1[4], d2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                da[q] = pick(dq[q], ax);
+                d1[q] = pick(dq[q], b1);
+                d2[q] = pick(dq[q], b2);
+            }
+            const float Ca = pick(c.C, ax), C1 = pick(c.C, b1), C2 = pick(c.C, b2);
+            const float oa = pick(A.o, ax);
+            float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float x0 = Ca + zlo * da[q], x1 = Ca + zhi * da[q];
+                lo = fminf(lo, fminf(x0, x1));
+                hi = fmaxf(hi, fmaxf(x0, x1));
+            }
+            const int vla = ax == 0 ? vlo[0] : (ax == 1 ? vlo[1] : vlo[2]);
+            const int vha = ax == 0 ? vhi[0] : (ax == 1 ? vhi[1] : vhi[2]);
+            const int k0 = max((int)ceilf((lo - mg - oa) / A.h - 0.5f), vla);
+            const int k1 = min((int)floorf((hi + mg - oa) / A.h - 0.5f), vha);
+            const float o1 = pick(A.o, b1), o2 = pick(A.o, b2);
+            const int vl1 = b1 == 0 ? vlo[0] : vlo[1], vh1 = b1 == 0 ? vhi[0] : vhi[1];
+            const int vl2 = b2 == 2 ? vlo[2] : vlo[1], vh2 = b2 == 2 ? vhi[2] : vhi[1];
+            for (int kp = k0; kp <= k1; ++kp) {
+                const float P = oa + (kp + 0.5f) * A.h;
+                float l1 = INFINITY, h1 = -INFINITY, l2 = INFINITY, h2 = -INFINITY;
+                bool front = true;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float z = (P - Ca) / da[q];
+                    front = front && z > 0.0f;
+                    const float y1 = C1 + z * d1[q], y2 = C2 + z * d2[q];
+                    l1 = fminf(l1, y1);
+                    h1 = fmaxf(h1, y1);
+                    l2 = fminf(l2, y2);
+                    h2 = fmaxf(h2, y2);
+                }
+                if (!front) continue;
+                const int i1 = max((int)ceilf((l1 - mg - o1) / A.h - 0.5f), vl1);
+                const int j1 = min((int)floorf((h1 + mg - o1) / A.h - 0.5f), vh1);
+                const int i2 = max((int)ceilf((l2 - mg - o2) / A.h - 0.5f), vl2);
+                const int j2 = min((int)floorf((h2 + mg - o2) / A.h - 0.5f), vh2);
+                for (int u2 = i2; u2 <= j2; ++u2)
+                    for (int u1 = i1; u1 <= j1; ++u1) {
+                        const int gx = ax == 0 ? kp : u1;
+                        const int gy = ax == 1 ? kp : (ax == 0 ? u1 : u2);
+                        const int gz = ax == 2 ? kp : u2;
+                        visit(gx, gy, gz);
+                    }
+            }
+        } else {
+            // bounding box of the frustum between the window's two depths
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float x0 = c.C[a] + zlo * dq[q][a], x1 = c.C[a] + zhi * dq[q][a];
+                    lo[a] = fminf(lo[a], fminf(x0, x1));
+                    hi[a] = fmaxf(hi[a], fmaxf(x0, x1));
+                }
+            int r0[3], r1[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                r0[a] = max(lo_idx(lo[a], a), vlo[a]);
+                r1[a] = min(hi_idx(hi[a], a), vhi[a]);
+            }
+            for (int gz = r0[2]; gz <= r1[2]; ++gz)
+                for (int gy = r0[1]; gy <= r1[1]; ++gy)
+                    for (int gx = r0[0]; gx <= r1[0]; ++gx) visit(gx, gy, gz);
+        }
+    }
+}
+
 PyrLayout make_layout(int W, int H)
 {
     PyrLayout L;
@@ -244,6 +452,44 @@ unsigned grid_for(tgv_domain* d, int64_t n, int block)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Brick index of every brick cell of the active bricks' bounding box (scatter form),
+// built on first use; a level's bricks do not change after creation.
+tgv_status build_brick_grid(tgv_domain* d, TgvLevel& L)
+{
+    if (L.bgrid || L.nb == 0) return TGV_OK;
+    int64_t mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) mn[a] = mx[a] = L.coords[a];
+    for (int64_t b = 1; b < L.nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min<int64_t>(mn[a], L.coords[3 * b + a]);
+            mx[a] = std::max<int64_t>(mx[a], L.coords[3 * b + a]);
+        }
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) cells *= mx[a] - mn[a] + 1;
+    if (cells > ((int64_t)1 << 28) || mn[0] < -(1 << 27) || mx[0] >= (1 << 27) || mn[1] < -(1 << 27) ||
+        mx[1] >= (1 << 27) || mn[2] < -(1 << 27) || mx[2] >= (1 << 27))
+        return tgv_fail(d, TGV_ERR_UNSUPPORTED, "scatter-form histograms: the bricks' bounding box is too large");
+    std::vector<int32_t> grid((size_t)cells, -1);
+    for (int64_t b = 0; b < L.nb; ++b) {
+        const int64_t x = L.coords[3 * b] - mn[0], y = L.coords[3 * b + 1] - mn[1], z = L.coords[3 * b + 2] - mn[2];
+        grid[(size_t)((z * (mx[1] - mn[1] + 1) + y) * (mx[0] - mn[0] + 1) + x)] = (int32_t)b;
+    }
+    for (int a = 0; a < 3; ++a) {
+        L.bgmin[a] = (int32_t)mn[a];
+        L.bgdim[a] = (int32_t)(mx[a] - mn[a] + 1);
+    }
+    cudaError_t e = cudaMalloc(&L.bgrid, grid.size() * 4);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        L.bgrid = nullptr;
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "brick grid allocation failed");
+    }
+    d->bytes += (int64_t)grid.size() * 4;
+    e = cudaMemcpyAsync(L.bgrid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "brick grid upload");
+}
+
 }  // namespace
 
 tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& Lv, const tgv_camera* cams, int nmaps, const float* depth,
@@ -251,6 +497,15 @@ tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& Lv, const tgv_camera* 
 {
     const int W = cams[0].width, H = cams[0].height;
     const PyrLayout L = make_layout(W, H);
+    const bool scatter = d->prm.hist_form == TGV_HIST_SCATTER;
+    if (scatter) {
+        for (int m = 0; m < nmaps; ++m)
+            if (cams[m].model != TGV_PINHOLE)
+                return tgv_fail(d, TGV_ERR_UNSUPPORTED, "scatter-form histograms take pinhole maps only");
+        if (Lv.nb == 0) return TGV_OK;
+        tgv_status st = build_brick_grid(d, Lv);
+        if (st != TGV_OK) return st;
+    }
     for (int m0 = 0; m0 < nmaps; m0 += TGV_MAPS_PER_LAUNCH) {
         const int nm = nmaps - m0 < TGV_MAPS_PER_LAUNCH ? nmaps - m0 : TGV_MAPS_PER_LAUNCH;
         tgv_status st = tgv_scratch(d, d->pyr, sizeof(float) * (size_t)L.size * nm);
@@ -291,9 +546,48 @@ tgv_status tgv_launch_accumulate(tgv_domain* d, TgvLevel& Lv, const tgv_camera* 
             g.model = c.model;
         }
         A.coords = Lv.coords_dev;
-        hist_accumulate_kernel<<<(unsigned)Lv.nb, TGV_BVOX, 0, d->stream>>>(A);
+        if (!scatter) {
+            hist_accumulate_kernel<<<(unsigned)Lv.nb, TGV_BVOX, 0, d->stream>>>(A);
+        } else {
+            ScatArgs S;
+            S.hist = Lv.hist;
+            S.grid = Lv.bgrid;
+            for (int a = 0; a < 3; ++a) {
+                S.gmin[a] = Lv.bgmin[a];
+                S.gdim[a] = Lv.bgdim[a];
+                S.o[a] = A.o[a];
+            }
+            S.pyr = pyr;
+            S.nmaps = nm;
+            S.nbins = A.nbins;
+            S.npairs = A.npairs;
+            S.h = A.h;
+            S.r = A.r;
+            S.L = L;
+            for (int m = 0; m < nm; ++m) {
+                S.cam[m] = A.cam[m];
+                // camera depth range of the box of voxel centres (its 8 corners), widened
+                const tgv_camera& c = cams[m0 + m];
+                double zmin = INFINITY, zmax = -INFINITY;
+                for (int corner = 0; corner < 8; ++corner) {
+                    double zc = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        const int64_t vi = (corner >> a) & 1 ? 8 * ((int64_t)Lv.bgmin[a] + Lv.bgdim[a]) - 1
+                                                             : 8 * (int64_t)Lv.bgmin[a];
+                        const double X = Lv.origin[a] + ((double)vi + 0.5) * Lv.h;
+                        zc += c.R[6 + a] * (X - c.C[a]);
+                    }
+                    zmin = std::min(zmin, zc);
+                    zmax = std::max(zmax, zc);
+                }
+                const double pad = 0.05 * Lv.h + 1e-5 * (fabs(zmin) + fabs(zmax));
+                S.zdom[m][0] = (float)(zmin - pad);
+                S.zdom[m][1] = (float)(zmax + pad);
+            }
+            hist_scatter_kernel<<<grid_for(d, (int64_t)nm * L.size, 256), 256, 0, d->stream>>>(S);
+        }
         d->launches++;
-        st = tgv_cuda_check(d, cudaGetLastError(), "hist_accumulate_kernel launch");
+        st = tgv_cuda_check(d, cudaGetLastError(), scatter ? "hist_scatter_kernel launch" : "hist_accumulate_kernel launch");
         if (st != TGV_OK) return st;
     }
     return TGV_OK;

@@ -92,6 +92,8 @@ struct TgvLevel {
     std::vector<int32_t> nbr_host;
     std::vector<int32_t> work_host;
     int32_t* up7 = nullptr;    // marching cubes: nb x 7 upper-neighbour bricks (built on first use)
+    int32_t* bgrid = nullptr;  // scatter-form histograms: active brick per cell of their bounding box
+    int32_t bgmin[3] = {0, 0, 0}, bgdim[3] = {0, 0, 0};
     int xrun = 0;              // cached automatic run length, valid for (xrun_gen, xrun_slots)
     uint64_t xrun_gen = 0;
     int64_t xrun_slots = 0;

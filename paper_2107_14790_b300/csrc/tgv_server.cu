@@ -205,6 +205,7 @@ tgv_status tgv_server_create(const tgv_server_cfg* cfg, const tgv_params* prm, v
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
     if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
     if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
+    if (prm->hist_form != TGV_HIST_GATHER && prm->hist_form != TGV_HIST_SCATTER) return TGV_ERR_INVALID_ARG;
     tgv_server* s = new (std::nothrow) tgv_server();
     if (!s) return TGV_ERR_OUT_OF_MEMORY;
     s->cap_active = cfg->capacity_bricks;

@@ -22,6 +22,7 @@ TGV_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "budget exceeded", 4: "CUDA error",
           5: "device wait timed out", 6: "domain in error state", 7: "unsupported"}
 STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+HIST_FORMS = {"gather": 0, "scatter": 1}
 FIELDS = {"u": (0, 1), "ubar": (1, 1), "v": (2, 3), "vbar": (3, 3), "p": (4, 3), "q": (5, 6)}
 
 
@@ -36,7 +37,7 @@ class tgv_params(ctypes.Structure):
                 ("lam", ctypes.c_float), ("tau", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("clamp_u", ctypes.c_int32), ("centres", ctypes.c_int32),
                 ("box_v", ctypes.c_float), ("iter_kernel", ctypes.c_int32),
-                ("x_run", ctypes.c_int32)]
+                ("x_run", ctypes.c_int32), ("hist_form", ctypes.c_int32)]
 
 
 class tgv_level_desc(ctypes.Structure):
@@ -179,7 +180,7 @@ ITER_KERNELS = {"pipelined": 0, "one_brick_per_cta": 1, "paired": 2}
 
 
 def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, storage="fp32", clamp_u=True,
-                centres=0, box_v=2.0, iter_kernel="paired", x_run=0) -> tgv_params:
+                centres=0, box_v=2.0, iter_kernel="paired", x_run=0, hist_form="gather") -> tgv_params:
     p = tgv_params()
     _check(None, lib().tgv_default_params(ctypes.byref(p)))
     p.nbins, p.alpha1, p.alpha0, p.lam, p.tau, p.sigma = int(nbins), alpha1, alpha0, lam, tau, sigma
@@ -187,6 +188,7 @@ def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, st
     p.clamp_u, p.centres, p.box_v = int(bool(clamp_u)), int(centres), box_v
     p.iter_kernel = ITER_KERNELS[iter_kernel] if isinstance(iter_kernel, str) else int(iter_kernel)
     p.x_run = int(x_run)
+    p.hist_form = HIST_FORMS[hist_form] if isinstance(hist_form, str) else int(hist_form)
     return p
 
 
