@@ -515,8 +515,11 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
         return TGV_ERR_OUT_OF_MEMORY;
     }
     unsigned long long* dsc = (unsigned long long*)sc.p;
+    // slots: twice the sample bricks grown by the band (a layer thickens by 2 band + 1
+    // bricks, a line by its square), at least 2^20; a table that fills is redone larger
+    const uint64_t grow = std::min<uint64_t>((uint64_t)(2 * cfg->band + 1) * (2 * cfg->band + 1), 32);
     uint64_t cap2 = (uint64_t)1 << 20;
-    while (cap2 < 64 * (uint64_t)nu) cap2 <<= 1;
+    while (cap2 < 2 * grow * (uint64_t)nu) cap2 <<= 1;
     for (int attempt = 0; nu > 0; ++attempt) {
         for (DevBuf* b : {&act, &frz, &lst, &lst2, &tmp, &hist}) {
             if (b->p) cudaFree(b->p);

@@ -87,3 +87,25 @@ def test_maps_without_samples_give_empty_levels(sphere_scene):
     nan = torch.full((2, sc.depths[0].shape[0], sc.depths[0].shape[1]), float("nan"), device="cuda")
     lv, ns = tgv.tgv_octree_build(sc.cameras[:2], nan, np.zeros(3), 1.0, 3, 6, 1)
     assert ns == 0 and all(L.nbricks == 0 and L.nfrozen == 0 for L in lv)
+
+
+def test_scattered_samples_outgrow_the_first_level_table():
+    """About 2000 isolated sample bricks on one deep level, dilated by 4 rings: 9^3 = 729
+    bricks each, about 1.5 M in all, above the level-set table's first size (2 x 32 slots
+    per sample brick, rounded up to 2^20), so the build redoes the sets in a larger table;
+    the levels still equal the oracle's."""
+    rng = np.random.default_rng(11)
+    W = H = 512
+    fx, fy, cx, cy = synth.pinhole_intrinsics(W, H, 20.0)
+    cams, deps = [], []
+    for k in range(2):
+        C = np.array([0.5 + 0.01 * k, 0.5, 2.5])
+        cams.append(synth.Camera(fx, fy, cx, cy, synth.look_at(C, np.array([0.5, 0.5, 0.0]), up=(0.0, 1.0, 0.0)),
+                                 C, W, H))
+        d = np.full((H, W), np.nan, np.float32)
+        for by in range(0, H, 16):
+            for bx in range(0, W, 16):
+                d[by + 7:by + 9, bx + 7:bx + 9] = rng.uniform(1.7, 2.3)  # a 2 x 2 patch: radius from its neighbours
+        deps.append(d)
+    lv = check_same(cams, deps, np.zeros(3), 1.0, 12, 12, 4)
+    assert lv[0].nbricks > 1_100_000
