@@ -820,17 +820,28 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
         // the row of the item in hand is no longer read: reuse it for item itnn
         if (t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
         C.phase_b(s, bcur, links, to_next);
+        bool late = false;
         if (itn < nit) {
+            // no CTA barrier between phase B of this item and phase A of the next: they
+            // work on different stages, except the hand-over slots of stage s (the -x
+            // halo p slot and the parked partial sums of row (y, z)), which only lanes of
+            // one warp share (a warp holds one z layer); a warp starts phase A once its
+            // lanes are past phase B and the next stage has landed.  A wait that gives up
+            // is agreed on at the barrier that closes the interval.
             const bool ok = mbar_wait_bounded(&bar[ns], (parity >> ns) & 1u, P.wait_budget);
-            if (__syncthreads_or(!ok)) {
-                bail = true;
-                break;
+            if (ok) {
+                parity ^= 1u << ns;
+                pending &= ~(1u << ns);
             }
-            parity ^= 1u << ns;
-            pending &= ~(1u << ns);
+            late = !ok;
+            __syncwarp();
             next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
         }
-        __syncthreads();  // stage s, the phase A results of item itn and the hand-over are settled
+        // stage s, the phase A results of item itn and the hand-over are settled
+        if (__syncthreads_or(late)) {
+            bail = true;
+            break;
+        }
         if (t == 0 && itnn < nit) {
             fence_proxy_async_smem();
             C.issue(s, bnn);
