@@ -322,16 +322,24 @@ template <typename S, int NB>
 __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> A)
 {
     constexpr int NBM = NB ? NB : TGV_MAX_BINS;
-    __shared__ int32_t s_nbr[TGV_NNBR];
+    __shared__ int32_t s_nbr2[2][TGV_NNBR];
     __shared__ double s_red[3][16];
     const int t = threadIdx.x;
     const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    auto brick_of = [&](int64_t i) -> int64_t { return A.work ? (int64_t)A.work[i] : i; };
+    // neighbour rows double-buffered: the next brick's row is loaded while this one
+    // is evaluated and stored before the barrier that opens the next brick
+    if (t < TGV_NNBR && (int64_t)blockIdx.x < A.nitems) s_nbr2[0][t] = A.nbr[brick_of(blockIdx.x) * TGV_NNBR + t];
+    int buf = 0;
     // per-warp running sums over the CTA's bricks (FP64, in brick order)
     double acc_en = 0.0, acc_du = 0.0, acc_vm = 0.0;
-    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int64_t b = A.work ? (int64_t)A.work[item] : item;
-    __syncthreads();  // the previous brick's neighbour row is no longer read
-    if (t < TGV_NNBR) s_nbr[t] = A.nbr[b * TGV_NNBR + t];
+    for (int64_t item = blockIdx.x; item < A.nitems; item += gridDim.x, buf ^= 1) {
+    const int64_t b = brick_of(item);
+    const int64_t nx = item + gridDim.x;
+    int32_t nbr_next = 0;
+    if (t < TGV_NNBR && nx < A.nitems) nbr_next = A.nbr[brick_of(nx) * TGV_NNBR + t];
+    __syncthreads();  // this brick's row is in place; the other buffer is no longer read
+    const int32_t* s_nbr = s_nbr2[buf];
     const int nbins = NB ? NB : A.nbins;
     const float* ub = A.u + b * TGV_BVOX;
     const S* vb = A.v + b * 3 * TGV_BVOX;
@@ -346,7 +354,6 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) q[c] = ld_s(qb + c * TGV_BVOX + t);
-    __syncthreads();  // s_nbr
 
     float gmv2 = 0.0f, k0 = 0.0f, dm[3][3], dk[3][3], div1 = 0.0f, div2[3] = {0, 0, 0};
     float vmax = 0.0f;
@@ -457,6 +464,7 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
     acc_en += (double)en;
     acc_du += (double)du;
     acc_vm = fmax(acc_vm, (double)vm);
+    if (t < TGV_NNBR && nx < A.nitems) s_nbr2[buf ^ 1][t] = nbr_next;
     }
     const int w = t >> 5, lane = t & 31;
     if (lane == 0) {
