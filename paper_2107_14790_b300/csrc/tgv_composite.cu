@@ -21,8 +21,8 @@
 // clamp, v update, over-relaxation), one thread per leaf.
 #include <math.h>
 
+#include <algorithm>
 #include <memory>
-#include <unordered_map>
 #include <vector>
 
 #include "tgv_internal.cuh"
@@ -31,7 +31,7 @@ struct tgv_composite {
     tgv_domain* d = nullptr;
     int64_t n = 0;
     std::vector<int64_t> level_first;             // first leaf of each level (and the total)
-    std::vector<std::vector<int32_t>> leaf_slot;  // per level: slot (brick * 512 + local) of each leaf
+    int32_t* slot = nullptr;                      // [n]: slot (brick * 512 + local) of each leaf in its level
     float *u = nullptr, *ubar = nullptr, *v = nullptr, *vbar = nullptr, *p = nullptr, *q = nullptr;
     uint32_t* hist = nullptr;                     // [n][npairs]
     int32_t* nb6 = nullptr;                       // [n][6]: +x +y +z -x -y -z neighbour of a regular leaf
@@ -223,20 +223,273 @@ __global__ void comp_scatter_u(float* dst, const float* src, const int32_t* slot
         dst[slot[x]] = src[x];
 }
 
-inline uint64_t ckey(int64_t x, int64_t y, int64_t z)
+// ---- building the leaves and their lists on the device
+//
+// Per level a hash table maps brick coordinates to the active brick index.  A
+// brick's refined octants (those whose 8^3 children form an active brick of the
+// next level) give its leaf count; an exclusive scan over all bricks, level by
+// level, numbers the leaves in level, brick and voxel order.  One thread per leaf
+// then forms its forward and backward lists, appends itself to the reverse lists
+// of the leaves it lists (compare-and-swap into the first free of four slots)
+// and, after each reverse list is sorted by leaf id (the order a serial pass in
+// leaf order gives), classifies it as regular or irregular.
+constexpr uint64_t kNoKey = ~(uint64_t)0;
+constexpr int kCoordBits = 20;  // brick coordinates lie in [-2^19, 2^19)
+constexpr int kMaxProbeC = 4096;
+
+struct CBLevel {
+    const int32_t* coords;  // 3 per brick, active first
+    int64_t nb;             // active bricks
+    int64_t bfirst;         // first brick of the level in the global brick order
+    uint64_t hoff, hcap;    // the level's slice of the hash table (cap a power of two)
+    int64_t lfirst;         // first leaf of the level
+};
+
+struct CBArgs {
+    CBLevel L[32];
+    int nlev;
+    uint64_t* hkeys;
+    int32_t* hvals;
+    uint32_t* base;        // [bricks]: leaf count, then (scanned) the brick's first leaf
+    uint8_t* mask;         // [bricks]: octants refined by the next level
+    int32_t* leaf_of;      // [bricks * 512]: leaf id of each voxel slot, -1 refined
+    int32_t* slot;         // [n]: slot of each leaf in its level
+    int32_t* lists;        // [n][4 kinds][3 axes][4]
+    int32_t* nb6;
+    int64_t n, nbt;
+    unsigned int* err;     // [0] a refined voxel lacks a child, [1] more than four over a face, [2] table full
+};
+
+__device__ __forceinline__ uint64_t cb_mix(uint64_t z)
 {
-    const int64_t B = (int64_t)1 << 20;
-    return ((uint64_t)(z + B) * (uint64_t)(2 * B) + (uint64_t)(y + B)) * (uint64_t)(2 * B) + (uint64_t)(x + B);
+    // splitmix64 finaliser (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
 }
 
-inline int64_t fdiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ bool cb_key(int64_t x, int64_t y, int64_t z, uint64_t& key)
+{
+    const int64_t B = (int64_t)1 << (kCoordBits - 1);
+    if (x < -B || x >= B || y < -B || y >= B || z < -B || z >= B) return false;
+    key = (uint64_t)(x + B) | ((uint64_t)(y + B) << kCoordBits) | ((uint64_t)(z + B) << (2 * kCoordBits));
+    return true;
+}
+
+// active brick index of brick (x, y, z) on level l, -1 none
+__device__ __forceinline__ int64_t cb_brick(const CBArgs& A, int l, int64_t x, int64_t y, int64_t z)
+{
+    uint64_t key;
+    if (l < 0 || l >= A.nlev || !cb_key(x, y, z, key)) return -1;
+    const CBLevel& L = A.L[l];
+    if (L.nb == 0) return -1;
+    uint64_t h = cb_mix(key) & (L.hcap - 1);
+    for (int probe = 0; probe < kMaxProbeC; ++probe) {
+        const uint64_t cur = A.hkeys[L.hoff + h];
+        if (cur == key) return A.hvals[L.hoff + h];
+        if (cur == kNoKey) return -1;
+        h = (h + 1) & (L.hcap - 1);
+    }
+    return -1;
+}
+
+// leaf at global voxel (x, y, z) of level l: its id, -1 refined, -2 no voxel there
+__device__ __forceinline__ int64_t cb_leaf(const CBArgs& A, int l, int64_t x, int64_t y, int64_t z)
+{
+    const int64_t b = cb_brick(A, l, x >> 3, y >> 3, z >> 3);
+    if (b < 0) return -2;
+    return A.leaf_of[(A.L[l].bfirst + b) * TGV_BVOX + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
+}
+
+__device__ __forceinline__ int cb_level_of_brick(const CBArgs& A, int64_t g)
+{
+    int l = 0;
+    while (l + 1 < A.nlev && A.L[l + 1].bfirst <= g) ++l;
+    return l;
+}
+
+__device__ __forceinline__ int cb_level_of_leaf(const CBArgs& A, int64_t x)
+{
+    int l = 0;
+    while (l + 1 < A.nlev && A.L[l + 1].lfirst <= x) ++l;
+    return l;
+}
+
+__global__ void cb_insert_kernel(const CBArgs A)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.nbt; g += (int64_t)gridDim.x * blockDim.x) {
+        const int l = cb_level_of_brick(A, g);
+        const CBLevel& L = A.L[l];
+        const int64_t b = g - L.bfirst;
+        uint64_t key;
+        cb_key(L.coords[3 * b], L.coords[3 * b + 1], L.coords[3 * b + 2], key);  // in range (checked at creation)
+        uint64_t h = cb_mix(key) & (L.hcap - 1);
+        bool done = false;
+        for (int probe = 0; probe < kMaxProbeC && !done; ++probe) {
+            const uint64_t prev = atomicCAS((unsigned long long*)&A.hkeys[L.hoff + h], (unsigned long long)kNoKey,
+                                            (unsigned long long)key);
+            if (prev == kNoKey) {
+                A.hvals[L.hoff + h] = (int32_t)b;
+                done = true;
+            } else {
+                h = (h + 1) & (L.hcap - 1);
+            }
+        }
+        if (!done) atomicAdd(&A.err[2], 1u);
+    }
+}
+
+// refined octants of each brick and its leaf count (64 per octant left)
+__global__ void cb_mask_kernel(const CBArgs A)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.nbt; g += (int64_t)gridDim.x * blockDim.x) {
+        const int l = cb_level_of_brick(A, g);
+        const CBLevel& L = A.L[l];
+        const int64_t b = g - L.bfirst;
+        const int64_t c0 = L.coords[3 * b], c1 = L.coords[3 * b + 1], c2 = L.coords[3 * b + 2];
+        uint32_t m = 0;
+        for (int o = 0; o < 8; ++o)
+            if (cb_brick(A, l + 1, 2 * c0 + (o & 1), 2 * c1 + ((o >> 1) & 1), 2 * c2 + (o >> 2)) >= 0) m |= 1u << o;
+        A.mask[g] = (uint8_t)m;
+        A.base[g] = 64u * (8u - (uint32_t)__popc(m));
+    }
+}
+
+// one CTA per brick: leaf ids of its voxels in voxel order
+__global__ void __launch_bounds__(TGV_BVOX) cb_leaves_kernel(const CBArgs A)
+{
+    __shared__ uint32_t wsum[TGV_BVOX / 32];
+    const int64_t g = blockIdx.x;
+    const int v = threadIdx.x, w = v >> 5, lane = v & 31;
+    const int o = ((v & 7) >> 2) | ((((v >> 3) & 7) >> 2) << 1) | (((v >> 6) >> 2) << 2);
+    const bool leaf = !((A.mask[g] >> o) & 1u);
+    const unsigned bal = __ballot_sync(0xffffffffu, leaf);
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    before += __popc(bal & ((1u << lane) - 1u));
+    const uint32_t id = A.base[g] + before;
+    A.leaf_of[g * TGV_BVOX + v] = leaf ? (int32_t)id : -1;
+    if (leaf) {
+        const int l = cb_level_of_brick(A, g);
+        A.slot[id] = (int32_t)((g - A.L[l].bfirst) * TGV_BVOX + v);
+    }
+}
+
+// forward (kind 0) and backward (kind 1) lists of every leaf
+__global__ void cb_lists_kernel(const CBArgs A)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < A.n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int l = cb_level_of_leaf(A, x);
+        const CBLevel& L = A.L[l];
+        const int64_t s = A.slot[x], b = s / TGV_BVOX, v = s % TGV_BVOX;
+        const int64_t gv[3] = {8 * (int64_t)L.coords[3 * b] + (v & 7), 8 * (int64_t)L.coords[3 * b + 1] + ((v >> 3) & 7),
+                               8 * (int64_t)L.coords[3 * b + 2] + (v >> 6)};
+        for (int a = 0; a < 3; ++a)
+            for (int side = 0; side < 2; ++side) {
+                int64_t qv[3] = {gv[0], gv[1], gv[2]};
+                qv[a] += side == 0 ? 1 : -1;
+                int32_t* dst = A.lists + ((x * 4 + side) * 3 + a) * kList;
+                const int64_t same = cb_leaf(A, l, qv[0], qv[1], qv[2]);
+                if (same >= 0) {
+                    dst[0] = (int32_t)same;
+                } else if (same == -1) {  // refined: the 4 children on the face next to x
+                    int64_t c0[3] = {2 * qv[0], 2 * qv[1], 2 * qv[2]};
+                    if (side == 1) c0[a] += 1;
+                    const int o0 = a == 0 ? 1 : 0, o1 = a == 2 ? 1 : 2;
+                    int m = 0;
+                    for (int d1 = 0; d1 < 2; ++d1)
+                        for (int d0 = 0; d0 < 2; ++d0) {
+                            int64_t cc[3] = {c0[0], c0[1], c0[2]};
+                            cc[o0] += d0;
+                            cc[o1] += d1;
+                            const int64_t f = cb_leaf(A, l + 1, cc[0], cc[1], cc[2]);
+                            if (f < 0) atomicAdd(&A.err[0], 1u);
+                            else dst[m++] = (int32_t)f;
+                        }
+                } else if (l > 0) {
+                    const int64_t cr = cb_leaf(A, l - 1, qv[0] >> 1, qv[1] >> 1, qv[2] >> 1);
+                    if (cr >= 0) dst[0] = (int32_t)cr;
+                }
+            }
+    }
+}
+
+// reverse lists: each leaf enters the +a (-a) reverse list of the leaves in its +a
+// (-a) list, with weight 1 / (list length), into the first free of four slots
+__global__ void cb_reverse_kernel(const CBArgs A)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < A.n; x += (int64_t)gridDim.x * blockDim.x)
+        for (int side = 0; side < 2; ++side)
+            for (int a = 0; a < 3; ++a) {
+                const int32_t* src = A.lists + ((x * 4 + side) * 3 + a) * kList;
+                int cnt = 0;
+                while (cnt < kList && src[cnt] >= 0) ++cnt;
+                for (int k = 0; k < cnt; ++k) {
+                    int* rev = (int*)(A.lists + (((int64_t)src[k] * 4 + 2 + side) * 3 + a) * kList);
+                    const int val = (int)((uint32_t)x | (cnt == 4 ? kQuarter : 0u));
+                    int m = 0;
+                    while (m < kList && atomicCAS(rev + m, -1, val) != -1) ++m;
+                    if (m == kList) atomicAdd(&A.err[1], 1u);
+                }
+            }
+}
+
+// reverse lists in leaf order; regular leaves get their six ids, irregular ones a mark
+__global__ void cb_classify_kernel(const CBArgs A, uint32_t* irr)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < A.n; x += (int64_t)gridDim.x * blockDim.x) {
+        int32_t* L0 = A.lists + x * 4 * 3 * kList;
+        for (int r = 6; r < 12; ++r) {  // kinds 2, 3: insertion sort by leaf id
+            int32_t* e = L0 + r * kList;
+            for (int i = 1; i < kList && e[i] != -1; ++i) {
+                const int32_t key = e[i];
+                int j = i - 1;
+                while (j >= 0 && (e[j] & 0x7fffffff) > (key & 0x7fffffff)) {
+                    e[j + 1] = e[j];
+                    --j;
+                }
+                e[j + 1] = key;
+            }
+        }
+        bool regular = true;
+        for (int a = 0; a < 3 && regular; ++a) {
+            const int32_t* f = L0 + (0 * 3 + a) * kList;
+            const int32_t* bk = L0 + (1 * 3 + a) * kList;
+            const int32_t* rf = L0 + (2 * 3 + a) * kList;
+            const int32_t* rb = L0 + (3 * 3 + a) * kList;
+            regular = f[1] < 0 && bk[1] < 0 && rf[1] == -1 && rb[1] == -1 && rf[0] == bk[0] && rb[0] == f[0];
+        }
+        if (regular) {
+            for (int a = 0; a < 3; ++a) {
+                A.nb6[x * 6 + a] = L0[(0 * 3 + a) * kList];
+                A.nb6[x * 6 + 3 + a] = L0[(1 * 3 + a) * kList];
+            }
+        }
+        irr[x] = regular ? 0u : 1u;
+    }
+}
+
+// irregular leaves: their index among the irregular ones (scanned flags) and full lists
+__global__ void cb_irregular_kernel(const CBArgs A, const uint32_t* irr_idx, int32_t* irr_lists, int64_t nirr)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < A.n; x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = irr_idx[x];
+        const bool is_irr = x + 1 < A.n ? irr_idx[x + 1] > k : (int64_t)k < nirr;
+        if (!is_irr) continue;
+        A.nb6[x * 6] = (int32_t)(-2 - (int64_t)k);
+        const int32_t* L0 = A.lists + x * 4 * 3 * kList;
+        for (int i = 0; i < 4 * 3 * kList; ++i) irr_lists[(int64_t)k * 4 * 3 * kList + i] = L0[i];
+    }
+}
 
 unsigned grid_of(int64_t n, int sms) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 32)); }
 
 void free_comp(tgv_composite* c)
 {
     for (void* p : {(void*)c->u, (void*)c->ubar, (void*)c->v, (void*)c->vbar, (void*)c->p, (void*)c->q, (void*)c->hist,
-                    (void*)c->lists, (void*)c->nb6})
+                    (void*)c->lists, (void*)c->nb6, (void*)c->slot})
         if (p) cudaFree(p);
 }
 
@@ -251,137 +504,38 @@ tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out)
     if (!d) return TGV_ERR_INVALID_ARG;
     if (d->broken) return TGV_ERR_STATE;
     const int nlev = (int)d->levels.size();
-    // brick index per level, and leaf ids
-    std::vector<std::unordered_map<uint64_t, int64_t>> bidx(nlev);
-    for (int l = 0; l < nlev; ++l) {
-        const TgvLevel& L = d->levels[l];
-        bidx[l].reserve((size_t)L.nb * 2);
-        for (int64_t b = 0; b < L.nb; ++b) bidx[l].emplace(ckey(L.coords[3 * b], L.coords[3 * b + 1], L.coords[3 * b + 2]), b);
-    }
-    auto brick_at = [&](int l, int64_t x, int64_t y, int64_t z) -> int64_t {
-        if (l < 0 || l >= nlev) return -1;
-        auto it = bidx[l].find(ckey(fdiv(x, 8), fdiv(y, 8), fdiv(z, 8)));
-        return it == bidx[l].end() ? -1 : it->second;
-    };
+    if (nlev > 32) return TGV_ERR_UNSUPPORTED;
     std::unique_ptr<tgv_composite> c(new (std::nothrow) tgv_composite());
     if (!c) return TGV_ERR_OUT_OF_MEMORY;
     c->d = d;
-    c->leaf_slot.resize(nlev);
-    std::vector<std::vector<int32_t>> leaf_id(nlev);  // per level slot -> leaf id (-1: refined)
-    int64_t n = 0;
+    cudaStream_t st = d->stream;
+    CBArgs A;
+    A.nlev = nlev;
+    int64_t nbt = 0;
+    uint64_t hcap_total = 0;
     for (int l = 0; l < nlev; ++l) {
         const TgvLevel& L = d->levels[l];
-        c->level_first.push_back(n);
-        leaf_id[l].assign((size_t)L.nb * TGV_BVOX, -1);
-        for (int64_t b = 0; b < L.nb; ++b) {
-            bool fine[8];
-            for (int o = 0; o < 8; ++o)
-                fine[o] = brick_at(l + 1, 16 * (int64_t)L.coords[3 * b] + 8 * (o & 1),
-                                   16 * (int64_t)L.coords[3 * b + 1] + 8 * ((o >> 1) & 1),
-                                   16 * (int64_t)L.coords[3 * b + 2] + 8 * (o >> 2)) >= 0;
-            for (int v = 0; v < TGV_BVOX; ++v) {
-                const int o = ((v & 7) >> 2) | ((((v >> 3) & 7) >> 2) << 1) | (((v >> 6) >> 2) << 2);
-                if (fine[o]) continue;
-                leaf_id[l][(size_t)b * TGV_BVOX + v] = (int32_t)n++;
-                c->leaf_slot[l].push_back((int32_t)(b * TGV_BVOX + v));
-            }
-        }
-        if (n >= ((int64_t)1 << 31) - 1) return TGV_ERR_UNSUPPORTED;
+        A.L[l].coords = L.coords_dev;
+        A.L[l].nb = L.nb;
+        A.L[l].bfirst = nbt;
+        uint64_t cap = 16;
+        while (cap < 2 * (uint64_t)L.nb) cap <<= 1;
+        A.L[l].hoff = hcap_total;
+        A.L[l].hcap = cap;
+        A.L[l].lfirst = 0;
+        hcap_total += cap;
+        nbt += L.nb;
     }
-    c->level_first.push_back(n);
-    c->n = n;
-    // neighbour lists
-    std::vector<int32_t> lists((size_t)n * 4 * 3 * kList, -1);
-    auto leaf_of = [&](int l, int64_t x, int64_t y, int64_t z) -> int64_t {
-        const int64_t b = brick_at(l, x, y, z);
-        if (b < 0) return -2;  // no voxel at this level
-        return leaf_id[l][(size_t)b * TGV_BVOX + (x - 8 * fdiv(x, 8)) + 8 * (y - 8 * fdiv(y, 8)) + 64 * (z - 8 * fdiv(z, 8))];
-    };
-    bool ok = true;
-    for (int l = 0; l < nlev && ok; ++l) {
-        const TgvLevel& L = d->levels[l];
-        for (size_t k = 0; k < c->leaf_slot[l].size() && ok; ++k) {
-            const int64_t s = c->leaf_slot[l][k], b = s / TGV_BVOX, v = s % TGV_BVOX;
-            const int64_t g[3] = {8 * (int64_t)L.coords[3 * b] + (v & 7), 8 * (int64_t)L.coords[3 * b + 1] + ((v >> 3) & 7),
-                                  8 * (int64_t)L.coords[3 * b + 2] + (v >> 6)};
-            const int64_t x = c->level_first[l] + (int64_t)k;
-            for (int a = 0; a < 3; ++a)
-                for (int side = 0; side < 2; ++side) {
-                    int64_t qv[3] = {g[0], g[1], g[2]};
-                    qv[a] += side == 0 ? 1 : -1;
-                    int32_t* dst = &lists[(((size_t)x * 4 + side) * 3 + a) * kList];
-                    const int64_t same = leaf_of(l, qv[0], qv[1], qv[2]);
-                    if (same >= 0) {
-                        dst[0] = (int32_t)same;
-                    } else if (same == -1) {  // refined: the 4 children on the face next to x
-                        int64_t c0[3] = {2 * qv[0], 2 * qv[1], 2 * qv[2]};
-                        if (side == 1) c0[a] += 1;
-                        const int o0 = a == 0 ? 1 : 0, o1 = a == 2 ? 1 : 2;
-                        int m = 0;
-                        for (int d1 = 0; d1 < 2; ++d1)
-                            for (int d0 = 0; d0 < 2; ++d0) {
-                                int64_t cc[3] = {c0[0], c0[1], c0[2]};
-                                cc[o0] += d0;
-                                cc[o1] += d1;
-                                const int64_t f = leaf_of(l + 1, cc[0], cc[1], cc[2]);
-                                if (f < 0) ok = false;
-                                else dst[m++] = (int32_t)f;
-                            }
-                    } else if (l > 0) {
-                        const int64_t cr = leaf_of(l - 1, qv[0] >> 1, qv[1] >> 1, qv[2] >> 1);
-                        if (cr >= 0) dst[0] = (int32_t)cr;
-                    }
-                }
+    if (nbt * TGV_BVOX >= ((int64_t)1 << 31) - 1) return TGV_ERR_UNSUPPORTED;
+    A.nbt = nbt;
+    // temporaries of the build
+    struct Tmp {
+        void* p = nullptr;
+        ~Tmp()
+        {
+            if (p) cudaFree(p);
         }
-    }
-    if (!ok) return tgv_fail(d, TGV_ERR_INVALID_ARG, "levels are not 2:1 nested (a refined voxel lacks a child)");
-    // reverse lists: leaves whose +a (-a) list holds x, with weight 1 / list length
-    for (int64_t x = 0; x < n && ok; ++x)
-        for (int side = 0; side < 2; ++side)
-            for (int a = 0; a < 3; ++a) {
-                const int32_t* src = &lists[(((size_t)x * 4 + side) * 3 + a) * kList];
-                int cnt = 0;
-                while (cnt < kList && src[cnt] >= 0) ++cnt;
-                for (int k = 0; k < cnt; ++k) {
-                    int32_t* rev = &lists[(((size_t)src[k] * 4 + 2 + side) * 3 + a) * kList];
-                    int m = 0;
-                    while (m < kList && rev[m] != -1) ++m;
-                    if (m == kList) {
-                        ok = false;
-                        break;
-                    }
-                    rev[m] = (int32_t)((uint32_t)x | (cnt == 4 ? kQuarter : 0u));
-                }
-            }
-    if (!ok) return tgv_fail(d, TGV_ERR_INVALID_ARG, "a leaf has more than four neighbours over a face");
-    // regular leaves: at most one neighbour per side and mirrored reverse lists of weight 1
-    std::vector<int32_t> nb6((size_t)n * 6, -1), irr_lists;
-    int64_t nirr = 0;
-    for (int64_t x = 0; x < n; ++x) {
-        const int32_t* L0 = &lists[(size_t)x * 4 * 3 * kList];
-        bool regular = true;
-        for (int a = 0; a < 3 && regular; ++a) {
-            const int32_t* f = L0 + (0 * 3 + a) * kList;
-            const int32_t* bk = L0 + (1 * 3 + a) * kList;
-            const int32_t* rf = L0 + (2 * 3 + a) * kList;
-            const int32_t* rb = L0 + (3 * 3 + a) * kList;
-            regular = f[1] < 0 && bk[1] < 0 && rf[1] == -1 && rb[1] == -1 && rf[0] == bk[0] && rb[0] == f[0];
-        }
-        if (regular) {
-            for (int a = 0; a < 3; ++a) {
-                nb6[(size_t)x * 6 + a] = L0[(0 * 3 + a) * kList];
-                nb6[(size_t)x * 6 + 3 + a] = L0[(1 * 3 + a) * kList];
-            }
-        } else {
-            nb6[(size_t)x * 6] = (int32_t)(-2 - nirr);
-            irr_lists.insert(irr_lists.end(), L0, L0 + 4 * 3 * kList);
-            ++nirr;
-        }
-    }
-    c->nirr = nirr;
-    std::vector<int32_t>().swap(lists);
-    const int npairs = (d->prm.nbins + 1) / 2;
-    cudaStream_t st = d->stream;
+    } hkeys, hvals, base, mask, leaf_of, lists, err, irr;
     auto alloc = [&](void** p, size_t bytes) {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
             cudaGetLastError();
@@ -390,38 +544,142 @@ tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out)
         }
         return true;
     };
-    const size_t nn = (size_t)std::max<int64_t>(n, 1);
-    if (!alloc((void**)&c->u, nn * 4) || !alloc((void**)&c->ubar, nn * 4) || !alloc((void**)&c->v, nn * 12) ||
-        !alloc((void**)&c->vbar, nn * 12) || !alloc((void**)&c->p, nn * 12) || !alloc((void**)&c->q, nn * 24) ||
-        !alloc((void**)&c->hist, nn * npairs * 4) || !alloc((void**)&c->lists, irr_lists.size() * 4 + 16) ||
-        !alloc((void**)&c->nb6, nb6.size() * 4)) {
+    const size_t nbz = (size_t)std::max<int64_t>(nbt, 1);
+    if (!alloc(&hkeys.p, hcap_total * 8) || !alloc(&hvals.p, hcap_total * 4) || !alloc(&base.p, nbz * 4) ||
+        !alloc(&mask.p, nbz) || !alloc(&leaf_of.p, nbz * TGV_BVOX * 4) || !alloc(&err.p, 16))
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite build allocation failed");
+    A.hkeys = (uint64_t*)hkeys.p;
+    A.hvals = (int32_t*)hvals.p;
+    A.base = (uint32_t*)base.p;
+    A.mask = (uint8_t*)mask.p;
+    A.leaf_of = (int32_t*)leaf_of.p;
+    A.err = (unsigned int*)err.p;
+    A.slot = nullptr;
+    A.lists = nullptr;
+    A.nb6 = nullptr;
+    A.n = 0;
+    cudaError_t e = cudaMemsetAsync(hkeys.p, 0xff, hcap_total * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err.p, 0, 16, st);
+    const unsigned bgrid = grid_of(nbt, d->sm_count);
+    if (e == cudaSuccess && nbt > 0) {
+        cb_insert_kernel<<<bgrid, 256, 0, st>>>(A);
+        cb_mask_kernel<<<bgrid, 256, 0, st>>>(A);
+        c->launches += 2;
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "composite brick tables");
+    // leaf numbering: exclusive scan of the leaf counts over all bricks
+    uint64_t n = 0;
+    TgvScratch scan_tmp;
+    tgv_status s0 = nbt > 0 ? tgv_exclusive_scan_u32(d, A.base, nbt, scan_tmp, &n) : TGV_OK;
+    std::vector<uint32_t> base_h((size_t)nbt);
+    if (s0 == TGV_OK && nbt > 0) {
+        e = cudaMemcpyAsync(base_h.data(), A.base, (size_t)nbt * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s0 = tgv_cuda_check(d, e, "composite leaf numbering");
+    }
+    auto free_scan_tmp = [&]() {
+        if (scan_tmp.ptr) {
+            cudaFree(scan_tmp.ptr);
+            d->bytes -= (int64_t)scan_tmp.cap;
+        }
+        scan_tmp.ptr = nullptr;
+        scan_tmp.cap = 0;
+    };
+    free_scan_tmp();
+    if (s0 != TGV_OK) return s0;
+    unsigned int herr[4] = {0, 0, 0, 0};
+    for (int l = 0; l < nlev; ++l) {
+        A.L[l].lfirst = A.L[l].bfirst < nbt ? (int64_t)base_h[(size_t)A.L[l].bfirst] : (int64_t)n;
+        c->level_first.push_back(A.L[l].lfirst);
+    }
+    c->level_first.push_back((int64_t)n);
+    c->n = (int64_t)n;
+    A.n = (int64_t)n;
+    const size_t nn = (size_t)std::max<uint64_t>(n, 1);
+    const int npairs = (d->prm.nbins + 1) / 2;
+    if (!alloc((void**)&c->slot, nn * 4) || !alloc(&lists.p, nn * 4 * 3 * kList * 4) ||
+        !alloc((void**)&c->nb6, nn * 6 * 4) || !alloc(&irr.p, nn * 4)) {
+        free_comp(c.get());
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite list allocation failed");
+    }
+    A.slot = c->slot;
+    A.lists = (int32_t*)lists.p;
+    A.nb6 = c->nb6;
+    e = cudaMemsetAsync(lists.p, 0xff, nn * 4 * 3 * kList * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nb6, 0xff, nn * 6 * 4, st);
+    const unsigned lgrid = grid_of((int64_t)n, d->sm_count);
+    if (e == cudaSuccess && nbt > 0) {
+        cb_leaves_kernel<<<(unsigned)nbt, TGV_BVOX, 0, st>>>(A);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n > 0) {
+        cb_lists_kernel<<<lgrid, 256, 0, st>>>(A);
+        cb_reverse_kernel<<<lgrid, 256, 0, st>>>(A);
+        cb_classify_kernel<<<lgrid, 256, 0, st>>>(A, (uint32_t*)irr.p);
+        c->launches += 3;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_comp(c.get());
+        return tgv_cuda_check(d, e, "composite lists");
+    }
+    if (herr[2]) {
+        free_comp(c.get());
+        return tgv_fail(d, TGV_ERR_BUDGET, "composite brick table full");
+    }
+    if (herr[0]) {
+        free_comp(c.get());
+        return tgv_fail(d, TGV_ERR_INVALID_ARG, "levels are not 2:1 nested (a refined voxel lacks a child)");
+    }
+    if (herr[1]) {
+        free_comp(c.get());
+        return tgv_fail(d, TGV_ERR_INVALID_ARG, "a leaf has more than four neighbours over a face");
+    }
+    // irregular leaves: number them and keep their full lists
+    uint64_t nirr = 0;
+    s0 = n > 0 ? tgv_exclusive_scan_u32(d, (uint32_t*)irr.p, (int64_t)n, scan_tmp, &nirr) : TGV_OK;
+    free_scan_tmp();
+    if (s0 != TGV_OK) {
+        free_comp(c.get());
+        return s0;
+    }
+    c->nirr = (int64_t)nirr;
+    if (!alloc((void**)&c->lists, (size_t)nirr * 4 * 3 * kList * 4 + 16)) {
         free_comp(c.get());
         return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite allocation failed");
     }
-    cudaError_t e = cudaMemcpyAsync(c->nb6, nb6.data(), nb6.size() * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !irr_lists.empty())
-        e = cudaMemcpyAsync(c->lists, irr_lists.data(), irr_lists.size() * 4, cudaMemcpyHostToDevice, st);
+    if (n > 0) {
+        cb_irregular_kernel<<<lgrid, 256, 0, st>>>(A, (const uint32_t*)irr.p, c->lists, (int64_t)nirr);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    // state of the leaves
+    if (e == cudaSuccess &&
+        (!alloc((void**)&c->u, nn * 4) || !alloc((void**)&c->ubar, nn * 4) || !alloc((void**)&c->v, nn * 12) ||
+         !alloc((void**)&c->vbar, nn * 12) || !alloc((void**)&c->p, nn * 12) || !alloc((void**)&c->q, nn * 24) ||
+         !alloc((void**)&c->hist, nn * npairs * 4))) {
+        free_comp(c.get());
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite allocation failed");
+    }
     for (void* p : {(void*)c->v, (void*)c->vbar, (void*)c->p, (void*)c->q}) {
         const size_t bytes = p == c->q ? nn * 24 : nn * 12;
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, st);
     }
     // u, ubar and histograms of the leaves from their levels
-    int32_t* slots = nullptr;
-    if (e == cudaSuccess && !alloc((void**)&slots, nn * 4)) e = cudaErrorMemoryAllocation;
     for (int l = 0; l < nlev && e == cudaSuccess; ++l) {
-        const int64_t nl = (int64_t)c->leaf_slot[l].size();
+        const int64_t o = c->level_first[l], nl = c->level_first[l + 1] - o;
         if (nl == 0) continue;
-        e = cudaMemcpyAsync(slots, c->leaf_slot[l].data(), (size_t)nl * 4, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) break;
-        const int64_t o = c->level_first[l];
-        comp_gather_u<<<grid_of(nl, d->sm_count), 256, 0, st>>>(c->u + o, c->ubar + o, d->levels[l].u, slots, nl);
+        comp_gather_u<<<grid_of(nl, d->sm_count), 256, 0, st>>>(c->u + o, c->ubar + o, d->levels[l].u, c->slot + o, nl);
         comp_gather_hist<<<grid_of(nl * npairs, d->sm_count), 256, 0, st>>>(c->hist + o * npairs, d->levels[l].hist,
-                                                                             slots, nl, npairs);
+                                                                             c->slot + o, nl, npairs);
         c->launches += 2;
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `slots` is reused for the next level
     }
-    if (slots) cudaFree(slots);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the build's temporaries are freed on return
     if (e != cudaSuccess) {
         free_comp(c.get());
         return tgv_cuda_check(d, e, "composite initialisation");
@@ -469,8 +727,8 @@ int64_t tgv_composite_leaves(const tgv_composite* c) { return c ? c->n : 0; }
 
 int64_t tgv_composite_level_leaves(const tgv_composite* c, int32_t level)
 {
-    if (!c || level < 0 || level >= (int32_t)c->leaf_slot.size()) return -1;
-    return (int64_t)c->leaf_slot[level].size();
+    if (!c || level < 0 || level + 1 >= (int32_t)c->level_first.size()) return -1;
+    return c->level_first[level + 1] - c->level_first[level];
 }
 
 tgv_status tgv_composite_extract(tgv_composite* c, float* u_out, int64_t count)
@@ -488,25 +746,15 @@ tgv_status tgv_composite_scatter(tgv_composite* c)
     if (!c) return TGV_ERR_INVALID_ARG;
     tgv_domain* d = c->d;
     if (d->broken) return TGV_ERR_STATE;
-    int32_t* slots = nullptr;
-    const size_t nn = (size_t)std::max<int64_t>(c->n, 1);
-    if (cudaMalloc(&slots, nn * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "composite scatter scratch");
-    }
     cudaError_t e = cudaSuccess;
-    for (size_t l = 0; l < c->leaf_slot.size() && e == cudaSuccess; ++l) {
-        const int64_t nl = (int64_t)c->leaf_slot[l].size();
+    for (size_t l = 0; l + 1 < c->level_first.size() && e == cudaSuccess; ++l) {
+        const int64_t o = c->level_first[l], nl = c->level_first[l + 1] - o;
         if (nl == 0) continue;
-        e = cudaMemcpyAsync(slots, c->leaf_slot[l].data(), (size_t)nl * 4, cudaMemcpyHostToDevice, d->stream);
-        if (e != cudaSuccess) break;
-        comp_scatter_u<<<grid_of(nl, d->sm_count), 256, 0, d->stream>>>(d->levels[l].u, c->u + c->level_first[l],
-                                                                        slots, nl);
+        comp_scatter_u<<<grid_of(nl, d->sm_count), 256, 0, d->stream>>>(d->levels[l].u, c->u + o, c->slot + o, nl);
         c->launches++;
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     }
-    cudaFree(slots);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     return tgv_cuda_check(d, e, "composite scatter");
 }
 
