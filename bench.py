@@ -34,8 +34,12 @@ WORKLOAD = dict(workload="dense-256^3-terrain-64x512^2-maps-10bins-500it", n=256
                 iterations=500, check_every=25)
 SMALL = dict(workload="dense-64^3-sphere-16x128^2-maps-8bins-200it", n=64, nmaps=16, res=128, nbins=8,
              iterations=200, check_every=25)
-ITER_KERNEL_SRCS = [os.path.join(ROOT, "paper_2107_14790_b300", "csrc", f)
-                    for f in ("tgv_solve.cu", "tgv_iter_pipe.cu", "tgv_iter_pair.cu", "tgv_internal.cuh", "tgv_async.cuh")]
+# sources that define each form of the fused iteration kernel (the traffic counters are
+# valid only for the sources they were taken on)
+ITER_KERNEL_SRCS = {form: [os.path.join(ROOT, "paper_2107_14790_b300", "csrc", f)
+                           for f in (main, "tgv_internal.cuh", "tgv_async.cuh")]
+                    for form, main in (("paired", "tgv_iter_pair.cu"), ("pipelined", "tgv_iter_pipe.cu"),
+                                       ("one_brick_per_cta", "tgv_solve.cu"))}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tgv_iter_kernel_dense256_traffic.json")
 
 
@@ -85,9 +89,9 @@ def algorithmic_bytes_per_voxel(nbins: int, storage: str) -> int:
     return 2 * state + 2 * nbins
 
 
-def kernel_hash() -> str:
+def kernel_hash(form: str = "paired") -> str:
     h = hashlib.sha256()
-    for p in ITER_KERNEL_SRCS:
+    for p in ITER_KERNEL_SRCS[form]:
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
@@ -227,7 +231,7 @@ def run_ours(args, cfg):
     traffic = None
     try:
         tr = json.load(open(TRAFFIC_FILE))
-        if (tr.get("kernel_sha") == kernel_hash() and tr.get("storage", "fp32") == args.storage
+        if (tr.get("kernel_sha") == kernel_hash(args.iter_kernel) and tr.get("storage", "fp32") == args.storage
                 and tr.get("voxels", 16777216) == nvox and tr.get("nbins", 10) == nbins
                 and tr.get("iter_kernel") == args.iter_kernel):
             traffic = tr["dram_bytes_per_launch"]

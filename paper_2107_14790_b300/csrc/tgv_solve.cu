@@ -14,6 +14,8 @@
 // u, ubar, v, vbar, p, q once (halo re-reads hit L2).
 #include <math.h>
 
+#include <atomic>
+
 #include "tgv_internal.cuh"
 
 namespace {
@@ -489,12 +491,17 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
 // CTAs of the persistent energy kernel: three per SM (capped by the bricks)
 static int64_t energy_grid(int64_t nitems)
 {
-    static int sms[64] = {0};
+    // SM count of the current device, cached per device (threads may race to fill an
+    // entry; they all store the same value)
+    static std::atomic<int> sms[64];
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    const int64_t g = 3 * (int64_t)(sms[dev] > 0 ? sms[dev] : 1);
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int n = sms[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        sms[dev].store(n, std::memory_order_relaxed);
+    }
+    const int64_t g = 3 * (int64_t)n;
     return nitems < g ? nitems : g;
 }
 
