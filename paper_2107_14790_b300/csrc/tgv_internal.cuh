@@ -161,6 +161,9 @@ void tgv_bin_centres(const tgv_params& prm, float* c);
 
 // Marching cubes of level L into the domain's mesh buffers (synchronises).
 tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t* ntris);
+// CTAs (= partial sums) of the energy kernel for nitems bricks: three per SM of the
+// current device, at most nitems
+int64_t tgv_energy_grid(int64_t nitems);
 // exclusive prefix sum of n counts in place on the domain's stream (its tile sums in
 // tmp); *total = the sum (synchronises).  Sums must stay below 2^32.
 tgv_status tgv_exclusive_scan_u32(tgv_domain* d, uint32_t* data, int64_t n, TgvScratch& tmp, uint64_t* total);

@@ -8,9 +8,11 @@
 
 namespace {
 
-// 3 partial sums per active brick, then the 4 result doubles.  Every GPU that
-// loads this library holds it (about 1.5 MB) until the process exits.
-constexpr int64_t kPartialDoubles = 3 * (int64_t)TGV_NOALLOC_MAX_BRICKS;
+// 3 partial sums per CTA of the energy kernel (a persistent grid of three CTAs per
+// SM, whatever the brick count), then the 4 result doubles.  Every GPU that loads
+// this library holds it (about 100 KB) until the process exits.
+constexpr int64_t kMaxPartials = 4096;
+constexpr int64_t kPartialDoubles = 3 * kMaxPartials;
 static __device__ __align__(256) double g_noalloc_scratch[kPartialDoubles + 4];
 
 constexpr int kMaxDevices = 64;
@@ -46,7 +48,6 @@ extern "C" tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_para
 {
     if (!s || !prm || !out) return TGV_ERR_INVALID_ARG;
     if (s->nbricks < 0 || s->nall < s->nbricks) return TGV_ERR_INVALID_ARG;
-    if (s->nbricks > TGV_NOALLOC_MAX_BRICKS) return TGV_ERR_BUDGET;  // the fixed scratch is too small
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
     if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
     if (prm->centres != TGV_CENTRES_ENDPOINTS && prm->centres != TGV_CENTRES_MIDPOINTS) return TGV_ERR_INVALID_ARG;
@@ -59,6 +60,7 @@ extern "C" tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_para
         return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;
     }
     if (!s->u || !s->v || !s->p || !s->q || !s->hist || !s->nbr) return TGV_ERR_INVALID_ARG;
+    if (tgv_energy_grid(s->nbricks) > kMaxPartials) return TGV_ERR_BUDGET;  // a GPU with over 1365 SMs
     double* scratch = nullptr;
     tgv_status rc = scratch_for_current_device(&scratch);
     if (rc != TGV_OK) return rc;

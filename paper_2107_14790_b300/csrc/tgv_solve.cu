@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(512, 3) tgv_energy_kernel(const EnergyArgs<S> 
 }
 
 // CTAs of the persistent energy kernel: three per SM (capped by the bricks)
-static int64_t energy_grid(int64_t nitems)
+int64_t tgv_energy_grid(int64_t nitems)
 {
     // SM count of the current device, cached per device (threads may race to fill an
     // entry; they all store the same value)
@@ -509,7 +509,7 @@ static int64_t energy_grid(int64_t nitems)
 template <typename S>
 static int64_t launch_energy_kernel(EnergyArgs<S> A, int64_t nitems, cudaStream_t stream)
 {
-    const int64_t grid = energy_grid(nitems);
+    const int64_t grid = tgv_energy_grid(nitems);
     A.nitems = nitems;
     switch (A.nbins) {
     case 8: tgv_energy_kernel<S, 8><<<(unsigned)grid, TGV_BVOX, 0, stream>>>(A); break;

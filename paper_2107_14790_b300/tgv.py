@@ -279,8 +279,7 @@ def tgv_energy_noalloc(nbricks: int, nall: int, u, v, p, q, hist, nbr, params: t
 
     For callers that may not allocate device memory; u, v, p, q, hist, nbr are
     device tensors in the layout documented at tgv_state_view in include/tgv.h.
-    Raises TgvError on a non-zero status (BUDGET: more than
-    TGV_NOALLOC_MAX_BRICKS active bricks).
+    Raises TgvError on a non-zero status.
     """
     view = tgv_state_view(int(nbricks), int(nall), _ptr(u), _ptr(v), _ptr(p), _ptr(q), _ptr(hist), _ptr(nbr))
     if out is None:
@@ -289,8 +288,6 @@ def tgv_energy_noalloc(nbricks: int, nall: int, u, v, p, q, hist, nbr, params: t
     _check(None, st)
     return out
 
-
-NOALLOC_MAX_BRICKS = 65536
 
 
 def tgv_extract_field(d, level: int, field: str, out=None):

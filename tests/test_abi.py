@@ -66,10 +66,3 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(tgv, "_LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         tgv.lib()
-
-
-def test_noalloc_limit_matches_header():
-    from paper_2107_14790_b300 import tgv
-    text = open(HEADER).read()
-    m = re.search(r"#define TGV_NOALLOC_MAX_BRICKS (\d+)", text)
-    assert m and int(m.group(1)) == tgv.NOALLOC_MAX_BRICKS
