@@ -122,8 +122,10 @@ __global__ void comp_dual_kernel(const CompArgs A)
 
 __device__ __forceinline__ int qidx_c(int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); }
 
+template <int NB>  // bin count (0: read at run time)
 __global__ void comp_primal_kernel(const CompArgs A)
 {
+    constexpr int NBM = NB ? NB : TGV_MAX_BINS;
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.n) return;
     float d1 = 0.0f, d2[3] = {0.0f, 0.0f, 0.0f};
@@ -169,18 +171,21 @@ __global__ void comp_primal_kernel(const CompArgs A)
     const float u0 = A.u[x];
     const float ut = u0 + A.tau * d1;
     // prox: generalised median = max_i min(ut - tau*lambda*W_i, c_i), c_n = +inf
-    float hs = 0.0f, hb_[TGV_MAX_BINS];
-    for (int k = 0; k < TGV_MAX_BINS; ++k) {
-        hb_[k] = 0.0f;
-        if (k < A.nbins) {
-            const uint32_t w = A.hist[x * A.npairs + (k >> 1)];
-            hb_[k] = (float)((w >> ((k & 1) * 16)) & 0xffffu);
-            hs += hb_[k];
-        }
+    const int nbins = NB ? NB : A.nbins;
+    const int npairs = NB ? (NB + 1) / 2 : A.npairs;
+    uint32_t hw[(NBM + 1) / 2];
+#pragma unroll
+    for (int k = 0; k < (NBM + 1) / 2; ++k) hw[k] = (NB || k < npairs) ? A.hist[x * npairs + k] : 0u;
+    float hs = 0.0f, hb_[NBM];
+#pragma unroll
+    for (int k = 0; k < NBM; ++k) {
+        hb_[k] = (float)((hw[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
+        hs += hb_[k];
     }
     float W = -hs, un = -INFINITY;
-    for (int i = 0; i < TGV_MAX_BINS; ++i) {
-        if (i < A.nbins) {
+#pragma unroll
+    for (int i = 0; i < NBM; ++i) {
+        if (NB || i < nbins) {
             un = fmaxf(un, fminf(ut - A.taulam * W, A.c[i]));
             W += 2.0f * hb_[i];
         }
@@ -717,7 +722,12 @@ tgv_status tgv_composite_solve(tgv_composite* c, int32_t iterations)
     const unsigned grid = (unsigned)((c->n + 255) / 256);
     for (int it = 0; it < iterations; ++it) {
         comp_dual_kernel<<<grid, 256, 0, d->stream>>>(A);
-        comp_primal_kernel<<<grid, 256, 0, d->stream>>>(A);
+        switch (A.nbins) {
+        case 8: comp_primal_kernel<8><<<grid, 256, 0, d->stream>>>(A); break;
+        case 10: comp_primal_kernel<10><<<grid, 256, 0, d->stream>>>(A); break;
+        case 12: comp_primal_kernel<12><<<grid, 256, 0, d->stream>>>(A); break;
+        default: comp_primal_kernel<0><<<grid, 256, 0, d->stream>>>(A); break;
+        }
         c->launches += 2;
     }
     return tgv_cuda_check(d, cudaGetLastError(), "composite iteration launch");
