@@ -260,3 +260,97 @@ def test_spherical_votes_of_five():
     lvl = oracle.OracleLevel(sc.domain, sc.nbins)
     votes = sum(lvl.accumulate(c, d, 5) for c, d in zip(sc.cameras, sc.depths))
     assert votes > 0 and int(lvl.hist.sum()) == 5 * votes and np.all(lvl.hist % 5 == 0)
+
+
+def _pyramid_np(depth):
+    """Depth pyramid written independently: level l+1 = min of the valid children (NaN none)."""
+    d = np.where(np.isfinite(depth) & (depth > 0), depth.astype(np.float64), np.nan)
+    levels = [d]
+    while max(levels[-1].shape) > 1:
+        a = levels[-1]
+        h, w = a.shape
+        p = np.full((h + h % 2, w + w % 2), np.nan)
+        p[:h, :w] = a
+        blocks = p.reshape(p.shape[0] // 2, 2, p.shape[1] // 2, 2).transpose(0, 2, 1, 3).reshape(-1, 4)
+        ok = ~np.all(np.isnan(blocks), axis=1)
+        m = np.full(blocks.shape[0], np.nan)
+        m[ok] = np.nanmin(blocks[ok], axis=1)
+        levels.append(m.reshape(p.shape[0] // 2, p.shape[1] // 2))
+    return levels
+
+
+def test_scatter_from_pixels_equals_the_gather(sphere_scene):
+    """Alg. 1 from the pixel side: every valid pyramid pixel (level l, i, j) gives its vote to
+    the voxels it owns (centre in its square at level l, level of detail l, a >= -eta), in
+    FP64 numpy with its own pyramid; the oracle's FP32 gather must give the same counts on
+    every voxel none of whose decisions lies within 1e-4 of a border (pixel edge, level
+    threshold, bin edge, occlusion cut)."""
+    sc = sphere_scene
+    n = 32
+    desc = synth.DomainDesc(np.zeros(3), 1.0 / n, synth.dense_bricks(n // 8))
+    nbins = 8
+    cams = sc.cameras[:3] + [synth.Camera(*synth.pinhole_intrinsics(128, 128, 50.0),
+                                          synth.look_at(np.array([0.1, 0.12, 0.15]), np.array([0.5, 0.5, 0.5])),
+                                          np.array([0.1, 0.12, 0.15]), 128, 128)]
+    deps = [d for d in sc.depths[:3]]
+    c4 = cams[3]
+    dirs = c4.ray_directions()
+    oc = c4.C - np.array([0.5, 0.5, 0.5])
+    b = np.einsum("hwk,k->hw", dirs, oc)
+    aa = np.einsum("hwk,hwk->hw", dirs, dirs)
+    disc = b * b - aa * (oc @ oc - 0.35 ** 2)
+    t = np.where(disc >= 0, (-b - np.sqrt(np.maximum(disc, 0))) / aa, np.nan)
+    deps.append(t.astype(np.float32))
+    g = desc.bricks[:, None, :] * 8 + np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8),
+                                                            indexing="ij"), -1).reshape(-1, 3)[:, ::-1][None]
+    g = g.reshape(-1, 3)  # global voxel index, in the oracle's voxel order (x fastest within a brick)
+    X = desc.origin + (g + 0.5) * desc.h
+    r = desc.h / 2
+    delta, eta = 6 * r, 18 * r
+    scatter = np.zeros((len(X), nbins), np.int64)
+    safe = np.ones(len(X), bool)
+    used_levels = set()
+    for cam, dep in zip(cams, deps):
+        levels = _pyramid_np(dep)
+        R = np.asarray(cam.R).reshape(3, 3)
+        Xc = (X - cam.C) @ R.T
+        front = Xc[:, 2] > 0
+        zc = np.where(front, Xc[:, 2], 1.0)
+        px = cam.fx * Xc[:, 0] / zc + cam.cx
+        py = cam.fy * Xc[:, 1] / zc + cam.cy
+        fp = cam.fx * 2 * r / zc
+        lod = np.clip(np.floor(np.log2(np.maximum(fp, 1.0))), 0, len(levels) - 1).astype(int)
+        # borders: the level threshold, the pixel edges at that level
+        lg = np.log2(np.maximum(fp, 1.0))
+        safe &= ~front | (np.abs(lg - np.round(lg)) > 1e-4) | (fp < 1.0) | (lg > len(levels) - 1 + 1e-4)
+        sx, sy = px / 2.0 ** lod, py / 2.0 ** lod
+        safe &= ~front | ((np.abs(sx - np.round(sx)) > 1e-4) & (np.abs(sy - np.round(sy)) > 1e-4))
+        # the pixel side: each valid pixel of each level collects the voxels it owns
+        owner = {}
+        for v in np.nonzero(front)[0]:
+            l = lod[v]
+            i, j = int(np.floor(sx[v])), int(np.floor(sy[v]))
+            hl, wl = levels[l].shape
+            if 0 <= i < wl and 0 <= j < hl:
+                owner.setdefault((l, i, j), []).append(v)
+        for (l, i, j), vox in owner.items():
+            D = levels[l][j, i]
+            if np.isnan(D):
+                continue
+            used_levels.add(l)
+            for v in vox:
+                a = D - zc[v]
+                if abs(a + eta) < 1e-4:
+                    safe[v] = False
+                if a < -eta:
+                    continue
+                s = (min(1.0, max(-1.0, a / delta)) + 1.0) / 2.0 * nbins
+                if abs(s - round(s)) < 1e-4 and 0 < round(s) < nbins:
+                    safe[v] = False
+                scatter[v, min(int(np.floor(s)), nbins - 1)] += 1
+    orc = oracle.OracleLevel(desc, nbins)
+    for cam, dep in zip(cams, deps):
+        orc.accumulate(cam, dep, 1)
+    assert safe.mean() > 0.9
+    assert scatter[safe].sum() > 10_000 and len(used_levels) >= 3
+    np.testing.assert_array_equal(orc.hist[safe].astype(np.int64), scatter[safe])
