@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree", "composite",
-                             "histforms"],
+                             "histforms", "precision"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
                          "300 iterations; serving: Poisson stream of 2000 chunk-solve requests")
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
@@ -547,6 +547,97 @@ def run_multilevel(args):
                              "scaled-down scene in tests/test_gpu_multilevel.py"}
 
 
+def _dense_zyx(vals, bricks, n):
+    """Per-voxel values (brick order, x fastest in a brick) on an (n, n, n) [z, y, x] grid."""
+    li = np.arange(512)
+    loc = np.stack([li % 8, (li // 8) % 8, li // 64], axis=1)
+    g = (8 * np.asarray(bricks)[:, None, :] + loc[None]).reshape(-1, 3)
+    out = np.zeros((n, n, n), dtype=np.float64)
+    out[g[:, 2], g[:, 1], g[:, 0]] = np.asarray(vals, np.float64).reshape(-1)
+    return out
+
+
+def _field_diff(U, R, eps=1e-3):
+    """Differences of field U against the reference R on one grid: max and RMS of |U - R|,
+    and on voxel edges whose endpoints have |value| > eps in both fields: the share of
+    edges where the sign pattern differs and the displacement of the zero crossing
+    (linear interpolation, in voxel edges h) where both cross."""
+    d = U - R
+    out = {"linf": float(np.abs(d).max()), "rms": float(np.sqrt(np.mean(d * d)))}
+    n_edges = n_mismatch = 0
+    disp = []
+    for ax in range(3):
+        s0 = [slice(None)] * 3
+        s1 = [slice(None)] * 3
+        s0[ax] = slice(0, -1)
+        s1[ax] = slice(1, None)
+        ua, ub, ra, rb = U[tuple(s0)], U[tuple(s1)], R[tuple(s0)], R[tuple(s1)]
+        ok = (np.abs(ua) > eps) & (np.abs(ub) > eps) & (np.abs(ra) > eps) & (np.abs(rb) > eps)
+        cu = np.sign(ua) != np.sign(ub)
+        cr = np.sign(ra) != np.sign(rb)
+        n_edges += int(np.count_nonzero(ok & (cu | cr)))
+        n_mismatch += int(np.count_nonzero(ok & (cu != cr)))
+        both = ok & cu & cr
+        tu = ua[both] / (ua[both] - ub[both])
+        tr = ra[both] / (ra[both] - rb[both])
+        disp.append(np.abs(tu - tr))
+    disp = np.concatenate(disp)
+    out.update({"crossing_edges": n_edges, "sign_mismatch_share": n_mismatch / max(n_edges, 1),
+                "crossing_disp_max_h": float(disp.max()) if len(disp) else 0.0,
+                "crossing_disp_mean_h": float(disp.mean()) if len(disp) else 0.0})
+    return out
+
+
+def run_precision(args):
+    """Reduced-precision storage of v, vbar, p, q against FP32 and the FP64 oracle: max and
+    RMS difference of u and the displacement of its zero crossings, on the sphere case
+    (64^3, 16 maps, 200 iterations; against the oracle) and the terrain case (256^3, 64
+    maps, 500 iterations; against the FP32 run)."""
+    import torch
+    import synth
+    import oracle
+    from paper_2107_14790_b300 import build, tgv
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    res = {}
+    sph = synth.sphere_scene()
+    # cpu_baseline leg: the oracle's run of the sphere case, timed; its field is the reference
+    t_cpu = time.perf_counter()
+    orc = oracle.OracleLevel(sph.domain, 8)
+    for c, d in zip(sph.cameras, sph.depths):
+        orc.accumulate(c, d, 1)
+    orc.iterate(200)
+    t_cpu = time.perf_counter() - t_cpu
+    n1 = 64
+    ref1 = _dense_zyx(orc.u, sph.domain.bricks, n1)
+    dep1 = torch.from_numpy(np.stack(sph.depths)).cuda()
+    sc = synth.terrain_scene(1002, 256, 64, 512, 10, 500, device="cuda")
+    dep2 = torch.from_numpy(np.stack(sc.depths)).cuda()
+    ref2 = None
+    for storage in ("fp32", "fp16", "bf16"):
+        with tgv.Domain([sph.domain], nbins=8, storage=storage, stream=stream.cuda_stream) as dom:
+            dom.accumulate(0, sph.cameras, dep1)
+            dom.solve(0, 200)
+            u1 = _dense_zyx(dom.field(0, "u")[:, 0], sph.domain.bricks, n1)
+        with tgv.Domain([sc.domain], nbins=10, storage=storage, stream=stream.cuda_stream) as dom:
+            dom.accumulate(0, sc.cameras, dep2)
+            dom.solve(0, 500)
+            u2 = _dense_zyx(dom.field(0, "u")[:, 0], sc.domain.bricks, 256)
+        if storage == "fp32":
+            ref2 = u2
+        res[storage] = {"sphere_64_vs_fp64_oracle": _field_diff(u1, ref1),
+                        "terrain_256_vs_fp32": _field_diff(u2, ref2) if storage != "fp32" else None}
+    return {"metric": "precision of reduced storage: |du| max / RMS and zero-crossing displacement",
+            "value": res["fp16"]["terrain_256_vs_fp32"]["linf"], "unit": "max |u_fp16 - u_fp32| (terrain)",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32-math/fp16,bf16-storage",
+            "data": "synthetic (seeded sphere and terrain scenes)",
+            "config": {"workload": "sphere-64^3-200it-vs-oracle+terrain-256^3-500it-vs-fp32"}, "results": res,
+            "cpu_baseline": {"value": sph.domain.nvox * 200 / t_cpu, "unit": "voxel-updates/s",
+                             "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "the sphere case whole (16 maps' histograms + 200 iterations)"}}
+
+
 def run_histforms(args):
     """The two forms of the histogram kernel on the 256^3 terrain's 64 aerial maps 512^2:
     gather (one thread per voxel, every map) and scatter (one thread per pyramid pixel,
@@ -923,6 +1014,9 @@ def main():
         return
     if args.workload == "histforms":
         print(json.dumps(run_histforms(args)), flush=True)
+        return
+    if args.workload == "precision":
+        print(json.dumps(run_precision(args)), flush=True)
         return
     cfg = SMALL if args.small else WORKLOAD
     if args.impl == "reference":
