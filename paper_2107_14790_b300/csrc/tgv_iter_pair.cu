@@ -18,7 +18,12 @@
 //   * brick i needs the new q on the x = 0 layer of brick i+1, which only
 //     phase A of brick i+1 produces, after phase B of brick i: the v update of
 //     brick i's x = 7 voxels leaves the +x term out (it is added last), parks
-//     the partial sum, and phase A of brick i+1 completes and stores it.
+//     the partial sum, and phase A of brick i+1 completes it and stores the
+//     x = 6, 7 pair (the x = 6 results wait in brick i's dead v and vbar slots,
+//     so no row is written in two pieces).
+// Phase B of one brick and phase A of the next touch different stages except
+// for these hand-over slots, which only lanes of one warp share: a warp goes from
+// one to the other after a warp sync, and one CTA barrier closes each interval.
 // The dual updates use explicitly rounded arithmetic, so a dual recomputed as
 // a halo equals the owner's bit for bit and results do not depend on R, the
 // grid size or the order of the work items.
@@ -531,16 +536,18 @@ struct PairCta {
             const float* hq_prev = hal_q(ps);
             const float* pn_prev = pn_own(ps);
             const S* sv_prev = (const S*)(stage(ps) + O_V);
-            const uint32_t l7 = 7 + 8 * y + 64 * z;
+            const S* svb_prev = (const S*)(stage(ps) + O_VB);
+            const uint32_t l6 = 6 + 8 * y + 64 * z;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int qc = qidx(0, c);
                 const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qn0[qc]);
-                const float v0 = ld_s(sv_prev + c * 512 + l7);
-                const float v1 = vnew(v0, pn_prev[c * 512 + l7], d2, A.tau);
-                const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l7;
-                st_s(A.v + oi, v1);
-                st_s(A.vbar_out + oi, vbar_of(v1, v0));
+                const float v0 = ld_s(sv_prev + c * 512 + l6 + 1);
+                const float v1 = vnew(v0, pn_prev[c * 512 + l6 + 1], d2, A.tau);
+                // with the x = 6 values parked by its phase B: one pair store per field
+                const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l6;
+                PS::st(A.v + oi, make_float2(ld_s(sv_prev + c * 512 + l6), v1));
+                PS::st(A.vbar_out + oi, make_float2(ld_s(svb_prev + c * 512 + l6), vbar_of(v1, v0)));
             }
         }
 
@@ -727,9 +734,12 @@ struct PairCta {
             const float2 v0 = PS::ld(sv + c * 512 + l0);
             const float v1a = vnew(v0.x, pn0[c], d2a[c], A.tau);
             if (park) {
+                // x = 6 is final, x = 7 waits for the next item's q: keep both stores as one
+                // pair store (no split sectors) by parking x = 6's new v and vbar in this
+                // stage's v and vbar slots, which nothing reads any more
                 hal_q(s)[qidx(0, c) * 192 + y + 8 * z] = d2b[c];
-                st_s(A.v + oi, v1a);
-                st_s(A.vbar_out + oi, vbar_of(v1a, v0.x));
+                st_s((S*)(st + O_V) + c * 512 + l0, v1a);
+                st_s((S*)(st + O_VB) + c * 512 + l0, vbar_of(v1a, v0.x));
             } else {
                 if (L & 8u) d2b[c] = __fadd_rn(d2b[c], j < 3 ? qno[qidx(0, c) * 512 + l0 + 2]
                                                              : hq[qidx(0, c) * 192 + y + 8 * z]);
