@@ -733,19 +733,23 @@ struct PairCta {
             const size_t oi = ((size_t)b * 3 + c) * TGV_BVOX + l0;
             const float2 v0 = PS::ld(sv + c * 512 + l0);
             const float v1a = vnew(v0.x, pn0[c], d2a[c], A.tau);
+            const float vba = vbar_of(v1a, v0.x);
+            // every lane forms the pair (a parking lane's x = 7 value is not used), so
+            // only the stores below depend on the lane
+            const float part = d2b[c];
+            const float fwdq = j < 3 ? qno[qidx(0, c) * 512 + l0 + 2] : hq[qidx(0, c) * 192 + y + 8 * z];
+            const float d2c = (L & 8u) ? __fadd_rn(part, fwdq) : part;
+            const float v1b = vnew(v0.y, pn1[c], d2c, A.tau);
             if (park) {
                 // x = 6 is final, x = 7 waits for the next item's q: keep both stores as one
                 // pair store (no split sectors) by parking x = 6's new v and vbar in this
                 // stage's v and vbar slots, which nothing reads any more
-                hal_q(s)[qidx(0, c) * 192 + y + 8 * z] = d2b[c];
+                hal_q(s)[qidx(0, c) * 192 + y + 8 * z] = part;
                 st_s((S*)(st + O_V) + c * 512 + l0, v1a);
-                st_s((S*)(st + O_VB) + c * 512 + l0, vbar_of(v1a, v0.x));
+                st_s((S*)(st + O_VB) + c * 512 + l0, vba);
             } else {
-                if (L & 8u) d2b[c] = __fadd_rn(d2b[c], j < 3 ? qno[qidx(0, c) * 512 + l0 + 2]
-                                                             : hq[qidx(0, c) * 192 + y + 8 * z]);
-                const float v1b = vnew(v0.y, pn1[c], d2b[c], A.tau);
                 PS::st(A.v + oi, make_float2(v1a, v1b));
-                PS::st(A.vbar_out + oi, make_float2(vbar_of(v1a, v0.x), vbar_of(v1b, v0.y)));
+                PS::st(A.vbar_out + oi, make_float2(vba, vbar_of(v1b, v0.y)));
             }
             PS::st(A.p_out + oi, make_float2(pn0[c], pn1[c]));
         }
