@@ -57,13 +57,20 @@ tgv_status tgv_kernel_setup(const void* kernel, int threads, size_t smem, int* p
         *per_sm = it->second;
         return TGV_OK;
     }
-    // The limit is raised to the device maximum (not to `smem`): the same kernel may be
+    // The limit is raised to the device maximum (less the kernel's static shared memory,
+    // not to `smem`): the same kernel may be
     // launched with different shared-memory sizes, and a lower limit set for one
     // size would make launches with a larger one fail.
     int optin = 0;
+    cudaFuncAttributes fa;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        (size_t)optin < smem ||
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return TGV_ERR_CUDA;
+    }
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts too
+    if (dyn_max < 0 || (size_t)dyn_max < smem ||
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return TGV_ERR_CUDA;
