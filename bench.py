@@ -239,7 +239,7 @@ def run_ours(args, cfg):
         pass
     last = energies[-1]
     result = {
-        "metric": "TGV voxel-updates/s (histograms + 500 fused primal-dual iterations + energy/gap)",
+        "metric": "TGV voxel-updates/s (histograms + %d fused primal-dual iterations + energy/gap)" % iters,
         "value": value, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else f"f32-math/{args.storage}-storage",
@@ -347,7 +347,7 @@ def run_reference(args, cfg):
         secs.append(dt)
     value = statistics.median(vals)
     cores = oracle.max_threads()
-    return {"impl": "reference", "metric": "TGV voxel-updates/s (histograms + 500 fused primal-dual iterations + energy/gap)",
+    return {"impl": "reference", "metric": "TGV voxel-updates/s (histograms + %d fused primal-dual iterations + energy/gap)" % cfg["iterations"],
             "value": value, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": scene_note(cfg),
