@@ -109,3 +109,11 @@ def test_scattered_samples_outgrow_the_first_level_table():
         deps.append(d)
     lv = check_same(cams, deps, np.zeros(3), 1.0, 12, 12, 4)
     assert lv[0].nbricks > 1_100_000
+
+
+def test_deep_level_long_keys(sphere_scene):
+    """One level at depth 18 (2^15 bricks per axis: 45-bit Morton codes, six radix passes
+    of the device sort), every sample its own brick, one ring of band."""
+    sc = sphere_scene
+    lv = check_same(sc.cameras[:4], sc.depths[:4], np.array([-0.5, -0.5, -0.5]), 2.0, 18, 18, 1)
+    assert lv[0].nbricks > 100_000
