@@ -183,7 +183,7 @@ __device__ __forceinline__ int alg1_bin_of(float depth, float dist, float delta,
     ac = fminf(1.0f, ac);
     ac = fmaxf(-1.0f, ac);
     const float t1 = __fadd_rn(ac, 1.0f);
-    const float t2 = __fdiv_rn(t1, 2.0f);
+    const float t2 = __fmul_rn(t1, 0.5f);  // = t1 / 2 exactly (a power of two)
     const float t3 = __fmul_rn(t2, (float)nbins);
     int bin = (int)floorf(t3);
     return bin > nbins - 1 ? nbins - 1 : bin;
@@ -216,23 +216,20 @@ __global__ void __launch_bounds__(512) hist_accumulate_kernel(const AccArgs A)
     const float diam = __fmul_rn(A.r, 2.0f);
     const float delta = __fmul_rn(6.0f, A.r);
     const float eta = __fmul_rn(3.0f, delta);
-    uint32_t acc[TGV_MAX_BINS / 2];
+    // this thread's packed counts of the launch, in shared memory so that a vote is
+    // one indexed add (column t of word k: no two threads share a word)
+    __shared__ uint32_t s_acc[TGV_MAX_BINS / 2][TGV_BVOX];
 #pragma unroll
-    for (int k = 0; k < TGV_MAX_BINS / 2; ++k) acc[k] = 0u;
+    for (int k = 0; k < TGV_MAX_BINS / 2; ++k) s_acc[k][t] = 0u;
     for (int m = 0; m < A.nmaps; ++m) {
         const int bin = alg1_bin(A.cam[m], A.L, A.pyr + (int64_t)m * A.L.size, X, diam, delta, eta, A.nbins);
-        if (bin >= 0) {
-            const uint32_t inc = A.cam[m].vote << ((bin & 1) * 16);
-#pragma unroll
-            for (int k = 0; k < TGV_MAX_BINS / 2; ++k)
-                if (k == (bin >> 1)) acc[k] += inc;
-        }
+        if (bin >= 0) s_acc[bin >> 1][t] += A.cam[m].vote << ((bin & 1) * 16);
     }
-#pragma unroll
-    for (int k = 0; k < TGV_MAX_BINS / 2; ++k) {
-        if (k < A.npairs && acc[k] != 0u) {
+    for (int k = 0; k < A.npairs; ++k) {
+        const uint32_t a = s_acc[k][t];
+        if (a != 0u) {
             uint32_t* w = A.hist + ((int64_t)b * A.npairs + k) * TGV_BVOX + t;
-            *w += acc[k];
+            *w += a;
         }
     }
 }
