@@ -433,7 +433,7 @@ TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nbricks, cons
  * The reduction scratch is a fixed array inside this library (on every GPU
  * that loads the library, held until the process exits), so the call
  * allocates nothing and frees nothing.  It holds one set of partial sums per
- * CTA of the energy kernel (three CTAs per SM), so any number of active bricks
+ * CTA of the energy kernel (sixteen CTAs per SM), so any number of active bricks
  * fits.  Consequences:
  *  - every call on a device uses the same scratch: calls whose device work
  *    overlaps (different streams, or other host threads) race and may return
@@ -445,7 +445,7 @@ TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nbricks, cons
  * `stream`: the cudaStream_t to run on (NULL = legacy default stream); the
  * call waits for its own work.  `out`: 4 doubles, host or device memory,
  * receiving the same values as tgv_energy.  Errors: INVALID_ARG (null
- * pointers, bad parameters), BUDGET (a device with more than 1365 SMs), CUDA.
+ * pointers, bad parameters), BUDGET (a device with more than 256 SMs), CUDA.
  * ------------------------------------------------------------------------- */
 
 /* One level's state in device memory owned by the caller (the library's

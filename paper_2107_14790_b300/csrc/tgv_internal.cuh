@@ -161,7 +161,7 @@ void tgv_bin_centres(const tgv_params& prm, float* c);
 
 // Marching cubes of level L into the domain's mesh buffers (synchronises).
 tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t* ntris);
-// CTAs (= partial sums) of the energy kernel for nitems bricks: three per SM of the
+// CTAs (= partial sums) of the energy kernel for nitems bricks: sixteen per SM of the
 // current device, at most nitems
 int64_t tgv_energy_grid(int64_t nitems);
 // exclusive prefix sum of n counts in place on the domain's stream (its tile sums in

@@ -8,7 +8,7 @@
 
 namespace {
 
-// 3 partial sums per CTA of the energy kernel (a persistent grid of three CTAs per
+// 3 partial sums per CTA of the energy kernel (a persistent grid of sixteen CTAs per
 // SM, whatever the brick count), then the 4 result doubles.  Every GPU that loads
 // this library holds it (about 100 KB) until the process exits.
 constexpr int64_t kMaxPartials = 4096;
@@ -60,7 +60,7 @@ extern "C" tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_para
         return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;
     }
     if (!s->u || !s->v || !s->p || !s->q || !s->hist || !s->nbr) return TGV_ERR_INVALID_ARG;
-    if (tgv_energy_grid(s->nbricks) > kMaxPartials) return TGV_ERR_BUDGET;  // a GPU with over 1365 SMs
+    if (tgv_energy_grid(s->nbricks) > kMaxPartials) return TGV_ERR_BUDGET;  // a GPU with over 256 SMs
     double* scratch = nullptr;
     tgv_status rc = scratch_for_current_device(&scratch);
     if (rc != TGV_OK) return rc;
