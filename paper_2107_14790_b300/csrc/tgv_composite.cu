@@ -64,9 +64,8 @@ __device__ __forceinline__ const int32_t* list_of(const CompArgs& A, int64_t irr
 // Most leaves are regular: one same-level neighbour (or none) on every side,
 // so their reverse lists are the mirrored neighbours with weight 1 and six ids
 // describe them.  Leaves at 2:1 faces keep the full lists.
-__global__ void comp_dual_kernel(const CompArgs A)
+__device__ __forceinline__ void comp_dual_leaf(const CompArgs& A, const int64_t x)
 {
-    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.n) return;
     const float ub = A.ubar[x];
     float vb[3], g[3], dm[3][3];
@@ -120,13 +119,19 @@ __global__ void comp_dual_kernel(const CompArgs A)
     for (int c = 0; c < 6; ++c) A.q[6 * x + c] = qn[c];
 }
 
+__global__ void comp_dual_kernel(const CompArgs A)
+{
+    const int64_t x = (int64_t)blockIdx.x * (2 * blockDim.x) + threadIdx.x;
+    comp_dual_leaf(A, x);
+    comp_dual_leaf(A, x + blockDim.x);
+}
+
 __device__ __forceinline__ int qidx_c(int a, int b) { return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)); }
 
 template <int NB>  // bin count (0: read at run time)
-__global__ void comp_primal_kernel(const CompArgs A)
+__device__ __forceinline__ void comp_primal_leaf(const CompArgs& A, const int64_t x)
 {
     constexpr int NBM = NB ? NB : TGV_MAX_BINS;
-    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.n) return;
     float d1 = 0.0f, d2[3] = {0.0f, 0.0f, 0.0f};
     const int32_t m0 = A.nb6[6 * x];
@@ -200,6 +205,15 @@ __global__ void comp_primal_kernel(const CompArgs A)
         A.v[3 * x + c] = v1;
         A.vbar[3 * x + c] = 2.0f * v1 - v0;
     }
+}
+
+// two leaves per thread (x and x + blockDim.x of the block's 2 blockDim.x leaves)
+template <int NB>
+__global__ void comp_primal_kernel(const CompArgs A)
+{
+    const int64_t x = (int64_t)blockIdx.x * (2 * blockDim.x) + threadIdx.x;
+    comp_primal_leaf<NB>(A, x);
+    comp_primal_leaf<NB>(A, x + blockDim.x);
 }
 
 // leaf histograms: gather the packed words of each leaf from its level
@@ -719,7 +733,7 @@ tgv_status tgv_composite_solve(tgv_composite* c, int32_t iterations)
     A.sigma = d->prm.sigma;
     A.taulam = d->prm.tau * d->prm.lambda;
     tgv_bin_centres(d->prm, A.c);
-    const unsigned grid = (unsigned)((c->n + 255) / 256);
+    const unsigned grid = (unsigned)((c->n + 511) / 512);  // two leaves per thread
     for (int it = 0; it < iterations; ++it) {
         comp_dual_kernel<<<grid, 256, 0, d->stream>>>(A);
         switch (A.nbins) {
