@@ -569,8 +569,8 @@ void tgv_destroy_domain(tgv_domain* d)
     DeviceGuard g(d->device);
     cudaStreamSynchronize(d->stream);
     for (TgvLevel& L : d->levels) free_level(L);
-    for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table, &d->mesh_flags, &d->mesh_count, &d->mesh_scan,
-                          &d->mesh_v, &d->mesh_t})
+    for (TgvScratch* s : {&d->pyr, &d->red, &d->tmp, &d->table, &d->mesh_flags, &d->mesh_count, &d->mesh_cells,
+                          &d->mesh_scan, &d->mesh_v, &d->mesh_t})
         if (s->ptr) cudaFree(s->ptr);
     if (d->red_out) cudaFree(d->red_out);
     if (d->err) cudaFree(d->err);

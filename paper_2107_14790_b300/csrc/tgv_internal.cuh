@@ -142,7 +142,7 @@ struct tgv_domain {
     TgvScratch red;     // per-block partial sums of the energy reduction
     TgvScratch tmp;     // staging for host <-> device field copies
     TgvScratch table;   // per-brick parent table of tgv_prolong
-    TgvScratch mesh_flags, mesh_count, mesh_scan, mesh_v, mesh_t;  // marching cubes
+    TgvScratch mesh_flags, mesh_count, mesh_cells, mesh_scan, mesh_v, mesh_t;  // marching cubes
     int64_t mesh_nv = -1, mesh_nt = -1;  // counts of the last extracted mesh (-1: none)
     double* red_out = nullptr;   // 4 doubles: final reduction result (device)
     int* err = nullptr;          // device flag: 1 after a bounded device-side wait gave up

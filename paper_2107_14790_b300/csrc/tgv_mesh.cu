@@ -25,9 +25,19 @@
 //     cell fall back to the unconstrained programme).
 // Vertex ids: 4 slot + a for the crossing on edge (slot, a), 4 slot + 3 for a
 // cell's centroid; vertices are numbered by increasing id, triangles come in
-// cell order.  Passes: count (per-cell triangle counts, referenced ids marked),
-// two exclusive scans (vertex ranks, triangle offsets), write (triangles and the
-// positions of the vertices each cell references).
+// cell order.  Passes:
+//   classify  one bit per cell whose corners change sign (a warp ballot per word);
+//   compact   the crossing cells into a list in cell order (exclusive scan of the
+//             words' popcounts; rank = word prefix + popcount of the lower bits);
+//   count     per listed cell: the loops and their triangulation; the triangles are
+//             kept as edge-index triples in a per-cell record and the vertex ids
+//             they reference are set in a bit set (4 ids per voxel slot);
+//   scans     of the vertex bit set's word popcounts (vertex rank, as above) and of
+//             the listed cells' triangle counts (triangle offsets);
+//   write     per listed cell: triangles from its record, vertex positions.
+// Only a few per cent of the cells cross the surface: listing them keeps the
+// lanes of a warp busy in the loop triangulation, and the record spares the write
+// pass from repeating it.
 #include <math.h>
 
 #include <unordered_map>
@@ -74,10 +84,24 @@ struct MeshArgs {
     const int32_t* up7;     // nb x 7: bricks at +x, +y, +xy, +z, +xz, +yz, +xyz (-1 none)
     int64_t nb;
     float o[3], h;
-    uint32_t* flags;        // 4 ids per voxel slot: marked, then exclusive ranks
-    uint32_t* tcount;       // per cell: triangle count, then exclusive offsets
+    uint32_t* vbits;        // bit set over the vertex ids (4 per voxel slot)
+    const uint32_t* vrank;  // exclusive prefix of the words' popcounts
+    const uint32_t* cells;  // the crossing cells in cell order (ncross)
+    int64_t ncross;
+    uint32_t* tcount;       // per listed cell: triangle count, then exclusive offsets
+    struct MeshRec* rec;    // per listed cell
     float* verts;
     int32_t* tris;
+};
+
+// The triangles of one listed cell: triangle t is the edge-index triple
+// (e0 | e1 << 4 | e2 << 8) at bits 12 (t % 5) of tri[t / 5] (12 = the centroid).
+// At most 12 triangles: a loop of k crossings gives k - 2, or k around the
+// centroid (once per cell), and the loops share the 12 cell edges.
+struct MeshRec {
+    uint64_t tri[3];
+    float centre[3];
+    uint32_t head;  // bits 0-11 crossing edges, 12 centroid used, 16-19 triangle count
 };
 
 // Everything about one cell.
@@ -189,17 +213,21 @@ __device__ __forceinline__ float area2(const float (*P)[3], int i, int m, int j)
 // (only when constrained).
 __device__ int triangulate(int k, const float (*P)[3], const int8_t* edges, bool constrained, int8_t (*tri)[3])
 {
+    if (k < 3) return k == 2 ? 0 : -1;  // two crossings: no triangle; one: no triangulation
     float Cst[kMaxPoly][kMaxPoly];
     int8_t best[kMaxPoly][kMaxPoly];
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) {
-            Cst[i][j] = 0.0f;
-            best[i][j] = j == i + 1 ? (int8_t)k : (int8_t)-1;
-        }
+    // entries (i, j) with j > i only, each written before it is read
+    for (int i = 0; i + 1 < k; ++i) {
+        Cst[i][i + 1] = 0.0f;
+        best[i][i + 1] = (int8_t)k;
+    }
     for (int len = 2; len < k; ++len)
         for (int i = 0; i + len < k; ++i) {
             const int j = i + len;
-            if (constrained && len < k - 1 && on_common_face(edges[i], edges[j])) continue;
+            if (constrained && len < k - 1 && on_common_face(edges[i], edges[j])) {
+                best[i][j] = -1;
+                continue;
+            }
             float bc = 0.0f;
             int bm = -1;
             for (int m = i + 1; m < j; ++m) {
@@ -264,6 +292,10 @@ __device__ int cell_triangles(const MeshArgs& A, const Cell& C, float centre[3],
             done |= 1 << e;
             e = C.next[e];
         } while (e != e0 && e >= 0 && k < kMaxPoly);
+        if (k == 3) {  // the programme's only triangulation, never constrained out
+            emit(ntri++, poly[0], poly[1], poly[2]);
+            continue;
+        }
         float P[kMaxPoly][3];
         for (int v = 0; v < k; ++v) crossing_point(A, C, poly[v], P[v]);
         int8_t tri[kMaxPoly][3];
@@ -283,56 +315,138 @@ __device__ int cell_triangles(const MeshArgs& A, const Cell& C, float centre[3],
     return ntri;
 }
 
+// bit (cell & 31) of word[cell >> 5]: the cell exists and its corners change sign.
+// 64 threads per brick, one per (i, j) column of 8 cells: the thread walks k = 0..7
+// keeping the corner layer that the next cell shares; a warp holds four rows j, so
+// each step k makes one word of the bit set by ballot.
+__global__ void __launch_bounds__(256) mc_classify_kernel(const MeshArgs A, uint32_t* word)
+{
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 6;
+    if (b >= A.nb) return;  // whole warps: 64 threads per brick
+    const int t = threadIdx.x & 63, i = t & 7, j = t >> 3;
+    const int32_t* up = A.up7 + b * 7;
+    const float* col[4];  // corner columns (dx, dy) = (c & 1, c >> 1): z = 0..7, then z = 8
+    const float* top[4];
+    bool lo_ok = true, hi_ok = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int x = i + (c & 1), y = j + (c >> 1);
+        const int code = (x >> 3) | ((y >> 3) << 1);
+        const int64_t nlo = code == 0 ? b : (int64_t)up[code - 1], nhi = up[code + 3];
+        const int off = (x & 7) + 8 * (y & 7);
+        lo_ok = lo_ok && nlo >= 0;
+        hi_ok = hi_ok && nhi >= 0;
+        col[c] = A.u + (nlo < 0 ? 0 : nlo) * TGV_BVOX + off;
+        top[c] = A.u + (nhi < 0 ? 0 : nhi) * TGV_BVOX + off;
+    }
+    hi_ok = hi_ok && lo_ok;
+    float v0[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v0[c] = lo_ok ? col[c][0] : 0.0f;
+    uint32_t* w = word + b * (TGV_BVOX / 32) + (j >> 2);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool ok = k < 7 ? lo_ok : hi_ok;
+        int in = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v1 = !ok ? 0.0f : (k < 7 ? col[c][64 * (k + 1)] : top[c][0]);
+            in |= ((v0[c] < 0.0f) << c) | ((v1 < 0.0f) << (c + 4));
+            v0[c] = v1;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, ok && in != 0 && in != 0xff);
+        if ((threadIdx.x & 31) == 0) w[2 * k] = m;
+    }
+}
+
+// cnt[w] = popcount(word[w]) for w < nw, cnt[nw] = 0 (the exclusive scan of cnt then
+// ranks the set bits)
+__global__ void mc_popc_kernel(const uint32_t* word, int64_t nw, uint32_t* cnt)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) cnt[w] = (uint32_t)__popc(word[w]);
+    else if (w == nw) cnt[w] = 0u;
+}
+
+__device__ __forceinline__ uint32_t bit_rank(const uint32_t* word, const uint32_t* prefix, uint64_t k)
+{
+    return prefix[k >> 5] + (uint32_t)__popc(word[k >> 5] & ((1u << (k & 31)) - 1u));
+}
+
+// cells[rank] = cell for every crossing cell, one thread per bit-set word
+__global__ void mc_compact_kernel(const uint32_t* word, const uint32_t* prefix, int64_t nw, uint32_t* cells)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    uint32_t m = word[w], r = prefix[w];
+    while (m) {
+        cells[r++] = (uint32_t)(32 * w) + (uint32_t)(__ffs(m) - 1);
+        m &= m - 1;
+    }
+}
+
+__device__ __forceinline__ void mark(uint32_t* bits, uint64_t id) { atomicOr(bits + (id >> 5), 1u << (id & 31)); }
+
 __global__ void mc_count_kernel(const MeshArgs A)
 {
-    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= A.nb * TGV_BVOX) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncross) return;
+    const uint32_t cell = A.cells[i];
     Cell C;
-    uint32_t nt = 0;
+    uint32_t nt = 0, head = 0;
+    uint64_t tri[3] = {0, 0, 0};
+    float cen[3] = {0.0f, 0.0f, 0.0f};
     if (load_cell(A, cell / TGV_BVOX, (int)(cell % TGV_BVOX), C)) {
         cell_topology(C);
         if (C.ncross > 0) {
-            float cen[3];
             bool used;
-            nt = (uint32_t)cell_triangles(A, C, cen, &used, [](int, int, int, int) {});
+            nt = (uint32_t)cell_triangles(A, C, cen, &used, [&](int n, int e0, int e1, int e2) {
+                if (n < 15) tri[n / 5] |= (uint64_t)(e0 | (e1 << 4) | (e2 << 8)) << (12 * (n % 5));
+            });
             for (int e = 0; e < 12; ++e)
-                if ((C.cross >> e) & 1) A.flags[vid(C, e)] = 1u;
-            if (used) A.flags[vid(C, 12)] = 1u;
+                if ((C.cross >> e) & 1) mark(A.vbits, vid(C, e));
+            if (used) mark(A.vbits, vid(C, 12));
+            head = (uint32_t)C.cross | ((uint32_t)used << 12) | (nt << 16);
         }
     }
-    A.tcount[cell] = nt;
+    MeshRec& R = A.rec[i];
+    for (int w = 0; w < 3; ++w) R.tri[w] = tri[w];
+    for (int q = 0; q < 3; ++q) R.centre[q] = cen[q];
+    R.head = head;
+    A.tcount[i] = nt;
 }
 
-// Triangles of every cell at its offset, and the positions of the vertices it
-// references: a crossing is written by each cell that has it (up to four), all
+// Triangles of every listed cell at its offset, and the positions of the vertices
+// it references: a crossing is written by each cell that has it (up to four), all
 // with the same value (the same two corner values and voxel coordinates).
 __global__ void mc_write_kernel(const MeshArgs A)
 {
-    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= A.nb * TGV_BVOX) return;
-    const uint32_t o = A.tcount[cell], o1 = A.tcount[cell + 1];
-    if (o1 == o) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncross) return;
+    const uint32_t o = A.tcount[i];
+    const MeshRec& R = A.rec[i];
+    const uint32_t head = R.head;
+    const int nt = (int)(head >> 16);
+    if (nt == 0) return;
+    const uint32_t cell = A.cells[i];
     Cell C;
     if (!load_cell(A, cell / TGV_BVOX, (int)(cell % TGV_BVOX), C)) return;
-    cell_topology(C);
-    float cen[3];
-    bool used;
+    C.cross = (int)(head & 0xfffu);
     int32_t* T = A.tris + 3 * (int64_t)o;
-    const uint32_t* F = A.flags;
-    cell_triangles(A, C, cen, &used, [&](int n, int e0, int e1, int e2) {
-        T[3 * n + 0] = (int32_t)F[vid(C, e0)];
-        T[3 * n + 1] = (int32_t)F[vid(C, e1)];
-        T[3 * n + 2] = (int32_t)F[vid(C, e2)];
-    });
-    if (used) {
-        float* P = A.verts + 3 * (int64_t)F[vid(C, 12)];
-        for (int q = 0; q < 3; ++q) P[q] = cen[q];
+    const uint32_t* B = A.vbits;
+    for (int n = 0; n < nt; ++n) {
+        const uint32_t code = (uint32_t)(R.tri[n / 5] >> (12 * (n % 5))) & 0xfffu;
+        for (int q = 0; q < 3; ++q) T[3 * n + q] = (int32_t)bit_rank(B, A.vrank, vid(C, (code >> (4 * q)) & 15u));
+    }
+    if ((head >> 12) & 1u) {
+        float* P = A.verts + 3 * (int64_t)bit_rank(B, A.vrank, vid(C, 12));
+        for (int q = 0; q < 3; ++q) P[q] = R.centre[q];
     }
     for (int e = 0; e < 12; ++e) {
         if (!((C.cross >> e) & 1)) continue;
         float P[3];
         crossing_point(A, C, e, P);
-        float* V = A.verts + 3 * (int64_t)F[vid(C, e)];
+        float* V = A.verts + 3 * (int64_t)bit_rank(B, A.vrank, vid(C, e));
         for (int q = 0; q < 3; ++q) V[q] = P[q];
     }
 }
@@ -482,8 +596,9 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
     }
     if (nids >= ((int64_t)1 << 32) - 1 || ncell >= ((int64_t)1 << 32) - 1)
         return tgv_fail(d, TGV_ERR_UNSUPPORTED, "level too large for 32-bit mesh indices");
-    if ((st = tgv_scratch(d, d->mesh_flags, sizeof(uint32_t) * (size_t)nids)) != TGV_OK) return st;
-    if ((st = tgv_scratch(d, d->mesh_count, sizeof(uint32_t) * (size_t)(ncell + 1))) != TGV_OK) return st;
+    const int64_t nwv = (nids + 31) / 32, nwc = (ncell + 31) / 32;  // bit-set words
+    if ((st = tgv_scratch(d, d->mesh_flags, sizeof(uint32_t) * (size_t)(2 * nwv + 1))) != TGV_OK) return st;
+    if ((st = tgv_scratch(d, d->mesh_count, sizeof(uint32_t) * (size_t)(2 * nwc + 1))) != TGV_OK) return st;
     MeshArgs A;
     A.u = L.u;
     A.coords = L.coords_dev;
@@ -491,26 +606,51 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
     A.nb = L.nb;
     for (int a = 0; a < 3; ++a) A.o[a] = (float)L.origin[a];
     A.h = (float)L.h;
-    A.flags = (uint32_t*)d->mesh_flags.ptr;
-    A.tcount = (uint32_t*)d->mesh_count.ptr;
-    cudaError_t e = cudaMemsetAsync(A.flags, 0, sizeof(uint32_t) * (size_t)nids, d->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(A.tcount + ncell, 0, sizeof(uint32_t), d->stream);
+    A.vbits = (uint32_t*)d->mesh_flags.ptr;
+    uint32_t* vcnt = A.vbits + nwv;
+    A.vrank = vcnt;
+    uint32_t* cword = (uint32_t*)d->mesh_count.ptr;
+    uint32_t* ccnt = cword + nwc;
+    cudaError_t e = cudaMemsetAsync(A.vbits, 0, sizeof(uint32_t) * (size_t)nwv, d->stream);
     if ((st = tgv_cuda_check(d, e, "mesh scratch clear")) != TGV_OK) return st;
-    const unsigned cgrid = (unsigned)((ncell + 127) / 128);
-    mc_count_kernel<<<cgrid, 128, 0, d->stream>>>(A);
+    mc_classify_kernel<<<(unsigned)((L.nb + 3) / 4), 256, 0, d->stream>>>(A, cword);
+    mc_popc_kernel<<<(unsigned)((nwc + 256) / 256), 256, 0, d->stream>>>(cword, nwc, ccnt);
+    d->launches += 2;
+    if ((st = tgv_cuda_check(d, cudaGetLastError(), "mc_classify_kernel launch")) != TGV_OK) return st;
+    uint64_t nc = 0, nv = 0, nt = 0;
+    if ((st = tgv_exclusive_scan_u32(d, ccnt, nwc + 1, d->mesh_scan, &nc)) != TGV_OK) return st;
+    // listed cells: cell ids, triangle counts (nc + 1), records (8-byte aligned)
+    const size_t rec_off = ((sizeof(uint32_t) * (2 * (size_t)nc + 1)) + 15) & ~(size_t)15;
+    if ((st = tgv_scratch(d, d->mesh_cells, rec_off + sizeof(MeshRec) * (size_t)std::max<uint64_t>(nc, 1))) != TGV_OK)
+        return st;
+    uint32_t* cells = (uint32_t*)d->mesh_cells.ptr;
+    A.cells = cells;
+    A.ncross = (int64_t)nc;
+    A.tcount = cells + nc;
+    A.rec = (MeshRec*)((char*)d->mesh_cells.ptr + rec_off);
+    const unsigned lgrid = (unsigned)((nc + 127) / 128);
+    if (nc > 0) {
+        mc_compact_kernel<<<(unsigned)((nwc + 255) / 256), 256, 0, d->stream>>>(cword, ccnt, nwc, cells);
+        mc_count_kernel<<<lgrid, 128, 0, d->stream>>>(A);
+        d->launches += 2;
+    }
+    mc_popc_kernel<<<(unsigned)((nwv + 256) / 256), 256, 0, d->stream>>>(A.vbits, nwv, vcnt);
     d->launches++;
-    if ((st = tgv_cuda_check(d, cudaGetLastError(), "mc_count_kernel launch")) != TGV_OK) return st;
-    uint64_t nv = 0, nt = 0;
-    if ((st = tgv_exclusive_scan_u32(d, A.flags, nids, d->mesh_scan, &nv)) != TGV_OK) return st;
-    if ((st = tgv_exclusive_scan_u32(d, A.tcount, ncell + 1, d->mesh_scan, &nt)) != TGV_OK) return st;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.tcount + nc, 0, sizeof(uint32_t), d->stream);
+    if ((st = tgv_cuda_check(d, e, "mc_count_kernel launch")) != TGV_OK) return st;
+    if ((st = tgv_exclusive_scan_u32(d, vcnt, nwv + 1, d->mesh_scan, &nv)) != TGV_OK) return st;
+    if ((st = tgv_exclusive_scan_u32(d, A.tcount, (int64_t)nc + 1, d->mesh_scan, &nt)) != TGV_OK) return st;
     if (nv >= ((uint64_t)1 << 31) || nt >= ((uint64_t)1 << 31))
         return tgv_fail(d, TGV_ERR_UNSUPPORTED, "mesh too large for 32-bit vertex indices");
     if ((st = tgv_scratch(d, d->mesh_v, sizeof(float) * 3 * (size_t)std::max<uint64_t>(nv, 1))) != TGV_OK) return st;
     if ((st = tgv_scratch(d, d->mesh_t, sizeof(int32_t) * 3 * (size_t)std::max<uint64_t>(nt, 1))) != TGV_OK) return st;
     A.verts = (float*)d->mesh_v.ptr;
     A.tris = (int32_t*)d->mesh_t.ptr;
-    mc_write_kernel<<<cgrid, 128, 0, d->stream>>>(A);
-    d->launches++;
+    if (nc > 0) {
+        mc_write_kernel<<<lgrid, 128, 0, d->stream>>>(A);
+        d->launches++;
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if ((st = tgv_cuda_check(d, e, "mc_write_kernel")) != TGV_OK) return st;

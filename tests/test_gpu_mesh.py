@@ -79,6 +79,25 @@ def test_ragged_domain_with_frozen_bricks_identical():
     assert len(T) > 5000
 
 
+def test_repeated_extraction_on_one_domain():
+    """The same domain meshed again after its field changes (more, then fewer crossing
+    cells, then none) gives each field's own mesh: the scratch sized by the previous
+    extraction is reused or regrown, never read stale."""
+    d = synth.DomainDesc(np.zeros(3), 1.0 / 32, synth.dense_bricks(4))
+    X, _ = centres(d)
+    rng = np.random.default_rng(3)
+    sphere = (np.linalg.norm(X - 0.5, axis=1) - 0.3).astype(np.float32)
+    noisy = (sphere + rng.uniform(-1, 1, len(X)) * 4.0 / 32).astype(np.float32)
+    small = (np.linalg.norm(X - 0.5, axis=1) - 0.1).astype(np.float32)
+    with tgv.Domain([d], nbins=8, stream=torch.cuda.current_stream().cuda_stream) as dom:
+        for u in (sphere, noisy, small, np.ones_like(sphere), sphere):
+            dom.set_field(0, "u", u.reshape(-1, 1))
+            V, T = dom.mesh(0)
+            Vo, To = oracle.mesh(d, u)
+            np.testing.assert_array_equal(V, Vo)
+            np.testing.assert_array_equal(T, To)
+
+
 def test_empty_and_state_errors():
     d = synth.DomainDesc(np.zeros(3), 1.0 / 16, synth.dense_bricks(2))
     with tgv.Domain([d], nbins=8, stream=torch.cuda.current_stream().cuda_stream) as dom:
