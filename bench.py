@@ -860,7 +860,8 @@ def run_octree(args):
 def run_composite(args):
     """Joint solve across levels on the composite grid (2:1 faces): the 5 octree levels built
     from the 64 terrain maps (depths 5..9, band 1), Alg. 1 histograms on every level, then
-    joint iterations (dual kernel + primal kernel per iteration over every leaf)."""
+    joint iterations (dual kernel + primal kernel per iteration over every leaf); the treetop
+    of the leaves (wall time of the library call)."""
     import torch
     import synth
     from paper_2107_14790_b300 import build, tgv
@@ -891,6 +892,20 @@ def run_composite(args):
     ms = float(np.median(times))
     n = comp.leaves
     per_level = [comp.level_leaves(l) for l in range(len(levels))]
+    # treetop (Sec. 4.3) of the leaf cubes: root = the octree root, voxel depth 9 + 3
+    # (wall time of tgv_composite_treetop, which synchronises; the parts copied afterwards)
+    import ctypes
+    treetop = {}
+    for N in (1 << 24, 1 << 20):
+        tt, nparts = [], ctypes.c_int64(0)
+        for _ in range(4):
+            t0 = time.perf_counter()
+            tgv._check(dom.handle, tgv.lib().tgv_composite_treetop(comp.handle, 12, N, ctypes.byref(nparts)))
+            tt.append(time.perf_counter() - t0)
+        dpt, _, first, last, _ = tgv.tgv_composite_treetop_parts(comp.handle, dom.handle, nparts.value)
+        treetop[f"N=2^{N.bit_length() - 1}"] = {"parts": int(len(dpt)), "ms": 1e3 * float(np.median(tt[1:])),
+                                                 "largest_part": int(np.max(last - first + 1)),
+                                                 "depths": sorted(set(int(x) for x in dpt))}
     comp.close()
     dom.close()
     bpl = 192  # state bytes per leaf-update (dual: read 13, write 9 floats; primal: read 13 + hist, write 8)
@@ -910,6 +925,7 @@ def run_composite(args):
             "config": {"workload": "terrain-octree-depths-5..9-composite-100it", "leaves": n,
                        "leaves_per_level": per_level},
             "ms_per_100_iterations": ms, "build_s": t_build,
+            "treetop": treetop,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "algorithmic_bytes_per_leaf": bpl,
                          "note": "state bytes only; regular leaves add 24 B of neighbour ids, leaves at 2:1 faces 192 B of lists"},

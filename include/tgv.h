@@ -353,6 +353,29 @@ TGV_API tgv_status tgv_composite_extract(tgv_composite* c, float* u_out, int64_t
  * tgv_extract_field / tgv_extract_mesh see the joint result.  Synchronises. */
 TGV_API tgv_status tgv_composite_scatter(tgv_composite* c);
 TGV_API int64_t tgv_composite_launch_count(const tgv_composite* c);
+
+/* Treetop of the composite grid (Sec. 4.3): the leaves are the octree's leaf
+ * cubes; in Z-order (Morton order of their lower corners) the leaves under any
+ * octree node are consecutive, and the treetop is the smallest rooted subtree
+ * whose leaf nodes each hold fewer than max_cubes leaf cubes.  The root is the
+ * cube [0, 2^root_bits)^3 in voxel units of the finest level (for levels from
+ * tgv_octree_build: root_bits = dmax + 3, and node depths are octree depths);
+ * a node of depth k is an aligned cube of 2^(root_bits - k) finest voxels per
+ * axis, with code = the top 3k bits of its cubes' Morton codes.  Nodes holding
+ * no leaf are not parts.  A part is a leaf node of the treetop: the leaves
+ * under it form the range [first, last] of the Z-ordered leaves (the paper's
+ * two indices per treetop leaf, the unit of independent work).  Writes the
+ * number of parts; parts come in Z-order.
+ * Errors: INVALID_ARG (root_bits outside 1..21, max_cubes < 2, a leaf with a
+ * negative coordinate or outside the root cube), UNSUPPORTED (3 root_bits +
+ * ceil(log2 leaves) > 64), OUT_OF_MEMORY, STATE, CUDA.  Synchronises. */
+TGV_API tgv_status tgv_composite_treetop(tgv_composite* c, int32_t root_bits, int64_t max_cubes, int64_t* nparts);
+/* Copies the last treetop: per part its depth, code, first and last Z-index
+ * (host arrays of nparts entries, each nullable), and per leaf (composite
+ * order) its part index (leaves int32, host or device, nullable).  STATE
+ * without a treetop.  Synchronises. */
+TGV_API tgv_status tgv_composite_treetop_parts(tgv_composite* c, int32_t* depth, uint64_t* code, int64_t* first,
+                                               int64_t* last, int32_t* leaf_part);
 TGV_API void tgv_composite_destroy(tgv_composite* c);
 
 /* ---------------------------------------------------------------------------

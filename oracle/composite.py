@@ -192,3 +192,84 @@ class Composite:
             lam = float(np.sqrt(np.sum(ku * ku) + np.sum(kv * kv)))
             u, v = ku, kv
         return lam
+
+
+def leaf_keys(level_bricks):
+    """(level, x, y, z) of every leaf in the composite order (level, brick, local voxel):
+    the voxels of level l whose children are not in an active brick of level l + 1."""
+    vox = [_voxels(b) for b in level_bricks]
+    keys = []
+    for l, v in enumerate(vox):
+        finer = set(map(tuple, vox[l + 1].tolist())) if l + 1 < len(vox) else set()
+        keys += [(l, *g) for g in v.tolist() if (2 * g[0], 2 * g[1], 2 * g[2]) not in finer]
+    return keys
+
+
+def morton_code(x, y, z, bits: int):
+    """Morton code of non-negative integer coordinates: bit b of x, y, z at bits 3b,
+    3b + 1, 3b + 2 (one bit at a time, plain integer arithmetic)."""
+    x, y, z = (np.asarray(a, np.uint64) for a in (x, y, z))
+    m = np.zeros(x.shape, np.uint64)
+    one = np.uint64(1)
+    for b in range(bits):
+        sb = np.uint64(b)
+        m |= ((x >> sb) & one) << np.uint64(3 * b)
+        m |= ((y >> sb) & one) << np.uint64(3 * b + 1)
+        m |= ((z >> sb) & one) << np.uint64(3 * b + 2)
+    return m
+
+
+def treetop(keys, nlev: int, root_bits: int, max_cubes: int):
+    """Treetop of the leaf cubes (Sec. 4.3): the smallest rooted subtree of the octree
+    whose leaf nodes each hold fewer than max_cubes cubes.
+
+    keys: (level, x, y, z) of every leaf (``Composite.keys``); a leaf of level l is
+    the cube of edge 2^(nlev-1-l) at (x, y, z) 2^(nlev-1-l) in finest voxel units.
+    The root is [0, 2^root_bits)^3; a node of depth k is an aligned cube of edge
+    2^(root_bits - k), its children numbered x + 2 y + 4 z by their half along
+    each axis, its code the child numbers from the root down (three bits each).
+    A node holds the cubes whose lower corner lies in it.  Nodes with no cube are
+    not parts.  Starting from the root, a node holding fewer than max_cubes cubes
+    is a part; any other node is split into its children.
+
+    Returns (depth, code, first, last, part): per part in Z-order (Morton order of
+    the lower corners), the range [first, last] of the Z-ordered cubes it holds, and
+    the part of every leaf (key order).  Raises ValueError when a cube lies outside
+    the root or a part's cubes are not consecutive in Z-order."""
+    k = np.asarray(keys, np.int64).reshape(-1, 4)
+    n = len(k)
+    size = np.left_shift(np.int64(1), (nlev - 1 - k[:, 0]))
+    corner = k[:, 1:] * size[:, None]
+    if n and (corner.min() < 0 or corner.max() >= (1 << root_bits)):
+        raise ValueError("a cube lies outside the root")
+    z = morton_code(corner[:, 0], corner[:, 1], corner[:, 2], root_bits)
+    order = np.argsort(z, kind="stable")
+    zpos = np.empty(n, np.int64)
+    zpos[order] = np.arange(n)
+    parts = []  # (depth, code, first, last)
+
+    def visit(depth, code, lo, members):
+        if len(members) == 0:
+            return
+        if len(members) < max_cubes:
+            pos = np.sort(zpos[members])
+            if pos[-1] - pos[0] + 1 != len(pos):
+                raise ValueError("a part's cubes are not consecutive in Z-order")
+            parts.append((depth, code, int(pos[0]), int(pos[-1])))
+            return
+        half = 1 << (root_bits - depth - 1)
+        for ch in range(8):
+            clo = lo + half * np.array([ch & 1, (ch >> 1) & 1, ch >> 2], np.int64)
+            c = corner[members]
+            inside = np.all((c >= clo) & (c < clo + half), axis=1)
+            visit(depth + 1, code * 8 + ch, clo, members[inside])
+
+    visit(0, 0, np.zeros(3, np.int64), np.arange(n))
+    depth = np.array([p[0] for p in parts], np.int32)
+    code = np.array([p[1] for p in parts], np.uint64)
+    first = np.array([p[2] for p in parts], np.int64)
+    last = np.array([p[3] for p in parts], np.int64)
+    part = np.full(n, -1, np.int32)
+    for j, (f, l) in enumerate(zip(first, last)):
+        part[order[f:l + 1]] = j
+    return depth, code, first, last, part

@@ -19,6 +19,11 @@
 // neighbour ids; leaves at 2:1 faces carry the full lists.  One iteration = a dual kernel (p, q from ubar, vbar and the neighbour
 // lists) and a primal kernel (divergences through the reverse lists, prox,
 // clamp, v update, over-relaxation), one thread per leaf.
+//
+// Treetop (Sec. 4.3): the leaves are the octree's leaf cubes.  In Z-order (Morton
+// order of the lower corners, in finest voxel units) the cubes under a node are
+// consecutive; the treetop keeps splitting, from the root down, every node that
+// holds N or more cubes, and its leaf nodes (parts) each hold fewer than N.
 #include <math.h>
 
 #include <algorithm>
@@ -26,6 +31,7 @@
 #include <vector>
 
 #include "tgv_internal.cuh"
+#include "tgv_zorder.cuh"
 
 struct tgv_composite {
     tgv_domain* d = nullptr;
@@ -38,6 +44,11 @@ struct tgv_composite {
     int32_t* lists = nullptr;                     // [irregular][4 kinds][3 axes][4]: fwd, bwd, rev fwd, rev bwd
     int64_t nirr = 0;
     int64_t launches = 0;
+    // treetop of the last tgv_composite_treetop call (Sec. 4.3)
+    std::vector<int32_t> tt_depth;
+    std::vector<uint64_t> tt_code;
+    std::vector<int64_t> tt_first, tt_last;
+    int32_t* tt_part = nullptr;                   // [n]: treetop part of each leaf
 };
 
 namespace {
@@ -508,8 +519,77 @@ unsigned grid_of(int64_t n, int sms) { return (unsigned)std::max<int64_t>(1, std
 void free_comp(tgv_composite* c)
 {
     for (void* p : {(void*)c->u, (void*)c->ubar, (void*)c->v, (void*)c->vbar, (void*)c->p, (void*)c->q, (void*)c->hist,
-                    (void*)c->lists, (void*)c->nb6, (void*)c->slot})
+                    (void*)c->lists, (void*)c->nb6, (void*)c->slot, (void*)c->tt_part})
         if (p) cudaFree(p);
+}
+
+// ---- treetop (Sec. 4.3): the leaves in Z-order, split into the subtrees of the
+// shallowest nodes that hold fewer than N of them
+
+struct TTKeyArgs {
+    const int32_t* slot;
+    const int32_t* coords[32];
+    int64_t lfirst[33];
+    int nlev, root_bits, ib;
+    int64_t n;
+    uint64_t* keys;
+    unsigned int* err;
+};
+
+// key of leaf i: Morton code of its lower corner in finest-level voxel units, above
+// the leaf index (ib bits)
+__global__ void tt_key_kernel(const TTKeyArgs A)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < A.nlev && i >= A.lfirst[l + 1]) ++l;
+        const int32_t sl = A.slot[i];
+        const int32_t* cb = A.coords[l] + 3 * (int64_t)(sl >> 9);
+        const int loc = sl & 511, sh = A.nlev - 1 - l;
+        const int64_t g[3] = {8 * (int64_t)cb[0] + (loc & 7), 8 * (int64_t)cb[1] + ((loc >> 3) & 7),
+                              8 * (int64_t)cb[2] + (loc >> 6)};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && g[a] >= 0 && ((g[a] << sh) >> A.root_bits) == 0;
+        if (!ok) {
+            atomicOr(A.err, 1u);
+            A.keys[i] = 0;
+            continue;
+        }
+        A.keys[i] = (morton3((uint64_t)g[0] << sh, (uint64_t)g[1] << sh, (uint64_t)g[2] << sh) << A.ib) | (uint64_t)i;
+    }
+}
+
+// first position in [lo, hi) of the sorted keys at or after child c of node k
+// (children at depth d + 1: code (node << 3) | c, `shift` = 3 (root_bits - d - 1) + ib)
+__global__ void tt_split_kernel(const uint64_t* keys, int shift, const uint64_t* code, const int64_t* lo,
+                                const int64_t* hi, int64_t nnodes, int64_t* lb)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * nnodes) return;
+    const int64_t k = t >> 3;
+    const uint64_t target = (code[k] << 3) | (uint64_t)(t & 7);
+    int64_t a = lo[k], b = hi[k];
+    while (a < b) {
+        const int64_t m = a + ((b - a) >> 1);
+        if ((keys[m] >> shift) < target) a = m + 1;
+        else b = m;
+    }
+    lb[t] = a;
+}
+
+// part[leaf] = the part whose Z-range holds the leaf's position
+__global__ void tt_part_kernel(const uint64_t* keys, int64_t n, uint64_t idx_mask, const int64_t* first, int64_t nparts,
+                               int32_t* part)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, b = nparts;  // first index with first[.] > i, minus one
+        while (a < b) {
+            const int64_t m = a + ((b - a) >> 1);
+            if (first[m] <= i) a = m + 1;
+            else b = m;
+        }
+        part[keys[i] & idx_mask] = (int32_t)(a - 1);
+    }
 }
 
 }  // namespace
@@ -783,6 +863,179 @@ tgv_status tgv_composite_scatter(tgv_composite* c)
 }
 
 int64_t tgv_composite_launch_count(const tgv_composite* c) { return c ? c->launches : 0; }
+
+tgv_status tgv_composite_treetop(tgv_composite* c, int32_t root_bits, int64_t max_cubes, int64_t* nparts)
+{
+    if (nparts) *nparts = 0;
+    if (!c || !nparts || root_bits < 1 || root_bits > 21 || max_cubes < 2) return TGV_ERR_INVALID_ARG;
+    tgv_domain* d = c->d;
+    if (d->broken) return TGV_ERR_STATE;
+    const int nlev = (int)c->level_first.size() - 1;
+    const int64_t n = c->n;
+    int ib = 1;
+    while (((int64_t)1 << ib) < n) ++ib;
+    if (3 * root_bits + ib > 64) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "treetop keys exceed 64 bits");
+    c->tt_depth.clear();
+    c->tt_code.clear();
+    c->tt_first.clear();
+    c->tt_last.clear();
+    if (c->tt_part) cudaFree(c->tt_part);
+    c->tt_part = nullptr;
+    cudaStream_t st = d->stream;
+    struct Buf {
+        void* p = nullptr;
+        ~Buf()
+        {
+            if (p) cudaFree(p);
+        }
+    } keys, tmp, hist, err, nodes, lbuf;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        return true;
+    };
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    if (!alloc(&keys.p, nn * 8) || !alloc(&tmp.p, nn * 8) ||
+        !alloc(&hist.p, (size_t)tgv_radix_hist_words(n) * 4) || !alloc(&err.p, 16))
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "treetop allocation failed");
+    if (n == 0) {
+        if (!alloc((void**)&c->tt_part, 16)) return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "treetop allocation failed");
+        return TGV_OK;
+    }
+    TTKeyArgs K;
+    K.slot = c->slot;
+    for (int l = 0; l < nlev; ++l) {
+        K.coords[l] = d->levels[l].coords_dev;
+        K.lfirst[l] = c->level_first[l];
+    }
+    K.lfirst[nlev] = n;
+    K.nlev = nlev;
+    K.root_bits = root_bits;
+    K.ib = ib;
+    K.n = n;
+    K.keys = (uint64_t*)keys.p;
+    K.err = (unsigned int*)err.p;
+    cudaError_t e = cudaMemsetAsync(err.p, 0, 16, st);
+    if (e == cudaSuccess) {
+        tt_key_kernel<<<grid_of(n, d->sm_count), 256, 0, st>>>(K);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    unsigned int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "treetop keys");
+    if (herr) return tgv_fail(d, TGV_ERR_INVALID_ARG, "treetop: a leaf lies outside the root cube");
+    // Z-order: the Morton digits only (the sort is stable and the keys come in index order)
+    e = tgv_radix_sort_u64((uint64_t*)keys.p, (uint64_t*)tmp.p, (uint32_t*)hist.p, n, ib, 3 * root_bits, st,
+                           &c->launches);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "treetop sort");
+    auto emit = [&](int32_t depth, uint64_t code, int64_t lo, int64_t hi) {
+        c->tt_depth.push_back(depth);
+        c->tt_code.push_back(code);
+        c->tt_first.push_back(lo);
+        c->tt_last.push_back(hi - 1);
+    };
+    // top-down: the children of every node holding >= max_cubes leaves, by binary search
+    std::vector<uint64_t> fcode{0};
+    std::vector<int64_t> flo{0}, fhi{n};
+    if (n < max_cubes) {
+        emit(0, 0, 0, n);
+        fcode.clear();
+    }
+    for (int depth = 0; !fcode.empty(); ++depth) {
+        const int64_t nf = (int64_t)fcode.size();
+        if (depth >= root_bits) return tgv_fail(d, TGV_ERR_STATE, "treetop: a finest-level node holds several leaves");
+        if (nodes.p) cudaFree(nodes.p);
+        if (lbuf.p) cudaFree(lbuf.p);
+        nodes.p = lbuf.p = nullptr;
+        if (!alloc(&nodes.p, (size_t)nf * 24) || !alloc(&lbuf.p, (size_t)nf * 64))
+            return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "treetop allocation failed");
+        uint64_t* dcode = (uint64_t*)nodes.p;
+        int64_t* dlo = (int64_t*)(dcode + nf);
+        int64_t* dhi = dlo + nf;
+        std::vector<int64_t> lb((size_t)(8 * nf));
+        e = cudaMemcpyAsync(dcode, fcode.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dlo, flo.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dhi, fhi.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            tt_split_kernel<<<(unsigned)((8 * nf + 255) / 256), 256, 0, st>>>(
+                (const uint64_t*)keys.p, 3 * (root_bits - depth - 1) + ib, dcode, dlo, dhi, nf, (int64_t*)lbuf.p);
+            c->launches++;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lb.data(), lbuf.p, (size_t)nf * 64, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return tgv_cuda_check(d, e, "treetop split");
+        std::vector<uint64_t> ncode;
+        std::vector<int64_t> nlo, nhi;
+        for (int64_t k = 0; k < nf; ++k)
+            for (int ch = 0; ch < 8; ++ch) {
+                const int64_t a = lb[(size_t)(8 * k + ch)], b = ch < 7 ? lb[(size_t)(8 * k + ch + 1)] : fhi[(size_t)k];
+                if (b <= a) continue;
+                const uint64_t cc = (fcode[(size_t)k] << 3) | (uint64_t)ch;
+                if (b - a < max_cubes) {
+                    emit(depth + 1, cc, a, b);
+                } else {
+                    ncode.push_back(cc);
+                    nlo.push_back(a);
+                    nhi.push_back(b);
+                }
+            }
+        fcode.swap(ncode);
+        flo.swap(nlo);
+        fhi.swap(nhi);
+    }
+    // parts in Z-order (their ranges are disjoint), then each leaf's part
+    const size_t np = c->tt_first.size();
+    std::vector<size_t> ord(np);
+    for (size_t k = 0; k < np; ++k) ord[k] = k;
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return c->tt_first[a] < c->tt_first[b]; });
+    auto permute = [&](auto& v) {
+        auto w = v;
+        for (size_t k = 0; k < np; ++k) w[k] = v[ord[k]];
+        v.swap(w);
+    };
+    permute(c->tt_depth);
+    permute(c->tt_code);
+    permute(c->tt_first);
+    permute(c->tt_last);
+    if (nodes.p) cudaFree(nodes.p);
+    nodes.p = nullptr;
+    if (!alloc(&nodes.p, np * 8) || !alloc((void**)&c->tt_part, nn * 4))
+        return tgv_fail(d, TGV_ERR_OUT_OF_MEMORY, "treetop allocation failed");
+    e = cudaMemcpyAsync(nodes.p, c->tt_first.data(), np * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        tt_part_kernel<<<grid_of(n, d->sm_count), 256, 0, st>>>((const uint64_t*)keys.p, n,
+                                                                 ((uint64_t)1 << ib) - 1, (const int64_t*)nodes.p,
+                                                                 (int64_t)np, c->tt_part);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return tgv_cuda_check(d, e, "treetop parts");
+    *nparts = (int64_t)np;
+    return TGV_OK;
+}
+
+tgv_status tgv_composite_treetop_parts(tgv_composite* c, int32_t* depth, uint64_t* code, int64_t* first,
+                                       int64_t* last, int32_t* leaf_part)
+{
+    if (!c) return TGV_ERR_INVALID_ARG;
+    if (!c->tt_part) return TGV_ERR_STATE;
+    if (depth) std::copy(c->tt_depth.begin(), c->tt_depth.end(), depth);
+    if (code) std::copy(c->tt_code.begin(), c->tt_code.end(), code);
+    if (first) std::copy(c->tt_first.begin(), c->tt_first.end(), first);
+    if (last) std::copy(c->tt_last.begin(), c->tt_last.end(), last);
+    if (!leaf_part || c->n == 0) return TGV_OK;
+    tgv_domain* d = c->d;
+    cudaError_t e = cudaMemcpyAsync(leaf_part, c->tt_part, (size_t)c->n * 4, cudaMemcpyDefault, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    return tgv_cuda_check(d, e, "treetop parts copy");
+}
 
 void tgv_composite_destroy(tgv_composite* c)
 {

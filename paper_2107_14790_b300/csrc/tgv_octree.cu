@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "tgv_internal.cuh"
+#include "tgv_zorder.cuh"
 
 struct tgv_octree {
     struct Level {
@@ -42,34 +43,6 @@ namespace {
 
 constexpr uint64_t kEmpty = ~(uint64_t)0;
 constexpr int kMaxProbe = 4096;
-
-__host__ __device__ __forceinline__ uint64_t spread3(uint64_t v)
-{
-    // bits 0..20 of v to every third bit
-    v &= 0x1fffffull;
-    v = (v | (v << 32)) & 0x1f00000000ffffull;
-    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
-    v = (v | (v << 8)) & 0x100f00f00f00f00full;
-    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-    v = (v | (v << 2)) & 0x1249249249249249ull;
-    return v;
-}
-
-__host__ __device__ __forceinline__ uint64_t morton3(uint64_t x, uint64_t y, uint64_t z)
-{
-    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
-}
-
-__host__ __device__ __forceinline__ uint64_t compact3(uint64_t v)
-{
-    v &= 0x1249249249249249ull;
-    v = (v | (v >> 2)) & 0x10c30c30c30c30c3ull;
-    v = (v | (v >> 4)) & 0x100f00f00f00f00full;
-    v = (v | (v >> 8)) & 0x1f0000ff0000ffull;
-    v = (v | (v >> 16)) & 0x1f00000000ffffull;
-    v = (v | (v >> 32)) & 0x1fffffull;
-    return v;
-}
 
 // splitmix64 finaliser (Steele, Lea, Flood 2014) as the hash of a key
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
@@ -284,12 +257,12 @@ __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint64_t* key
     hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = s[threadIdx.x];
 }
 
-// exclusive prefix sum of m counts in place, one block of 1024 threads
-__global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t* a, int64_t m)
+// exclusive prefix sum of m counts in place, by one block of 1024 threads, starting
+// from `carry`
+__device__ void block_exclusive_scan(uint32_t* a, int64_t m, uint32_t carry)
 {
     __shared__ uint32_t wsum[32];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    uint32_t carry = 0;
     for (int64_t base = 0; base < m; base += 1024) {
         const int64_t i = base + t;
         const uint32_t v = i < m ? a[i] : 0u;
@@ -315,6 +288,36 @@ __global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t* a, int64_t m)
         carry += wsum[31];
         __syncthreads();  // wsum is rewritten by the next chunk
     }
+}
+
+__global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t* a, int64_t m) { block_exclusive_scan(a, m, 0u); }
+
+// Larger count arrays: segments of kRsSeg counts, one block each -- the segment sums,
+// their scan (one block), then each segment's scan from its prefix.
+constexpr int64_t kRsSeg = 8192;
+
+__global__ void __launch_bounds__(1024) rs_seg_sum_kernel(const uint32_t* a, int64_t m, uint32_t* sums)
+{
+    __shared__ uint32_t wsum[32];
+    const int64_t base = (int64_t)blockIdx.x * kRsSeg;
+    uint32_t x = 0;
+    for (int64_t i = base + threadIdx.x; i < base + kRsSeg && i < m; i += 1024) x += a[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        x = wsum[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = x;
+    }
+}
+
+__global__ void __launch_bounds__(1024) rs_seg_scan_kernel(uint32_t* a, int64_t m, const uint32_t* sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kRsSeg;
+    block_exclusive_scan(a + base, m - base < kRsSeg ? m - base : kRsSeg, sums[blockIdx.x]);
 }
 
 // each tile's keys to their slots: the tile's first slot of the digit plus the key's
@@ -353,18 +356,31 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter_kernel(const uint64_t* 
     }
 }
 
+int64_t radix_hist_words(int64_t n)
+{
+    const int64_t m = 256 * std::max<int64_t>((n + kRsTile - 1) / kRsTile, 1);
+    return m + (m + kRsSeg - 1) / kRsSeg + 1;
+}
+
 // sorts n keys by the 8-bit digits at `shifts` (least significant first); `tmp`
-// holds n keys, `hist` 256 * ceil(n / 1024) counts
+// holds n keys, `hist` radix_hist_words(n) counts; adds its launches to *launches
 cudaError_t radix_sort(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, const std::vector<int>& shifts,
-                       cudaStream_t s)
+                       cudaStream_t s, int64_t* launches = nullptr)
 {
     if (n <= 1) return cudaSuccess;
-    const int64_t tiles = (n + kRsTile - 1) / kRsTile;
+    const int64_t tiles = (n + kRsTile - 1) / kRsTile, m = 256 * tiles, segs = (m + kRsSeg - 1) / kRsSeg;
     uint64_t *a = keys, *b = tmp;
     for (int sh : shifts) {
         rs_hist_kernel<<<(unsigned)tiles, kRsThreads, 0, s>>>(a, n, sh, hist, tiles);
-        rs_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
+        if (segs == 1) {
+            rs_scan_kernel<<<1, 1024, 0, s>>>(hist, m);
+        } else {
+            rs_seg_sum_kernel<<<(unsigned)segs, 1024, 0, s>>>(hist, m, hist + m);
+            rs_scan_kernel<<<1, 1024, 0, s>>>(hist + m, segs);
+            rs_seg_scan_kernel<<<(unsigned)segs, 1024, 0, s>>>(hist, m, hist + m);
+        }
         rs_scatter_kernel<<<(unsigned)tiles, kRsThreads, 0, s>>>(a, b, n, sh, hist, tiles);
+        if (launches) *launches += segs == 1 ? 3 : 5;
         std::swap(a, b);
     }
     if (a != keys) return cudaMemcpyAsync(keys, a, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
@@ -391,6 +407,16 @@ struct DevBuf {
 };
 
 }  // namespace
+
+cudaError_t tgv_radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, int lo_bit, int nbits,
+                               cudaStream_t s, int64_t* launches)
+{
+    std::vector<int> shifts;
+    for (int b = 0; b < nbits; b += 8) shifts.push_back(lo_bit + b);
+    return radix_sort(keys, tmp, hist, n, shifts, s, launches);
+}
+
+int64_t tgv_radix_hist_words(int64_t n) { return radix_hist_words(n); }
 
 extern "C" {
 
@@ -529,7 +555,7 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
         if (cudaMalloc(&act.p, kb) != cudaSuccess || cudaMalloc(&frz.p, kb) != cudaSuccess ||
             cudaMalloc(&lst.p, kb) != cudaSuccess || cudaMalloc(&lst2.p, kb) != cudaSuccess ||
             cudaMalloc(&tmp.p, kb) != cudaSuccess ||
-            cudaMalloc(&hist.p, sizeof(uint32_t) * 256 * (cap2 / kRsTile + 1)) != cudaSuccess) {
+            cudaMalloc(&hist.p, sizeof(uint32_t) * (size_t)radix_hist_words(cap2)) != cudaSuccess) {
             cudaGetLastError();
             return TGV_ERR_OUT_OF_MEMORY;
         }

@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "tgv_composite_extract": (i32, [P, P, i64]),
         "tgv_composite_scatter": (i32, [P]),
         "tgv_composite_launch_count": (i64, [P]),
+        "tgv_composite_treetop": (i32, [P, i32, i64, P]),
+        "tgv_composite_treetop_parts": (i32, [P, P, P, P, P, P]),
         "tgv_composite_destroy": (None, [P]),
         "tgv_octree_levels": (i32, [P]),
         "tgv_octree_samples": (i64, [P]),
@@ -391,6 +393,26 @@ def tgv_composite_launch_count(c) -> int:
     return int(lib().tgv_composite_launch_count(c))
 
 
+def tgv_composite_treetop(c, d, root_bits: int, max_cubes: int):
+    """Treetop parts (Sec. 4.3): (depth, code, first, last) per part in Z-order and the
+    part of every leaf (composite order)."""
+    n = ctypes.c_int64(0)
+    _check(d, lib().tgv_composite_treetop(c, int(root_bits), int(max_cubes), ctypes.byref(n)))
+    return tgv_composite_treetop_parts(c, d, n.value)
+
+
+def tgv_composite_treetop_parts(c, d, k: int):
+    """The last treetop's k parts and the part of every leaf."""
+    depth = np.zeros(k, np.int32)
+    code = np.zeros(k, np.uint64)
+    first = np.zeros(k, np.int64)
+    last = np.zeros(k, np.int64)
+    part = np.zeros(tgv_composite_leaves(c), np.int32)
+    _check(d, lib().tgv_composite_treetop_parts(c, depth.ctypes.data, code.ctypes.data, first.ctypes.data,
+                                                last.ctypes.data, part.ctypes.data))
+    return depth, code, first, last, part
+
+
 def tgv_composite_destroy(c):
     lib().tgv_composite_destroy(c)
 
@@ -417,6 +439,9 @@ class Composite:
 
     def scatter(self):
         tgv_composite_scatter(self.handle, self.dom.handle)
+
+    def treetop(self, root_bits, max_cubes):
+        return tgv_composite_treetop(self.handle, self.dom.handle, root_bits, max_cubes)
 
     @property
     def launches(self):

@@ -8,6 +8,8 @@ import torch
 import oracle
 import synth
 from oracle.composite import Composite as OracleComposite
+from oracle.composite import leaf_keys as oracle_leaf_keys
+from oracle.composite import treetop as oracle_treetop
 from paper_2107_14790_b300 import tgv
 
 pytestmark = pytest.mark.gpu
@@ -120,3 +122,57 @@ def test_frozen_bricks_of_the_levels_are_ignored(sphere_scene):
                 comp.solve(15)
                 outs.append(comp.u())
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# ---- treetop (Sec. 4.3) against the oracle's recursive definition
+
+def gpu_treetops(levels, root_bits, Ns):
+    with tgv.Domain(levels, nbins=8, stream=stream()) as dom:
+        with tgv.Composite(dom) as comp:
+            return [comp.treetop(root_bits, N) for N in Ns]
+
+
+def same_treetop(got, want):
+    for g, w, name in zip(got, want, ("depth", "code", "first", "last", "part")):
+        np.testing.assert_array_equal(g, w, err_msg=name)
+
+
+def test_treetop_two_levels_by_hand():
+    levels = [synth.DomainDesc(np.zeros(3), 1.0 / 16, np.array([[0, 0, 0]], np.int32)),
+              synth.DomainDesc(np.zeros(3), 1.0 / 32, np.array([[0, 0, 0]], np.int32))]
+    keys = oracle_leaf_keys([L.bricks for L in levels])
+    Ns = [600, 100, 961, 2]
+    for N, got in zip(Ns, gpu_treetops(levels, 4, Ns)):
+        same_treetop(got, oracle_treetop(keys, 2, 4, N))
+    assert len(gpu_treetops(levels, 4, [100])[0][0]) == 15
+
+
+def test_treetop_of_the_sphere_octree(sphere_scene):
+    """Three octree levels (depths 5..7 of the root cube, voxel depth 10): parts of many
+    sizes, from single cubes to the whole root."""
+    sc = sphere_scene
+    dep = torch.from_numpy(np.stack(sc.depths)).cuda()
+    lv, _ = tgv.tgv_octree_build(sc.cameras, dep, np.array([-0.5, -0.5, -0.5]), 2.0, 5, 7, 1, stream=stream())
+    levels = [synth.DomainDesc(L.origin, L.h, L.bricks) for L in lv]
+    keys = oracle_leaf_keys([L.bricks for L in levels])
+    assert len(keys) > 100_000
+    Ns = [2, 37, 4096, 1 << 17, 1 << 30]
+    for N, got in zip(Ns, gpu_treetops(levels, 10, Ns)):
+        same_treetop(got, oracle_treetop(keys, 3, 10, N))
+
+
+def test_treetop_argument_errors():
+    inside = [synth.DomainDesc(np.zeros(3), 1.0 / 16, np.array([[0, 0, 0]], np.int32))]
+    with tgv.Domain(inside, nbins=8, stream=stream()) as dom:
+        with tgv.Composite(dom) as comp:
+            assert tgv.lib().tgv_composite_treetop_parts(comp.handle, None, None, None, None, None) == 6  # STATE
+            for root_bits, N in ((3, 1), (0, 10), (22, 10), (2, 10)):  # N < 2, bits out of range, cube outside
+                with pytest.raises(tgv.TgvError):
+                    comp.treetop(root_bits, N)
+            d, c, f, l, p = comp.treetop(3, 10 ** 9)
+            assert list(d) == [0] and list(f) == [0] and list(l) == [511] and np.all(p == 0)
+    negative = [synth.DomainDesc(np.zeros(3), 1.0 / 16, np.array([[-1, 0, 0]], np.int32))]
+    with tgv.Domain(negative, nbins=8, stream=stream()) as dom:
+        with tgv.Composite(dom) as comp:
+            with pytest.raises(tgv.TgvError):
+                comp.treetop(10, 100)
