@@ -98,6 +98,39 @@ def test_repeated_extraction_on_one_domain():
             np.testing.assert_array_equal(T, To)
 
 
+def test_chunks_with_frozen_halos_mesh_without_seams():
+    """A domain cut into two chunks along x, each seeing the other's border bricks as
+    frozen bricks with their u: the two meshes together are the whole domain's mesh,
+    triangle for triangle with bit-identical coordinates, and no triangle is made twice
+    (a cell belongs to the chunk of its lower corner)."""
+    rng = np.random.default_rng(21)
+    full = synth.DomainDesc(np.zeros(3), 1.0 / 32, synth.dense_bricks(4))
+    def field(X):
+        return (np.linalg.norm(X - 0.5, axis=1) - 0.3 + rng.uniform(-1, 1, len(X)) * 1.5 / 32).astype(np.float32)
+    X, g = centres(full)
+    u_full = field(X)
+    lookup = {tuple(v): u_full[i] for i, v in enumerate(g.tolist())}
+    def chunk(active, frozen):
+        d0 = synth.DomainDesc(full.origin, full.h, active, frozen=frozen)
+        _, gf = centres(d0, frozen=True)
+        fu = np.array([lookup[tuple(v)] for v in gf.tolist()], np.float32).reshape(-1, 512)
+        d = synth.DomainDesc(full.origin, full.h, active, frozen=frozen, frozen_u=fu)
+        _, ga = centres(d)
+        ua = np.array([lookup[tuple(v)] for v in ga.tolist()], np.float32)
+        return gpu_mesh(d, ua)
+    def triangles(V, T):
+        return {V[t].tobytes() for t in T}
+    b = full.bricks
+    lo, hi = b[b[:, 0] < 2], b[b[:, 0] >= 2]
+    tri_a = triangles(*chunk(lo, b[b[:, 0] == 2]))
+    tri_b = triangles(*chunk(hi, np.zeros((0, 3), np.int32)))
+    V, T = gpu_mesh(full, u_full)
+    whole = triangles(V, T)
+    assert len(whole) == len(T) and len(T) > 1000
+    assert not (tri_a & tri_b)
+    assert tri_a | tri_b == whole
+
+
 def test_empty_and_state_errors():
     d = synth.DomainDesc(np.zeros(3), 1.0 / 16, synth.dense_bricks(2))
     with tgv.Domain([d], nbins=8, stream=torch.cuda.current_stream().cuda_stream) as dom:
