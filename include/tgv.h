@@ -380,9 +380,14 @@ TGV_API void tgv_composite_destroy(tgv_composite* c);
 
 /* ---------------------------------------------------------------------------
  * Brick domains from depth maps (Sec. 3.3 Eq. 4, Sec. 4.1-4.2; in memory, one
- * GPU).  Every valid pixel of a pinhole map is a sample: its z-depth
- * unprojected to X, radius r = half the mean distance to the points of its
- * valid 4-neighbours (left, right, up, down).  Eq. 4 puts it in the cube of
+ * GPU).  Every valid pixel is a sample: a pinhole map's z-depth, or a
+ * spherical map's range along the pixel's direction (azimuth phi =
+ * (i + 0.5 - cx) / fx, elevation theta = (cy - (j + 0.5)) / fy; direction
+ * (cos theta cos phi, cos theta sin phi, sin theta) in the scanner's axes, with
+ * sin and cos evaluated in FP32 by the library's own reduction by pi/2 and
+ * Taylor polynomials, |error| < 1.2e-7), unprojected to X; radius r = half the
+ * mean distance to the points of its valid 4-neighbours (left, right, up, down;
+ * a scan's azimuth seam is not crossed).  Eq. 4 puts it in the cube of
  * depth d with 0.75 r <= r_root 2^-d < 1.5 r (r_root = root_edge / 2): the
  * smallest d in [depth_min, depth_max] with r_root 2^-d < 1.5 r (depth_max if
  * none), cube q = floor(((X - root_min) / root_edge) 2^d), samples outside the
@@ -406,11 +411,11 @@ typedef struct {
 
 typedef struct tgv_octree tgv_octree; /* opaque, library-owned (host memory) */
 
-/* Builds the levels from nmaps pinhole maps of one size (map m at depth_dev +
- * m * map_stride_elems, rows of pitch_elems floats, device memory; cams on the
- * host) on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (a spherical map),
- * OUT_OF_MEMORY, BUDGET (the device hash set could not hold the bricks),
- * CUDA.  Synchronises the stream. */
+/* Builds the levels from nmaps maps of one size, pinhole or spherical (map m at
+ * depth_dev + m * map_stride_elems, rows of pitch_elems floats, device memory;
+ * cams on the host) on `stream`.  Errors: INVALID_ARG (also an unknown camera
+ * model), OUT_OF_MEMORY, BUDGET (the device hash set could not hold the
+ * bricks), CUDA.  Synchronises the stream. */
 TGV_API tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, int32_t nmaps,
                                     const float* depth_dev, int64_t pitch_elems, int64_t map_stride_elems,
                                     void* stream, tgv_octree** out);

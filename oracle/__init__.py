@@ -65,6 +65,7 @@ def lib():
             "orc_mesh": (i64, [i64, P, i64, P, P, P, f64, P, P, P]),
             "orc_mc_triangulate": (i32, [i32, P, P, P]),
             "orc_octree_samples": (i64, [P, i32, i32, P, P, f64, i32, i32, P, P, P]),
+            "orc_sincos_tay_many": (None, [P, i64, P, P]),
             "orc_octree_build": (i64, [i32, P, i32, i32, P, P, f64, i32, i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -144,8 +145,19 @@ def triangulate_min_area(P: np.ndarray) -> np.ndarray:
     return out[:n]
 
 
+def sincos_tay(x) -> tuple:
+    """(sin x, cos x) in FP32 by the oracle's own reduction and Taylor polynomials
+    (the spherical unprojection of the octree build), |x| <= 4."""
+    x = _c(np.atleast_1d(x), np.float32)
+    s = np.empty_like(x)
+    c = np.empty_like(x)
+    lib().orc_sincos_tay_many(_p(x), x.size, _p(s), _p(c))
+    return s, c
+
+
 def octree_samples(cam, depth: np.ndarray, root_min, root_edge: float, dmin: int, dmax: int):
-    """Per pixel of one pinhole map: (depth d or -1, cube coords (H, W, 3), radius r)."""
+    """Per pixel of one map (pinhole or spherical): (depth d or -1, cube coords (H, W, 3),
+    radius r)."""
     d = _c(depth, np.float32)
     H, W = d.shape
     dd = np.empty((H, W), np.int32)
@@ -157,7 +169,7 @@ def octree_samples(cam, depth: np.ndarray, root_min, root_edge: float, dmin: int
 
 
 def octree_build(cams, depths, root_min, root_edge: float, dmin: int, dmax: int, band: int = 1):
-    """Brick domain from pinhole depth maps (Eq. 4, Sec. 4.1-4.2): per level (active, frozen)
+    """Brick domain from depth maps (pinhole or spherical; Eq. 4, Sec. 4.1-4.2): per level (active, frozen)
     brick coordinate arrays in Morton order, and the sample count."""
     dep = _c(np.stack(depths), np.float32)
     nm, H, W = dep.shape

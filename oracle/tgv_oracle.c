@@ -1271,7 +1271,47 @@ static uint64_t orc_morton(int64_t x, int64_t y, int64_t z)
     return orc_spread3((uint64_t)x) | (orc_spread3((uint64_t)y) << 1) | (orc_spread3((uint64_t)z) << 2);
 }
 
-/* One sample per valid pixel of one map: writes depth d (or -1) and cube coords. */
+/* sin and cos of x in FP32 (|x| <= 4), one rounding per operation: Cody-Waite
+ * reduction by pi/2 -- k = nearest integer to x (2/pi), r = x - k pi/2 in two fused
+ * multiply-adds with pi/2 split into a float head and tail -- then the Taylor
+ * polynomials of sin (to r^9) and cos (to r^10) on |r| <= pi/4 (truncation below
+ * 2e-9) by Horner's rule in fused multiply-adds, and the quadrant k mod 4. */
+void orc_sincos_tay(float x, float* s, float* c)
+{
+    const float two_over_pi = (float)(2.0 / 3.14159265358979323846);
+    const float p1 = (float)(3.14159265358979323846 / 2.0);
+    const float p2 = (float)(3.14159265358979323846 / 2.0 - (double)p1);
+    const float kf = rintf(x * two_over_pi);
+    float r = fmaf(-kf, p1, x);
+    r = fmaf(-kf, p2, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, (float)(1.0 / 362880.0), (float)(-1.0 / 5040.0));
+    ps = fmaf(ps, r2, (float)(1.0 / 120.0));
+    ps = fmaf(ps, r2, (float)(-1.0 / 6.0));
+    const float sr = fmaf(r2 * r, ps, r);
+    float pc = fmaf(r2, (float)(-1.0 / 3628800.0), (float)(1.0 / 40320.0));
+    pc = fmaf(pc, r2, (float)(-1.0 / 720.0));
+    pc = fmaf(pc, r2, (float)(1.0 / 24.0));
+    pc = fmaf(pc, r2, -0.5f);
+    const float cr = fmaf(pc, r2, 1.0f);
+    switch ((int)kf & 3) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+    }
+}
+
+void orc_sincos_tay_many(const float* x, int64_t n, float* s, float* c)
+{
+    for (int64_t i = 0; i < n; ++i) orc_sincos_tay(x[i], s + i, c + i);
+}
+
+/* One sample per valid pixel of one map: writes depth d (or -1) and cube coords.
+ * Pinhole: the camera-frame point ((i + 0.5 - cx) / fx z, (j + 0.5 - cy) / fy z, z).
+ * Spherical (a LIDAR scan, z = range): azimuth phi = (i + 0.5 - cx) / fx, elevation
+ * theta = (cy - (j + 0.5)) / fy, point z (cos theta cos phi, cos theta sin phi,
+ * sin theta) with orc_sincos_tay. */
 int64_t orc_octree_samples(const double* cam, int W, int H, const float* depth, const double* root_min, double root_edge,
                            int dmin, int dmax, int32_t* d_out, int64_t* q_out, float* r_out)
 {
@@ -1281,6 +1321,7 @@ int64_t orc_octree_samples(const double* cam, int W, int H, const float* depth, 
     for (int k = 0; k < 3; ++k) C[k] = (float)cam[13 + k];
     for (int k = 0; k < 3; ++k) m[k] = (float)root_min[k];
     float E = (float)root_edge, rroot = E * 0.5f;
+    const int spherical = cam[16] == 1.0;
     float* X = (float*)malloc(sizeof(float) * 3 * (size_t)W * (size_t)H);
     char* ok = (char*)malloc((size_t)W * (size_t)H);
     for (int j = 0; j < H; ++j)
@@ -1290,9 +1331,19 @@ int64_t orc_octree_samples(const double* cam, int W, int H, const float* depth, 
             ok[p] = isfinite(z) && z > 0.0f;
             if (!ok[p]) continue;
             float pc[3];
-            pc[0] = (((float)i + 0.5f) - cx) / fx * z;
-            pc[1] = (((float)j + 0.5f) - cy) / fy * z;
-            pc[2] = z;
+            if (spherical) {
+                float sp, cp, st, ct;
+                orc_sincos_tay((((float)i + 0.5f) - cx) / fx, &sp, &cp);
+                orc_sincos_tay((cy - ((float)j + 0.5f)) / fy, &st, &ct);
+                const float rc = z * ct;
+                pc[0] = rc * cp;
+                pc[1] = rc * sp;
+                pc[2] = z * st;
+            } else {
+                pc[0] = (((float)i + 0.5f) - cx) / fx * z;
+                pc[1] = (((float)j + 0.5f) - cy) / fy * z;
+                pc[2] = z;
+            }
             for (int a = 0; a < 3; ++a) {
                 float s = R[0 + a] * pc[0] + R[3 + a] * pc[1];
                 s = s + R[6 + a] * pc[2];

@@ -1,8 +1,9 @@
 // Brick domains from depth maps (Sec. 3.3 Eq. 4, Sec. 4.1-4.2), in memory.
 //
-// Every valid pixel of a pinhole map is a point sample X (its z-depth
-// unprojected) with radius r = half the mean distance to the points of its
-// valid 4-neighbours (left, right, up, down).  Eq. 4 puts the sample in the cube
+// Every valid pixel is a point sample X (a pinhole map's z-depth, or a spherical
+// map's range along the pixel's azimuth and elevation, unprojected) with radius
+// r = half the mean distance to the points of its valid 4-neighbours (left,
+// right, up, down).  Eq. 4 puts the sample in the cube
 // of depth d with 0.75 r <= r_root 2^-d < 1.5 r: the smallest d in
 // [depth_min, depth_max] with r_root 2^-d < 1.5 r (depth_max if none), cube
 // q = floor(((X - root_min) / E) 2^d).  All of it in FP32 with one rounding
@@ -89,7 +90,40 @@ __device__ __forceinline__ bool set_contains(const uint64_t* table, uint64_t cap
 
 struct OctCam {
     float fx, fy, cx, cy, R[9], C[3];
+    int spherical;
 };
+
+// sin and cos of x in FP32 (|x| <= 4), one rounding per operation: Cody-Waite
+// reduction by pi/2 (k = nearest integer to x 2/pi; r = x - k pi/2 in two fused
+// multiply-adds, pi/2 split into a float head and tail), the Taylor polynomials of
+// sin (to r^9) and cos (to r^10) on |r| <= pi/4 by Horner's rule in fused
+// multiply-adds (truncation below 2e-9), then the quadrant k mod 4.  The oracle
+// evaluates the same steps, so spherical samples unproject bit for bit alike.
+__device__ __forceinline__ void sincos_tay(float x, float* s, float* c)
+{
+    const float two_over_pi = (float)(2.0 / 3.14159265358979323846);
+    const float p1 = (float)(3.14159265358979323846 / 2.0);
+    const float p2 = (float)(3.14159265358979323846 / 2.0 - (double)(float)(3.14159265358979323846 / 2.0));
+    const float kf = rintf(__fmul_rn(x, two_over_pi));
+    float r = __fmaf_rn(-kf, p1, x);
+    r = __fmaf_rn(-kf, p2, r);
+    const float r2 = __fmul_rn(r, r);
+    float ps = __fmaf_rn(r2, (float)(1.0 / 362880.0), (float)(-1.0 / 5040.0));
+    ps = __fmaf_rn(ps, r2, (float)(1.0 / 120.0));
+    ps = __fmaf_rn(ps, r2, (float)(-1.0 / 6.0));
+    const float sr = __fmaf_rn(__fmul_rn(r2, r), ps, r);
+    float pc = __fmaf_rn(r2, (float)(-1.0 / 3628800.0), (float)(1.0 / 40320.0));
+    pc = __fmaf_rn(pc, r2, (float)(-1.0 / 720.0));
+    pc = __fmaf_rn(pc, r2, (float)(1.0 / 24.0));
+    pc = __fmaf_rn(pc, r2, -0.5f);
+    const float cr = __fmaf_rn(pc, r2, 1.0f);
+    switch ((int)kf & 3) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+    }
+}
 
 struct OctArgs {
     const float* depth;
@@ -116,12 +150,24 @@ __global__ void oct_unproject_kernel(const OctArgs A)
         float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (isfinite(z) && z > 0.0f) {
             const OctCam& c = A.cam[m];
-            const float pc0 = __fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn(__int2float_rn(i), 0.5f), c.cx), c.fx), z);
-            const float pc1 = __fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn(__int2float_rn(j), 0.5f), c.cy), c.fy), z);
+            float pc0, pc1, pc2;
+            if (c.spherical) {  // a LIDAR scan: z is the range along the pixel's direction
+                float sp, cp, st, ct;
+                sincos_tay(__fdiv_rn(__fsub_rn(__fadd_rn(__int2float_rn(i), 0.5f), c.cx), c.fx), &sp, &cp);
+                sincos_tay(__fdiv_rn(__fsub_rn(c.cy, __fadd_rn(__int2float_rn(j), 0.5f)), c.fy), &st, &ct);
+                const float rc = __fmul_rn(z, ct);
+                pc0 = __fmul_rn(rc, cp);
+                pc1 = __fmul_rn(rc, sp);
+                pc2 = __fmul_rn(z, st);
+            } else {
+                pc0 = __fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn(__int2float_rn(i), 0.5f), c.cx), c.fx), z);
+                pc1 = __fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn(__int2float_rn(j), 0.5f), c.cy), c.fy), z);
+                pc2 = z;
+            }
             float x[3];
             for (int a = 0; a < 3; ++a) {
                 float s = __fadd_rn(__fmul_rn(c.R[a], pc0), __fmul_rn(c.R[3 + a], pc1));
-                s = __fadd_rn(s, __fmul_rn(c.R[6 + a], z));
+                s = __fadd_rn(s, __fmul_rn(c.R[6 + a], pc2));
                 x[a] = __fadd_rn(c.C[a], s);
             }
             out = make_float4(x[0], x[1], x[2], 1.0f);
@@ -437,7 +483,7 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
     for (int m = 0; m < nmaps; ++m) {
         const tgv_camera& c = cams[m];
         if (c.width != W || c.height != H) return TGV_ERR_INVALID_ARG;
-        if (c.model != TGV_PINHOLE) return TGV_ERR_UNSUPPORTED;
+        if (c.model != TGV_PINHOLE && c.model != TGV_SPHERICAL) return TGV_ERR_INVALID_ARG;
         bool ok = isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy) && c.fx > 0 && c.fy > 0;
         for (int k = 0; k < 9; ++k) ok = ok && isfinite(c.R[k]);
         for (int k = 0; k < 3; ++k) ok = ok && isfinite(c.C[k]);
@@ -485,6 +531,7 @@ tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, i
                 g.cy = (float)c.cy;
                 for (int k = 0; k < 9; ++k) g.R[k] = (float)c.R[k];
                 for (int k = 0; k < 3; ++k) g.C[k] = (float)c.C[k];
+                g.spherical = c.model == TGV_SPHERICAL;
             }
             A.X = (float4*)X.p;
             for (int a = 0; a < 3; ++a) A.m[a] = (float)cfg->root_min[a];

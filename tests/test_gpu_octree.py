@@ -68,7 +68,7 @@ def test_built_levels_drive_a_coarse_to_fine_solve(sphere_scene):
     assert np.all(np.abs(u) <= 1.0) and (u < 0).any() and (u > 0).any()
 
 
-def test_invalid_configs_and_spherical_maps(sphere_scene):
+def test_invalid_configs_and_camera_models(sphere_scene):
     sc = sphere_scene
     d = dev(sc.depths[:1])
     for bad in [dict(root_edge=0.0), dict(depth_min=2), dict(depth_max=22), dict(band=-1)]:
@@ -76,10 +76,26 @@ def test_invalid_configs_and_spherical_maps(sphere_scene):
         kw.update(bad)
         with pytest.raises(tgv.TgvError):
             tgv.tgv_octree_build(sc.cameras[:1], d, **kw)
-    scan = synth.spherical_scanner(np.array([0.5, 0.5, 0.5]), 128, 64)
+    bad = synth.spherical_scanner(np.array([0.5, 0.5, 0.5]), 128, 64)
+    bad.model = 2  # neither pinhole nor spherical
     with pytest.raises(tgv.TgvError) as e:
-        tgv.tgv_octree_build([scan], torch.ones((1, 64, 128), device="cuda"), np.zeros(3), 1.0, 3, 6, 1)
-    assert e.value.status == 7
+        tgv.tgv_octree_build([bad], torch.ones((1, 64, 128), device="cuda"), np.zeros(3), 1.0, 3, 6, 1)
+    assert e.value.status == 1
+
+
+def test_lidar_scan_levels_identical():
+    """Four full spherical scans of the sphere (ranges, Sec. 3.4): the samples unproject
+    through the same FP32 sin / cos on both sides, so every level is identical."""
+    sc = synth.lidar_sphere_scene(n=64, nscans=4, width=512, height=256)
+    lv = check_same(sc.cameras, sc.depths, np.zeros(3), 1.0, 3, 7, 1)
+    assert sum(L.nbricks for L in lv) > 100
+
+
+def test_scan_from_inside_a_sphere_identical():
+    C = np.array([0.5, 0.5, 0.5])
+    cam = synth.spherical_scanner(C, 1024, 512)
+    dep = np.full((512, 1024), 0.3, np.float32)
+    check_same([cam], [dep], np.zeros(3), 1.0, 3, 9, 1)
 
 
 def test_maps_without_samples_give_empty_levels(sphere_scene):

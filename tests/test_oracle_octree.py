@@ -104,3 +104,56 @@ def test_sphere_scene_construction_properties(sphere_scene):
         if l + 1 < len(levels):
             parents = {(x >> 1, y >> 1, z >> 1) for (x, y, z) in map(tuple, levels[l + 1][0].tolist())}
             assert dilate(parents, nbr) <= A  # 2:1: the finer level is wrapped by this one
+
+
+# ---- spherical maps (LIDAR scans): the own sin / cos and the unprojection
+
+def test_sincos_against_the_library_and_by_hand():
+    x = np.linspace(-3.3, 3.3, 100001).astype(np.float32)
+    s, c = oracle.sincos_tay(x)
+    assert np.abs(s - np.sin(x.astype(np.float64))).max() < 1.2e-7
+    assert np.abs(c - np.cos(x.astype(np.float64))).max() < 1.2e-7
+    s, c = oracle.sincos_tay(np.array([0.0, np.float32(math.pi)], np.float32))
+    assert s[0] == 0.0 and c[0] == 1.0 and c[1] == -1.0
+    # sin of the float nearest pi is pi - float(pi) (to FP32)
+    assert s[1] == np.float32(math.pi - float(np.float32(math.pi)))
+    # odd and even, quadrant by quadrant
+    y = np.float32([0.3, 1.9, 2.7])
+    s1, c1 = oracle.sincos_tay(y)
+    s2, c2 = oracle.sincos_tay(-y)
+    np.testing.assert_array_equal(s1, -s2)
+    np.testing.assert_array_equal(c1, c2)
+
+
+def test_spherical_sample_by_hand():
+    """Scanner at (0.5, 0.5, 0.5), world axes, 8 pixels per radian, range 0.25
+    everywhere: pixel (8, 4) looks along +x (azimuth 0, elevation 0), so X =
+    (0.75, 0.5, 0.5); its 4 neighbours are 1/8 rad away, r = 0.25 sin(1/16) and
+    Eq. 4 gives depth 5 (2^-5 / 2 < 1.5 r <= 2^-4 / 2): cube (24, 16, 16)."""
+    cam = synth.Camera(8.0, 8.0, 8.5, 4.5, np.eye(3), np.array([0.5, 0.5, 0.5]), 16, 8, model=1)
+    dep = np.full((8, 16), 0.25, np.float32)
+    dd, qq, rr = oracle.octree_samples(cam, dep, np.zeros(3), 1.0, 3, 8)
+    r = 0.25 * math.sin(1.0 / 16.0)
+    assert abs(rr[4, 8] - r) < 1e-7
+    assert 0.5 * 2.0 ** -5 < 1.5 * r <= 0.5 * 2.0 ** -4
+    assert dd[4, 8] == 5
+    assert list(qq[4, 8]) == [24, 16, 16]
+
+
+def test_spherical_scan_from_inside_a_sphere():
+    """A full scan from the centre of a sphere of radius 0.3: every sample's cube lies on
+    the sphere (its centre within half a cube diagonal plus the sample radius)."""
+    C = np.array([0.5, 0.5, 0.5])
+    cam = synth.spherical_scanner(C, 256, 128)
+    dep = np.full((128, 256), 0.3, np.float32)
+    dd, qq, rr = oracle.octree_samples(cam, dep, np.zeros(3), 1.0, 3, 10)
+    ok = dd >= 0
+    assert ok.all()
+    edge = 2.0 ** -dd[ok].astype(np.float64)
+    centre = (qq[ok] + 0.5) * edge[:, None]
+    dist = np.linalg.norm(centre - C, axis=1)
+    assert np.all(np.abs(dist - 0.3) <= 0.5 * math.sqrt(3) * edge + 1e-6)
+    # Eq. 4: the cube radius lies in [0.75 r, 1.5 r) wherever the depth range allows
+    inner = (dd[ok] > 3) & (dd[ok] < 10)
+    rc = 0.5 * edge[inner]
+    assert np.all((0.75 * rr[ok][inner] <= rc) & (rc < 1.5 * rr[ok][inner]))
