@@ -517,8 +517,8 @@ def tgv_octree_destroy(o):
 
 def tgv_octree_build(cams, depth, root_min, root_edge: float, depth_min: int, depth_max: int, band: int = 1,
                      stream: int = 0):
-    """Brick levels from pinhole depth maps (CUDA tensor (nmaps, H, W)); returns
-    (list of OctreeLevel, number of samples)."""
+    """Brick levels from depth maps, pinhole or spherical (CUDA tensor (nmaps, H, W));
+    returns (list of OctreeLevel, number of samples)."""
     if depth.dim() == 2:
         depth = depth.unsqueeze(0)
     nmaps = depth.shape[0]
