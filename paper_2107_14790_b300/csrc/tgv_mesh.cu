@@ -28,7 +28,9 @@
 // cell order.  Passes:
 //   classify  one bit per cell whose corners change sign (a warp ballot per word);
 //   compact   the crossing cells into a list in cell order (exclusive scan of the
-//             words' popcounts; rank = word prefix + popcount of the lower bits);
+//             words' popcounts; rank = word prefix + popcount of the lower bits),
+//             then an order of the list grouped by the cells' corner signs (one
+//             stable radix pass), in which the count pass takes the cells;
 //   count     per listed cell: the loops and their triangulation; the triangles are
 //             kept as edge-index triples in a per-cell record and the vertex ids
 //             they reference are set in a bit set (4 ids per voxel slot);
@@ -36,14 +38,16 @@
 //             the listed cells' triangle counts (triangle offsets);
 //   write     per listed cell: triangles from its record, vertex positions.
 // Only a few per cent of the cells cross the surface: listing them keeps the
-// lanes of a warp busy in the loop triangulation, and the record spares the write
-// pass from repeating it.
+// lanes of a warp busy in the loop triangulation, grouping them by sign pattern
+// keeps those lanes on one path, and the record spares the write pass from
+// repeating the triangulation.  Results go to list positions: cell order holds.
 #include <math.h>
 
 #include <unordered_map>
 #include <vector>
 
 #include "tgv_internal.cuh"
+#include "tgv_zorder.cuh"
 
 namespace {
 
@@ -87,6 +91,7 @@ struct MeshArgs {
     uint32_t* vbits;        // bit set over the vertex ids (4 per voxel slot)
     const uint32_t* vrank;  // exclusive prefix of the words' popcounts
     const uint32_t* cells;  // the crossing cells in cell order (ncross)
+    const uint64_t* order;  // list positions grouped by corner signs: code << 32 | position
     int64_t ncross;
     uint32_t* tcount;       // per listed cell: triangle count, then exclusive offsets
     struct MeshRec* rec;    // per listed cell
@@ -315,11 +320,11 @@ __device__ int cell_triangles(const MeshArgs& A, const Cell& C, float centre[3],
     return ntri;
 }
 
-// bit (cell & 31) of word[cell >> 5]: the cell exists and its corners change sign.
-// 64 threads per brick, one per (i, j) column of 8 cells: the thread walks k = 0..7
+// bit (cell & 31) of word[cell >> 5]: the cell exists and its corners change sign;
+// code[cell]: its corner signs (bit c: corner c inside).  64 threads per brick, one per (i, j) column of 8 cells: the thread walks k = 0..7
 // keeping the corner layer that the next cell shares; a warp holds four rows j, so
 // each step k makes one word of the bit set by ballot.
-__global__ void __launch_bounds__(256) mc_classify_kernel(const MeshArgs A, uint32_t* word)
+__global__ void __launch_bounds__(256) mc_classify_kernel(const MeshArgs A, uint32_t* word, uint8_t* code)
 {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 6;
     if (b >= A.nb) return;  // whole warps: 64 threads per brick
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(256) mc_classify_kernel(const MeshArgs A, uint
         }
         const uint32_t m = __ballot_sync(0xffffffffu, ok && in != 0 && in != 0xff);
         if ((threadIdx.x & 31) == 0) w[2 * k] = m;
+        code[b * TGV_BVOX + t + 64 * k] = (uint8_t)in;
     }
 }
 
@@ -373,24 +379,33 @@ __device__ __forceinline__ uint32_t bit_rank(const uint32_t* word, const uint32_
     return prefix[k >> 5] + (uint32_t)__popc(word[k >> 5] & ((1u << (k & 31)) - 1u));
 }
 
-// cells[rank] = cell for every crossing cell, one thread per bit-set word
-__global__ void mc_compact_kernel(const uint32_t* word, const uint32_t* prefix, int64_t nw, uint32_t* cells)
+// cells[rank] = cell for every crossing cell, one thread per bit-set word, and the
+// sort key (corner signs << 32 | rank) that groups the cells of one sign pattern
+__global__ void mc_compact_kernel(const uint32_t* word, const uint32_t* prefix, int64_t nw, const uint8_t* code,
+                                  uint32_t* cells, uint64_t* key)
 {
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nw) return;
     uint32_t m = word[w], r = prefix[w];
     while (m) {
-        cells[r++] = (uint32_t)(32 * w) + (uint32_t)(__ffs(m) - 1);
+        const uint32_t cell = (uint32_t)(32 * w) + (uint32_t)(__ffs(m) - 1);
+        cells[r] = cell;
+        key[r] = ((uint64_t)code[cell] << 32) | r;
+        ++r;
         m &= m - 1;
     }
 }
 
 __device__ __forceinline__ void mark(uint32_t* bits, uint64_t id) { atomicOr(bits + (id >> 5), 1u << (id & 31)); }
 
+// One thread per listed cell, cells of one sign pattern side by side (the same
+// crossings and face joins: the lanes of a warp follow the same path); results
+// are stored at the cell's list position, so the output keeps cell order.
 __global__ void mc_count_kernel(const MeshArgs A)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.ncross) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.ncross) return;
+    const int64_t i = (int64_t)(A.order[j] & 0xffffffffu);
     const uint32_t cell = A.cells[i];
     Cell C;
     uint32_t nt = 0, head = 0;
@@ -419,6 +434,7 @@ __global__ void mc_count_kernel(const MeshArgs A)
 // Triangles of every listed cell at its offset, and the positions of the vertices
 // it references: a crossing is written by each cell that has it (up to four), all
 // with the same value (the same two corner values and voxel coordinates).
+// (In list order: the pass does not triangulate, and its stores stay sequential.)
 __global__ void mc_write_kernel(const MeshArgs A)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,7 +614,8 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
         return tgv_fail(d, TGV_ERR_UNSUPPORTED, "level too large for 32-bit mesh indices");
     const int64_t nwv = (nids + 31) / 32, nwc = (ncell + 31) / 32;  // bit-set words
     if ((st = tgv_scratch(d, d->mesh_flags, sizeof(uint32_t) * (size_t)(2 * nwv + 1))) != TGV_OK) return st;
-    if ((st = tgv_scratch(d, d->mesh_count, sizeof(uint32_t) * (size_t)(2 * nwc + 1))) != TGV_OK) return st;
+    if ((st = tgv_scratch(d, d->mesh_count, sizeof(uint32_t) * (size_t)(2 * nwc + 1) + (size_t)ncell)) != TGV_OK)
+        return st;
     MeshArgs A;
     A.u = L.u;
     A.coords = L.coords_dev;
@@ -611,28 +628,42 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
     A.vrank = vcnt;
     uint32_t* cword = (uint32_t*)d->mesh_count.ptr;
     uint32_t* ccnt = cword + nwc;
+    uint8_t* code = (uint8_t*)(ccnt + nwc + 1);
     cudaError_t e = cudaMemsetAsync(A.vbits, 0, sizeof(uint32_t) * (size_t)nwv, d->stream);
     if ((st = tgv_cuda_check(d, e, "mesh scratch clear")) != TGV_OK) return st;
-    mc_classify_kernel<<<(unsigned)((L.nb + 3) / 4), 256, 0, d->stream>>>(A, cword);
+    mc_classify_kernel<<<(unsigned)((L.nb + 3) / 4), 256, 0, d->stream>>>(A, cword, code);
     mc_popc_kernel<<<(unsigned)((nwc + 256) / 256), 256, 0, d->stream>>>(cword, nwc, ccnt);
     d->launches += 2;
     if ((st = tgv_cuda_check(d, cudaGetLastError(), "mc_classify_kernel launch")) != TGV_OK) return st;
     uint64_t nc = 0, nv = 0, nt = 0;
     if ((st = tgv_exclusive_scan_u32(d, ccnt, nwc + 1, d->mesh_scan, &nc)) != TGV_OK) return st;
-    // listed cells: cell ids, triangle counts (nc + 1), records (8-byte aligned)
-    const size_t rec_off = ((sizeof(uint32_t) * (2 * (size_t)nc + 1)) + 15) & ~(size_t)15;
-    if ((st = tgv_scratch(d, d->mesh_cells, rec_off + sizeof(MeshRec) * (size_t)std::max<uint64_t>(nc, 1))) != TGV_OK)
+    // listed cells: cell ids, triangle counts (nc + 1), records, sort keys and the
+    // sort's temporaries (16-byte aligned parts)
+    const size_t ncz = (size_t)std::max<uint64_t>(nc, 1);
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t rec_off = up16(sizeof(uint32_t) * (2 * (size_t)nc + 1));
+    const size_t key_off = up16(rec_off + sizeof(MeshRec) * ncz);
+    const size_t tmp_off = key_off + 8 * ncz, hist_off = tmp_off + 8 * ncz;
+    if ((st = tgv_scratch(d, d->mesh_cells, hist_off + 4 * (size_t)tgv_radix_hist_words((int64_t)ncz))) != TGV_OK)
         return st;
-    uint32_t* cells = (uint32_t*)d->mesh_cells.ptr;
+    char* base = (char*)d->mesh_cells.ptr;
+    uint32_t* cells = (uint32_t*)base;
+    uint64_t* keys = (uint64_t*)(base + key_off);
     A.cells = cells;
+    A.order = keys;
     A.ncross = (int64_t)nc;
     A.tcount = cells + nc;
-    A.rec = (MeshRec*)((char*)d->mesh_cells.ptr + rec_off);
+    A.rec = (MeshRec*)(base + rec_off);
     const unsigned lgrid = (unsigned)((nc + 127) / 128);
     if (nc > 0) {
-        mc_compact_kernel<<<(unsigned)((nwc + 255) / 256), 256, 0, d->stream>>>(cword, ccnt, nwc, cells);
+        mc_compact_kernel<<<(unsigned)((nwc + 255) / 256), 256, 0, d->stream>>>(cword, ccnt, nwc, code, cells, keys);
+        d->launches++;
+        // group the cells by corner signs (one stable 8-bit pass: ties keep list order)
+        e = tgv_radix_sort_u64(keys, (uint64_t*)(base + tmp_off), (uint32_t*)(base + hist_off), (int64_t)nc, 32, 8,
+                               d->stream, &d->launches);
+        if ((st = tgv_cuda_check(d, e, "mesh cell grouping")) != TGV_OK) return st;
         mc_count_kernel<<<lgrid, 128, 0, d->stream>>>(A);
-        d->launches += 2;
+        d->launches++;
     }
     mc_popc_kernel<<<(unsigned)((nwv + 256) / 256), 256, 0, d->stream>>>(A.vbits, nwv, vcnt);
     d->launches++;
