@@ -104,7 +104,8 @@ typedef struct tgv_domain tgv_domain; /* opaque, library-owned */
  * Defaults (tgv_default_params): nbins 8 (Alg. 1), alpha1 1, alpha0 2, lambda 1,
  * tau = sigma = 0.2 (tau*sigma*24 < 1: ||K||^2 <= 24 for the forward/backward
  * difference operators), FP32 storage, clamp_u 1, endpoint centres, box_v 2,
- * paired iteration kernel, x_run 0 (automatic), gather-form histograms. */
+ * paired iteration kernel, x_run 0 (automatic), gather-form histograms, default
+ * wait budget, wait_test 0. */
 typedef struct {
     int32_t nbins;       /* histogram bins, 2..16 */
     float alpha1;        /* weight of |grad u - v| */
@@ -122,6 +123,16 @@ typedef struct {
                           * duals through shared memory; results do not depend on it.
                           * 0 = chosen from the item and SM counts, 1 = no runs. */
     int32_t hist_form;   /* TGV_HIST_* form of the histogram kernel */
+    int64_t wait_cycles; /* budget of each bounded device-side wait of the PAIRED and PIPELINED
+                          * iteration kernels (a CTA waiting for its bulk copies), in SM clock
+                          * cycles; 0 = 2e9 (about one second).  A wait that runs out sets the
+                          * domain's error flag: the next call that synchronises returns
+                          * TGV_ERR_TIMEOUT and every later call TGV_ERR_STATE.  After giving up,
+                          * a CTA still waits for its own copies in flight with the default budget,
+                          * whatever this value, so none lands in released shared memory. */
+    int32_t wait_test;   /* testing only, 0 in normal use.  1: the first wait of every CTA of the
+                          * PAIRED kernel targets a barrier that no copy completes, so it runs out
+                          * after wait_cycles (a way to exercise the timeout path without a fault) */
 } tgv_params;
 
 /* One level of a domain (all arrays host memory, copied at creation).

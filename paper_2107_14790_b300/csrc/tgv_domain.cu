@@ -521,6 +521,8 @@ tgv_status tgv_default_params(tgv_params* out)
     out->iter_kernel = TGV_ITER_PAIRED;
     out->x_run = 0;
     out->hist_form = TGV_HIST_GATHER;
+    out->wait_cycles = 0;
+    out->wait_test = 0;
     return TGV_OK;
 }
 
@@ -538,6 +540,7 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
         return TGV_ERR_INVALID_ARG;
     if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
     if (prm->hist_form != TGV_HIST_GATHER && prm->hist_form != TGV_HIST_SCATTER) return TGV_ERR_INVALID_ARG;
+    if (prm->wait_cycles < 0 || (prm->wait_test != 0 && prm->wait_test != 1)) return TGV_ERR_INVALID_ARG;
     if (!(prm->alpha1 > 0.0f) || !(prm->alpha0 > 0.0f) || !(prm->lambda >= 0.0f) || !(prm->tau > 0.0f) ||
         !(prm->sigma > 0.0f) || !(prm->box_v > 0.0f))
         return TGV_ERR_INVALID_ARG;

@@ -29,6 +29,14 @@
 #define TGV_NNBR 12
 #define TGV_MAX_BINS 16
 #define TGV_MAPS_PER_LAUNCH 32
+// default budget of a bounded device-side wait, in SM clock cycles (about one second)
+#define TGV_WAIT_CYCLES_DEFAULT 2000000000LL
+
+// budget of the iteration kernels' bounded waits for a domain's parameters
+inline long long tgv_wait_budget(const tgv_params& p)
+{
+    return p.wait_cycles > 0 ? (long long)p.wait_cycles : TGV_WAIT_CYCLES_DEFAULT;
+}
 
 // Neighbour slots: the six faces, then the six edge bricks whose offset has
 // -1 on one axis and +1 on another ("MX_PY" = offset (-1, +1, 0)).  The edge

@@ -35,9 +35,9 @@
 // their inputs are loaded into registers before the CTA waits for its stage.
 //
 // The bin count is a template parameter for 8, 10 and 12 bins (0 = read at
-// run time).  Every mbarrier wait is bounded (about a second); a CTA that
-// gives up sets the domain's error flag, waits (bounded) for its copies in
-// flight and returns.
+// run time).  Every mbarrier wait is bounded (tgv_params.wait_cycles, about a
+// second by default); a CTA that gives up sets the domain's error flag, waits
+// (bounded, default budget) for its copies in flight and returns.
 #include <math.h>
 
 #include <vector>
@@ -182,7 +182,8 @@ template <typename S>
 struct PairArgs {
     IterArgs<S> it;
     int* err;
-    long long wait_budget;
+    long long wait_budget;             // cycles per wait for a stage (tgv_params.wait_cycles)
+    int wait_test;                     // 1: the prologue waits on a barrier nothing completes
     uint32_t stage_bytes, tx_bytes;
     uint32_t pn_bytes;                 // bytes of one own-new-dual buffer (0 when it aliases the stage)
     uint32_t off_pn, off_hal, off_nbr, off_bar;
@@ -785,6 +786,7 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);  // never arrived on: the target of a test-mode wait
         fence_mbar_init();
     }
     if (t < TGV_NNBR) {
@@ -811,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
     // prologue: phase A of the first item
     C.load_inputs(C.nbr_row(0), false, to_next);
     {
-        const bool ok = mbar_wait_bounded(&bar[0], 0, P.wait_budget);
+        const bool ok = mbar_wait_bounded(&bar[P.wait_test ? 2 : 0], 0, P.wait_budget);
         if (__syncthreads_or(!ok)) bail = true;
     }
     uint32_t links = 0;
@@ -872,9 +874,10 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairAr
     }
     if (bail && t == 0) {
         atomicExch(P.err, 1);
-        // copies still in flight land before the CTA's shared memory is released
+        // copies still in flight land before the CTA's shared memory is released (the
+        // default budget, not the possibly tiny one of the wait that gave up)
         for (int k = 0; k < 2; ++k)
-            if (pending & (1u << k)) mbar_wait_bounded(&bar[k], (parity >> k) & 1u, P.wait_budget);
+            if (pending & (1u << k)) mbar_wait_bounded(&bar[k], (parity >> k) & 1u, TGV_WAIT_CYCLES_DEFAULT);
     }
 }
 
@@ -972,7 +975,7 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     off += 2 * TGV_NNBR * 4;
     off = (off + 15) / 16 * 16;
     P.off_bar = off;
-    off += 2 * 8;
+    off += 3 * 8;
     const size_t smem = off;
     auto kern = tgv_iter_pair_kernel<S, NB>;
     int per_sm = 0;
@@ -995,7 +998,8 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     const int64_t grid = nruns < slots ? nruns : slots;
     P.xrun = (uint32_t)R;
     P.err = d->err;
-    P.wait_budget = 2000000000LL;  // about one second at 2 GHz
+    P.wait_budget = tgv_wait_budget(d->prm);
+    P.wait_test = d->prm.wait_test;
     P.stage_bytes = stage;
     P.tx_bytes = tx;
     for (int it = 0; it < iters; ++it) {

@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         atomicExch(P.err, 1);
         // copies may still be landing in either stage: wait for them (bounded) before leaving
         for (int k = 0; k < 2; ++k) {
-            if (it + k * G < nit) mbar_wait_bounded(&bar[s ^ k], (parity >> (s ^ k)) & 1u, P.wait_budget);
+            if (it + k * G < nit) mbar_wait_bounded(&bar[s ^ k], (parity >> (s ^ k)) & 1u, TGV_WAIT_CYCLES_DEFAULT);
         }
     }
 }
@@ -492,7 +492,7 @@ tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
     int64_t grid = (int64_t)per_sm * d->sm_count;
     if (grid > tgv_work_items(L)) grid = tgv_work_items(L);
     P.err = d->err;
-    P.wait_budget = 2000000000LL;  // about one second at 2 GHz
+    P.wait_budget = tgv_wait_budget(d->prm);
     P.stage_bytes = stage;
     P.tx_bytes = tx;
     for (int it = 0; it < iters; ++it) {

@@ -37,7 +37,8 @@ class tgv_params(ctypes.Structure):
                 ("lam", ctypes.c_float), ("tau", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("clamp_u", ctypes.c_int32), ("centres", ctypes.c_int32),
                 ("box_v", ctypes.c_float), ("iter_kernel", ctypes.c_int32),
-                ("x_run", ctypes.c_int32), ("hist_form", ctypes.c_int32)]
+                ("x_run", ctypes.c_int32), ("hist_form", ctypes.c_int32), ("wait_cycles", ctypes.c_int64),
+                ("wait_test", ctypes.c_int32)]
 
 
 class tgv_level_desc(ctypes.Structure):
@@ -182,7 +183,8 @@ ITER_KERNELS = {"pipelined": 0, "one_brick_per_cta": 1, "paired": 2}
 
 
 def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, storage="fp32", clamp_u=True,
-                centres=0, box_v=2.0, iter_kernel="paired", x_run=0, hist_form="gather") -> tgv_params:
+                centres=0, box_v=2.0, iter_kernel="paired", x_run=0, hist_form="gather", wait_cycles=0,
+                wait_test=0) -> tgv_params:
     p = tgv_params()
     _check(None, lib().tgv_default_params(ctypes.byref(p)))
     p.nbins, p.alpha1, p.alpha0, p.lam, p.tau, p.sigma = int(nbins), alpha1, alpha0, lam, tau, sigma
@@ -191,6 +193,7 @@ def make_params(nbins=8, alpha1=1.0, alpha0=2.0, lam=1.0, tau=0.2, sigma=0.2, st
     p.iter_kernel = ITER_KERNELS[iter_kernel] if isinstance(iter_kernel, str) else int(iter_kernel)
     p.x_run = int(x_run)
     p.hist_form = HIST_FORMS[hist_form] if isinstance(hist_form, str) else int(hist_form)
+    p.wait_cycles, p.wait_test = int(wait_cycles), int(wait_test)
     return p
 
 
