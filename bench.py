@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched block of the default line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving block of the default line")
+    ap.add_argument("--block-chunks", type=int, default=32, help="batched block: chunks (c4's size distribution)")
+    ap.add_argument("--block-requests", type=int, default=200, help="serving block: requests")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree", "composite",
                              "histforms", "precision"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
@@ -87,6 +91,13 @@ def algorithmic_bytes_per_voxel(nbins: int, storage: str) -> int:
     s = 4 if storage == "fp32" else 2
     state = 4 + 4 + (3 + 3 + 3 + 6) * s
     return 2 * state + 2 * nbins
+
+
+def state_bytes(nvox: int, nbins: int, storage: str) -> int:
+    """Device bytes of a level's iteration state and histograms (what both arms print as the
+    working set): u, ubar x2, v, vbar x2, p x2, q x2 and the packed 16-bit counts."""
+    s = 4 if storage == "fp32" else 2
+    return nvox * (4 + 2 * 4 + (3 + 2 * 3 + 2 * 3 + 2 * 6) * s + 4 * ((nbins + 1) // 2))
 
 
 def kernel_hash(form: str = "paired") -> str:
@@ -244,7 +255,7 @@ def run_ours(args, cfg):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else f"f32-math/{args.storage}-storage",
         "data": scene_note(cfg),
-        "config": arm_config(cfg, args, nvox, dom.nbytes, world),
+        "config": arm_config(cfg, args, nvox, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "kernel": {"paired": "tgv_iter_pair_kernel", "pipelined": "tgv_iter_pipe_kernel",
@@ -274,6 +285,22 @@ def run_ours(args, cfg):
                          "h2d_bytes_per_step": int(depth_host.numel() * 4),
                          "d2h_bytes_per_step": int(nvox * 4 + 8 * 4 * len(blocks))}
     dom.close()
+    del depth_dev
+    torch.cuda.empty_cache()
+    # bounded blocks of the batched and served forms (the metric's chunk-solve latency)
+    if not args.no_batched and not args.small:
+        result["batched"] = batched_block(stream, rank, world, local, nchunks=args.block_chunks)
+    if not args.no_serving and not args.small:
+        from paper_2107_14790_b300.multigpu import gather_dict, reduce_scalar
+        sv = serving_block("fp32", args.block_requests, 60.0, rank=rank)
+        lat = np.concatenate(list(gather_dict({rank: sv.pop("latencies")}).values()))
+        span = reduce_scalar(sv["makespan_s"], "max")
+        vu = reduce_scalar(sv["voxel_updates_per_s"] * sv["makespan_s"], "sum")
+        sv["latency_s"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())}
+        sv["voxel_updates_per_s"] = vu / span
+        sv["ranks"] = world
+        result["serving"] = sv
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, sc)
     if world > 1:
@@ -307,8 +334,9 @@ def scene_note(cfg):
     return f"synthetic (seeded {kind} scene, ray-cast depth maps)"
 
 
-def arm_config(cfg, args, nvox, nbytes, world):
-    """The workload description both arms print."""
+def arm_config(cfg, args, nvox, world):
+    """The workload description both arms print (identical for the same arguments)."""
+    nbytes = state_bytes(nvox, cfg["nbins"], args.storage)
     return {"workload": cfg["workload"], "voxels": nvox, "maps": cfg["nmaps"], "map_res": cfg["res"],
             "nbins": cfg["nbins"], "iterations": cfg["iterations"], "energy_every": cfg["check_every"],
             "storage": args.storage,
@@ -317,11 +345,34 @@ def arm_config(cfg, args, nvox, nbytes, world):
             "parallelism": f"independent instance per GPU x{world}"}
 
 
+def oracle_full_sphere():
+    """The whole 64^3 sphere workload (16 maps 128^2, 8 bins, 200 iterations + energy) on the
+    oracle: the one configuration the oracle finishes in full within seconds."""
+    import oracle
+    import synth
+    sc = synth.sphere_scene()
+    lvl = oracle.OracleLevel(sc.domain, sc.nbins)
+    t0 = time.perf_counter()
+    for cam, d in zip(sc.cameras, sc.depths):
+        lvl.accumulate(cam, d, 1)
+    lvl.iterate(SMALL["iterations"])
+    lvl.energy()
+    dt = time.perf_counter() - t0
+    return {"workload": SMALL["workload"], "value": lvl.n * SMALL["iterations"] / dt, "unit": "voxel-updates/s",
+            "seconds": dt}
+
+
 def cpu_baseline(cfg, sc):
     import oracle
     ups, dt, note = oracle_sample(cfg, sc)
-    return {"value": ups, "unit": "voxel-updates/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": note, "seconds": dt}
+    out = {"value": ups, "unit": "voxel-updates/s", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": note, "seconds": dt}
+    if cfg["n"] != 64:
+        upd = sc.domain.nvox * cfg["iterations"]
+        out["why_a_sample"] = ("the full workload is %.2g voxel-updates, about %.0f minutes of the oracle at this "
+                               "rate: beyond the few-minute bound of a benchmark run" % (upd, upd / ups / 60))
+        out["full_sphere_64"] = oracle_full_sphere()
+    return out
 
 
 def run_reference(args, cfg):
@@ -351,8 +402,7 @@ def run_reference(args, cfg):
             "value": value, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": scene_note(cfg),
-            "config": arm_config(cfg, args, sc.domain.nvox, sc.domain.nvox * (140 if args.storage == "fp32" else 92),
-                                 world),
+            "config": arm_config(cfg, args, sc.domain.nvox, world),
             "cpu_baseline": {"value": value, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle",
                              "sample": note},
             "e2e": {"value": value, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -385,6 +435,125 @@ def _oracle_u(spec, iters):
     lvl.hist[:] = h.cpu().numpy() if hasattr(h, "cpu") else h
     lvl.iterate(iters)
     return lvl.u
+
+
+def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fp16")):
+    """Bounded form of the batched workload for the default line: `nchunks` chunks of the
+    c4 size distribution (log-uniform 32^3..192^3 active voxels, frozen one-brick shell,
+    10 bins, `iters` iterations), sharded over the ranks (strong scaling: each rank solves
+    its own chunks, no collective on the path).  Forms: one union level replayed as a CUDA
+    graph per storage type, and the plain form (every chunk its own domain, FP32)."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import tgv
+    from paper_2107_14790_b300.batching import union_level
+    from paper_2107_14790_b300.multigpu import reduce_scalar, shard
+    geo = synth.chunk_workload(1004, nchunks, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="none")
+    mine = shard([g.domain.nvox for g in geo], rank, world)
+    specs = [geo[k] for k in mine]
+    for sp in specs:
+        sp.hist = synth.chunk_histogram(sp, f"cuda:{local}")
+    nvox = sum(sp.domain.nvox for sp in specs)
+    tot = reduce_scalar(nvox, "sum")
+    U = union_level([sp.domain for sp in specs])
+    hist = torch.cat([sp.hist for sp in specs])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return reduce_scalar(e0.elapsed_time(e1), "max")
+
+    out = {"chunks": nchunks, "voxels": int(tot), "iterations": iters, "l2": "inputs larger than L2 "
+           "(state %.2f GB)" % (state_bytes(int(tot), 10, "fp32") / 1e9)}
+    launches = 0
+    for storage in storages:
+        dom = tgv.Domain([U], nbins=10, storage=storage, stream=stream.cuda_stream)
+        dom.set_histograms(0, hist)
+        dom.solve_graph(0, iters)  # first call: plain launches, captures the graph
+        dom.reset(0)
+        l0 = dom.launches
+        ms = timed(lambda: dom.solve_graph(0, iters))
+        launches += dom.launches - l0
+        out[f"union_graph_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms}
+        dom.close()
+    doms = []
+    for sp in specs:
+        d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)
+        d.set_histograms(0, sp.hist)
+        doms.append(d)
+    l0 = sum(d.launches for d in doms)
+    ms = timed(lambda: [tgv.tgv_solve(d.handle, 0, iters, False) for d in doms])
+    launches += sum(d.launches for d in doms) - l0
+    out["plain_fp32"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms}
+    for d in doms:
+        d.close()
+    base = out["plain_fp32"]["voxel_updates_per_s"]
+    for storage in storages:
+        out[f"union_graph_{storage}"]["speedup_over_plain_fp32"] = \
+            out[f"union_graph_{storage}"]["voxel_updates_per_s"] / base
+    out["gpu_launches"] = int(reduce_scalar(launches, "sum"))
+    return out
+
+
+def serving_block(storage, nreq, budget_gb, seed=1005, rank=0, overload=0):
+    """Poisson stream of `nreq` chunk-solve requests (16k..8M active voxels, 8..12 bins,
+    200..600 iterations) through one server per bin count: a saturation run (requests all
+    arriving at once) gives the saturated rate; the stream then arrives at 0.8x that rate.
+    `overload` > 0 adds a run of that many requests arriving at 2x the saturated rate.
+    Returns p50/p99 latency, queue wait and voxel-updates/s (each rank its own requests)."""
+    import torch
+    import synth
+    from paper_2107_14790_b300 import tgv
+    from paper_2107_14790_b300.batching import Request, RequestStream
+    specs = synth.chunk_workload(seed + 1000 * rank, nreq, 16 * 1024, 8 * 1024 * 1024, (8, 12), (200, 600),
+                                 rate=1.0, hist="none")
+    bins = sorted({sp.nbins for sp in specs})
+    budget = budget_gb * 1e9
+    streams = {n: torch.cuda.Stream() for n in bins}
+
+    def brick_bytes(n):
+        npairs = (n + 1) // 2
+        sb = 4 if storage == "fp32" else 2
+        return 512 * (4 + 8 + (3 + 6 + 6 + 12) * sb + 4 * npairs) + 48, 512 * (4 + 8 + 9 * sb)
+
+    servers = {}
+    for n in bins:
+        ba, bf = brick_bytes(n)
+        cap = int(budget / len(bins) / (ba + bf))
+        servers[n] = tgv.Server(cap, cap, nbins=n, storage=storage, stream=streams[n].cuda_stream,
+                                staging_bytes=64 << 20)
+
+    def req(k, t):
+        sp = specs[k]
+        return Request(k, sp.domain, sp.nbins, sp.iterations, t, lambda sp=sp: synth.chunk_histogram(sp, "cuda"))
+
+    RequestStream(servers, streams).run([req(k, 0.0) for k in range(min(8, nreq))])  # warm-up
+    nsat = max(1, nreq // 2)
+    sat = RequestStream(servers, streams).run([req(k, 0.0) for k in range(nsat)])
+    sat_rate = nsat / sat.makespan
+    rate = 0.8 * sat_rate
+    main = RequestStream(servers, streams).run([req(k, specs[k].arrival / rate) for k in range(nreq)])
+    p = lambda a, q: float(np.percentile(a, q))
+    over = None
+    if overload:
+        o = RequestStream(servers, streams).run([req(k, specs[k].arrival / (2.0 * sat_rate))
+                                                 for k in range(min(nreq, overload))])
+        over = {"requests": o.completed, "p50": p(o.latencies, 50), "p99": p(o.latencies, 99),
+                "voxel_updates_per_s": o.voxel_updates / o.makespan}
+    for s_ in servers.values():
+        s_.close()
+    return {"requests": nreq, "budget_gb": budget_gb, "servers": len(servers), "storage": storage,
+            "arrival_rate_per_s": rate, "saturated_rate_per_s": sat_rate,
+            "latency_s": {"p50": p(main.latencies, 50), "p99": p(main.latencies, 99),
+                          "mean": float(main.latencies.mean()), "max": float(main.latencies.max())},
+            "queue_wait_s": {"p50": p(main.wait, 50), "p99": p(main.wait, 99)},
+            "voxel_updates_per_s": main.voxel_updates / main.makespan, "makespan_s": main.makespan,
+            "saturated_voxel_updates_per_s": sat.voxel_updates / sat.makespan, "max_running": main.max_running,
+            "overload_2x": over, "latencies": main.latencies}
 
 
 def run_batched(args):
@@ -950,73 +1119,29 @@ def run_composite(args):
 
 def run_serving(args):
     """Poisson stream of chunk-solve requests (16k..8M voxels, 8..12 bins, 200..600 iterations)
-    through one server per bin count, arenas sized from the HBM budget."""
+    through one server per bin count, arenas sized from the HBM budget; plus an overload run."""
     import torch
-    import synth
-    from paper_2107_14790_b300 import build, tgv
-    from paper_2107_14790_b300.batching import Request, RequestStream
+    from paper_2107_14790_b300 import build
     build.build()
     torch.cuda.set_device(0)
-    nreq = args.requests
-    specs = synth.chunk_workload(1005, nreq, 16 * 1024, 8 * 1024 * 1024, (8, 12), (200, 600), rate=1.0, hist="none")
-    bins = sorted({sp.nbins for sp in specs})
-    budget = args.budget_gb * 1e9
-    streams = {n: torch.cuda.Stream() for n in bins}
-
-    def brick_bytes(n):
-        npairs = (n + 1) // 2
-        sb = 4 if args.storage == "fp32" else 2
-        return 512 * (4 + 8 + (3 + 6 + 6 + 12) * sb + 4 * npairs) + 48, 512 * (4 + 8 + 9 * sb)
-
-    servers = {}
-    for n in bins:
-        ba, bf = brick_bytes(n)
-        share = budget / len(bins)
-        cap = int(share / (ba + bf))
-        servers[n] = tgv.Server(cap, cap, nbins=n, storage=args.storage, stream=streams[n].cuda_stream,
-                                staging_bytes=64 << 20)
-
-    def make(sp):
-        return lambda: synth.chunk_histogram(sp, "cuda")
-
-    def requests(k0, k1, scale):
-        return [Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, specs[k].arrival * scale, make(specs[k]))
-                for k in range(k0, k1)]
-
-    # saturated throughput: a block of requests all arriving at once
-    nsat = min(200, nreq)
-    warm = RequestStream(servers, streams).run([Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, 0.0,
-                                                        make(specs[k])) for k in range(min(16, nreq))])
-    sat = RequestStream(servers, streams).run([Request(k, specs[k].domain, specs[k].nbins, specs[k].iterations, 0.0,
-                                                       make(specs[k])) for k in range(nsat)])
-    sat_rate = nsat / sat.makespan
-    # the stream at 0.8x the saturated rate (unit-rate arrival times scaled)
-    rate = 0.8 * sat_rate
-    main = RequestStream(servers, streams).run(requests(0, nreq, 1.0 / rate))
-    over = RequestStream(servers, streams).run(requests(0, min(nreq, 400), 1.0 / (2.0 * sat_rate)))
-    for s_ in servers.values():
-        s_.close()
-    p = lambda a, q: float(np.percentile(a, q))
-    vu_main = main.voxel_updates
+    r = serving_block(args.storage, args.requests, args.budget_gb, overload=min(args.requests, 400))
+    r.pop("latencies")
     return {"metric": "chunk-solve serving: p50/p99 latency and voxel-updates/s (Poisson arrivals, 0.8x saturated rate)",
-            "value": vu_main / main.makespan, "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True,
+            "value": r["voxel_updates_per_s"], "unit": "voxel-updates/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32" if args.storage == "fp32" else f"f32-math/{args.storage}-storage",
             "data": "synthetic (seeded chunk requests)",
-            "config": {"workload": "serving-2000-requests-16k..8M-voxels-8..12bins-200..600it",
-                       "requests": nreq, "budget_gb": args.budget_gb, "servers": len(servers),
+            "config": {"workload": "serving-%d-requests-16k..8M-voxels-8..12bins-200..600it" % args.requests,
+                       "requests": args.requests, "budget_gb": args.budget_gb, "servers": r["servers"],
                        "round_iterations": 10},
-            "latency_s": {"p50": p(main.latencies, 50), "p99": p(main.latencies, 99),
-                          "mean": float(main.latencies.mean()), "max": float(main.latencies.max())},
-            "queue_wait_s": {"p50": p(main.wait, 50), "p99": p(main.wait, 99)},
-            "arrival_rate_per_s": rate, "saturated_rate_per_s": sat_rate,
-            "saturated_voxel_updates_per_s": sat.voxel_updates / sat.makespan,
-            "makespan_s": main.makespan, "max_running": main.max_running,
-            "overload_2x": {"requests": over.completed, "p50": p(over.latencies, 50), "p99": p(over.latencies, 99),
-                            "voxel_updates_per_s": over.voxel_updates / over.makespan}}
+            "serving": r}
 
 
 def main():
     args = parse()
+    from paper_2107_14790_b300.multigpu import launched_as_rank, relaunch
+    if args.gpus > 1 and not launched_as_rank():
+        # one process per GPU: start `--gpus` ranks of this same command under torch.distributed.run
+        sys.exit(relaunch(args.gpus, os.path.abspath(__file__), sys.argv[1:]))
     if args.profile:
         run_profile_case(args)
         return

@@ -8,7 +8,11 @@ time and the totals.
 """
 from __future__ import annotations
 
-from typing import List, Sequence
+import os
+import socket
+import subprocess
+import sys
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -43,3 +47,44 @@ def reduce_scalar(value: float, op: str = "max") -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM, "min": dist.ReduceOp.MIN}[op])
     return float(t.item())
+
+
+def free_port() -> int:
+    """A free TCP port on 127.0.0.1 for a rendezvous."""
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def launched_as_rank() -> bool:
+    """True inside a process started by torch.distributed.run (or with WORLD_SIZE set)."""
+    return "WORLD_SIZE" in os.environ
+
+
+def relaunch(nproc: int, script: str, argv: Sequence[str], port: Optional[int] = None,
+             env: Optional[Dict[str, str]] = None) -> int:
+    """Runs `script argv` as `nproc` ranks of one node under torch.distributed.run
+    (rendezvous on 127.0.0.1) and returns the launcher's exit code.  Each rank reads
+    RANK / LOCAL_RANK / WORLD_SIZE / MASTER_ADDR / MASTER_PORT from its environment."""
+    if nproc < 1:
+        raise ValueError("nproc must be >= 1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={int(nproc)}",
+           "--master-addr=127.0.0.1", f"--master-port={int(port or free_port())}", script, *argv]
+    return subprocess.run(cmd, env=dict(os.environ, **(env or {}))).returncode
+
+
+def gather_dict(local: dict) -> dict:
+    """Merges every rank's dict of results on every rank (host objects over the default
+    process group; returns `local` unchanged without one)."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dict(local)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, local)
+    out = {}
+    for p in parts:
+        out.update(p)
+    return out

@@ -61,6 +61,7 @@ def test_u_after_500_iterations_within_1e4(runs):
     _, _, _, gpu, orc, _ = runs
     du = np.abs(gpu["u"][:, 0] - orc.u)
     assert np.abs(orc.u).max() > 0.9  # a converging field, not a trivial one
+    print(f"terrain 128^3, {ITERS} iterations: max |du| = {du.max():.3e}, rms {np.sqrt(np.mean(du ** 2)):.3e}")
     assert du.max() <= 1e-4, f"max |du| = {du.max():.3e} at voxel {int(du.argmax())}"
 
 
@@ -68,6 +69,7 @@ def test_v_p_q_after_500_iterations_within_1e3(runs):
     _, _, _, gpu, orc, _ = runs
     for f, want in (("v", orc.v), ("p", orc.p), ("q", orc.q)):
         d = np.abs(gpu[f] - want).max()
+        print(f"terrain 128^3, {ITERS} iterations: max |d{f}| = {d:.3e}")
         assert np.abs(want).max() > 0.01
         assert d <= 1e-3, f"max |d{f}| = {d:.3e}"
 
@@ -107,4 +109,5 @@ def test_zero_level_set_agrees(runs):
     a = np.array([c[0] for c in common])
     b = np.array([c[1] for c in common])
     disp = np.linalg.norm(pg[a] - po[b], axis=1).max() / h
+    print(f"terrain 128^3, {ITERS} iterations: {len(common)} crossings, max displacement {disp:.2e} h")
     assert disp <= 1e-3, f"crossing displacement {disp:.2e} h"
