@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="64^3 sphere case instead of the 256^3 terrain")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "fx16"])
     ap.add_argument("--iter-kernel", default="paired", choices=["paired", "pipelined", "one_brick_per_cta"])
     ap.add_argument("--x-run", type=int, default=0, help="paired kernel: work items per run (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -784,7 +784,7 @@ def run_precision(args):
     sc = synth.terrain_scene(1002, 256, 64, 512, 10, 500, device="cuda")
     dep2 = torch.from_numpy(np.stack(sc.depths)).cuda()
     ref2 = None
-    for storage in ("fp32", "fp16", "bf16"):
+    for storage in ("fp32", "fx16", "fp16", "bf16"):
         with tgv.Domain([sph.domain], nbins=8, storage=storage, stream=stream.cuda_stream) as dom:
             dom.accumulate(0, sph.cameras, dep1)
             dom.solve(0, 200)
@@ -798,8 +798,8 @@ def run_precision(args):
         res[storage] = {"sphere_64_vs_fp64_oracle": _field_diff(u1, ref1),
                         "terrain_256_vs_fp32": _field_diff(u2, ref2) if storage != "fp32" else None}
     return {"metric": "precision of reduced storage: |du| max / RMS and zero-crossing displacement",
-            "value": res["fp16"]["terrain_256_vs_fp32"]["linf"], "unit": "max |u_fp16 - u_fp32| (terrain)",
-            "n_gpus": 1, "higher_is_better": False, "dtype": "f32-math/fp16,bf16-storage",
+            "value": res["fx16"]["terrain_256_vs_fp32"]["linf"], "unit": "max |u_fx16 - u_fp32| (terrain)",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32-math/fx16,fp16,bf16-storage",
             "data": "synthetic (seeded sphere and terrain scenes)",
             "config": {"workload": "sphere-64^3-200it-vs-oracle+terrain-256^3-500it-vs-fp32"}, "results": res,
             "cpu_baseline": {"value": sph.domain.nvox * 200 / t_cpu, "unit": "voxel-updates/s",

@@ -58,8 +58,13 @@ typedef enum {
     TGV_ERR_UNSUPPORTED = 7    /* a recognised option that is not built */
 } tgv_status;
 
-/* Storage type of v, vbar, p, q (u and ubar are always FP32; arithmetic is FP32). */
-enum { TGV_STORAGE_FP32 = 0, TGV_STORAGE_BF16 = 1, TGV_STORAGE_FP16 = 2 };
+/* Storage type of v, vbar, p, q (u and ubar are always FP32; arithmetic is FP32).
+ * FX16: v and vbar in FP16; p and q as 16-bit fixed point scaled by the radius of the
+ * ball their projection keeps them in (Eq. 2's constraints |p| <= alpha1, |q|_F <=
+ * alpha0): the stored integer is round(x * 32767 / alpha), so the step is alpha / 32767
+ * everywhere in the ball instead of FP16's 2^-11 relative step near its edge.  Same
+ * bytes as FP16; not a form of the paper (which keeps everything in floating point). */
+enum { TGV_STORAGE_FP32 = 0, TGV_STORAGE_BF16 = 1, TGV_STORAGE_FP16 = 2, TGV_STORAGE_FX16 = 3 };
 
 /* Histogram bin centres c_b (the data term sum_b h_b |u - c_b|, Sec. 3.4).
  * ENDPOINTS: c_b = -1 + 2b/(n-1)  (bin 0 = occluded -1, bin n-1 = free space +1)

@@ -180,27 +180,30 @@ __global__ void f32_to_s_kernel(const float* __restrict__ src, S* __restrict__ d
 }
 
 // brick-major [brick][comp][512] storage <-> voxel-major [voxel][comp] float
+// (sc: decode scale of fixed-point duals, ignored by the other storage types)
 template <typename S>
-__global__ void field_extract_kernel(const S* __restrict__ f, float* __restrict__ out, int64_t nvox, int ncomp)
+__global__ void field_extract_kernel(const S* __restrict__ f, float* __restrict__ out, int64_t nvox, int ncomp,
+                                     float sc)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * ncomp;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t vox = i / ncomp;
         const int c = (int)(i - vox * ncomp);
         const int64_t b = vox >> 9, l = vox & 511;
-        out[i] = ld_s(f + (b * ncomp + c) * TGV_BVOX + l);
+        out[i] = ld_d(f + (b * ncomp + c) * TGV_BVOX + l, sc);
     }
 }
 
+// (sc: encode scale of fixed-point duals, ignored by the other storage types)
 template <typename S>
-__global__ void field_set_kernel(S* __restrict__ f, const float* __restrict__ in, int64_t nvox, int ncomp)
+__global__ void field_set_kernel(S* __restrict__ f, const float* __restrict__ in, int64_t nvox, int ncomp, float sc)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvox * ncomp;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t vox = i / ncomp;
         const int c = (int)(i - vox * ncomp);
         const int64_t b = vox >> 9, l = vox & 511;
-        st_s(f + (b * ncomp + c) * TGV_BVOX + l, in[i]);
+        st_d(f + (b * ncomp + c) * TGV_BVOX + l, in[i], sc);
     }
 }
 
@@ -533,7 +536,7 @@ tgv_status tgv_create_domain(const tgv_level_desc* levels, int32_t nlevels, cons
     *out = nullptr;
     if (!levels || nlevels <= 0 || nlevels > 32 || !prm) return TGV_ERR_INVALID_ARG;
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
-    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FX16) return TGV_ERR_INVALID_ARG;
     if (prm->centres != TGV_CENTRES_ENDPOINTS && prm->centres != TGV_CENTRES_MIDPOINTS) return TGV_ERR_INVALID_ARG;
     if (prm->iter_kernel != TGV_ITER_PIPELINED && prm->iter_kernel != TGV_ITER_ONE_BRICK_PER_CTA &&
         prm->iter_kernel != TGV_ITER_PAIRED)
@@ -667,11 +670,16 @@ tgv_status tgv_extract_field(tgv_domain* d, int32_t level, int32_t field, float*
     }
     const void* f = field_ptr(*L, field);
     const bool fp32 = field == TGV_FIELD_U || field == TGV_FIELD_UBAR || d->prm.storage == TGV_STORAGE_FP32;
+    const bool fx = d->prm.storage == TGV_STORAGE_FX16 && (field == TGV_FIELD_P || field == TGV_FIELD_Q);
+    const DualScales ds = tgv_dual_scales(d->prm);
     const unsigned gr = grid1(count, 256, d->sm_count);
-    if (fp32) field_extract_kernel<float><<<gr, 256, 0, d->stream>>>((const float*)f, dst, nvox, nc);
+    if (fp32) field_extract_kernel<float><<<gr, 256, 0, d->stream>>>((const float*)f, dst, nvox, nc, 0.0f);
+    else if (fx)
+        field_extract_kernel<int16_t><<<gr, 256, 0, d->stream>>>((const int16_t*)f, dst, nvox, nc,
+                                                                 field == TGV_FIELD_P ? ds.dsp : ds.dsq);
     else if (d->prm.storage == TGV_STORAGE_BF16)
-        field_extract_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((const __nv_bfloat16*)f, dst, nvox, nc);
-    else field_extract_kernel<__half><<<gr, 256, 0, d->stream>>>((const __half*)f, dst, nvox, nc);
+        field_extract_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((const __nv_bfloat16*)f, dst, nvox, nc, 0.0f);
+    else field_extract_kernel<__half><<<gr, 256, 0, d->stream>>>((const __half*)f, dst, nvox, nc, 0.0f);
     d->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, (size_t)count * 4, cudaMemcpyDeviceToHost, d->stream);
@@ -728,12 +736,17 @@ tgv_status tgv_set_field(tgv_domain* d, int32_t level, int32_t field, const floa
     }
     void* f = field_ptr(*L, field);
     const bool fp32 = field == TGV_FIELD_U || field == TGV_FIELD_UBAR || d->prm.storage == TGV_STORAGE_FP32;
+    const bool fx = d->prm.storage == TGV_STORAGE_FX16 && (field == TGV_FIELD_P || field == TGV_FIELD_Q);
+    const DualScales ds = tgv_dual_scales(d->prm);
     const unsigned gr = grid1(count, 256, d->sm_count);
     if (e == cudaSuccess) {
-        if (fp32) field_set_kernel<float><<<gr, 256, 0, d->stream>>>((float*)f, src, nvox, nc);
+        if (fp32) field_set_kernel<float><<<gr, 256, 0, d->stream>>>((float*)f, src, nvox, nc, 0.0f);
+        else if (fx)
+            field_set_kernel<int16_t><<<gr, 256, 0, d->stream>>>((int16_t*)f, src, nvox, nc,
+                                                                 field == TGV_FIELD_P ? ds.isp : ds.isq);
         else if (d->prm.storage == TGV_STORAGE_BF16)
-            field_set_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((__nv_bfloat16*)f, src, nvox, nc);
-        else field_set_kernel<__half><<<gr, 256, 0, d->stream>>>((__half*)f, src, nvox, nc);
+            field_set_kernel<__nv_bfloat16><<<gr, 256, 0, d->stream>>>((__nv_bfloat16*)f, src, nvox, nc, 0.0f);
+        else field_set_kernel<__half><<<gr, 256, 0, d->stream>>>((__half*)f, src, nvox, nc, 0.0f);
         d->launches++;
         e = cudaGetLastError();
     }

@@ -69,6 +69,33 @@ template <> __device__ __forceinline__ void st_s<__half>(__half* p, float x) { *
 
 inline size_t storage_bytes(int storage) { return storage == TGV_STORAGE_FP32 ? 4 : 2; }
 
+// ---------------------------------------------------------------- dual storage
+// p and q are stored in the form's storage type, except in TGV_STORAGE_FX16: there they
+// are 16-bit fixed point, the integer round(x * 32767 / bound) with bound = alpha1 for p
+// and alpha0 for q (the radii of the balls the projections keep them in, so every
+// component fits).  dsc = bound / 32767 decodes, isc = 32767 / bound encodes; both are
+// ignored by the other storage types.
+__device__ __forceinline__ int16_t fx16_encode(float x, float isc)
+{
+    const float y = fminf(fmaxf(__fmul_rn(x, isc), -32767.0f), 32767.0f);
+    return (int16_t)__float2int_rn(y);
+}
+__device__ __forceinline__ float fx16_decode(int16_t i, float dsc) { return __fmul_rn((float)i, dsc); }
+
+template <typename D> __device__ __forceinline__ float ld_d(const D* p, float /*dsc*/) { return ld_s(p); }
+template <> __device__ __forceinline__ float ld_d<int16_t>(const int16_t* p, float dsc) { return fx16_decode(*p, dsc); }
+template <typename D> __device__ __forceinline__ void st_d(D* p, float x, float /*isc*/) { st_s(p, x); }
+template <> __device__ __forceinline__ void st_d<int16_t>(int16_t* p, float x, float isc) { *p = fx16_encode(x, isc); }
+
+// decode / encode scales of p and q for a parameter set
+struct DualScales {
+    float dsp, dsq, isp, isq;
+};
+inline DualScales tgv_dual_scales(const tgv_params& prm)
+{
+    return {prm.alpha1 / 32767.0f, prm.alpha0 / 32767.0f, 32767.0f / prm.alpha1, 32767.0f / prm.alpha0};
+}
+
 // ---------------------------------------------------------------- host state
 struct TgvLevel {
     int64_t nb = 0, nf = 0;  // active and frozen bricks
@@ -107,8 +134,9 @@ struct TgvLevel {
     int64_t xrun_slots = 0;
 };
 
-// Arguments of one fused primal-dual iteration over the active bricks of a level.
-template <typename S>
+// Arguments of one fused primal-dual iteration over the active bricks of a level
+// (S: storage type of v and vbar; D: of p and q).
+template <typename S, typename D = S>
 struct IterArgs {
     float* u;
     const float* ubar_in;
@@ -116,10 +144,10 @@ struct IterArgs {
     S* v;
     const S* vbar_in;
     S* vbar_out;
-    const S* p_in;
-    S* p_out;
-    const S* q_in;
-    S* q_out;
+    const D* p_in;
+    D* p_out;
+    const D* q_in;
+    D* q_out;
     const uint32_t* hist;
     const int32_t* nbr;
     const int32_t* work;  // work item -> active brick (nullptr: item i is brick i)
@@ -128,6 +156,7 @@ struct IterArgs {
     int64_t nall;  // active + frozen bricks (stride of the in-place fields' brick index)
     int nbins, npairs, clamp_u;
     float alpha1, alpha0, tau, sigma, taulam;
+    DualScales ds;          // fixed-point scales of p and q (TGV_STORAGE_FX16)
     float c[TGV_MAX_BINS];  // bin centres
 };
 
@@ -180,10 +209,10 @@ tgv_status tgv_exclusive_scan_u32(tgv_domain* d, uint32_t* data, int64_t n, TgvS
 inline int64_t tgv_work_items(const TgvLevel& L) { return L.work ? L.nwork : L.nb; }
 
 // Iteration arguments for the current ping-pong copy of a level.
-template <typename S>
-inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
+template <typename S, typename D = S>
+inline IterArgs<S, D> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
 {
-    IterArgs<S> A;
+    IterArgs<S, D> A;
     const int c = L.cur, o = 1 - L.cur;
     A.u = L.u;
     A.ubar_in = L.ubar[c];
@@ -191,10 +220,10 @@ inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
     A.v = (S*)L.v;
     A.vbar_in = (const S*)L.vbar[c];
     A.vbar_out = (S*)L.vbar[o];
-    A.p_in = (const S*)L.p[c];
-    A.p_out = (S*)L.p[o];
-    A.q_in = (const S*)L.q[c];
-    A.q_out = (S*)L.q[o];
+    A.p_in = (const D*)L.p[c];
+    A.p_out = (D*)L.p[o];
+    A.q_in = (const D*)L.q[c];
+    A.q_out = (D*)L.q[o];
     A.hist = L.hist;
     A.nbr = L.nbr;
     A.work = L.work;
@@ -209,6 +238,7 @@ inline IterArgs<S> tgv_make_iter_args(tgv_domain* d, TgvLevel& L)
     A.tau = d->prm.tau;
     A.sigma = d->prm.sigma;
     A.taulam = d->prm.tau * d->prm.lambda;
+    A.ds = tgv_dual_scales(d->prm);
     tgv_bin_centres(d->prm, A.c);
     return A;
 }

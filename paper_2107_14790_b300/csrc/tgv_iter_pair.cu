@@ -71,6 +71,24 @@ template <> struct Pair<__half> {
     static __device__ __forceinline__ void st(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
 };
 
+// pairs of dual values (p, q): the storage type's pair, or two 16-bit fixed-point values
+// in one 32-bit word (TGV_STORAGE_FX16; sc = the decode or encode scale)
+template <typename D> struct DPair {
+    static __device__ __forceinline__ float2 ld(const D* p, float /*dsc*/) { return Pair<D>::ld(p); }
+    static __device__ __forceinline__ void st(D* p, float2 v, float /*isc*/) { Pair<D>::st(p, v); }
+};
+template <> struct DPair<int16_t> {
+    static __device__ __forceinline__ float2 ld(const int16_t* p, float dsc)
+    {
+        const uint32_t w = *(const uint32_t*)p;
+        return make_float2(fx16_decode((int16_t)(w & 0xffffu), dsc), fx16_decode((int16_t)(w >> 16), dsc));
+    }
+    static __device__ __forceinline__ void st(int16_t* p, float2 v, float isc)
+    {
+        *(uint32_t*)p = (uint32_t)(uint16_t)fx16_encode(v.x, isc) | ((uint32_t)(uint16_t)fx16_encode(v.y, isc) << 16);
+    }
+};
+
 __device__ __forceinline__ float2 ldf2(const float* p) { return *(const float2*)p; }
 __device__ __forceinline__ void stf2(float* p, float2 v) { *(float2*)p = v; }
 
@@ -178,9 +196,9 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
 
 }  // namespace
 
-template <typename S>
+template <typename S, typename D>
 struct PairArgs {
-    IterArgs<S> it;
+    IterArgs<S, D> it;
     int* err;
     long long wait_budget;             // cycles per wait for a stage (tgv_params.wait_cycles)
     int wait_test;                     // 1: the prologue waits on a barrier nothing completes
@@ -207,17 +225,18 @@ struct PairArgs {
 //   * task 3 of brick i is skipped: phase B of brick i parks the partial div2 q sum of
 //     its x = 7 voxels in hal_q[qidx(0,c)][y+8z] of its own stage (the slots task 3
 //     would have filled); phase A of brick i+1 adds its new q and stores v, vbar.
-template <typename S, int NB>
+template <typename S, typename D, int NB>
 struct PairCta {
     using PS = Pair<S>;
-    static constexpr uint32_t SB = sizeof(S);
+    using DP = DPair<D>;
+    static constexpr uint32_t SB = sizeof(S), SD = sizeof(D);
     static constexpr uint32_t O_U = 0, O_UB = 2048, O_V = 4096, O_VB = O_V + 3 * 512 * SB,
-                              O_P = O_VB + 3 * 512 * SB, O_Q = O_P + 3 * 512 * SB, O_H = O_Q + 6 * 512 * SB;
+                              O_P = O_VB + 3 * 512 * SB, O_Q = O_P + 3 * 512 * SD, O_H = O_Q + 6 * 512 * SD;
     static constexpr int NP_MAX = NB ? (NB + 1) / 2 : TGV_MAX_BINS / 2;
     static constexpr int NB_MAX = NB ? NB : TGV_MAX_BINS;
 
-    const PairArgs<S>& P;
-    const IterArgs<S>& A;
+    const PairArgs<S, D>& P;
+    const IterArgs<S, D>& A;
     unsigned char* smem;
     int t, j, y, z, x0, task, tk, nbk, nbins, npairs;
     uint32_t l0;
@@ -232,7 +251,7 @@ struct PairCta {
     uint32_t hm;
     int hn;
 
-    __device__ __forceinline__ PairCta(const PairArgs<S>& p, unsigned char* sm)
+    __device__ __forceinline__ PairCta(const PairArgs<S, D>& p, unsigned char* sm)
         : P(p), A(p.it), smem(sm)
     {
         t = threadIdx.x;
@@ -256,11 +275,11 @@ struct PairCta {
     __device__ __forceinline__ unsigned char* stage(int s) const { return smem + (size_t)s * P.stage_bytes; }
     __device__ __forceinline__ float* pn_own(int s) const
     {
-        return (float*)(SB == 4 ? stage(s) + O_P : smem + P.off_pn + (size_t)s * P.pn_bytes);
+        return (float*)(SD == 4 ? stage(s) + O_P : smem + P.off_pn + (size_t)s * P.pn_bytes);
     }
     __device__ __forceinline__ float* qn_own(int s) const
     {
-        return (float*)(SB == 4 ? stage(s) + O_Q : smem + P.off_pn + (size_t)s * P.pn_bytes + 3 * 512 * 4);
+        return (float*)(SD == 4 ? stage(s) + O_Q : smem + P.off_pn + (size_t)s * P.pn_bytes + 3 * 512 * 4);
     }
     __device__ __forceinline__ float* hal_p(int s) const { return (float*)(smem + P.off_hal) + s * (9 * 192); }
     __device__ __forceinline__ float* hal_q(int s) const { return hal_p(s) + 3 * 192; }
@@ -276,8 +295,8 @@ struct PairCta {
         bulk_copy_g2s(st + O_UB, A.ubar_in + (size_t)brick * TGV_BVOX, 2048, b);
         bulk_copy_g2s(st + O_V, A.v + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
         bulk_copy_g2s(st + O_VB, A.vbar_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SB, b);
+        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SD, b);
+        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SD, b);
         bulk_copy_g2s(st + O_H, A.hist + brick * (size_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, b);
     }
 
@@ -344,7 +363,7 @@ struct PairCta {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
-                h[12 + 2 * c] = ld_s(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+                h[12 + 2 * c] = ld_d(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh, A.ds.dsp);
             }
         } else if (task == 1 || task == 2) {  // -y / -z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 1) or y (task 2)
@@ -382,7 +401,7 @@ struct PairCta {
                 float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
                 h[6 + 2 * c] = w.x;
                 h[7 + 2 * c] = w.y;
-                w = PS::ld(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+                w = DP::ld(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh, A.ds.dsp);
                 h[12 + 2 * c] = w.x;
                 h[13 + 2 * c] = w.y;
             }
@@ -412,7 +431,7 @@ struct PairCta {
                 hm |= 2u;
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_s(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh);
+            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_d(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh, A.ds.dsq);
         } else {  // task 4 / 5: +y / +z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 4) or y (task 5)
             const uint32_t lh = task == 4 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;
@@ -457,7 +476,7 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const float2 w = PS::ld(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh);
+                const float2 w = DP::ld(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh, A.ds.dsq);
                 h[18 + 2 * c] = w.x;
                 h[19 + 2 * c] = w.y;
             }
@@ -476,8 +495,8 @@ struct PairCta {
         unsigned char* st = stage(s);
         const float* sub = (const float*)(st + O_UB);
         const S* svb = (const S*)(st + O_VB);
-        const S* sp = (const S*)(st + O_P);
-        const S* sq = (const S*)(st + O_Q);
+        const D* sp = (const D*)(st + O_P);
+        const D* sq = (const D*)(st + O_Q);
         const float2 ub = ldf2(sub + l0);
         float vb0[3], vb1[3], pn0[3], pn1[3], qn0[6], qn1[6];
 #pragma unroll
@@ -485,13 +504,13 @@ struct PairCta {
             float2 w = PS::ld(svb + c * 512 + l0);
             vb0[c] = w.x;
             vb1[c] = w.y;
-            w = PS::ld(sp + c * 512 + l0);
+            w = DP::ld(sp + c * 512 + l0, A.ds.dsp);
             pn0[c] = w.x;
             pn1[c] = w.y;
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float2 w = PS::ld(sq + c * 512 + l0);
+            const float2 w = DP::ld(sq + c * 512 + l0, A.ds.dsq);
             qn0[c] = w.x;
             qn1[c] = w.y;
         }
@@ -752,10 +771,11 @@ struct PairCta {
                 PS::st(A.v + oi, make_float2(v1a, v1b));
                 PS::st(A.vbar_out + oi, make_float2(vba, vbar_of(v1b, v0.y)));
             }
-            PS::st(A.p_out + oi, make_float2(pn0[c], pn1[c]));
+            DP::st(A.p_out + oi, make_float2(pn0[c], pn1[c]), A.ds.isp);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) PS::st(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
+        for (int c = 0; c < 6; ++c)
+            DP::st(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]), A.ds.isq);
     }
 };
 
@@ -763,11 +783,11 @@ struct PairCta {
 // consecutive items each): in one barrier interval a CTA finishes item i (phase
 // B) and starts the next item (its halo loads are issued first, so their
 // latency overlaps phase B; then phase A once its stage has landed).
-template <typename S, int NB>
-__global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairArgs<S> P)
+template <typename S, typename D, int NB>
+__global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairArgs<S, D> P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    PairCta<S, NB> C(P, smem);
+    PairCta<S, D, NB> C(P, smem);
     const uint32_t G = gridDim.x;
     const uint32_t R = P.xrun;
     const uint32_t nit = (uint32_t)P.it.nitems;
@@ -957,16 +977,16 @@ int pair_run_length(const int32_t* nbr, int64_t nb, const int32_t* work, int64_t
     return best;
 }
 
-template <typename S, int NB>
+template <typename S, typename D, int NB>
 tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
 {
-    const uint32_t SB = sizeof(S);
+    const uint32_t SB = sizeof(S), SD = sizeof(D);
     const int npairs = (d->prm.nbins + 1) / 2;
-    const uint32_t stage = (uint32_t)((4096 + 15 * 512 * SB + npairs * 2048 + 127) / 128 * 128);
-    const uint32_t tx = 4096 + 15 * 512 * SB + npairs * 2048;
+    const uint32_t tx = 4096 + (6 * SB + 9 * SD) * 512 + npairs * 2048;
+    const uint32_t stage = (tx + 127) / 128 * 128;
     uint32_t off = 2 * stage;
-    PairArgs<S> P;
-    P.pn_bytes = SB == 4 ? 0 : 9 * 512 * 4;
+    PairArgs<S, D> P;
+    P.pn_bytes = SD == 4 ? 0 : 9 * 512 * 4;
     P.off_pn = off;
     off += 2 * P.pn_bytes;
     P.off_hal = off;
@@ -977,7 +997,7 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     P.off_bar = off;
     off += 3 * 8;
     const size_t smem = off;
-    auto kern = tgv_iter_pair_kernel<S, NB>;
+    auto kern = tgv_iter_pair_kernel<S, D, NB>;
     int per_sm = 0;
     tgv_status st = tgv_kernel_setup((const void*)kern, kThreads, smem, &per_sm);
     if (st != TGV_OK) return tgv_fail(d, st, "pair kernel setup (shared memory attribute / occupancy) failed");
@@ -1003,7 +1023,7 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     P.stage_bytes = stage;
     P.tx_bytes = tx;
     for (int it = 0; it < iters; ++it) {
-        P.it = tgv_make_iter_args<S>(d, L);
+        P.it = tgv_make_iter_args<S, D>(d, L);
         kern<<<(unsigned)grid, kThreads, smem, d->stream>>>(P);
         d->launches++;
         L.cur ^= 1;
@@ -1011,14 +1031,14 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     return tgv_cuda_check(d, cudaGetLastError(), "tgv_iter_pair_kernel launch");
 }
 
-template <typename S>
+template <typename S, typename D = S>
 tgv_status launch_pair_bins(tgv_domain* d, TgvLevel& L, int iters)
 {
     switch (d->prm.nbins) {
-    case 8: return launch_pair_t<S, 8>(d, L, iters);
-    case 10: return launch_pair_t<S, 10>(d, L, iters);
-    case 12: return launch_pair_t<S, 12>(d, L, iters);
-    default: return launch_pair_t<S, 0>(d, L, iters);
+    case 8: return launch_pair_t<S, D, 8>(d, L, iters);
+    case 10: return launch_pair_t<S, D, 10>(d, L, iters);
+    case 12: return launch_pair_t<S, D, 12>(d, L, iters);
+    default: return launch_pair_t<S, D, 0>(d, L, iters);
     }
 }
 
@@ -1031,6 +1051,7 @@ tgv_status tgv_launch_iterations_pair(tgv_domain* d, TgvLevel& L, int iters)
     case TGV_STORAGE_FP32: return launch_pair_bins<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_pair_bins<__nv_bfloat16>(d, L, iters);
     case TGV_STORAGE_FP16: return launch_pair_bins<__half>(d, L, iters);
+    case TGV_STORAGE_FX16: return launch_pair_bins<__half, int16_t>(d, L, iters);
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
 }
@@ -1039,7 +1060,7 @@ extern "C" TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nb
                                           int64_t slots, int32_t storage, int32_t* run_length)
 {
     if (!nbr || nbricks <= 0 || slots <= 0 || !run_length || (work && nwork < 0)) return TGV_ERR_INVALID_ARG;
-    if (storage < TGV_STORAGE_FP32 || storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (storage < TGV_STORAGE_FP32 || storage > TGV_STORAGE_FX16) return TGV_ERR_INVALID_ARG;
     const int64_t n = work ? nwork : nbricks;
     if (work) {
         std::vector<uint8_t> seen((size_t)nbricks, 0);

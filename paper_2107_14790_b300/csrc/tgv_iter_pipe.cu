@@ -39,8 +39,8 @@ template <int A> struct FaceAxes {
 };
 
 // ---- halo p on the -A face: voxel (coordinate 7 along A in brick n); loads before the stage wait
-template <typename S, int A>
-__device__ __forceinline__ void halo_p_load(const IterArgs<S>& P, const int* nrow, uint32_t n, int k, float hr[15],
+template <typename S, typename D, int A>
+__device__ __forceinline__ void halo_p_load(const IterArgs<S, D>& P, const int* nrow, uint32_t n, int k, float hr[15],
                                             uint32_t& hmask)
 {
     constexpr int B1 = FaceAxes<A>::B1, B2 = FaceAxes<A>::B2;
@@ -71,12 +71,12 @@ __device__ __forceinline__ void halo_p_load(const IterArgs<S>& P, const int* nro
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         hr[3 + c] = ld_s(P.vbar_in + ((size_t)n * 3 + c) * TGV_BVOX + lh);
-        hr[6 + c] = ld_s(P.p_in + ((size_t)n * 3 + c) * TGV_BVOX + lh);
+        hr[6 + c] = ld_d(P.p_in + ((size_t)n * 3 + c) * TGV_BVOX + lh, P.ds.dsp);
     }
 }
 
-template <typename S, int A>
-__device__ __forceinline__ void halo_p_compute(const IterArgs<S>& P, const float* sub, float* hal_p, int k,
+template <typename S, typename D, int A>
+__device__ __forceinline__ void halo_p_compute(const IterArgs<S, D>& P, const float* sub, float* hal_p, int k,
                                                const float hr[15], uint32_t hmask, float a1sq)
 {
     constexpr int B1 = FaceAxes<A>::B1, B2 = FaceAxes<A>::B2;
@@ -101,8 +101,8 @@ __device__ __forceinline__ void halo_p_compute(const IterArgs<S>& P, const float
 }
 
 // ---- halo q on the +A face: voxel (coordinate 0 along A in brick n)
-template <typename S, int A>
-__device__ __forceinline__ void halo_q_load(const IterArgs<S>& P, const int* nrow, uint32_t n, int k, float hr[15],
+template <typename S, typename D, int A>
+__device__ __forceinline__ void halo_q_load(const IterArgs<S, D>& P, const int* nrow, uint32_t n, int k, float hr[15],
                                             uint32_t& hmask)
 {
     constexpr int B1 = FaceAxes<A>::B1, B2 = FaceAxes<A>::B2;
@@ -137,11 +137,11 @@ __device__ __forceinline__ void halo_q_load(const IterArgs<S>& P, const int* nro
         }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) hr[9 + c] = ld_s(P.q_in + ((size_t)n * 6 + c) * TGV_BVOX + lh);
+    for (int c = 0; c < 6; ++c) hr[9 + c] = ld_d(P.q_in + ((size_t)n * 6 + c) * TGV_BVOX + lh, P.ds.dsq);
 }
 
-template <typename S, int A>
-__device__ __forceinline__ void halo_q_compute(const IterArgs<S>& P, const S* svb, float* hal_q, int k,
+template <typename S, typename D, int A>
+__device__ __forceinline__ void halo_q_compute(const IterArgs<S, D>& P, const S* svb, float* hal_q, int k,
                                                const float hr[15], uint32_t hmask, float a0sq)
 {
     constexpr int B1 = FaceAxes<A>::B1, B2 = FaceAxes<A>::B2;
@@ -170,9 +170,9 @@ __device__ __forceinline__ void halo_q_compute(const IterArgs<S>& P, const S* sv
 
 }  // namespace
 
-template <typename S>
+template <typename S, typename D>
 struct PipeArgs {
-    IterArgs<S> it;
+    IterArgs<S, D> it;
     int* err;              // set to 1 when a bounded wait gives up
     long long wait_budget; // clock cycles per wait
     uint32_t stage_bytes;  // bytes of one stage (multiple of 128)
@@ -182,14 +182,14 @@ struct PipeArgs {
     uint32_t off_nbr, off_bar;    // neighbour rows [2][12], mbarriers [2]
 };
 
-template <typename S, int NB>
-__global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S> P)
+template <typename S, typename D, int NB>
+__global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S, D> P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const IterArgs<S>& A = P.it;
-    constexpr uint32_t SB = sizeof(S);
+    const IterArgs<S, D>& A = P.it;
+    constexpr uint32_t SB = sizeof(S), SD = sizeof(D);
     constexpr uint32_t O_U = 0, O_UB = 2048, O_V = 4096, O_VB = O_V + 3 * 512 * SB, O_P = O_VB + 3 * 512 * SB,
-                       O_Q = O_P + 3 * 512 * SB, O_H = O_Q + 6 * 512 * SB;
+                       O_Q = O_P + 3 * 512 * SD, O_H = O_Q + 6 * 512 * SD;
     constexpr int NP_MAX = NB ? (NB + 1) / 2 : TGV_MAX_BINS / 2;
     constexpr int NB_MAX = NB ? NB : TGV_MAX_BINS;
     const int nbins = NB ? NB : A.nbins;
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         bulk_copy_g2s(st + O_UB, A.ubar_in + (size_t)brick * TGV_BVOX, 2048, &bar[s]);
         bulk_copy_g2s(st + O_V, A.v + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
         bulk_copy_g2s(st + O_VB, A.vbar_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, &bar[s]);
-        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SB, &bar[s]);
+        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SD, &bar[s]);
+        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SD, &bar[s]);
         bulk_copy_g2s(st + O_H, A.hist + brick * (size_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, &bar[s]);
     };
 
@@ -284,13 +284,13 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         for (int k = 0; k < 15; ++k) hr[k] = 0.0f;
         if (hn >= 0) {
             if (ptask) {
-                if (ha == 0) halo_p_load<S, 0>(A, nrow, (uint32_t)hn, hk, hr, hmask);
-                else if (ha == 1) halo_p_load<S, 1>(A, nrow, (uint32_t)hn, hk, hr, hmask);
-                else halo_p_load<S, 2>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                if (ha == 0) halo_p_load<S, D, 0>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                else if (ha == 1) halo_p_load<S, D, 1>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                else halo_p_load<S, D, 2>(A, nrow, (uint32_t)hn, hk, hr, hmask);
             } else {
-                if (ha == 0) halo_q_load<S, 0>(A, nrow, (uint32_t)hn, hk, hr, hmask);
-                else if (ha == 1) halo_q_load<S, 1>(A, nrow, (uint32_t)hn, hk, hr, hmask);
-                else halo_q_load<S, 2>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                if (ha == 0) halo_q_load<S, D, 0>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                else if (ha == 1) halo_q_load<S, D, 1>(A, nrow, (uint32_t)hn, hk, hr, hmask);
+                else halo_q_load<S, D, 2>(A, nrow, (uint32_t)hn, hk, hr, hmask);
             }
         }
         // neighbour row of the next brick of this CTA (its previous user finished at the last barrier)
@@ -308,11 +308,11 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         const float* sub = (const float*)(st + O_UB);
         const S* sv = (const S*)(st + O_V);
         const S* svb = (const S*)(st + O_VB);
-        const S* sp = (const S*)(st + O_P);
-        const S* sq = (const S*)(st + O_Q);
+        const D* sp = (const D*)(st + O_P);
+        const D* sq = (const D*)(st + O_Q);
         const uint32_t* sh = (const uint32_t*)(st + O_H);
-        float* pn_own = (float*)(SB == 4 ? st + O_P : smem + P.off_pn);
-        float* qn_own = (float*)(SB == 4 ? st + O_Q : smem + P.off_qn);
+        float* pn_own = (float*)(SD == 4 ? st + O_P : smem + P.off_pn);
+        float* qn_own = (float*)(SD == 4 ? st + O_Q : smem + P.off_qn);
 
         // ---- phase A: dual ascent + projection at the own voxel
         const float ub = sub[t];
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
                     dm[a][c] = (bmask >> a) & 1u ? vb[c] - w : 0.0f;
                 }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) pn[c] = ld_s(sp + c * 512 + t) + A.sigma * (g[c] - vb[c]);
+            for (int c = 0; c < 3; ++c) pn[c] = ld_d(sp + c * 512 + t, A.ds.dsp) + A.sigma * (g[c] - vb[c]);
             const float pn2 = pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2];
             if (pn2 > a1sq) {
                 const float sc = A.alpha1 * rsqrtf(pn2);
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
             qn[4] = 0.5f * (dm[0][2] + dm[2][0]);
             qn[5] = 0.5f * (dm[1][2] + dm[2][1]);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) qn[c] = ld_s(sq + c * 512 + t) + A.sigma * qn[c];
+            for (int c = 0; c < 6; ++c) qn[c] = ld_d(sq + c * 512 + t, A.ds.dsq) + A.sigma * qn[c];
             const float qn2 =
                 qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + 2.0f * (qn[3] * qn[3] + qn[4] * qn[4] + qn[5] * qn[5]);
             if (qn2 > a0sq) {
@@ -369,13 +369,13 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
         // ---- halo duals
         if (hn >= 0) {
             if (ptask) {
-                if (ha == 0) halo_p_compute<S, 0>(A, sub, hal_p, hk, hr, hmask, a1sq);
-                else if (ha == 1) halo_p_compute<S, 1>(A, sub, hal_p, hk, hr, hmask, a1sq);
-                else halo_p_compute<S, 2>(A, sub, hal_p, hk, hr, hmask, a1sq);
+                if (ha == 0) halo_p_compute<S, D, 0>(A, sub, hal_p, hk, hr, hmask, a1sq);
+                else if (ha == 1) halo_p_compute<S, D, 1>(A, sub, hal_p, hk, hr, hmask, a1sq);
+                else halo_p_compute<S, D, 2>(A, sub, hal_p, hk, hr, hmask, a1sq);
             } else {
-                if (ha == 0) halo_q_compute<S, 0>(A, svb, hal_q, hk, hr, hmask, a0sq);
-                else if (ha == 1) halo_q_compute<S, 1>(A, svb, hal_q, hk, hr, hmask, a0sq);
-                else halo_q_compute<S, 2>(A, svb, hal_q, hk, hr, hmask, a0sq);
+                if (ha == 0) halo_q_compute<S, D, 0>(A, svb, hal_q, hk, hr, hmask, a0sq);
+                else if (ha == 1) halo_q_compute<S, D, 1>(A, svb, hal_q, hk, hr, hmask, a0sq);
+                else halo_q_compute<S, D, 2>(A, svb, hal_q, hk, hr, hmask, a0sq);
             }
         }
         __syncthreads();
@@ -434,10 +434,10 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
             const float v1 = v0 + A.tau * (pn[c] + div2[c]);
             st_s(A.v + oi, v1);
             st_s(A.vbar_out + oi, 2.0f * v1 - v0);
-            st_s(A.p_out + oi, pn[c]);
+            st_d(A.p_out + oi, pn[c], A.ds.isp);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) st_s(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + t, qn[c]);
+        for (int c = 0; c < 6; ++c) st_d(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + t, qn[c], A.ds.isq);
 
         // ---- every thread is done with stage s: refill it with brick b + 2G
         __syncthreads();
@@ -457,16 +457,16 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_pipe_kernel(const PipeArgs<S>
 
 namespace {
 
-template <typename S, int NB>
+template <typename S, typename D, int NB>
 tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
 {
-    const uint32_t SB = sizeof(S);
+    const uint32_t SB = sizeof(S), SD = sizeof(D);
     const int npairs = (d->prm.nbins + 1) / 2;
-    const uint32_t stage = (uint32_t)((4096 + 15 * 512 * SB + npairs * 2048 + 127) / 128 * 128);
-    const uint32_t tx = 4096 + 15 * 512 * SB + npairs * 2048;
+    const uint32_t tx = 4096 + (6 * SB + 9 * SD) * 512 + npairs * 2048;
+    const uint32_t stage = (tx + 127) / 128 * 128;
     uint32_t off = 2 * stage;
-    PipeArgs<S> P;
-    if (SB == 4) {
+    PipeArgs<S, D> P;
+    if (SD == 4) {
         P.off_pn = P.off_qn = 0;
     } else {
         P.off_pn = off;
@@ -484,7 +484,7 @@ tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
     P.off_bar = off;
     off += 2 * 8;
     const size_t smem = off;
-    auto kern = tgv_iter_pipe_kernel<S, NB>;
+    auto kern = tgv_iter_pipe_kernel<S, D, NB>;
     int per_sm = 0;
     tgv_status st = tgv_kernel_setup((const void*)kern, TGV_BVOX, smem, &per_sm);
     if (st != TGV_OK) return tgv_fail(d, st, "pipe kernel setup (shared memory attribute / occupancy) failed");
@@ -496,7 +496,7 @@ tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
     P.stage_bytes = stage;
     P.tx_bytes = tx;
     for (int it = 0; it < iters; ++it) {
-        P.it = tgv_make_iter_args<S>(d, L);
+        P.it = tgv_make_iter_args<S, D>(d, L);
         kern<<<(unsigned)grid, TGV_BVOX, smem, d->stream>>>(P);
         d->launches++;
         L.cur ^= 1;
@@ -504,14 +504,14 @@ tgv_status launch_pipe_t(tgv_domain* d, TgvLevel& L, int iters)
     return tgv_cuda_check(d, cudaGetLastError(), "tgv_iter_pipe_kernel launch");
 }
 
-template <typename S>
+template <typename S, typename D = S>
 tgv_status launch_pipe_bins(tgv_domain* d, TgvLevel& L, int iters)
 {
     switch (d->prm.nbins) {
-    case 8: return launch_pipe_t<S, 8>(d, L, iters);
-    case 10: return launch_pipe_t<S, 10>(d, L, iters);
-    case 12: return launch_pipe_t<S, 12>(d, L, iters);
-    default: return launch_pipe_t<S, 0>(d, L, iters);
+    case 8: return launch_pipe_t<S, D, 8>(d, L, iters);
+    case 10: return launch_pipe_t<S, D, 10>(d, L, iters);
+    case 12: return launch_pipe_t<S, D, 12>(d, L, iters);
+    default: return launch_pipe_t<S, D, 0>(d, L, iters);
     }
 }
 
@@ -527,6 +527,7 @@ tgv_status tgv_launch_iterations_pipe(tgv_domain* d, TgvLevel& L, int iters)
     case TGV_STORAGE_FP32: return launch_pipe_bins<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_pipe_bins<__nv_bfloat16>(d, L, iters);
     case TGV_STORAGE_FP16: return launch_pipe_bins<__half>(d, L, iters);
+    case TGV_STORAGE_FX16: return launch_pipe_bins<__half, int16_t>(d, L, iters);
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
 }

@@ -49,7 +49,7 @@ extern "C" tgv_status tgv_energy_noalloc(const tgv_state_view* s, const tgv_para
     if (!s || !prm || !out) return TGV_ERR_INVALID_ARG;
     if (s->nbricks < 0 || s->nall < s->nbricks) return TGV_ERR_INVALID_ARG;
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
-    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FX16) return TGV_ERR_INVALID_ARG;
     if (prm->centres != TGV_CENTRES_ENDPOINTS && prm->centres != TGV_CENTRES_MIDPOINTS) return TGV_ERR_INVALID_ARG;
     if (!(prm->box_v > 0.0f)) return TGV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;

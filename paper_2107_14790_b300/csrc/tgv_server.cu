@@ -203,7 +203,7 @@ tgv_status tgv_server_create(const tgv_server_cfg* cfg, const tgv_params* prm, v
     if (!cfg || !prm || !stream) return TGV_ERR_INVALID_ARG;
     if (cfg->capacity_bricks <= 0 || cfg->capacity_frozen < 0) return TGV_ERR_INVALID_ARG;
     if (prm->nbins < 2 || prm->nbins > TGV_MAX_BINS) return TGV_ERR_INVALID_ARG;
-    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FP16) return TGV_ERR_INVALID_ARG;
+    if (prm->storage < TGV_STORAGE_FP32 || prm->storage > TGV_STORAGE_FX16) return TGV_ERR_INVALID_ARG;
     if (prm->x_run < 0 || prm->x_run > 64) return TGV_ERR_INVALID_ARG;
     if (prm->hist_form != TGV_HIST_GATHER && prm->hist_form != TGV_HIST_SCATTER) return TGV_ERR_INVALID_ARG;
     tgv_server* s = new (std::nothrow) tgv_server();

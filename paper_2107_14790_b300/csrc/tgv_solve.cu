@@ -55,8 +55,8 @@ __device__ __forceinline__ int qi(int a, int b)
 
 }  // namespace
 
-template <typename S>
-__global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
+template <typename S, typename D>
+__global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S, D> A)
 {
     __shared__ float s_ub[TGV_BVOX];
     __shared__ float s_vb[3][TGV_BVOX];
@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
             }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) pn[c] = ld_s(A.p_in + (b * 3 + c) * TGV_BVOX + t) + A.sigma * (g[c] - vb[c]);
+        for (int c = 0; c < 3; ++c) pn[c] = ld_d(A.p_in + (b * 3 + c) * TGV_BVOX + t, A.ds.dsp) + A.sigma * (g[c] - vb[c]);
         proj3(pn, A.alpha1);
         float e[6] = {dm[0][0], dm[1][1], dm[2][2], 0.5f * (dm[0][1] + dm[1][0]), 0.5f * (dm[0][2] + dm[2][0]),
                       0.5f * (dm[1][2] + dm[2][1])};
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qn[c] = ld_s(A.q_in + (b * 6 + c) * TGV_BVOX + t) + A.sigma * e[c];
+        for (int c = 0; c < 6; ++c) qn[c] = ld_d(A.q_in + (b * 6 + c) * TGV_BVOX + t, A.ds.dsq) + A.sigma * e[c];
         proj6(qn, A.alpha0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) s_p[c][t] = pn[c];
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float vh = ld_s(A.vbar_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh);
-                ph[c] = ld_s(A.p_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh) + A.sigma * (g[c] - vh);
+                ph[c] = ld_d(A.p_in + ((int64_t)n * 3 + c) * TGV_BVOX + lh, A.ds.dsp) + A.sigma * (g[c] - vh);
             }
             proj3(ph, A.alpha1);
 #pragma unroll
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
             float qh[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c)
-                qh[c] = ld_s(A.q_in + ((int64_t)n * 6 + c) * TGV_BVOX + lh) + A.sigma * e[c];
+                qh[c] = ld_d(A.q_in + ((int64_t)n * 6 + c) * TGV_BVOX + lh, A.ds.dsq) + A.sigma * e[c];
             proj6(qh, A.alpha0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) s_q[c][TGV_BVOX + a * 64 + k] = qh[c];
@@ -271,22 +271,23 @@ __global__ void __launch_bounds__(512, 2) tgv_iter_kernel(const IterArgs<S> A)
         const float v1 = v0 + A.tau * (pn[c] + div2[c]);
         st_s(A.v + oi, v1);
         st_s(A.vbar_out + oi, 2.0f * v1 - v0);
-        st_s(A.p_out + oi, pn[c]);
+        st_d(A.p_out + oi, pn[c], A.ds.isp);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) st_s(A.q_out + (b * 6 + c) * TGV_BVOX + t, qn[c]);
+    for (int c = 0; c < 6; ++c) st_d(A.q_out + (b * 6 + c) * TGV_BVOX + t, qn[c], A.ds.isq);
 }
 
 // =====================================================================================
 // Energy, dual value and gap (FP32 per-voxel terms, FP64 accumulation,
 // fixed-order reduction: per-block partials, then one block sums them in order).
 // =====================================================================================
-template <typename S>
+template <typename S, typename D>
 struct EnergyArgs {
     const float* u;
     const S* v;
-    const S* p;
-    const S* q;
+    const D* p;
+    const D* q;
+    float dsp, dsq;  // fixed-point decode scales of p and q (TGV_STORAGE_FX16)
     const uint32_t* hist;
     const int32_t* nbr;
     const int32_t* work;  // item -> brick (nullptr: identity)
@@ -322,8 +323,8 @@ __device__ __forceinline__ double warp_max(double v)
 // brick at three CTAs per SM).  NB: bin count as a compile-time constant (8, 10,
 // 12), 0 = read at run time.  Own fields through per-brick base pointers;
 // neighbours in the same brick or across a face.
-template <typename S, int NB>
-__global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S> A)
+template <typename S, typename D, int NB>
+__global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S, D> A)
 {
     constexpr int NBM = NB ? NB : TGV_MAX_BINS;
     __shared__ int32_t s_nbr2[2][TGV_NNBR];
@@ -350,17 +351,17 @@ __global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S> 
     const int crd[3] = {t & 7, (t >> 3) & 7, t >> 6};
     const float* ub = A.u + b * TGV_BVOX;
     const S* vb = A.v + b * 3 * TGV_BVOX;
-    const S* pb = A.p + b * 3 * TGV_BVOX;
-    const S* qb = A.q + b * 6 * TGV_BVOX;
+    const D* pb = A.p + b * 3 * TGV_BVOX;
+    const D* qb = A.q + b * 6 * TGV_BVOX;
     const float u = ub[t];
     float v[3], p[3], q[6];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         v[c] = ld_s(vb + c * TGV_BVOX + t);
-        p[c] = ld_s(pb + c * TGV_BVOX + t);
+        p[c] = ld_d(pb + c * TGV_BVOX + t, A.dsp);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) q[c] = ld_s(qb + c * TGV_BVOX + t);
+    for (int c = 0; c < 6; ++c) q[c] = ld_d(qb + c * TGV_BVOX + t, A.dsq);
 
     float gmv2 = 0.0f, k0 = 0.0f, dm[3][3], dk[3][3], div1 = 0.0f, div2[3] = {0, 0, 0};
     float vmax = 0.0f;
@@ -405,12 +406,12 @@ __global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S> 
         }
         // div1 p and div2 q
         if (nf >= 0) div1 += p[a];
-        if (nbk >= 0 && nbk < A.nb) div1 -= ld_s(A.p + (nbk * 3 + a) * TGV_BVOX + lb);
+        if (nbk >= 0 && nbk < A.nb) div1 -= ld_d(A.p + (nbk * 3 + a) * TGV_BVOX + lb, A.dsp);
         const bool qact = nf >= 0 && nf < A.nb;
-        const S* qn = A.q + (qact ? nf * 6 * TGV_BVOX + lf : 0);
+        const D* qn = A.q + (qact ? nf * 6 * TGV_BVOX + lf : 0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if (qact) div2[c] += ld_s(qn + qi(a, c) * TGV_BVOX);
+            if (qact) div2[c] += ld_d(qn + qi(a, c) * TGV_BVOX, A.dsq);
             if (nbk >= 0) div2[c] -= q[qi(a, c)];
         }
     }
@@ -513,16 +514,16 @@ int64_t tgv_energy_grid(int64_t nitems)
 }
 
 // launches the energy kernel; returns its grid (the number of partials)
-template <typename S>
-static int64_t launch_energy_kernel(EnergyArgs<S> A, int64_t nitems, cudaStream_t stream)
+template <typename S, typename D>
+static int64_t launch_energy_kernel(EnergyArgs<S, D> A, int64_t nitems, cudaStream_t stream)
 {
     const int64_t grid = tgv_energy_grid(nitems);
     A.nitems = nitems;
     switch (A.nbins) {
-    case 8: tgv_energy_kernel<S, 8><<<(unsigned)grid, 64, 0, stream>>>(A); break;
-    case 10: tgv_energy_kernel<S, 10><<<(unsigned)grid, 64, 0, stream>>>(A); break;
-    case 12: tgv_energy_kernel<S, 12><<<(unsigned)grid, 64, 0, stream>>>(A); break;
-    default: tgv_energy_kernel<S, 0><<<(unsigned)grid, 64, 0, stream>>>(A); break;
+    case 8: tgv_energy_kernel<S, D, 8><<<(unsigned)grid, 64, 0, stream>>>(A); break;
+    case 10: tgv_energy_kernel<S, D, 10><<<(unsigned)grid, 64, 0, stream>>>(A); break;
+    case 12: tgv_energy_kernel<S, D, 12><<<(unsigned)grid, 64, 0, stream>>>(A); break;
+    default: tgv_energy_kernel<S, D, 0><<<(unsigned)grid, 64, 0, stream>>>(A); break;
     }
     return grid;
 }
@@ -568,12 +569,12 @@ __global__ void __launch_bounds__(1024) tgv_reduce_partials(const double* partia
 // =====================================================================================
 // host launchers
 // =====================================================================================
-template <typename S>
+template <typename S, typename D = S>
 static tgv_status launch_iters_t(tgv_domain* d, TgvLevel& L, int iters)
 {
     for (int it = 0; it < iters; ++it) {
-        IterArgs<S> A = tgv_make_iter_args<S>(d, L);
-        tgv_iter_kernel<S><<<(unsigned)A.nitems, TGV_BVOX, 0, d->stream>>>(A);
+        IterArgs<S, D> A = tgv_make_iter_args<S, D>(d, L);
+        tgv_iter_kernel<S, D><<<(unsigned)A.nitems, TGV_BVOX, 0, d->stream>>>(A);
         d->launches++;
         L.cur ^= 1;
     }
@@ -589,21 +590,25 @@ tgv_status tgv_launch_iterations(tgv_domain* d, TgvLevel& L, int iters)
     case TGV_STORAGE_FP32: return launch_iters_t<float>(d, L, iters);
     case TGV_STORAGE_BF16: return launch_iters_t<__nv_bfloat16>(d, L, iters);
     case TGV_STORAGE_FP16: return launch_iters_t<__half>(d, L, iters);
+    case TGV_STORAGE_FX16: return launch_iters_t<__half, int16_t>(d, L, iters);
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
 }
 
-template <typename S>
+template <typename S, typename D = S>
 static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
 {
     const int64_t nitems = tgv_work_items(L);
     tgv_status st = tgv_scratch(d, d->red, sizeof(double) * 3 * (size_t)nitems);
     if (st != TGV_OK) return st;
-    EnergyArgs<S> A;
+    EnergyArgs<S, D> A;
     A.u = L.u;
     A.v = (const S*)L.v;
-    A.p = (const S*)L.p[L.cur];
-    A.q = (const S*)L.q[L.cur];
+    A.p = (const D*)L.p[L.cur];
+    A.q = (const D*)L.q[L.cur];
+    const DualScales ds = tgv_dual_scales(d->prm);
+    A.dsp = ds.dsp;
+    A.dsq = ds.dsq;
     A.hist = L.hist;
     A.nbr = L.nbr;
     A.work = L.work;
@@ -617,7 +622,7 @@ static tgv_status launch_energy_t(tgv_domain* d, TgvLevel& L, double* host_out)
     A.box_v = d->prm.box_v;
     tgv_bin_centres(d->prm, A.c);
     A.partial = (double*)d->red.ptr;
-    const int64_t parts = launch_energy_kernel<S>(A, nitems, d->stream);
+    const int64_t parts = launch_energy_kernel<S, D>(A, nitems, d->stream);
     tgv_reduce_partials<<<1, 1024, 0, d->stream>>>(A.partial, parts, d->prm.box_v, d->red_out);
     d->launches += 2;
     st = tgv_cuda_check(d, cudaGetLastError(), "tgv_energy_kernel launch");
@@ -640,6 +645,7 @@ tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)
     case TGV_STORAGE_FP32: return launch_energy_t<float>(d, L, host_out);
     case TGV_STORAGE_BF16: return launch_energy_t<__nv_bfloat16>(d, L, host_out);
     case TGV_STORAGE_FP16: return launch_energy_t<__half>(d, L, host_out);
+    case TGV_STORAGE_FX16: return launch_energy_t<__half, int16_t>(d, L, host_out);
     }
     return tgv_fail(d, TGV_ERR_INVALID_ARG, "unknown storage type");
 }
@@ -647,15 +653,18 @@ tgv_status tgv_launch_energy(tgv_domain* d, TgvLevel& L, double* host_out)
 // Energy of a caller-described state with caller-given scratch: `partial`
 // holds 3 doubles per active brick, `result` 4 doubles.  Launches the same two
 // kernels as tgv_launch_energy on `stream`; no allocation, no synchronisation.
-template <typename S>
+template <typename S, typename D = S>
 static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_params& prm, cudaStream_t stream,
                                        double* partial, double* result)
 {
-    EnergyArgs<S> A;
+    EnergyArgs<S, D> A;
     A.u = s.u;
     A.v = (const S*)s.v;
-    A.p = (const S*)s.p;
-    A.q = (const S*)s.q;
+    A.p = (const D*)s.p;
+    A.q = (const D*)s.q;
+    const DualScales ds = tgv_dual_scales(prm);
+    A.dsp = ds.dsp;
+    A.dsq = ds.dsq;
     A.hist = s.hist;
     A.nbr = s.nbr;
     A.work = nullptr;
@@ -669,7 +678,7 @@ static cudaError_t launch_energy_view_t(const tgv_state_view& s, const tgv_param
     A.box_v = prm.box_v;
     tgv_bin_centres(prm, A.c);
     A.partial = partial;
-    const int64_t parts = launch_energy_kernel<S>(A, s.nbricks, stream);
+    const int64_t parts = launch_energy_kernel<S, D>(A, s.nbricks, stream);
     tgv_reduce_partials<<<1, 1024, 0, stream>>>(partial, parts, prm.box_v, result);
     return cudaGetLastError();
 }
@@ -680,6 +689,7 @@ cudaError_t tgv_launch_energy_view(const tgv_state_view& s, const tgv_params& pr
     switch (prm.storage) {
     case TGV_STORAGE_FP32: return launch_energy_view_t<float>(s, prm, stream, partial, result);
     case TGV_STORAGE_BF16: return launch_energy_view_t<__nv_bfloat16>(s, prm, stream, partial, result);
+    case TGV_STORAGE_FX16: return launch_energy_view_t<__half, int16_t>(s, prm, stream, partial, result);
     default: return launch_energy_view_t<__half>(s, prm, stream, partial, result);
     }
 }

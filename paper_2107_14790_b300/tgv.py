@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtgv.so"
 TGV_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "budget exceeded", 4: "CUDA error",
           5: "device wait timed out", 6: "domain in error state", 7: "unsupported"}
-STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2, "fx16": 3}
 HIST_FORMS = {"gather": 0, "scatter": 1}
 FIELDS = {"u": (0, 1), "ubar": (1, 1), "v": (2, 3), "vbar": (3, 3), "p": (4, 3), "q": (5, 6)}
 

@@ -71,9 +71,10 @@ def test_multilevel_matches_oracle(scene, oracle_run, form):
 def test_multilevel_reduced_precision_error(scene, oracle_run):
     _, ref_u = oracle_run
     errs = {}
-    for storage in ("fp16", "bf16"):
+    for storage in ("fx16", "fp16", "bf16"):
         _, us, _ = gpu_run(scene, storage=storage)
         errs[storage] = max(float(np.max(np.abs(us[l] - ref_u[l]))) for l in range(3))
     print("multilevel |du|_inf vs FP64 oracle:", errs)
+    assert errs["fx16"] <= 5e-3
     assert errs["fp16"] <= 5e-3
     assert errs["bf16"] <= 5e-2

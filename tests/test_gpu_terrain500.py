@@ -37,12 +37,20 @@ def runs():
     build.build()
     sc = synth.terrain_scene(seed=1002, n=N, nmaps=64, res=512, nbins=10, iterations=ITERS, device="cuda")
     s = torch.cuda.Stream()
+    depth = torch.from_numpy(np.stack(sc.depths)).cuda()
     with tgv.Domain([sc.domain], nbins=10, stream=s.cuda_stream) as dom:
-        dom.accumulate(0, sc.cameras, torch.from_numpy(np.stack(sc.depths)).cuda())
+        dom.accumulate(0, sc.cameras, depth)
         hist = dom.histograms(0)
         dom.solve(0, ITERS)
         gpu = {f: dom.field(0, f) for f in ("u", "v", "p", "q")}
         e_gpu = dom.energy(0)
+    for storage in ("fx16", "fp16"):  # reduced-precision storage forms, same workload
+        with tgv.Domain([sc.domain], nbins=10, storage=storage, stream=s.cuda_stream) as dom:
+            dom.accumulate(0, sc.cameras, depth)
+            dom.solve(0, ITERS)
+            gpu["u_" + storage] = dom.field(0, "u")
+            gpu["energy_" + storage] = dom.energy(0)
+            gpu["state_" + storage] = {f: dom.field(0, f) for f in ("v", "p", "q")}
     orc = oracle.OracleLevel(sc.domain, 10)
     for c, d in zip(sc.cameras, sc.depths):
         orc.accumulate(c, d, 1)
@@ -111,3 +119,55 @@ def test_zero_level_set_agrees(runs):
     disp = np.linalg.norm(pg[a] - po[b], axis=1).max() / h
     print(f"terrain 128^3, {ITERS} iterations: {len(common)} crossings, max displacement {disp:.2e} h")
     assert disp <= 1e-3, f"crossing displacement {disp:.2e} h"
+
+
+def _crossing_displacement(sc, u_a, u_b):
+    """Max distance (in h) between the zero crossings of two fields on the voxel edges both
+    cross, with both ends away from zero (|u| > 1e-3), and the number of such edges."""
+    h = sc.domain.h
+    A = dense_from_bricks(u_a.astype(np.float64), sc.domain.bricks, N)
+    B = dense_from_bricks(u_b.astype(np.float64), sc.domain.bricks, N)
+    mask = np.ones_like(A, dtype=bool)
+    pa, ia = edge_crossings(A, mask, h, eps=1e-3)
+    pb, ib = edge_crossings(B, mask, h, eps=1e-3)
+    ka = {tuple(r): k for k, r in enumerate(ia.tolist())}
+    common = [(ka[tuple(r)], k) for k, r in enumerate(ib.tolist()) if tuple(r) in ka]
+    a = np.array([c[0] for c in common])
+    b = np.array([c[1] for c in common])
+    return np.linalg.norm(pa[a] - pb[b], axis=1).max() / h, len(common), len(pb)
+
+
+def test_fixed_point_duals_meet_the_stated_accuracy(runs):
+    """16-bit storage (v, vbar FP16; p, q 16-bit fixed point scaled by alpha1, alpha0) after
+    all 500 iterations against the FP64 oracle: the stated accuracy of the reduced forms,
+    max |du| <= 5e-3 and zero crossings within 0.05 h.  FP16 duals are reported beside it."""
+    sc, _, _, gpu, orc, _ = runs
+    for storage in ("fx16", "fp16"):
+        u = gpu["u_" + storage][:, 0]
+        du = np.abs(u - orc.u)
+        disp, ncommon, nref = _crossing_displacement(sc, u, orc.u)
+        print(f"terrain 128^3, {ITERS} iterations, {storage} storage: max |du| = {du.max():.3e}, "
+              f"rms {np.sqrt(np.mean(du ** 2)):.3e}, crossings {ncommon}/{nref}, max displacement {disp:.3e} h")
+        if storage == "fx16":
+            assert du.max() <= 5e-3
+            assert disp <= 0.05
+            assert ncommon >= 0.99 * nref
+
+
+def test_fixed_point_energy_of_its_state(runs):
+    """The energy / gap the FX16 form reports is that of its own decoded state (oracle
+    evaluation of the same values within 1e-6 relative)."""
+    sc, hist, _, gpu, _, _ = runs
+    st = gpu["state_fx16"]
+    ev = oracle.OracleLevel(sc.domain, 10)
+    ev.hist[:] = hist
+    ev.u[:] = gpu["u_fx16"][:, 0]
+    ev.v[:] = st["v"]
+    ev.p[:] = st["p"]
+    ev.q[:] = st["q"]
+    e_orc = ev.energy()
+    e_gpu = gpu["energy_fx16"]
+    for k in range(3):
+        assert abs(e_gpu[k] - e_orc[k]) <= 1e-6 * abs(e_orc[0]), (k, e_gpu[k], e_orc[k])
+    # decoded duals are multiples of alpha / 32767 and stay in their balls
+    assert np.abs(st["p"]).max() <= 1.0 + 1e-6 and np.abs(st["q"]).max() <= 2.0 + 1e-6

@@ -73,7 +73,7 @@ def test_bad_wait_parameters_are_rejected():
         assert e.value.status == 1
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "fx16"])
 @pytest.mark.parametrize("n1,n2", [(13, 17), (8, 5)])
 def test_checkpoint_resume_is_bit_identical(storage, n1, n2):
     sp = chunk(73)
