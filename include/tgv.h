@@ -241,6 +241,31 @@ TGV_API tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, d
  * (UNSUPPORTED otherwise).  Graphs are freed with the domain. */
 TGV_API tgv_status tgv_solve_graph(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out);
 
+/* Persistent batched solve of independent chunks in one launch (Sec. 4.3: the treetop's
+ * parts are solved independently; Sec. 4.5: each with its border cubes frozen).
+ * Level `level` holds nchunks chunks: chunk c is the active bricks [first[c], first[c+1])
+ * (host array of nchunks + 1 ascending brick indices; active bricks outside every chunk
+ * keep their state); no face or edge link may join bricks of two chunks.  Chunk c runs
+ * iterations[c] (host, >= 0) iterations of tgv_solve's scheme, and its result equals the
+ * chunk solved alone by tgv_solve with the PAIRED kernel, bit for bit.
+ * One persistent kernel: CTAs take tickets from a counter -- a ticket is a run of
+ * run_length consecutive bricks of one chunk in one iteration, handed out iteration by
+ * iteration -- and before a run wait (bounded by tgv_params.wait_cycles) at the chunk's
+ * barrier until every run of the chunk's previous iteration has completed.  A CTA takes a
+ * ticket only when its previous run is done, and a run waits only on smaller tickets, so
+ * no wait depends on CTAs that are not running.  A wait that runs out makes the next
+ * synchronising call return TGV_ERR_TIMEOUT.
+ * run_length: 1..64 bricks, 0 = 16.  With a non-NULL stream the first call with a given
+ * chunk table, iteration counts, run length and current ping-pong copy captures its
+ * launches into a CUDA graph that later identical calls replay (up to 16 plans per level
+ * are kept; they are freed with the domain).  Afterwards every chunk's ubar, vbar, p, q
+ * are in the level's current copy.  Does not synchronise.
+ * Errors: INVALID_ARG (ranges, a link between two chunks, a work list set), UNSUPPORTED
+ * (levels of 2^31 bricks, a chunk with iterations x runs >= 2^31), OUT_OF_MEMORY, STATE,
+ * CUDA. */
+TGV_API tgv_status tgv_solve_chunks(tgv_domain* d, int32_t level, int32_t nchunks, const int64_t* first,
+                                    const int32_t* iterations, int32_t run_length);
+
 /* Restricts later iterations and energy evaluations of a level to the listed
  * active bricks (host or device int32 array of n distinct indices in [0,
  * nbricks)); bricks = NULL or n < 0 restores "every active brick".  Bricks

@@ -31,6 +31,11 @@ class UnionLevel:
     ranges: List[tuple]  # active-brick range [a, b) of each chunk
     radius: float = 0.0
 
+    @property
+    def first(self) -> np.ndarray:
+        """Brick ranges as the first-brick table of tgv_solve_chunks (nchunks + 1 entries)."""
+        return np.array([a for a, _ in self.ranges] + [self.ranges[-1][1]], np.int64)
+
 
 def union_level(domains: Sequence) -> UnionLevel:
     """One level holding every chunk of `domains` (DomainDesc-like): the chunks are laid

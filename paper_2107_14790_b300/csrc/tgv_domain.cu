@@ -117,19 +117,6 @@ void tgv_bin_centres(const tgv_params& prm, float* c)
 
 namespace {
 
-struct DeviceGuard {
-    int old = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
-        else old = -1;
-    }
-    ~DeviceGuard()
-    {
-        if (old >= 0) cudaSetDevice(old);
-    }
-};
-
 inline uint64_t brick_key(int32_t x, int32_t y, int32_t z)
 {
     const uint64_t B = (uint64_t)1 << 20;
@@ -278,6 +265,12 @@ tgv_status check_domain(tgv_domain* d)
     return TGV_OK;
 }
 
+}  // namespace
+
+tgv_status tgv_check_domain(tgv_domain* d) { return check_domain(d); }
+
+namespace {
+
 tgv_status get_level(tgv_domain* d, int32_t level, TgvLevel** L)
 {
     if (level < 0 || level >= (int32_t)d->levels.size()) return tgv_fail(d, TGV_ERR_INVALID_ARG, "level out of range");
@@ -302,6 +295,11 @@ void free_graphs(TgvLevel& L)
 {
     for (auto& g : L.graphs) cudaGraphExecDestroy(g.exec);
     L.graphs.clear();
+    for (auto& b : L.batches) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        if (b.dev) cudaFree(b.dev);
+    }
+    L.batches.clear();
 }
 
 void free_level(TgvLevel& L)

@@ -121,6 +121,16 @@ struct TgvLevel {
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
+    // plans of the persistent batched solve (tgv_solve_chunks): device tables, and the
+    // call captured as a CUDA graph when the domain has a stream
+    struct Batch {
+        uint64_t key = 0;
+        void* dev = nullptr;
+        size_t bytes = 0;
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;  // kernels one replay launches
+    };
+    std::vector<Batch> batches;
     int cur = 0;               // ping-pong copy holding the current ubar/vbar/p/q
     uint64_t max_votes = 0;    // upper bound on any voxel's total count
     // host copies of nbr (nb rows) and of the work list, for the paired kernel's run-length choice
@@ -190,8 +200,24 @@ struct tgv_domain {
 // stream is being captured once the first call has happened outside capture).
 tgv_status tgv_kernel_setup(const void* kernel, int threads, size_t smem, int* per_sm);
 
+// Makes `dev` the current device for the guard's lifetime.
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+        else old = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
 // helpers implemented in tgv_domain.cu
 tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg);
+// INVALID_ARG for NULL, STATE for a domain broken by an earlier error, else OK
+tgv_status tgv_check_domain(tgv_domain* d);
 tgv_status tgv_cuda_check(tgv_domain* d, cudaError_t e, const char* what);
 tgv_status tgv_scratch(tgv_domain* d, TgvScratch& s, size_t bytes);
 void tgv_bin_centres(const tgv_params& prm, float* c);

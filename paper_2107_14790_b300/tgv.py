@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "tgv_copy_mesh": (i32, [P, P, i64, P, i64]),
         "tgv_energy_noalloc": (i32, [P, P, P, P]),
         "tgv_solve_graph": (i32, [P, i32, i32, P]),
+        "tgv_solve_chunks": (i32, [P, i32, i32, P, P, i32]),
         "tgv_set_work_list": (i32, [P, i32, P, i64]),
         "tgv_server_create": (i32, [P, P, P, P]),
         "tgv_server_submit": (i32, [P, P, P, i32, P]),
@@ -261,6 +262,16 @@ def tgv_solve_graph(d, level: int, iterations: int, energy: bool = False):
     out = np.zeros(4) if energy else None
     _check(d, lib().tgv_solve_graph(d, level, iterations, _ptr(out)))
     return out
+
+
+def tgv_solve_chunks(d, level: int, first, iterations, run_length: int = 0):
+    """Persistent batched solve: chunk c = active bricks [first[c], first[c+1]) runs
+    iterations[c] iterations (host arrays of nchunks + 1 int64 and nchunks int32)."""
+    f = np.ascontiguousarray(first, dtype=np.int64)
+    it = np.ascontiguousarray(iterations, dtype=np.int32)
+    if f.size != it.size + 1:
+        raise ValueError("first needs one entry more than iterations")
+    _check(d, lib().tgv_solve_chunks(d, level, int(it.size), f.ctypes.data, it.ctypes.data, int(run_length)))
 
 
 def tgv_set_work_list(d, level: int, bricks=None):
@@ -608,6 +619,9 @@ class Domain:
 
     def set_work_list(self, level, bricks=None):
         tgv_set_work_list(self.handle, level, bricks)
+
+    def solve_chunks(self, level, first, iterations, run_length=0):
+        tgv_solve_chunks(self.handle, level, first, iterations, run_length)
 
     def field(self, level, name, out=None):
         return tgv_extract_field(self.handle, level, name, out)
