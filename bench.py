@@ -437,12 +437,14 @@ def _oracle_u(spec, iters):
     return lvl.u
 
 
-def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fp16")):
+def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fx16"), run_lengths=(16,)):
     """Bounded form of the batched workload for the default line: `nchunks` chunks of the
     c4 size distribution (log-uniform 32^3..192^3 active voxels, frozen one-brick shell,
     10 bins, `iters` iterations), sharded over the ranks (strong scaling: each rank solves
-    its own chunks, no collective on the path).  Forms: one union level replayed as a CUDA
-    graph per storage type, and the plain form (every chunk its own domain, FP32)."""
+    its own chunks, no collective on the path).  Forms per storage type: the persistent
+    launch (tgv_solve_chunks: one kernel drains every chunk's runs behind per-chunk
+    barriers, replayed as a CUDA graph), one union level with one launch per iteration
+    replayed as a CUDA graph; and the plain form (every chunk its own domain, FP32)."""
     import torch
     import synth
     from paper_2107_14790_b300 import tgv
@@ -470,6 +472,8 @@ def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("
     out = {"chunks": nchunks, "voxels": int(tot), "iterations": iters, "l2": "inputs larger than L2 "
            "(state %.2f GB)" % (state_bytes(int(tot), 10, "fp32") / 1e9)}
     launches = 0
+    first = U.first
+    its = [iters] * len(specs)
     for storage in storages:
         dom = tgv.Domain([U], nbins=10, storage=storage, stream=stream.cuda_stream)
         dom.set_histograms(0, hist)
@@ -479,6 +483,16 @@ def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("
         ms = timed(lambda: dom.solve_graph(0, iters))
         launches += dom.launches - l0
         out[f"union_graph_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms}
+        for R in run_lengths:
+            dom.reset(0)
+            dom.solve_chunks(0, first, its, run_length=R)  # first call captures the graph
+            dom.reset(0)
+            l0 = dom.launches
+            ms = timed(lambda: dom.solve_chunks(0, first, its, run_length=R))
+            launches += dom.launches - l0
+            key = f"persistent_{storage}" + ("" if len(run_lengths) == 1 else f"_R{R}")
+            out[key] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms, "run_length": R,
+                        "launches": dom.launches - l0}
         dom.close()
     doms = []
     for sp in specs:
@@ -492,9 +506,9 @@ def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("
     for d in doms:
         d.close()
     base = out["plain_fp32"]["voxel_updates_per_s"]
-    for storage in storages:
-        out[f"union_graph_{storage}"]["speedup_over_plain_fp32"] = \
-            out[f"union_graph_{storage}"]["voxel_updates_per_s"] / base
+    for key, rec in out.items():
+        if isinstance(rec, dict) and key != "plain_fp32" and "voxel_updates_per_s" in rec:
+            rec["speedup_over_plain_fp32"] = rec["voxel_updates_per_s"] / base
     out["gpu_launches"] = int(reduce_scalar(launches, "sum"))
     return out
 

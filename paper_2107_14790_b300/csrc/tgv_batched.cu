@@ -32,8 +32,8 @@
 
 template <typename S, typename D>
 struct BatchArgs {
-    PairArgs<S, D> pa;      // shared-memory layout, error flag, wait budget (pa.it unused)
-    IterArgs<S, D> it[2];   // it[k & 1]: iteration k of a chunk (reads copy cur ^ (k & 1))
+    PairArgs<S, D> pa;      // shared-memory layout, error flag, wait budget; pa.it reads copy
+                            // cur (a chunk's even iterations; odd ones swap in and out)
     // segments of iterations with the same set of active chunks (chunks sorted by
     // iteration count, descending): segment j covers iterations [seg_k[j], seg_k[j+1])
     // with the first seg_a[j] chunks active, and tickets [seg_t[j], seg_t[j+1])
@@ -47,7 +47,6 @@ struct BatchArgs {
     unsigned long long* ticket;
     int32_t nseg, R;
     uint32_t off_task;        // shared-memory slot where thread 0 posts the CTA's task
-    uint32_t off_it;          // shared-memory copy of it[2] (16-byte aligned)
 };
 
 namespace {
@@ -90,10 +89,6 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_batched_kernel(const BatchArg
         mbar_init(&bar[2], 1);
         fence_mbar_init();
     }
-    // both argument sets in shared memory, so one sweep serves either parity
-    IterArgs<S, D>* sit = (IterArgs<S, D>*)(smem + B.off_it);
-    static_assert(sizeof(B.it) % 4 == 0, "argument sets are copied as words");
-    for (int w = t; w < (int)(sizeof(B.it) / 4); w += blockDim.x) ((uint32_t*)sit)[w] = ((const uint32_t*)B.it)[w];
     const int64_t total = B.seg_t[B.nseg];
     uint32_t parity = 0;
     for (;;) {
@@ -139,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 2) tgv_batched_kernel(const BatchArg
         }
         const uint32_t i0 = (uint32_t)task[0], i1 = (uint32_t)task[1];
         const int c = (int)task[2];
-        PairCta<S, D, NB> C(B.pa, sit[task[3]], smem);
+        PairCta<S, D, NB> C(B.pa, smem, task[3] != 0);
         if (!pair_sweep(C, OneRun{i1}, i0, parity, false)) break;
         __syncthreads();  // every store of the run has been issued
         if (t == 0) {
@@ -214,27 +209,19 @@ tgv_status launch_batched_t(tgv_domain* d, TgvLevel& L, const BatchPlan& plan, T
 {
     const uint32_t SB = sizeof(S), SD = sizeof(D);
     const int npairs = (d->prm.nbins + 1) / 2;
-    const uint32_t tx = 4096 + (6 * SB + 9 * SD) * 512 + npairs * 2048;
-    const uint32_t stage = (tx + 127) / 128 * 128;
-    uint32_t off = 2 * stage;
+    const PairLayout LY = pair_layout(SB, SD, (uint32_t)npairs);
+    const uint32_t tx = LY.tx, stage = LY.stage;
+    uint32_t off = LY.end;
     BatchArgs<S, D> B;
     PairArgs<S, D>& P = B.pa;
-    P.pn_bytes = SD == 4 ? 0 : 9 * 512 * 4;
-    P.off_pn = off;
-    off += 2 * P.pn_bytes;
-    P.off_hal = off;
-    off += 2 * 9 * 192 * 4;
-    P.off_nbr = off;
-    off += 2 * TGV_NNBR * 4;
-    off = (off + 15) / 16 * 16;
-    P.off_bar = off;
-    off += 3 * 8;
+    P.pn_bytes = LY.pn_bytes;
+    P.off_pn = LY.off_pn;
+    P.off_hal = LY.off_hal;
+    P.off_nbr = LY.off_nbr;
+    P.off_bar = LY.off_bar;
     off = (off + 15) / 16 * 16;
     B.off_task = off;
     off += 5 * 8;
-    off = (off + 15) / 16 * 16;
-    B.off_it = off;
-    off += sizeof(B.it);
     const size_t smem = off;
     auto kern = tgv_batched_kernel<S, D, NB>;
     int per_sm = 0;
@@ -250,12 +237,8 @@ tgv_status launch_batched_t(tgv_domain* d, TgvLevel& L, const BatchPlan& plan, T
     P.stage_bytes = stage;
     P.tx_bytes = tx;
     const int cur0 = L.cur;
-    B.it[0] = tgv_make_iter_args<S, D>(d, L);
-    L.cur ^= 1;
-    B.it[1] = tgv_make_iter_args<S, D>(d, L);
-    L.cur = cur0;
-    B.it[0].work = B.it[1].work = nullptr;
-    P.it = B.it[0];
+    P.it = tgv_make_iter_args<S, D>(d, L);
+    P.it.work = nullptr;
     const BatchLayout lo = batch_layout(plan, (int)plan.cfirst.size());
     char* base = (char*)E.dev;
     B.seg_k = (const int64_t*)(base + lo.seg_k);

@@ -145,20 +145,15 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
 {
     const uint32_t SB = sizeof(S), SD = sizeof(D);
     const int npairs = (d->prm.nbins + 1) / 2;
-    const uint32_t tx = 4096 + (6 * SB + 9 * SD) * 512 + npairs * 2048;
-    const uint32_t stage = (tx + 127) / 128 * 128;
-    uint32_t off = 2 * stage;
+    const PairLayout LY = pair_layout(SB, SD, (uint32_t)npairs);
+    const uint32_t tx = LY.tx, stage = LY.stage;
+    uint32_t off = LY.end;
     PairArgs<S, D> P;
-    P.pn_bytes = SD == 4 ? 0 : 9 * 512 * 4;
-    P.off_pn = off;
-    off += 2 * P.pn_bytes;
-    P.off_hal = off;
-    off += 2 * 9 * 192 * 4;
-    P.off_nbr = off;
-    off += 2 * TGV_NNBR * 4;
-    off = (off + 15) / 16 * 16;
-    P.off_bar = off;
-    off += 3 * 8;
+    P.pn_bytes = LY.pn_bytes;
+    P.off_pn = LY.off_pn;
+    P.off_hal = LY.off_hal;
+    P.off_nbr = LY.off_nbr;
+    P.off_bar = LY.off_bar;
     const size_t smem = off;
     auto kern = tgv_iter_pair_kernel<S, D, NB>;
     int per_sm = 0;

@@ -161,6 +161,26 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
 
 }  // namespace
 
+// Shared-memory layout of a paired CTA: two stages (one brick's u, ubar, v, vbar, p, q
+// and packed histogram each), the FP32 new duals of each stage when the duals are stored
+// in 16 bits, the halo duals of each stage, two neighbour rows, three mbarriers.
+struct PairLayout {
+    uint32_t tx, stage, pn_bytes, off_pn, off_hal, off_nbr, off_bar, end;
+};
+__host__ __device__ constexpr PairLayout pair_layout(uint32_t sb, uint32_t sd, uint32_t npairs)
+{
+    PairLayout L{};
+    L.tx = 4096 + (6 * sb + 9 * sd) * 512 + npairs * 2048;
+    L.stage = (L.tx + 127) / 128 * 128;
+    L.pn_bytes = sd == 4 ? 0 : 9 * 512 * 4;
+    L.off_pn = 2 * L.stage;
+    L.off_hal = L.off_pn + 2 * L.pn_bytes;
+    L.off_nbr = L.off_hal + 2 * 9 * 192 * 4;
+    L.off_bar = (L.off_nbr + 2 * TGV_NNBR * 4 + 15) / 16 * 16;
+    L.end = L.off_bar + 3 * 8;
+    return L;
+}
+
 template <typename S, typename D>
 struct PairArgs {
     IterArgs<S, D> it;
@@ -199,6 +219,9 @@ struct PairCta {
                               O_P = O_VB + 3 * 512 * SB, O_Q = O_P + 3 * 512 * SD, O_H = O_Q + 6 * 512 * SD;
     static constexpr int NP_MAX = NB ? (NB + 1) / 2 : TGV_MAX_BINS / 2;
     static constexpr int NB_MAX = NB ? NB : TGV_MAX_BINS;
+    // with a compile-time bin count every offset is a constant (the launcher uses the same
+    // pair_layout); NB = 0 reads them from the arguments
+    static constexpr PairLayout LC = pair_layout(SB, SD, NB ? (NB + 1) / 2 : 1);
 
     const PairArgs<S, D>& P;
     const IterArgs<S, D>& A;
@@ -216,9 +239,12 @@ struct PairCta {
     uint32_t hm;
     int hn;
 
-    __device__ __forceinline__ PairCta(const PairArgs<S, D>& p, unsigned char* sm) : PairCta(p, p.it, sm) {}
-    __device__ __forceinline__ PairCta(const PairArgs<S, D>& p, const IterArgs<S, D>& a, unsigned char* sm)
-        : P(p), A(a), smem(sm)
+    // flip: the in and out ping-pong copies of A trade places (the batched kernel's odd
+    // iterations of a chunk); false in the level kernel, where the selects fold away
+    bool flip;
+
+    __device__ __forceinline__ PairCta(const PairArgs<S, D>& p, unsigned char* sm, bool fl = false)
+        : P(p), A(p.it), smem(sm), flip(fl)
     {
         t = threadIdx.x;
         j = t & 3;
@@ -238,31 +264,46 @@ struct PairCta {
         a0sq = alpha0 * alpha0;
     }
 
-    __device__ __forceinline__ unsigned char* stage(int s) const { return smem + (size_t)s * P.stage_bytes; }
+    __device__ __forceinline__ const float* ubi() const { return flip ? A.ubar_out : A.ubar_in; }
+    __device__ __forceinline__ float* ubo() const { return flip ? const_cast<float*>(A.ubar_in) : A.ubar_out; }
+    __device__ __forceinline__ const S* vbi() const { return flip ? A.vbar_out : A.vbar_in; }
+    __device__ __forceinline__ S* vbo() const { return flip ? const_cast<S*>(A.vbar_in) : A.vbar_out; }
+    __device__ __forceinline__ const D* pin() const { return flip ? A.p_out : A.p_in; }
+    __device__ __forceinline__ D* pout() const { return flip ? const_cast<D*>(A.p_in) : A.p_out; }
+    __device__ __forceinline__ const D* qin() const { return flip ? A.q_out : A.q_in; }
+    __device__ __forceinline__ D* qout() const { return flip ? const_cast<D*>(A.q_in) : A.q_out; }
+
+    __device__ __forceinline__ uint32_t stage_bytes() const { return NB ? LC.stage : P.stage_bytes; }
+    __device__ __forceinline__ uint32_t off_pn() const { return NB ? LC.off_pn : P.off_pn; }
+    __device__ __forceinline__ uint32_t off_hal() const { return NB ? LC.off_hal : P.off_hal; }
+    __device__ __forceinline__ uint32_t off_nbr() const { return NB ? LC.off_nbr : P.off_nbr; }
+    __device__ __forceinline__ uint32_t off_bar() const { return NB ? LC.off_bar : P.off_bar; }
+    __device__ __forceinline__ uint32_t tx_bytes() const { return NB ? LC.tx : P.tx_bytes; }
+    __device__ __forceinline__ unsigned char* stage(int s) const { return smem + (size_t)s * stage_bytes(); }
     __device__ __forceinline__ float* pn_own(int s) const
     {
-        return (float*)(SD == 4 ? stage(s) + O_P : smem + P.off_pn + (size_t)s * P.pn_bytes);
+        return (float*)(SD == 4 ? stage(s) + O_P : smem + off_pn() + (size_t)s * LC.pn_bytes);
     }
     __device__ __forceinline__ float* qn_own(int s) const
     {
-        return (float*)(SD == 4 ? stage(s) + O_Q : smem + P.off_pn + (size_t)s * P.pn_bytes + 3 * 512 * 4);
+        return (float*)(SD == 4 ? stage(s) + O_Q : smem + off_pn() + (size_t)s * LC.pn_bytes + 3 * 512 * 4);
     }
-    __device__ __forceinline__ float* hal_p(int s) const { return (float*)(smem + P.off_hal) + s * (9 * 192); }
+    __device__ __forceinline__ float* hal_p(int s) const { return (float*)(smem + off_hal()) + s * (9 * 192); }
     __device__ __forceinline__ float* hal_q(int s) const { return hal_p(s) + 3 * 192; }
-    __device__ __forceinline__ uint64_t* bar() const { return (uint64_t*)(smem + P.off_bar); }
-    __device__ __forceinline__ int* nbr_row(int s) const { return (int*)(smem + P.off_nbr) + s * TGV_NNBR; }
+    __device__ __forceinline__ uint64_t* bar() const { return (uint64_t*)(smem + off_bar()); }
+    __device__ __forceinline__ int* nbr_row(int s) const { return (int*)(smem + off_nbr()) + s * TGV_NNBR; }
 
     __device__ __forceinline__ void issue(int s, uint32_t brick) const
     {
         unsigned char* st = stage(s);
         uint64_t* b = bar() + s;
-        mbar_arrive_expect_tx(b, P.tx_bytes);
+        mbar_arrive_expect_tx(b, tx_bytes());
         bulk_copy_g2s(st + O_U, A.u + (size_t)brick * TGV_BVOX, 2048, b);
-        bulk_copy_g2s(st + O_UB, A.ubar_in + (size_t)brick * TGV_BVOX, 2048, b);
+        bulk_copy_g2s(st + O_UB, ubi() + (size_t)brick * TGV_BVOX, 2048, b);
         bulk_copy_g2s(st + O_V, A.v + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_VB, A.vbar_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
-        bulk_copy_g2s(st + O_P, A.p_in + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SD, b);
-        bulk_copy_g2s(st + O_Q, A.q_in + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SD, b);
+        bulk_copy_g2s(st + O_VB, vbi() + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SB, b);
+        bulk_copy_g2s(st + O_P, pin() + (size_t)brick * 3 * TGV_BVOX, 3 * 512 * SD, b);
+        bulk_copy_g2s(st + O_Q, qin() + (size_t)brick * 6 * TGV_BVOX, 6 * 512 * SD, b);
         bulk_copy_g2s(st + O_H, A.hist + brick * (size_t)npairs * TGV_BVOX, (uint32_t)npairs * 2048u, b);
     }
 
@@ -280,20 +321,20 @@ struct PairCta {
             vbb_x[c] = 0.0f;
             vbb_y[c] = vbb_z[c] = make_float2(0, 0);
         }
-        if (j == 3 && n_px >= 0) ubf_x = A.ubar_in[(size_t)n_px * TGV_BVOX + l0 + 1 - 7];
-        if (y == 7 && n_py >= 0) ubf_y = ldf2(A.ubar_in + (size_t)n_py * TGV_BVOX + l0 - 56);
-        if (z == 7 && n_pz >= 0) ubf_z = ldf2(A.ubar_in + (size_t)n_pz * TGV_BVOX + l0 - 448);
+        if (j == 3 && n_px >= 0) ubf_x = ubi()[(size_t)n_px * TGV_BVOX + l0 + 1 - 7];
+        if (y == 7 && n_py >= 0) ubf_y = ldf2(ubi() + (size_t)n_py * TGV_BVOX + l0 - 56);
+        if (z == 7 && n_pz >= 0) ubf_z = ldf2(ubi() + (size_t)n_pz * TGV_BVOX + l0 - 448);
         if (j == 0 && n_mx >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_x[c] = ld_s(A.vbar_in + ((size_t)n_mx * 3 + c) * TGV_BVOX + l0 + 7);
+            for (int c = 0; c < 3; ++c) vbb_x[c] = ld_s(vbi() + ((size_t)n_mx * 3 + c) * TGV_BVOX + l0 + 7);
         }
         if (y == 0 && n_my >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_y[c] = PS::ld(A.vbar_in + ((size_t)n_my * 3 + c) * TGV_BVOX + l0 + 56);
+            for (int c = 0; c < 3; ++c) vbb_y[c] = PS::ld(vbi() + ((size_t)n_my * 3 + c) * TGV_BVOX + l0 + 56);
         }
         if (z == 0 && n_mz >= 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(A.vbar_in + ((size_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
+            for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(vbi() + ((size_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
         }
         // halo inputs.  p tasks: h[0..1] ubar(h0,h1), h[2..3] forward along the first face
         // axis, h[4..5] along the second, h[6..11] vbar (3 x pair), h[12..17] p (3 x pair).
@@ -307,56 +348,60 @@ struct PairCta {
             if ((task == 0 && skip0) || (task == 3 && skip3)) hn = -1;
         }
         if (hn < 0) return;
-        const uint32_t nb0 = (size_t)hn * TGV_BVOX;
+        // the halo brick's fields: base pointers once, constant offsets per load
+        const float* ubn = ubi() + (size_t)hn * TGV_BVOX;
+        const S* vbn = vbi() + (size_t)hn * 3 * TGV_BVOX;
+        const D* pnb = pin() + (size_t)hn * 3 * TGV_BVOX;
+        const D* qnb = qin() + (size_t)hn * 6 * TGV_BVOX;
         if (task == 0) {  // -x face single: (7, hy, hz)
             const int hy = tk & 7, hz = tk >> 3;
             const uint32_t lh = 7 + 8 * hy + 64 * hz;
-            h[0] = A.ubar_in[nb0 + lh];
+            h[0] = ubn[lh];
             if (hy < 7) {
-                h[2] = A.ubar_in[nb0 + lh + 8];
+                h[2] = ubn[lh + 8];
                 hm |= 1u;
             } else if (nrow[NB_MX_PY] >= 0) {
-                h[2] = A.ubar_in[(size_t)nrow[NB_MX_PY] * TGV_BVOX + lh - 56];
+                h[2] = ubi()[(size_t)nrow[NB_MX_PY] * TGV_BVOX + lh - 56];
                 hm |= 1u;
             }
             if (hz < 7) {
-                h[4] = A.ubar_in[nb0 + lh + 64];
+                h[4] = ubn[lh + 64];
                 hm |= 2u;
             } else if (nrow[NB_MX_PZ] >= 0) {
-                h[4] = A.ubar_in[(size_t)nrow[NB_MX_PZ] * TGV_BVOX + lh - 448];
+                h[4] = ubi()[(size_t)nrow[NB_MX_PZ] * TGV_BVOX + lh - 448];
                 hm |= 2u;
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
-                h[12 + 2 * c] = ld_d(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh, A.ds.dsp);
+                h[6 + 2 * c] = ld_s(vbn + c * TGV_BVOX + lh);
+                h[12 + 2 * c] = ld_d(pnb + c * TGV_BVOX + lh, A.ds.dsp);
             }
         } else if (task == 1 || task == 2) {  // -y / -z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 1) or y (task 2)
             const uint32_t lh = task == 1 ? 2 * hj + 56 + 64 * hw : 2 * hj + 8 * hw + 448;
-            float2 u2 = ldf2(A.ubar_in + nb0 + lh);
+            float2 u2 = ldf2(ubn + lh);
             h[0] = u2.x;
             h[1] = u2.y;
             if (hj < 3) {  // forward along x of the pair's second voxel
-                h[2] = A.ubar_in[nb0 + lh + 2];
+                h[2] = ubn[lh + 2];
                 hm |= 1u;
             } else {
                 const int e = nrow[task == 1 ? NB_MY_PX : NB_MZ_PX];
                 if (e >= 0) {
-                    h[2] = A.ubar_in[(size_t)e * TGV_BVOX + lh + 1 - 7];
+                    h[2] = ubi()[(size_t)e * TGV_BVOX + lh + 1 - 7];
                     hm |= 1u;
                 }
             }
             const uint32_t ostr = task == 1 ? 64 : 8;  // the other face axis: z (task 1) or y (task 2)
             if (hw < 7) {
-                u2 = ldf2(A.ubar_in + nb0 + lh + ostr);
+                u2 = ldf2(ubn + lh + ostr);
                 h[4] = u2.x;
                 h[5] = u2.y;
                 hm |= 2u;
             } else {
                 const int e = nrow[task == 1 ? NB_MY_PZ : NB_MZ_PY];
                 if (e >= 0) {
-                    u2 = ldf2(A.ubar_in + (size_t)e * TGV_BVOX + lh - 7 * ostr);
+                    u2 = ldf2(ubi() + (size_t)e * TGV_BVOX + lh - 7 * ostr);
                     h[4] = u2.x;
                     h[5] = u2.y;
                     hm |= 2u;
@@ -364,10 +409,10 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+                float2 w = PS::ld(vbn + c * TGV_BVOX + lh);
                 h[6 + 2 * c] = w.x;
                 h[7 + 2 * c] = w.y;
-                w = DP::ld(A.p_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh, A.ds.dsp);
+                w = DP::ld(pnb + c * TGV_BVOX + lh, A.ds.dsp);
                 h[12 + 2 * c] = w.x;
                 h[13 + 2 * c] = w.y;
             }
@@ -375,47 +420,47 @@ struct PairCta {
             const int hy = tk & 7, hz = tk >> 3;
             const uint32_t lh = 8 * hy + 64 * hz;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+            for (int c = 0; c < 3; ++c) h[2 * c] = ld_s(vbn + c * TGV_BVOX + lh);
             if (hy > 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 8);
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(vbn + c * TGV_BVOX + lh - 8);
                 hm |= 1u;
             } else if (nrow[NB_MY_PX] >= 0) {
                 const size_t e = (size_t)nrow[NB_MY_PX];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 56);
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(vbi() + (e * 3 + c) * TGV_BVOX + lh + 56);
                 hm |= 1u;
             }
             if (hz > 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 64);
+                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(vbn + c * TGV_BVOX + lh - 64);
                 hm |= 2u;
             } else if (nrow[NB_MZ_PX] >= 0) {
                 const size_t e = (size_t)nrow[NB_MZ_PX];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(A.vbar_in + (e * 3 + c) * TGV_BVOX + lh + 448);
+                for (int c = 0; c < 3; ++c) h[12 + 2 * c] = ld_s(vbi() + (e * 3 + c) * TGV_BVOX + lh + 448);
                 hm |= 2u;
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_d(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh, A.ds.dsq);
+            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_d(qnb + c * TGV_BVOX + lh, A.ds.dsq);
         } else {  // task 4 / 5: +y / +z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 4) or y (task 5)
             const uint32_t lh = task == 4 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh);
+                const float2 w = PS::ld(vbn + c * TGV_BVOX + lh);
                 h[2 * c] = w.x;
                 h[2 * c + 1] = w.y;
             }
             if (hj > 0) {  // backward along x of the pair's first voxel
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - 1);
+                for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(vbn + c * TGV_BVOX + lh - 1);
                 hm |= 1u;
             } else {
                 const int e = nrow[task == 4 ? NB_MX_PY : NB_MX_PZ];
                 if (e >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(A.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7);
+                    for (int c = 0; c < 3; ++c) h[6 + 2 * c] = ld_s(vbi() + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7);
                     hm |= 1u;
                 }
             }
@@ -423,7 +468,7 @@ struct PairCta {
             if (hw > 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 w = PS::ld(A.vbar_in + ((size_t)hn * 3 + c) * TGV_BVOX + lh - ostr);
+                    const float2 w = PS::ld(vbn + c * TGV_BVOX + lh - ostr);
                     h[12 + 2 * c] = w.x;
                     h[13 + 2 * c] = w.y;
                 }
@@ -433,7 +478,7 @@ struct PairCta {
                 if (e >= 0) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float2 w = PS::ld(A.vbar_in + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7 * ostr);
+                        const float2 w = PS::ld(vbi() + ((size_t)e * 3 + c) * TGV_BVOX + lh + 7 * ostr);
                         h[12 + 2 * c] = w.x;
                         h[13 + 2 * c] = w.y;
                     }
@@ -442,7 +487,7 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const float2 w = DP::ld(A.q_in + ((size_t)hn * 6 + c) * TGV_BVOX + lh, A.ds.dsq);
+                const float2 w = DP::ld(qnb + c * TGV_BVOX + lh, A.ds.dsq);
                 h[18 + 2 * c] = w.x;
                 h[19 + 2 * c] = w.y;
             }
@@ -533,7 +578,7 @@ struct PairCta {
                 // with the x = 6 values parked by its phase B: one pair store per field
                 const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l6;
                 PS::st(A.v + oi, make_float2(ld_s(sv_prev + c * 512 + l6), v1));
-                PS::st(A.vbar_out + oi, make_float2(ld_s(svb_prev + c * 512 + l6), vbar_of(v1, v0)));
+                PS::st(vbo() + oi, make_float2(ld_s(svb_prev + c * 512 + l6), vbar_of(v1, v0)));
             }
         }
 
@@ -712,7 +757,7 @@ struct PairCta {
         }
         const size_t vi = (size_t)b * TGV_BVOX + l0;
         stf2(A.u + vi, make_float2(una, unb));
-        stf2(A.ubar_out + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
+        stf2(ubo() + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
         const bool park = to_next && j == 3;  // uniform per warp row group; implies L & 8
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -735,13 +780,13 @@ struct PairCta {
                 st_s((S*)(st + O_VB) + c * 512 + l0, vba);
             } else {
                 PS::st(A.v + oi, make_float2(v1a, v1b));
-                PS::st(A.vbar_out + oi, make_float2(vba, vbar_of(v1b, v0.y)));
+                PS::st(vbo() + oi, make_float2(vba, vbar_of(v1b, v0.y)));
             }
-            DP::st(A.p_out + oi, make_float2(pn0[c], pn1[c]), A.ds.isp);
+            DP::st(pout() + oi, make_float2(pn0[c], pn1[c]), A.ds.isp);
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c)
-            DP::st(A.q_out + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]), A.ds.isq);
+            DP::st(qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]), A.ds.isq);
     }
 };
 
