@@ -81,6 +81,17 @@ __device__ __forceinline__ int16_t fx16_encode(float x, float isc)
     return (int16_t)__float2int_rn(y);
 }
 __device__ __forceinline__ float fx16_decode(int16_t i, float dsc) { return __fmul_rn((float)i, dsc); }
+// Two values packed into one word (a low, b high) by the conversion to 16-bit integers,
+// which saturates at [-32768, 32767]; equal to fx16_encode for |x| <= 32767.5 / isc, which
+// holds for every dual the projections leave (|x| <= bound up to a few ulps).
+__device__ __forceinline__ uint32_t fx16_encode2(float a, float b, float isc)
+{
+    uint32_t r;
+    asm("{\n\t.reg .b16 lo, hi;\n\tcvt.rni.s16.f32 lo, %1;\n\tcvt.rni.s16.f32 hi, %2;\n\tmov.b32 %0, {lo, hi};\n\t}"
+        : "=r"(r)
+        : "f"(__fmul_rn(a, isc)), "f"(__fmul_rn(b, isc)));
+    return r;
+}
 
 template <typename D> __device__ __forceinline__ float ld_d(const D* p, float /*dsc*/) { return ld_s(p); }
 template <> __device__ __forceinline__ float ld_d<int16_t>(const int16_t* p, float dsc) { return fx16_decode(*p, dsc); }

@@ -50,7 +50,7 @@ template <> struct DPair<int16_t> {
     }
     static __device__ __forceinline__ void st(int16_t* p, float2 v, float isc)
     {
-        *(uint32_t*)p = (uint32_t)(uint16_t)fx16_encode(v.x, isc) | ((uint32_t)(uint16_t)fx16_encode(v.y, isc) << 16);
+        *(uint32_t*)p = fx16_encode2(v.x, v.y, isc);
     }
 };
 
