@@ -196,3 +196,60 @@ def in_flight_events(in_flight):
 def flush(in_flight):
     for _, keys in in_flight:
         yield from keys
+
+
+@dataclass
+class PartChunk:
+    """One treetop part of a level as an independent problem (its bricks active, its border
+    frozen): DomainDesc-like fields plus the part's brick indices in the level."""
+    origin: np.ndarray
+    h: float
+    bricks: np.ndarray
+    frozen: Optional[np.ndarray]
+    frozen_u: Optional[np.ndarray]
+    frozen_v: Optional[np.ndarray]
+    level_bricks: np.ndarray  # indices of the part's bricks in the level's brick list
+    radius: float = 0.0
+
+    @property
+    def nbricks(self) -> int:
+        return int(self.bricks.shape[0])
+
+    @property
+    def nvox(self) -> int:
+        return 512 * self.nbricks
+
+
+def part_chunks(level, brick_part: np.ndarray, u: np.ndarray, v: Optional[np.ndarray] = None) -> List[PartChunk]:
+    """Chunks of a level's treetop parts (Sec. 4.3: parts are solved independently; Sec.
+    4.5: the cubes of a part form the set A, its neighbouring cubes the set B whose
+    indicator stays fixed).  Part k's bricks (brick_part == k, parts numbered 0..K-1)
+    are active; every other brick of the level among their 26 neighbours is frozen with
+    its values from `u` (per voxel, the level's brick order, 512 per brick) and `v`
+    ((voxels, 3); zero if None) -- for a coarse-to-fine solve, the level's state after
+    tgv_prolong, i.e. the parent level's indicator.  Bricks of other levels or outside
+    the level are not part of the border (no link there)."""
+    b = np.asarray(level.bricks, np.int32).reshape(-1, 3)
+    index = {tuple(x): i for i, x in enumerate(b.tolist())}
+    u = np.asarray(u, np.float32).reshape(-1, 512)
+    v = np.zeros((b.shape[0] * 512, 3), np.float32) if v is None else np.asarray(v, np.float32).reshape(-1, 3)
+    vb = v.reshape(-1, 512, 3).transpose(0, 2, 1)  # [brick][component][512]
+    offs = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)]
+    out = []
+    for k in range(int(brick_part.max()) + 1):
+        mine = np.nonzero(brick_part == k)[0]
+        if len(mine) == 0:
+            continue
+        own = set(mine.tolist())
+        ring = set()
+        for i in mine.tolist():
+            x, y, z = b[i]
+            for dx, dy, dz in offs:
+                j = index.get((x + dx, y + dy, z + dz))
+                if j is not None and j not in own:
+                    ring.add(j)
+        ring = np.array(sorted(ring), np.int64)
+        out.append(PartChunk(np.asarray(level.origin, np.float64), float(level.h), b[mine],
+                             b[ring] if len(ring) else None, u[ring] if len(ring) else None,
+                             vb[ring] if len(ring) else None, mine, float(getattr(level, "radius", 0.0) or 0.0)))
+    return out
