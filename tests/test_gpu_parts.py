@@ -2,7 +2,7 @@
 A, its neighbouring cubes the set B whose indicator stays at the parent level's values).
 
 Coarse-to-fine on the sphere scene: level 0 (32^3) is solved, level 1 (64^3) starts from
-its prolongation.  The treetop of level 1's cubes (parts of fewer than 4096 cubes) splits
+its prolongation.  The treetop of level 1's cubes (parts of fewer than 5000 cubes) splits
 the level into parts; each part becomes a chunk whose border bricks are frozen to the
 prolonged field, and all parts run together in one persistent launch
 (tgv_solve_chunks).  Checks:
@@ -46,9 +46,9 @@ def setup():
     with tgv.Domain([fine], nbins=8, stream=s.cuda_stream) as dom:
         dom.set_histograms(0, hist)
         with tgv.Composite(dom) as comp:
-            _, _, _, _, leaf_part = comp.treetop(6, 4096)
+            _, _, _, _, leaf_part = comp.treetop(6, 5000)
     brick_part = leaf_part.reshape(-1, 512)
-    assert np.all(brick_part == brick_part[:, :1])  # parts hold whole bricks (4096 > 512)
+    assert np.all(brick_part == brick_part[:, :1])  # parts hold whole bricks (5000 > 512)
     brick_part = brick_part[:, 0]
     parts = part_chunks(fine, brick_part, u0, v0)
     return sc, fine, hist, u0, v0, parts, s
@@ -58,7 +58,7 @@ def test_treetop_gives_several_parts(setup):
     _, fine, _, _, _, parts, _ = setup
     assert len(parts) >= 8
     assert sum(p.nbricks for p in parts) == fine.nbricks
-    assert all(p.nvox < 4096 for p in parts)
+    assert all(p.nvox < 5000 for p in parts) and max(p.nbricks for p in parts) == 8
 
 
 @pytest.fixture(scope="module")
