@@ -437,7 +437,8 @@ def _oracle_u(spec, iters):
     return lvl.u
 
 
-def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fx16"), run_lengths=(16,)):
+def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fx16"), run_lengths=(16,),
+                  tune=True):
     """Bounded form of the batched workload for the default line: `nchunks` chunks of the
     c4 size distribution (log-uniform 32^3..192^3 active voxels, frozen one-brick shell,
     10 bins, `iters` iterations), sharded over the ranks (strong scaling: each rank solves
@@ -494,6 +495,23 @@ def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("
             out[key] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms, "run_length": R,
                         "launches": dom.launches - l0}
         dom.close()
+    if tune:
+        # the autotuner's choice for this chunk mix (timed on a sample of it, cached per mix)
+        from paper_2107_14790_b300 import autotune
+        from paper_2107_14790_b300.batching import batch_domain, run_batch
+        for storage in storages:
+            ch = autotune.tune_batch([sp.domain for sp in specs], 10, storage, hist_of=lambda dm, m={
+                id(sp.domain): sp.hist for sp in specs}: m[id(dm)])
+            dom = batch_domain(U, 10, storage, stream.cuda_stream, ch)
+            dom.set_histograms(0, hist)
+            run_batch(dom, U, iters, ch)
+            dom.reset(0)
+            l0 = dom.launches
+            ms = timed(lambda: run_batch(dom, U, iters, ch))
+            launches += dom.launches - l0
+            out[f"autotuned_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms,
+                                           "choice": {k: ch[k] for k in ("form", "iter_kernel", "run_length")}}
+            dom.close()
     doms = []
     for sp in specs:
         d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)
@@ -629,6 +647,23 @@ def run_batched(args):
                         "achieved_gbs": nvox * bpv / (ms / 1e3 / iters) / 1e9, "u_err_inf_vs_fp64_oracle": err}
         dom.close()
     # plain form: every chunk alone, FP32
+    if tune:
+        # the autotuner's choice for this chunk mix (timed on a sample of it, cached per mix)
+        from paper_2107_14790_b300 import autotune
+        from paper_2107_14790_b300.batching import batch_domain, run_batch
+        for storage in storages:
+            ch = autotune.tune_batch([sp.domain for sp in specs], 10, storage, hist_of=lambda dm, m={
+                id(sp.domain): sp.hist for sp in specs}: m[id(dm)])
+            dom = batch_domain(U, 10, storage, stream.cuda_stream, ch)
+            dom.set_histograms(0, hist)
+            run_batch(dom, U, iters, ch)
+            dom.reset(0)
+            l0 = dom.launches
+            ms = timed(lambda: run_batch(dom, U, iters, ch))
+            launches += dom.launches - l0
+            out[f"autotuned_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms,
+                                           "choice": {k: ch[k] for k in ("form", "iter_kernel", "run_length")}}
+            dom.close()
     doms = []
     for sp in specs:
         d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)

@@ -120,3 +120,98 @@ def choose(storage: str, nbins: int, nvox: int, allow_tuning: bool = True) -> Op
     if rec is None and allow_tuning:
         rec = tune(storage, nbins, cls)
     return rec
+
+
+# ------------------------------------------------------------------------ the batched solve
+# Candidates for a mix of chunks (one union level): the union form (one launch per iteration,
+# replayed as a CUDA graph) with the paired kernel at several run lengths or the pipelined
+# kernel (one voxel per thread, 512 threads: another CTA shape), and the persistent launch
+# (tgv_solve_chunks) at several run lengths.
+BATCH_CANDIDATES = ([("union_graph", "paired", x) for x in (0, 1, 4, 16)] + [("union_graph", "pipelined", 0)] +
+                    [("persistent", "paired", r) for r in (8, 16, 32)])
+
+
+def mix_signature(sizes) -> str:
+    """Size classes of a chunk mix: counts of chunks per power-of-two voxel count."""
+    cls = {}
+    for n in sizes:
+        k = int(np.log2(max(int(n), 1)))
+        cls[k] = cls.get(k, 0) + 1
+    return ",".join(f"{k}:{cls[k]}" for k in sorted(cls))
+
+
+def sample_chunks(chunks, max_voxels: int = 8 << 20):
+    """A sample of a chunk mix that keeps its size distribution: chunks taken at even steps
+    through the size-sorted list until `max_voxels` voxels are reached (at least one)."""
+    order = sorted(range(len(chunks)), key=lambda k: chunks[k].nvox)
+    out, tot = [], 0
+    step = max(1, len(order) // 16)
+    for i in list(range(0, len(order), step)) + list(range(1, len(order), step)):
+        c = chunks[order[i]]
+        if out and tot + c.nvox > max_voxels:
+            continue
+        out.append(c)
+        tot += c.nvox
+    return out
+
+
+def time_batch_candidate(U, hist, nbins: int, storage: str, cand, iters: int = 24) -> float:
+    """Nanoseconds per voxel-iteration of one candidate on union level U with counts `hist`."""
+    import torch
+    form, kernel, x = cand
+    stream = torch.cuda.Stream()
+    kw = dict(iter_kernel=kernel, x_run=x if form == "union_graph" else 0)
+    with tgv.Domain([U], nbins=nbins, storage=storage, stream=stream.cuda_stream, **kw) as dom:
+        dom.set_histograms(0, hist)
+        first = U.first
+        its = [iters] * len(U.ranges)
+
+        def run():
+            if form == "union_graph":
+                dom.solve_graph(0, iters)
+            else:
+                dom.solve_chunks(0, first, its, run_length=x)
+        run()  # warm up and capture
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        dom.synchronize()
+        return e0.elapsed_time(e1) * 1e6 / (iters * 512 * len(U.bricks))
+
+
+def tune_batch(chunks, nbins: int, storage: str, hist_of=None, force: bool = False, seed: int = 12) -> dict:
+    """Measures every batched candidate on a sample of the chunk mix it will serve and caches
+    the fastest per (device, storage, bins, size classes of the mix).  `chunks`: DomainDesc-
+    like chunks (bricks, frozen shell); `hist_of(chunk)` gives a chunk's counts (seeded
+    random counts when None).  Returns the record: form, kernel, run length, ns per
+    voxel-iteration and every candidate's time."""
+    import synth
+    from .batching import union_level
+    with _lock:
+        cache = _load()
+        key = f"batch|{_device_name()}|{storage}|{nbins}|{mix_signature([c.nvox for c in chunks])}"
+        if key in cache and not force:
+            return cache[key]
+        sample = sample_chunks(chunks)
+        U = union_level(sample)
+        rng = np.random.default_rng(seed)
+        def counts(c):
+            if hist_of is None:
+                return synth.random_histograms(rng, c.nvox, nbins, max_count=20)
+            x = hist_of(c)
+            return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+        hs = [counts(c) for c in sample]
+        hist = np.concatenate(hs).astype(np.uint32)
+        times = {}
+        for cand in BATCH_CANDIDATES:
+            times["/".join(map(str, cand))] = time_batch_candidate(U, hist, nbins, storage, cand)
+        best = min(times, key=times.get)
+        form, kernel, x = best.split("/")
+        rec = {"form": form, "iter_kernel": kernel, "run_length": int(x), "ns_per_voxel_iteration": times[best],
+               "sample_chunks": len(sample), "sample_voxels": int(sum(c.nvox for c in sample)),
+               "candidates": times}
+        cache[key] = rec
+        _store(cache)
+        return rec

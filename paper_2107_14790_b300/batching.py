@@ -253,3 +253,18 @@ def part_chunks(level, brick_part: np.ndarray, u: np.ndarray, v: Optional[np.nda
                              b[ring] if len(ring) else None, u[ring] if len(ring) else None,
                              vb[ring] if len(ring) else None, mine, float(getattr(level, "radius", 0.0) or 0.0)))
     return out
+
+
+def batch_domain(U: UnionLevel, nbins: int, storage: str, stream: int, choice: dict) -> "tgv.Domain":
+    """A domain over union level U set up for an autotuner choice (autotune.tune_batch)."""
+    x = choice["run_length"] if choice["form"] == "union_graph" else 0
+    return tgv.Domain([U], nbins=nbins, storage=storage, stream=stream, iter_kernel=choice["iter_kernel"], x_run=x)
+
+
+def run_batch(dom: "tgv.Domain", U: UnionLevel, iterations: int, choice: dict):
+    """`iterations` iterations of every chunk of U in the chosen form: the union level's
+    launches replayed as a CUDA graph, or one persistent launch (tgv_solve_chunks)."""
+    if choice["form"] == "union_graph":
+        dom.solve_graph(0, iterations)
+    else:
+        dom.solve_chunks(0, U.first, [iterations] * len(U.ranges), run_length=choice["run_length"])

@@ -213,3 +213,28 @@ def test_autotuner_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
         dom.solve(0, 9)
         u = dom.field(0, "u")[:, 0]
     np.testing.assert_array_equal(u, solve_alone(sp, 18, iter_kernel=rec["iter_kernel"]))
+
+
+def test_batch_autotuner_on_the_chunk_mix(tmp_path, monkeypatch):
+    """The batched tuner times every candidate (union launches at several run lengths, the
+    pipelined CTA shape, the persistent launch at several run lengths) on a sample of the
+    chunk mix, caches the winner per mix, and a batch run in the chosen form equals each
+    chunk solved alone."""
+    from paper_2107_14790_b300 import autotune
+    from paper_2107_14790_b300.batching import batch_domain, run_batch, union_level
+    monkeypatch.setenv("TGV_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    specs = chunks(48, 5, 4, 60)
+    doms = [sp.domain for sp in specs]
+    rec = autotune.tune_batch(doms, 10, "fp32", hist_of=lambda d: specs[doms.index(d)].hist)
+    assert len(rec["candidates"]) == len(autotune.BATCH_CANDIDATES)
+    assert rec["ns_per_voxel_iteration"] == min(rec["candidates"].values())
+    assert rec["form"] in ("union_graph", "persistent")
+    assert autotune.tune_batch(doms, 10, "fp32") == rec  # cached for this mix
+    U = union_level(doms)
+    s = torch.cuda.Stream()
+    with batch_domain(U, 10, "fp32", s.cuda_stream, rec) as dom:
+        dom.set_histograms(0, np.concatenate([sp.hist for sp in specs]))
+        run_batch(dom, U, 9, rec)
+        u = dom.field(0, "u")[:, 0]
+    for sp, (a, b) in zip(specs, U.ranges):
+        np.testing.assert_array_equal(u[512 * a:512 * b], solve_alone(sp, 9))
