@@ -237,4 +237,4 @@ def test_batch_autotuner_on_the_chunk_mix(tmp_path, monkeypatch):
         run_batch(dom, U, 9, rec)
         u = dom.field(0, "u")[:, 0]
     for sp, (a, b) in zip(specs, U.ranges):
-        np.testing.assert_array_equal(u[512 * a:512 * b], solve_alone(sp, 9))
+        np.testing.assert_array_equal(u[512 * a:512 * b], solve_alone(sp, 9, iter_kernel=rec["iter_kernel"]))
