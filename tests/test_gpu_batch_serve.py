@@ -225,7 +225,8 @@ def test_batch_autotuner_on_the_chunk_mix(tmp_path, monkeypatch):
     monkeypatch.setenv("TGV_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     specs = chunks(48, 5, 4, 60)
     doms = [sp.domain for sp in specs]
-    rec = autotune.tune_batch(doms, 10, "fp32", hist_of=lambda d: specs[doms.index(d)].hist)
+    by_id = {id(d): sp.hist for d, sp in zip(doms, specs)}
+    rec = autotune.tune_batch(doms, 10, "fp32", hist_of=lambda d: by_id[id(d)])
     assert len(rec["candidates"]) == len(autotune.BATCH_CANDIDATES)
     assert rec["ns_per_voxel_iteration"] == min(rec["candidates"].values())
     assert rec["form"] in ("union_graph", "persistent")
