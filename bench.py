@@ -37,7 +37,7 @@ SMALL = dict(workload="dense-64^3-sphere-16x128^2-maps-8bins-200it", n=64, nmaps
 # sources that define each form of the fused iteration kernel (the traffic counters are
 # valid only for the sources they were taken on)
 ITER_KERNEL_SRCS = {form: [os.path.join(ROOT, "paper_2107_14790_b300", "csrc", f)
-                           for f in (main, "tgv_internal.cuh", "tgv_async.cuh")]
+                           for f in (main, "tgv_internal.cuh", "tgv_async.cuh", "tgv_pair_cta.cuh")]
                     for form, main in (("paired", "tgv_iter_pair.cu"), ("pipelined", "tgv_iter_pipe.cu"),
                                        ("one_brick_per_cta", "tgv_solve.cu"))}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tgv_iter_kernel_dense256_traffic.json")

@@ -46,7 +46,7 @@
 // The level kernel: CTA r takes runs r, r + G, r + 2G, ... of R consecutive work items
 // (G = grid size) and sweeps them with the paired machinery.
 template <typename S, typename D, int NB>
-__global__ void __launch_bounds__(kThreads, 2) tgv_iter_pair_kernel(const PairArgs<S, D> P)
+__global__ void __launch_bounds__(kThreads, sizeof(D) == 2 ? 3 : 2) tgv_iter_pair_kernel(const PairArgs<S, D> P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     PairCta<S, D, NB> C(P, smem);

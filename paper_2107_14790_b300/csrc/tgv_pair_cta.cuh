@@ -54,6 +54,64 @@ template <> struct DPair<int16_t> {
     }
 };
 
+// A new dual as the level stores it.  16-bit duals are rounded to their storage type once,
+// right after the projection, and that stored value is what the primal step, the run
+// hand-overs and the recomputed halo duals use (so a brick's own new duals can live in its
+// stage, in place of the old ones); FP32 duals are unchanged.
+template <typename D> struct DRound {
+    static __device__ __forceinline__ float r(float x, float /*dsc*/, float /*isc*/) { return x; }
+};
+template <> struct DRound<__half> {
+    static __device__ __forceinline__ float r(float x, float, float) { return __half2float(__float2half_rn(x)); }
+};
+template <> struct DRound<__nv_bfloat16> {
+    static __device__ __forceinline__ float r(float x, float, float)
+    {
+        return __bfloat162float(__float2bfloat16_rn(x));
+    }
+};
+// Fixed point: adding 1.5 * 2^23 to y = x * isc (|y| <= 32768 < 2^22 for a projected dual)
+// rounds y to the nearest integer k (ties to even) in the FP32 addition itself, and k sits
+// in the low bits of the sum: the same k as fx16_encode, at two full-rate operations.
+constexpr float kRoundMagic = 12582912.0f;
+template <> struct DRound<int16_t> {
+    static __device__ __forceinline__ float r(float x, float dsc, float isc)
+    {
+        return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(x, isc), kRoundMagic), kRoundMagic), dsc);
+    }
+};
+
+// Stores a pair of new duals in the storage type and replaces them by the stored values.
+template <typename D> struct DRoundStore;
+template <> struct DRoundStore<float> {
+    static __device__ __forceinline__ void st(float* p, float2& v, float, float) { *(float2*)p = v; }
+};
+template <> struct DRoundStore<__half> {
+    static __device__ __forceinline__ void st(__half* p, float2& v, float, float)
+    {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        *(__half2*)p = h;
+        v = __half22float2(h);
+    }
+};
+template <> struct DRoundStore<__nv_bfloat16> {
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float2& v, float, float)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        *(__nv_bfloat162*)p = h;
+        v = __bfloat1622float2(h);
+    }
+};
+template <> struct DRoundStore<int16_t> {
+    static __device__ __forceinline__ void st(int16_t* p, float2& v, float dsc, float isc)
+    {
+        const float sa = __fadd_rn(__fmul_rn(v.x, isc), kRoundMagic);
+        const float sb = __fadd_rn(__fmul_rn(v.y, isc), kRoundMagic);
+        *(uint32_t*)p = __byte_perm(__float_as_uint(sa), __float_as_uint(sb), 0x5410);  // low halves: k_a, k_b
+        v = make_float2(__fmul_rn(__fsub_rn(sa, kRoundMagic), dsc), __fmul_rn(__fsub_rn(sb, kRoundMagic), dsc));
+    }
+};
+
 __device__ __forceinline__ float2 ldf2(const float* p) { return *(const float2*)p; }
 __device__ __forceinline__ void stf2(float* p, float2 v) { *(float2*)p = v; }
 
@@ -101,10 +159,11 @@ __device__ __forceinline__ float vnew(float v0, float p, float d2, float tau)
 }
 __device__ __forceinline__ float vbar_of(float v1, float v0) { return __fsub_rn(__fmul_rn(2.0f, v1), v0); }
 
-// new p for the halo pair (2hj, 7, hw) / (2hj, hw, 7) on the -AX face (AX = 1: y, 2: z)
-template <int AX>
+// new p for the halo pair (2hj, 7, hw) / (2hj, hw, 7) on the -AX face (AX = 1: y, 2: z),
+// rounded as the owner stores it (D, scales dsc / isc)
+template <typename D, int AX>
 __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const float* sub, float* hal_p, int tk,
-                                            float sigma, float alpha1, float a1sq)
+                                            float sigma, float alpha1, float a1sq, float dsc, float isc)
 {
     constexpr int OA = 3 - AX;  // the other face axis
     const int hj = tk & 3, hw = tk >> 2;
@@ -123,13 +182,14 @@ __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const f
     upd_p(pb, gb, vb, sigma, alpha1, a1sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) stf2(hal_p + c * 192 + AX * 64 + fi, make_float2(pa[c], pb[c]));
+    for (int c = 0; c < 3; ++c)
+        stf2(hal_p + c * 192 + AX * 64 + fi, make_float2(DRound<D>::r(pa[c], dsc, isc), DRound<D>::r(pb[c], dsc, isc)));
 }
 
-// new q for the halo pair (2hj, 0, hw) / (2hj, hw, 0) on the +AX face
-template <typename S, int AX>
+// new q for the halo pair (2hj, 0, hw) / (2hj, hw, 0) on the +AX face, rounded as stored
+template <typename S, typename D, int AX>
 __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S* svb, float* hal_q, int tk,
-                                            float sigma, float alpha0, float a0sq)
+                                            float sigma, float alpha0, float a0sq, float dsc, float isc)
 {
     constexpr int OA = 3 - AX;
     const int hj = tk & 3, hw = tk >> 2;
@@ -156,14 +216,15 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
     upd_q(eb, dmb, sigma, alpha0, a0sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) stf2(hal_q + c * 192 + AX * 64 + fi, make_float2(ea[c], eb[c]));
+    for (int c = 0; c < 6; ++c)
+        stf2(hal_q + c * 192 + AX * 64 + fi, make_float2(DRound<D>::r(ea[c], dsc, isc), DRound<D>::r(eb[c], dsc, isc)));
 }
 
 }  // namespace
 
 // Shared-memory layout of a paired CTA: two stages (one brick's u, ubar, v, vbar, p, q
-// and packed histogram each), the FP32 new duals of each stage when the duals are stored
-// in 16 bits, the halo duals of each stage, two neighbour rows, three mbarriers.
+// and packed histogram each; a brick's new duals replace its old ones in place), the halo
+// duals of each stage, two neighbour rows, three mbarriers.
 struct PairLayout {
     uint32_t tx, stage, pn_bytes, off_pn, off_hal, off_nbr, off_bar, end;
 };
@@ -172,7 +233,7 @@ __host__ __device__ constexpr PairLayout pair_layout(uint32_t sb, uint32_t sd, u
     PairLayout L{};
     L.tx = 4096 + (6 * sb + 9 * sd) * 512 + npairs * 2048;
     L.stage = (L.tx + 127) / 128 * 128;
-    L.pn_bytes = sd == 4 ? 0 : 9 * 512 * 4;
+    L.pn_bytes = 0;  // new duals live in the stage (16-bit ones rounded as stored)
     L.off_pn = 2 * L.stage;
     L.off_hal = L.off_pn + 2 * L.pn_bytes;
     L.off_nbr = L.off_hal + 2 * 9 * 192 * 4;
@@ -222,6 +283,11 @@ struct PairCta {
     // with a compile-time bin count every offset is a constant (the launcher uses the same
     // pair_layout); NB = 0 reads them from the arguments
     static constexpr PairLayout LC = pair_layout(SB, SD, NB ? (NB + 1) / 2 : 1);
+    // FP32 duals (two CTAs per SM): the next item's halo inputs are loaded into registers
+    // before phase B of the current one, so their latency overlaps it; 16-bit duals (three
+    // CTAs per SM, 80 registers): they are loaded just before phase A and the other CTAs'
+    // warps cover the latency
+    static constexpr bool kEarlyLoads = SD == 4;
 
     const PairArgs<S, D>& P;
     const IterArgs<S, D>& A;
@@ -280,13 +346,38 @@ struct PairCta {
     __device__ __forceinline__ uint32_t off_bar() const { return NB ? LC.off_bar : P.off_bar; }
     __device__ __forceinline__ uint32_t tx_bytes() const { return NB ? LC.tx : P.tx_bytes; }
     __device__ __forceinline__ unsigned char* stage(int s) const { return smem + (size_t)s * stage_bytes(); }
-    __device__ __forceinline__ float* pn_own(int s) const
+    // a brick's own new duals, in its stage in place of the old ones (storage type D; FP32
+    // or the rounded 16-bit value): pairs and single values at voxel index i of component c
+    __device__ __forceinline__ const D* np_(int s) const { return (const D*)(stage(s) + O_P); }
+    __device__ __forceinline__ const D* nq_(int s) const { return (const D*)(stage(s) + O_Q); }
+    __device__ __forceinline__ float2 ldp2(int s, int i) const { return DP::ld(np_(s) + i, A.ds.dsp); }
+    __device__ __forceinline__ float2 ldq2(int s, int i) const { return DP::ld(nq_(s) + i, A.ds.dsq); }
+    __device__ __forceinline__ float ldp1(int s, int i) const { return ld_d(np_(s) + i, A.ds.dsp); }
+    __device__ __forceinline__ float ldq1(int s, int i) const { return ld_d(nq_(s) + i, A.ds.dsq); }
+    // stores a new dual pair (rounded to the storage type) and returns the stored values
+    __device__ __forceinline__ float2 stp2(int s, int i, float2 v) const
     {
-        return (float*)(SD == 4 ? stage(s) + O_P : smem + off_pn() + (size_t)s * LC.pn_bytes);
+        DRoundStore<D>::st((D*)np_(s) + i, v, A.ds.dsp, A.ds.isp);
+        return v;
     }
-    __device__ __forceinline__ float* qn_own(int s) const
+    __device__ __forceinline__ float2 stq2(int s, int i, float2 v) const
     {
-        return (float*)(SD == 4 ? stage(s) + O_Q : smem + off_pn() + (size_t)s * LC.pn_bytes + 3 * 512 * 4);
+        DRoundStore<D>::st((D*)nq_(s) + i, v, A.ds.dsq, A.ds.isq);
+        return v;
+    }
+    __device__ __forceinline__ float rp(float x) const { return DRound<D>::r(x, A.ds.dsp, A.ds.isp); }
+    __device__ __forceinline__ float rq(float x) const { return DRound<D>::r(x, A.ds.dsq, A.ds.isq); }
+    // global store of a new dual pair held in the stage: the stored word itself (16-bit), or
+    // the FP32 values
+    __device__ __forceinline__ void out_p2(int s, int i, D* dst, float2 v) const
+    {
+        if constexpr (SD == 4) stf2((float*)dst, v);
+        else *(uint32_t*)dst = *(const uint32_t*)(np_(s) + i);
+    }
+    __device__ __forceinline__ void out_q2(int s, int i, D* dst, float2 v) const
+    {
+        if constexpr (SD == 4) stf2((float*)dst, v);
+        else *(uint32_t*)dst = *(const uint32_t*)(nq_(s) + i);
     }
     __device__ __forceinline__ float* hal_p(int s) const { return (float*)(smem + off_hal()) + s * (9 * 192); }
     __device__ __forceinline__ float* hal_q(int s) const { return hal_p(s) + 3 * 192; }
@@ -494,8 +585,8 @@ struct PairCta {
         }
     }
 
-    // ---- phase A of the brick in stage s: new p, q at the own pair (into pn_own / qn_own)
-    // and the halo duals (into hal_p / hal_q).  Returns the link bits phase B needs.
+    // ---- phase A of the brick in stage s: new p, q at the own pair (into the stage, in
+    // place of the old ones) and the halo duals (into hal_p / hal_q).  Returns the link bits phase B needs.
     // from_prev: this brick is the +x neighbour and run successor of brick bprev, whose
     // phase B parked the partial v update of its x = 7 voxels (completed here);
     // to_next: the next item is this brick's +x neighbour (its -x halo p is written here).
@@ -551,13 +642,20 @@ struct PairCta {
             upd_q(qn0, dm0, sigma, alpha0, a0sq);
             upd_q(qn1, dm1, sigma, alpha0, a0sq);
         }
-        // own old p / q were read above by this thread only; overwrite in place (FP32) or store
-        float* pno = pn_own(s);
-        float* qno = qn_own(s);
+        // the values the level stores (16-bit duals rounded once); own old p / q were read
+        // above by this thread only: overwrite them in place
 #pragma unroll
-        for (int c = 0; c < 3; ++c) stf2(pno + c * 512 + l0, make_float2(pn0[c], pn1[c]));
+        for (int c = 0; c < 3; ++c) {
+            const float2 r = stp2(s, c * 512 + l0, make_float2(pn0[c], pn1[c]));
+            pn0[c] = r.x;
+            pn1[c] = r.y;
+        }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) stf2(qno + c * 512 + l0, make_float2(qn0[c], qn1[c]));
+        for (int c = 0; c < 6; ++c) {
+            const float2 r = stq2(s, c * 512 + l0, make_float2(qn0[c], qn1[c]));
+            qn0[c] = r.x;
+            qn1[c] = r.y;
+        }
         // hand-over along the run
         if (to_next && j == 3) hal_p(s ^ 1)[y + 8 * z] = pn1[0];
         if (from_prev && j == 0) {
@@ -565,7 +663,6 @@ struct PairCta {
             // still in the other stage; add the x-forward term (this voxel's new q)
             const int ps = s ^ 1;
             const float* hq_prev = hal_q(ps);
-            const float* pn_prev = pn_own(ps);
             const S* sv_prev = (const S*)(stage(ps) + O_V);
             const S* svb_prev = (const S*)(stage(ps) + O_VB);
             const uint32_t l6 = 6 + 8 * y + 64 * z;
@@ -574,7 +671,7 @@ struct PairCta {
                 const int qc = qidx(0, c);
                 const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qn0[qc]);
                 const float v0 = ld_s(sv_prev + c * 512 + l6 + 1);
-                const float v1 = vnew(v0, pn_prev[c * 512 + l6 + 1], d2, A.tau);
+                const float v1 = vnew(v0, ldp1(ps, c * 512 + l6 + 1), d2, A.tau);
                 // with the x = 6 values parked by its phase B: one pair store per field
                 const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l6;
                 PS::st(A.v + oi, make_float2(ld_s(sv_prev + c * 512 + l6), v1));
@@ -594,11 +691,11 @@ struct PairCta {
                 const float vv[3] = {h[6], h[8], h[10]};
                 upd_p(pp, g, vv, sigma, alpha1, a1sq);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) hp[c * 192 + tk] = pp[c];
+                for (int c = 0; c < 3; ++c) hp[c * 192 + tk] = rp(pp[c]);
             } else if (task == 1) {
-                halo_p_pair<1>(h, hm, sub, hp, tk, sigma, alpha1, a1sq);
+                halo_p_pair<D, 1>(h, hm, sub, hp, tk, sigma, alpha1, a1sq, A.ds.dsp, A.ds.isp);
             } else if (task == 2) {
-                halo_p_pair<2>(h, hm, sub, hp, tk, sigma, alpha1, a1sq);
+                halo_p_pair<D, 2>(h, hm, sub, hp, tk, sigma, alpha1, a1sq, A.ds.dsp, A.ds.isp);
             } else if (task == 3) {  // q at (0, hy, hz) of the +x brick
                 const int hy = tk & 7, hz = tk >> 3;
                 const uint32_t lo = 7 + 8 * hy + 64 * hz;
@@ -614,11 +711,11 @@ struct PairCta {
                 for (int c = 0; c < 6; ++c) e[c] = h[18 + 2 * c];
                 upd_q(e, dm, sigma, alpha0, a0sq);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) hq[c * 192 + tk] = e[c];
+                for (int c = 0; c < 6; ++c) hq[c * 192 + tk] = rq(e[c]);
             } else if (task == 4) {
-                halo_q_pair<S, 1>(h, hm, svb, hq, tk, sigma, alpha0, a0sq);
+                halo_q_pair<S, D, 1>(h, hm, svb, hq, tk, sigma, alpha0, a0sq, A.ds.dsq, A.ds.isq);
             } else {
-                halo_q_pair<S, 2>(h, hm, svb, hq, tk, sigma, alpha0, a0sq);
+                halo_q_pair<S, D, 2>(h, hm, svb, hq, tk, sigma, alpha0, a0sq, A.ds.dsq, A.ds.isq);
             }
         }
         // link bits for phase B: bit 2k "any", bit 2k+1 "active", k = 0 (-x of voxel 0),
@@ -642,20 +739,18 @@ struct PairCta {
         const float* su = (const float*)(st + O_U);
         const S* sv = (const S*)(st + O_V);
         const uint32_t* sh = (const uint32_t*)(st + O_H);
-        const float* pno = pn_own(s);
-        const float* qno = qn_own(s);
         const float* hp = hal_p(s);
         const float* hq = hal_q(s);
         float pn0[3], pn1[3], qn0[6], qn1[6];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 w = ldf2(pno + c * 512 + l0);
+            const float2 w = ldp2(s, c * 512 + l0);
             pn0[c] = w.x;
             pn1[c] = w.y;
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float2 w = ldf2(qno + c * 512 + l0);
+            const float2 w = ldq2(s, c * 512 + l0);
             qn0[c] = w.x;
             qn1[c] = w.y;
         }
@@ -665,7 +760,7 @@ struct PairCta {
         //    voxel 1: backward = voxel 0, forward = (x0+2) or the +x brick
         // (voxel 1's x-forward div2 q term is added last, after y and z)
         d1a += pn0[0];
-        if (L & 2u) d1a -= j > 0 ? pno[l0 - 1] : hp[y + 8 * z];
+        if (L & 2u) d1a -= j > 0 ? ldp1(s, l0 - 1) : hp[y + 8 * z];
         if (L & 4u) d1b += pn1[0];
         d1b -= pn0[0];
 #pragma unroll
@@ -682,7 +777,7 @@ struct PairCta {
             d1b += pn1[1];
         }
         if (L & 128u) {
-            const float2 w = y > 0 ? ldf2(pno + 512 + l0 - 8) : ldf2(hp + 192 + fyi);
+            const float2 w = y > 0 ? ldp2(s, 512 + l0 - 8) : ldf2(hp + 192 + fyi);
             d1a -= w.x;
             d1b -= w.y;
         }
@@ -690,7 +785,7 @@ struct PairCta {
         for (int c = 0; c < 3; ++c) {
             const int qc = qidx(1, c);
             if (L & 32u) {
-                const float2 w = y < 7 ? ldf2(qno + qc * 512 + l0 + 8) : ldf2(hq + qc * 192 + fyi);
+                const float2 w = y < 7 ? ldq2(s, qc * 512 + l0 + 8) : ldf2(hq + qc * 192 + fyi);
                 d2a[c] += w.x;
                 d2b[c] += w.y;
             }
@@ -706,7 +801,7 @@ struct PairCta {
             d1b += pn1[2];
         }
         if (L & 2048u) {
-            const float2 w = z > 0 ? ldf2(pno + 1024 + l0 - 64) : ldf2(hp + 384 + fzi);
+            const float2 w = z > 0 ? ldp2(s, 1024 + l0 - 64) : ldf2(hp + 384 + fzi);
             d1a -= w.x;
             d1b -= w.y;
         }
@@ -714,7 +809,7 @@ struct PairCta {
         for (int c = 0; c < 3; ++c) {
             const int qc = qidx(2, c);
             if (L & 512u) {
-                const float2 w = z < 7 ? ldf2(qno + qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi);
+                const float2 w = z < 7 ? ldq2(s, qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi);
                 d2a[c] += w.x;
                 d2b[c] += w.y;
             }
@@ -768,7 +863,7 @@ struct PairCta {
             // every lane forms the pair (a parking lane's x = 7 value is not used), so
             // only the stores below depend on the lane
             const float part = d2b[c];
-            const float fwdq = j < 3 ? qno[qidx(0, c) * 512 + l0 + 2] : hq[qidx(0, c) * 192 + y + 8 * z];
+            const float fwdq = j < 3 ? ldq1(s, qidx(0, c) * 512 + l0 + 2) : hq[qidx(0, c) * 192 + y + 8 * z];
             const float d2c = (L & 8u) ? __fadd_rn(part, fwdq) : part;
             const float v1b = vnew(v0.y, pn1[c], d2c, A.tau);
             if (park) {
@@ -782,11 +877,11 @@ struct PairCta {
                 PS::st(A.v + oi, make_float2(v1a, v1b));
                 PS::st(vbo() + oi, make_float2(vba, vbar_of(v1b, v0.y)));
             }
-            DP::st(pout() + oi, make_float2(pn0[c], pn1[c]), A.ds.isp);
+            out_p2(s, c * 512 + l0, pout() + oi, make_float2(pn0[c], pn1[c]));
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c)
-            DP::st(qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]), A.ds.isq);
+            out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
     }
 };
 
@@ -869,7 +964,7 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, const Seq& q, u
         uint32_t next_links = 0;
         if (itn < nit) {
             next_to_next = itnn == itn + 1 && itnn < nit && C.nbr_row(ns)[NB_PX] == (int)bnn;
-            C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
+            if (PairCta<S, D, NB>::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
         }
         // the row of the item in hand is no longer read: reuse it for item itnn
         if (t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
@@ -889,6 +984,7 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, const Seq& q, u
             }
             late = !ok;
             __syncwarp();
+            if (!PairCta<S, D, NB>::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
             next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
         }
         // stage s, the phase A results of item itn and the hand-over are settled
