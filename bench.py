@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched block of the default line")
+    ap.add_argument("--no-reduced", action="store_true", help="skip the 16-bit storage block of the default line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving block of the default line")
     ap.add_argument("--block-chunks", type=int, default=32, help="batched block: chunks (c4's size distribution)")
     ap.add_argument("--block-requests", type=int, default=200, help="serving block: requests")
@@ -284,7 +285,13 @@ def run_ours(args, cfg):
         result["e2e"] = {"value": world * nvox * iters * args.steps / e_s, "unit": "voxel-updates/s",
                          "h2d_bytes_per_step": int(depth_host.numel() * 4),
                          "d2h_bytes_per_step": int(nvox * 4 + 8 * 4 * len(blocks))}
+    u_ref = dom.field(0, "u")[:, 0].copy()
     dom.close()
+    if not args.no_reduced and not args.small and args.storage == "fp32":
+        rb = reduced_block(sc, cfg, depth_dev, stream, u_ref)
+        rb["frac"] = rb["achieved_gbs"] / peak
+        rb["speedup_over_fp32"] = rb["voxel_updates_per_s"] / value
+        result["reduced_precision"] = rb
     del depth_dev
     torch.cuda.empty_cache()
     # bounded blocks of the batched and served forms (the metric's chunk-solve latency)
@@ -435,6 +442,51 @@ def _oracle_u(spec, iters):
     lvl.hist[:] = h.cpu().numpy() if hasattr(h, "cpu") else h
     lvl.iterate(iters)
     return lvl.u
+
+
+def reduced_block(sc, cfg, depth_dev, stream, u_ref, storage="fx16", steps=3):
+    """The default workload with 16-bit storage of v, vbar, p, q: the same step (reset,
+    histograms, the configured iterations with energy/gap checks), timed over `steps` steps;
+    the fused kernel's mean launch time and its algorithmic bandwidth; max and RMS of the
+    final u against the FP32 run's (the stated accuracy of the reduced forms: 5e-3)."""
+    import torch
+    from paper_2107_14790_b300 import tgv
+    nbins, iters, ce = cfg["nbins"], cfg["iterations"], cfg["check_every"]
+    blocks = [ce] * (iters // ce) + ([iters % ce] if iters % ce else [])
+    dom = tgv.Domain([sc.domain], nbins=nbins, storage=storage, stream=stream.cuda_stream)
+    nvox = dom.voxels(0)
+
+    def step(ev=None):
+        dom.reset(0, clear_hist=True)
+        dom.accumulate(0, sc.cameras, depth_dev)
+        for nb in blocks:
+            if ev is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            tgv.tgv_solve(dom.handle, 0, nb, False)
+            if ev is not None:
+                e1.record(stream)
+                ev.append((e0, e1, nb))
+            dom.energy(0)
+    step()
+    torch.cuda.synchronize()
+    ev = []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step(ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    per_launch = sum(a.elapsed_time(b) for a, b, _ in ev) / sum(n for _, _, n in ev) / 1e3
+    u = dom.field(0, "u")[:, 0]
+    dom.close()
+    d = np.abs(u.astype(np.float64) - u_ref.astype(np.float64))
+    bpv = algorithmic_bytes_per_voxel(nbins, storage)
+    return {"storage": storage, "voxel_updates_per_s": nvox * iters / (ms / 1e3), "ms_per_step": ms,
+            "mean_launch_us": per_launch * 1e6, "algorithmic_bytes_per_voxel": bpv,
+            "achieved_gbs": nvox * bpv / per_launch / 1e9, "u_err_inf_vs_fp32": float(d.max()),
+            "u_err_rms_vs_fp32": float(np.sqrt(np.mean(d * d))), "steps": steps}
 
 
 def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fx16"), run_lengths=(16,),

@@ -510,7 +510,11 @@ TGV_API tgv_status tgv_pair_run_length(const int32_t* nbr, int64_t nbricks, cons
  *    call);
  *  - the first call on a device looks up the scratch array's device address
  *    (once per device, with that device current); make that first call before
- *    any stream capture begins.
+ *    any stream capture begins;
+ *  - that address belongs to the device's context of the time: after a
+ *    cudaDeviceReset (or anything else that destroys the device's primary
+ *    context) in the same process it is stale, so do not call this entry point
+ *    on a device reset since its first call.
  * `stream`: the cudaStream_t to run on (NULL = legacy default stream); the
  * call waits for its own work.  `out`: 4 doubles, host or device memory,
  * receiving the same values as tgv_energy.  Errors: INVALID_ARG (null

@@ -77,7 +77,7 @@ __device__ __forceinline__ int upper_index(const int64_t* a, int n, int64_t x)
 }  // namespace
 
 template <typename S, typename D, int NB>
-__global__ void __launch_bounds__(kThreads, sizeof(D) == 2 ? 3 : 2) tgv_batched_kernel(const BatchArgs<S, D> B)
+__global__ void __launch_bounds__(kThreads, 2) tgv_batched_kernel(const BatchArgs<S, D> B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     int64_t* task = (int64_t*)(smem + B.off_task);  // first item, end item, chunk, parity, state

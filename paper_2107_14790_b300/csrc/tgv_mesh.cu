@@ -658,10 +658,13 @@ tgv_status tgv_mesh_extract(tgv_domain* d, TgvLevel& L, int64_t* nverts, int64_t
     if (nc > 0) {
         mc_compact_kernel<<<(unsigned)((nwc + 255) / 256), 256, 0, d->stream>>>(cword, ccnt, nwc, code, cells, keys);
         d->launches++;
-        // group the cells by corner signs (one stable 8-bit pass: ties keep list order)
+        // group the cells by corner signs (one stable 8-bit pass: ties keep list order); the
+        // count and write passes read the sorted keys where the pass left them
+        uint64_t* sorted = keys;
         e = tgv_radix_sort_u64(keys, (uint64_t*)(base + tmp_off), (uint32_t*)(base + hist_off), (int64_t)nc, 32, 8,
-                               d->stream, &d->launches);
+                               d->stream, &d->launches, &sorted);
         if ((st = tgv_cuda_check(d, e, "mesh cell grouping")) != TGV_OK) return st;
+        A.order = sorted;
         mc_count_kernel<<<lgrid, 128, 0, d->stream>>>(A);
         d->launches++;
     }

@@ -409,10 +409,13 @@ int64_t radix_hist_words(int64_t n)
 }
 
 // sorts n keys by the 8-bit digits at `shifts` (least significant first); `tmp`
-// holds n keys, `hist` radix_hist_words(n) counts; adds its launches to *launches
+// holds n keys, `hist` radix_hist_words(n) counts; adds its launches to *launches.
+// With `result` the sorted keys stay in whichever of keys / tmp the last pass wrote and
+// *result points there; without it they are copied back into keys.
 cudaError_t radix_sort(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, const std::vector<int>& shifts,
-                       cudaStream_t s, int64_t* launches = nullptr)
+                       cudaStream_t s, int64_t* launches = nullptr, uint64_t** result = nullptr)
 {
+    if (result) *result = keys;
     if (n <= 1) return cudaSuccess;
     const int64_t tiles = (n + kRsTile - 1) / kRsTile, m = 256 * tiles, segs = (m + kRsSeg - 1) / kRsSeg;
     uint64_t *a = keys, *b = tmp;
@@ -428,6 +431,10 @@ cudaError_t radix_sort(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n,
         rs_scatter_kernel<<<(unsigned)tiles, kRsThreads, 0, s>>>(a, b, n, sh, hist, tiles);
         if (launches) *launches += segs == 1 ? 3 : 5;
         std::swap(a, b);
+    }
+    if (result) {
+        *result = a;
+        return cudaGetLastError();
     }
     if (a != keys) return cudaMemcpyAsync(keys, a, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
     return cudaGetLastError();
@@ -455,11 +462,11 @@ struct DevBuf {
 }  // namespace
 
 cudaError_t tgv_radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, int lo_bit, int nbits,
-                               cudaStream_t s, int64_t* launches)
+                               cudaStream_t s, int64_t* launches, uint64_t** result)
 {
     std::vector<int> shifts;
     for (int b = 0; b < nbits; b += 8) shifts.push_back(lo_bit + b);
-    return radix_sort(keys, tmp, hist, n, shifts, s, launches);
+    return radix_sort(keys, tmp, hist, n, shifts, s, launches, result);
 }
 
 int64_t tgv_radix_hist_words(int64_t n) { return radix_hist_words(n); }

@@ -33,9 +33,10 @@ __host__ __device__ __forceinline__ uint64_t compact3(uint64_t v)
     return v;
 }
 
-// Stable LSD radix sort of n keys in place by bits [lo_bit, lo_bit + nbits), 8-bit
-// digits; `tmp` holds n keys, `hist` tgv_radix_hist_words(n) counts; adds the
-// kernels it launches to *launches (nullable).
+// Stable LSD radix sort of n keys by bits [lo_bit, lo_bit + nbits), 8-bit digits; `tmp`
+// holds n keys, `hist` tgv_radix_hist_words(n) counts; adds the kernels it launches to
+// *launches (nullable).  With `result` (nullable) the sorted keys are left in keys or tmp,
+// whichever the last pass wrote, and *result points there; without it they end in keys.
 cudaError_t tgv_radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint32_t* hist, int64_t n, int lo_bit, int nbits,
-                               cudaStream_t s, int64_t* launches);
+                               cudaStream_t s, int64_t* launches, uint64_t** result = nullptr);
 int64_t tgv_radix_hist_words(int64_t n);
