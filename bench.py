@@ -41,6 +41,21 @@ ITER_KERNEL_SRCS = {form: [os.path.join(ROOT, "paper_2107_14790_b300", "csrc", f
                     for form, main in (("paired", "tgv_iter_pair.cu"), ("pipelined", "tgv_iter_pipe.cu"),
                                        ("one_brick_per_cta", "tgv_solve.cu"))}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tgv_iter_kernel_dense256_traffic.json")
+TRAFFIC_FILE_FX16 = os.path.join(ROOT, "profiles", "tgv_iter_kernel_dense256_traffic_fx16.json")
+
+
+def measured_traffic(path, storage, nvox, nbins, form="paired"):
+    """DRAM bytes per launch of the fused kernel from a committed 1-pass ncu capture, or None
+    when the capture does not match (other sources, storage, size or bins)."""
+    try:
+        tr = json.load(open(path))
+        if (tr.get("kernel_sha") == kernel_hash(form) and tr.get("storage", "fp32") == storage
+                and tr.get("voxels", 16777216) == nvox and tr.get("nbins", 10) == nbins
+                and tr.get("iter_kernel") == form):
+            return tr["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
 
 
 def parse():
@@ -240,15 +255,8 @@ def run_ours(args, cfg):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
         peak, peak_src = 6400.0, "fallback"
-    traffic = None
-    try:
-        tr = json.load(open(TRAFFIC_FILE))
-        if (tr.get("kernel_sha") == kernel_hash(args.iter_kernel) and tr.get("storage", "fp32") == args.storage
-                and tr.get("voxels", 16777216) == nvox and tr.get("nbins", 10) == nbins
-                and tr.get("iter_kernel") == args.iter_kernel):
-            traffic = tr["dram_bytes_per_launch"]
-    except Exception:
-        pass
+    traffic = measured_traffic(TRAFFIC_FILE if args.storage == "fp32" else TRAFFIC_FILE_FX16, args.storage, nvox, nbins,
+                               args.iter_kernel)
     last = energies[-1]
     result = {
         "metric": "TGV voxel-updates/s (histograms + %d fused primal-dual iterations + energy/gap)" % iters,
@@ -290,6 +298,7 @@ def run_ours(args, cfg):
     if not args.no_reduced and not args.small and args.storage == "fp32":
         rb = reduced_block(sc, cfg, depth_dev, stream, u_ref)
         rb["frac"] = rb["achieved_gbs"] / peak
+        rb["traffic"] = measured_traffic(TRAFFIC_FILE_FX16, "fx16", nvox, nbins)
         rb["speedup_over_fp32"] = rb["voxel_updates_per_s"] / value
         result["reduced_precision"] = rb
     del depth_dev
@@ -433,15 +442,6 @@ def run_profile_case(args):
     e = dom.energy(0)
     dom.close()
     print(json.dumps({"profile_case": n, "voxels": desc.nvox, "energy": list(map(float, e))}))
-
-
-def _oracle_u(spec, iters):
-    import oracle
-    lvl = oracle.OracleLevel(spec.domain, spec.nbins)
-    h = spec.hist
-    lvl.hist[:] = h.cpu().numpy() if hasattr(h, "cpu") else h
-    lvl.iterate(iters)
-    return lvl.u
 
 
 def reduced_block(sc, cfg, depth_dev, stream, u_ref, storage="fx16", steps=3):
@@ -641,117 +641,70 @@ def serving_block(storage, nreq, budget_gb, seed=1005, rank=0, overload=0):
 
 
 def run_batched(args):
-    """256 uneven chunks (32^3..192^3 voxels, frozen one-brick shell, 10 bins, 300 iterations):
-    one union level advanced by graph-replayed fused launches, FP32 and BF16 storage, against
-    the plain form (each chunk its own domain, solved one after the other, FP32)."""
+    """256 uneven chunks (32^3..192^3 active voxels, frozen one-brick shell, 10 bins, 300
+    iterations), sharded over the ranks: per storage form (FP32, FX16, FP16, BF16) the
+    persistent launch, the union level's graph-replayed launches and the autotuner's choice,
+    against the plain form (each chunk its own domain, FP32); and every form's accuracy on
+    the 3 smallest chunks against the FP64 oracle (timed: the CPU baseline)."""
     import torch
     import torch.distributed as tdist
+    import oracle
     import synth
     from paper_2107_14790_b300 import build, tgv
     from paper_2107_14790_b300.batching import union_level
-    from paper_2107_14790_b300.multigpu import reduce_scalar, shard
+    from paper_2107_14790_b300.multigpu import shard
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     build.build()
-    iters = 300
-    t_gen = time.perf_counter()
-    geo = synth.chunk_workload(1004, 256, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="none")
-    mine = shard([g.domain.nvox for g in geo], rank, world)  # each rank solves its own chunks
-    specs = [geo[k] for k in mine]
+    iters, nchunks = 300, 256
+    stream = torch.cuda.Stream()
+    storages = ("fp32", "fx16", "fp16", "bf16")
+    t0 = time.perf_counter()
+    blk = batched_block(stream, rank, world, local, nchunks=nchunks, iters=iters, storages=storages)
+    t_blk = time.perf_counter() - t0
+    # accuracy on this rank's 3 smallest chunks: each form against the FP64 oracle
+    geo = synth.chunk_workload(1004, nchunks, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="none")
+    mine = shard([g.domain.nvox for g in geo], rank, world)
+    small = sorted(mine, key=lambda k: geo[k].domain.nbricks)[:3]
+    specs = [geo[k] for k in small]
     for sp in specs:
         sp.hist = synth.chunk_histogram(sp, f"cuda:{local}")
     U = union_level([sp.domain for sp in specs])
     hist = torch.cat([sp.hist for sp in specs])
-    t_gen = time.perf_counter() - t_gen
-    nvox = int(hist.shape[0])
-    stream = torch.cuda.Stream()
-    out = {}
-    # CPU baseline: the oracle on the 3 smallest chunks (timed); its fields also give
-    # the accuracy of every storage form on those chunks
-    sample = sorted(range(len(specs)), key=lambda k: specs[k].domain.nbricks)[:3]
     t_cpu = time.perf_counter()
-    ref = {k: _oracle_u(specs[k], iters) for k in sample}
-    t_cpu = time.perf_counter() - t_cpu
-    import oracle
-    cpu_baseline = {"value": sum(specs[k].domain.nvox for k in sample) * iters / t_cpu, "unit": "voxel-updates/s",
-                    "cores": oracle.max_threads(), "kind": "oracle",
-                    "sample": f"the 3 smallest chunks, {iters} iterations each"}
-    for storage in ("fp32", "bf16", "fp16"):
-        dom = tgv.Domain([U], nbins=10, storage=storage, stream=stream.cuda_stream)
-        dom.set_histograms(0, hist)
-        dom.solve_graph(0, iters)  # first call: plain launches, captures the graph
-        dom.reset(0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = dom.launches
-        e0.record(stream)
-        dom.solve_graph(0, iters)
-        e1.record(stream)
-        dom.synchronize()
-        ms = reduce_scalar(e0.elapsed_time(e1), "max")
-        u = dom.field(0, "u")[:, 0]
-        err = max(float(np.max(np.abs(u[512 * U.ranges[k][0]:512 * U.ranges[k][1]] - ref[k]))) for k in sample)
-        bpv = algorithmic_bytes_per_voxel(10, storage)
-        tot = reduce_scalar(nvox, "sum")
-        out[storage] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms, "launches": dom.launches - l0,
-                        "achieved_gbs": nvox * bpv / (ms / 1e3 / iters) / 1e9, "u_err_inf_vs_fp64_oracle": err}
-        dom.close()
-    # plain form: every chunk alone, FP32
-    if tune:
-        # the autotuner's choice for this chunk mix (timed on a sample of it, cached per mix)
-        from paper_2107_14790_b300 import autotune
-        from paper_2107_14790_b300.batching import batch_domain, run_batch
-        for storage in storages:
-            ch = autotune.tune_batch([sp.domain for sp in specs], 10, storage, hist_of=lambda dm, m={
-                id(sp.domain): sp.hist for sp in specs}: m[id(dm)])
-            dom = batch_domain(U, 10, storage, stream.cuda_stream, ch)
-            dom.set_histograms(0, hist)
-            run_batch(dom, U, iters, ch)
-            dom.reset(0)
-            l0 = dom.launches
-            ms = timed(lambda: run_batch(dom, U, iters, ch))
-            launches += dom.launches - l0
-            out[f"autotuned_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms,
-                                           "choice": {k: ch[k] for k in ("form", "iter_kernel", "run_length")}}
-            dom.close()
-    doms = []
+    ref = []
     for sp in specs:
-        d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)
-        d.set_histograms(0, sp.hist)
-        doms.append(d)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for d in doms:
-        tgv.tgv_solve(d.handle, 0, iters, False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_plain = reduce_scalar(e0.elapsed_time(e1), "max")
-    nvox = int(reduce_scalar(nvox, "sum"))
-    for d in doms:
-        d.close()
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
-    best = out["fp16"]["voxel_updates_per_s"]
+        lvl = oracle.OracleLevel(sp.domain, sp.nbins)
+        lvl.hist[:] = sp.hist.cpu().numpy()
+        lvl.iterate(iters)
+        ref.append(lvl.u)
+    t_cpu = time.perf_counter() - t_cpu
+    acc = {}
+    for storage in storages:
+        with tgv.Domain([U], nbins=10, storage=storage, stream=stream.cuda_stream) as dom:
+            dom.set_histograms(0, hist)
+            dom.solve_chunks(0, U.first, [iters] * len(specs))
+            u = dom.field(0, "u")[:, 0]
+        acc[storage] = max(float(np.max(np.abs(u[512 * a:512 * b] - r))) for (a, b), r in zip(U.ranges, ref))
     if world > 1:
         tdist.destroy_process_group()
     if rank != 0:
         return None
+    best = max((v["voxel_updates_per_s"], k) for k, v in blk.items() if isinstance(v, dict) and "speedup_over_plain_fp32" in v)
     return {"metric": "batched chunk solve: voxel-updates/s (256 chunks 32^3..192^3, 300 iterations)",
-            "value": best, "unit": "voxel-updates/s", "n_gpus": world, "scaling": "weak" if world == 1 else "strong",
-            "higher_is_better": True, "dtype": "f32-math/fp16-storage",
-            "data": "synthetic (seeded chunk scenes)",
-            "config": {"workload": "batched-256-chunks-32^3..192^3-10bins-300it", "chunks": len(specs),
-                       "voxels": nvox, "generation_s": t_gen},
-            "batched": out,
-            "plain_fp32": {"voxel_updates_per_s": nvox * iters / (ms_plain / 1e3), "ms": ms_plain},
-            "speedup_batched_fp16_over_plain_fp32": best / (nvox * iters / (ms_plain / 1e3)),
-            "roofline": {"bound": "hbm", "achieved": out["fp32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                         "frac": out["fp32"]["achieved_gbs"] / peak, "kernel": "tgv_iter_pair_kernel (fp32)"},
-            "cpu_baseline": cpu_baseline,
-            "accuracy_sample": f"3 smallest chunks vs FP64 oracle after {iters} iterations"}
+            "value": best[0], "unit": "voxel-updates/s", "n_gpus": world,
+            "scaling": "weak" if world == 1 else "strong", "higher_is_better": True,
+            "dtype": "f32-math/%s-storage" % best[1].split("_")[-1], "data": "synthetic (seeded chunk scenes)",
+            "config": {"workload": "batched-256-chunks-32^3..192^3-10bins-300it", "chunks": nchunks,
+                       "voxels": blk["voxels"], "seconds": t_blk},
+            "best_form": best[1], "batched": blk,
+            "u_err_inf_vs_fp64_oracle": acc,
+            "cpu_baseline": {"value": sum(sp.domain.nvox for sp in specs) * iters / t_cpu, "unit": "voxel-updates/s",
+                             "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"the 3 smallest chunks, {iters} iterations each"},
+            "accuracy_sample": f"3 smallest chunks vs FP64 oracle after {iters} iterations (persistent launch)"}
 
 
 def run_multilevel(args):
