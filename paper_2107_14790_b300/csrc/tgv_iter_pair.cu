@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(D) == 2 ? 3 : 2) tgv_iter_pai
         fence_mbar_init();
     }
     uint32_t parity = 0;
-    const StridedRuns q{P.xrun, gridDim.x, (uint32_t)P.it.nitems};
+    const StridedRuns q{P.xrun, gridDim.x, (uint32_t)P.it.nitems, 0u};
     pair_sweep(C, q, it0, parity, P.wait_test != 0);
 }
 

@@ -821,18 +821,20 @@ struct PairCta {
         const float2 u0 = ldf2(su + l0);
         const float uta = u0.x + A.tau * d1a, utb = u0.y + A.tau * d1b;
         // prox: generalised median = max_i min(ut - tau*lambda*W_i, c_i), c_n = +inf
+        // total counts in integers (exact; the same value as a float sum, which is exact
+        // below 2^24), one conversion each
         uint32_t hwa[NP_MAX], hwb[NP_MAX];
-        float hsa = 0.0f, hsb = 0.0f;
+        uint32_t hsa = 0u, hsb = 0u;
 #pragma unroll
         for (int k = 0; k < NP_MAX; ++k) {
             uint2 w = make_uint2(0u, 0u);
             if (NB || k < npairs) w = *(const uint2*)(sh + k * 512 + l0);
             hwa[k] = w.x;
             hwb[k] = w.y;
-            hsa += (float)(w.x & 0xffffu) + (float)(w.x >> 16);
-            hsb += (float)(w.y & 0xffffu) + (float)(w.y >> 16);
+            hsa += (w.x & 0xffffu) + (w.x >> 16);
+            hsb += (w.y & 0xffffu) + (w.y >> 16);
         }
-        float Wa = -hsa, Wb = -hsb;
+        float Wa = -(float)hsa, Wb = -(float)hsb;
         float una = -INFINITY, unb = -INFINITY;
 #pragma unroll
         for (int i = 0; i < NB_MAX; ++i) {
@@ -888,17 +890,26 @@ struct PairCta {
 
 // Item sequences a CTA sweeps through: the first item, then next(i) until an item >= end.
 // Strided runs (the level kernel): runs r = cta + m * grid of R consecutive items each.
+// next() is called on each item in turn, so the position within the run is counted
+// instead of taken modulo R.
 struct StridedRuns {
     uint32_t R, G, end;
-    __device__ __forceinline__ uint32_t next(uint32_t i) const { return (i + 1) % R ? i + 1 : i + 1 + (G - 1) * R; }
+    uint32_t pos;  // position within its run of the item next() was last called on
+    __device__ __forceinline__ uint32_t next(uint32_t i)
+    {
+        if (++pos < R) return i + 1;
+        pos = 0;
+        return i + 1 + (G - 1) * R;
+    }
 };
 // One contiguous run of items [first, end) (a task of the batched kernel).
 struct OneRun {
     uint32_t end;
-    __device__ __forceinline__ uint32_t next(uint32_t i) const { return i + 1; }
+    __device__ __forceinline__ uint32_t next(uint32_t i) { return i + 1; }
 };
 
-// Software-pipelined sweep of one CTA over the items first, q.next(first), ... < q.end:
+// Software-pipelined sweep of one CTA over the items first, q.next(first), ... < q.end
+// (q.next is called on each item once, in order):
 // in one barrier interval the CTA finishes item i (phase B) and starts the next item (its
 // halo loads are issued first, so their latency overlaps phase B; then phase A once its
 // stage has landed).  mbarriers 0 and 1 track the two stages; `parity` holds the phase
@@ -907,7 +918,7 @@ struct OneRun {
 // have landed (so the caller may return).  `test_wait`: the first wait targets mbarrier
 // 2, which nothing completes.
 template <typename S, typename D, int NB, typename Seq>
-__device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, const Seq& q, uint32_t it, uint32_t& parity,
+__device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t it, uint32_t& parity,
                                            bool test_wait)
 {
     const PairArgs<S, D>& P = C.P;
