@@ -842,8 +842,13 @@ struct PairCta {
                 const float ci = A.c[i];
                 una = fmaxf(una, fminf(uta - A.taulam * Wa, ci));
                 unb = fmaxf(unb, fminf(utb - A.taulam * Wb, ci));
-                Wa += 2.0f * (float)((hwa[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
-                Wb += 2.0f * (float)((hwb[i >> 1] >> ((i & 1) * 16)) & 0xffffu);
+                // count i as a float without an integer conversion: its 16 bits as the
+                // mantissa of 2^23 (a byte permute), minus 2^23 (exact)
+                const uint32_t sel = (i & 1) ? 0x7632u : 0x7610u;
+                const float ha = __fsub_rn(__uint_as_float(__byte_perm(hwa[i >> 1], 0x4B000000u, sel)), 8388608.0f);
+                const float hb = __fsub_rn(__uint_as_float(__byte_perm(hwb[i >> 1], 0x4B000000u, sel)), 8388608.0f);
+                Wa = __fmaf_rn(2.0f, ha, Wa);
+                Wb = __fmaf_rn(2.0f, hb, Wb);
             }
         }
         una = fmaxf(una, uta - A.taulam * Wa);
