@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving block of the default line")
     ap.add_argument("--block-chunks", type=int, default=32, help="batched block: chunks (c4's size distribution)")
     ap.add_argument("--block-requests", type=int, default=200, help="serving block: requests")
+    ap.add_argument("--group-voxels", type=int, default=None,
+                    help="batched forms: active voxels per union of grouped chunks (default: the tuned choice)")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "serving", "multilevel", "lidar", "mesh", "octree", "composite",
                              "histforms", "precision"],
                     help="dense: the 256^3 terrain (default line); batched: 256 chunks 32^3..192^3, "
@@ -305,7 +307,8 @@ def run_ours(args, cfg):
     torch.cuda.empty_cache()
     # bounded blocks of the batched and served forms (the metric's chunk-solve latency)
     if not args.no_batched and not args.small:
-        result["batched"] = batched_block(stream, rank, world, local, nchunks=args.block_chunks)
+        result["batched"] = batched_block(stream, rank, world, local, nchunks=args.block_chunks,
+                                          group_voxels=args.group_voxels)
     if not args.no_serving and not args.small:
         from paper_2107_14790_b300.multigpu import gather_dict, reduce_scalar
         sv = serving_block("fp32", args.block_requests, 60.0, rank=rank)
@@ -490,14 +493,16 @@ def reduced_block(sc, cfg, depth_dev, stream, u_ref, storage="fx16", steps=3):
 
 
 def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("fp32", "fx16"), run_lengths=(16,),
-                  tune=True):
+                  tune=True, group_voxels=None):
     """Bounded form of the batched workload for the default line: `nchunks` chunks of the
     c4 size distribution (log-uniform 32^3..192^3 active voxels, frozen one-brick shell,
     10 bins, `iters` iterations), sharded over the ranks (strong scaling: each rank solves
     its own chunks, no collective on the path).  Forms per storage type: the persistent
     launch (tgv_solve_chunks: one kernel drains every chunk's runs behind per-chunk
     barriers, replayed as a CUDA graph), one union level with one launch per iteration
-    replayed as a CUDA graph; and the plain form (every chunk its own domain, FP32)."""
+    replayed as a CUDA graph, the autotuner's choice over union levels of grouped chunks
+    (batching.BatchGroups, about 12 M voxels per group, group after group); and the plain
+    form (every chunk its own domain, FP32)."""
     import torch
     import synth
     from paper_2107_14790_b300 import tgv
@@ -550,20 +555,23 @@ def batched_block(stream, rank, world, local, nchunks=32, iters=300, storages=("
     if tune:
         # the autotuner's choice for this chunk mix (timed on a sample of it, cached per mix)
         from paper_2107_14790_b300 import autotune
-        from paper_2107_14790_b300.batching import batch_domain, run_batch
+        from paper_2107_14790_b300.batching import BatchGroups
         for storage in storages:
             ch = autotune.tune_batch([sp.domain for sp in specs], 10, storage, hist_of=lambda dm, m={
                 id(sp.domain): sp.hist for sp in specs}: m[id(dm)])
-            dom = batch_domain(U, 10, storage, stream.cuda_stream, ch)
-            dom.set_histograms(0, hist)
-            run_batch(dom, U, iters, ch)
-            dom.reset(0)
-            l0 = dom.launches
-            ms = timed(lambda: run_batch(dom, U, iters, ch))
-            launches += dom.launches - l0
-            out[f"autotuned_{storage}"] = {"voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms,
-                                           "choice": {k: ch[k] for k in ("form", "iter_kernel", "run_length")}}
-            dom.close()
+            # the chosen form over union levels of grouped chunks, group after group
+            with BatchGroups([sp.domain for sp in specs], [sp.hist for sp in specs], 10, storage,
+                             stream.cuda_stream, ch, max_voxels=group_voxels) as G:
+                G.run(iters)
+                G.reset()
+                l0 = G.launches
+                ms = timed(lambda: G.run(iters))
+                launches += G.launches - l0
+                out[f"autotuned_{storage}"] = {
+                    "voxel_updates_per_s": tot * iters / (ms / 1e3), "ms": ms, "groups": len(G.groups),
+                    "choice": {k: ch.get(k) for k in ("form", "iter_kernel", "run_length", "group_voxels")}}
+                if group_voxels is not None:
+                    out[f"autotuned_{storage}"]["choice"]["group_voxels"] = group_voxels
     doms = []
     for sp in specs:
         d = tgv.Domain([sp.domain], nbins=10, stream=stream.cuda_stream)
@@ -662,7 +670,8 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     storages = ("fp32", "fx16", "fp16", "bf16")
     t0 = time.perf_counter()
-    blk = batched_block(stream, rank, world, local, nchunks=nchunks, iters=iters, storages=storages)
+    blk = batched_block(stream, rank, world, local, nchunks=nchunks, iters=iters, storages=storages,
+                        group_voxels=args.group_voxels)
     t_blk = time.perf_counter() - t0
     # accuracy on this rank's 3 smallest chunks: each form against the FP64 oracle
     geo = synth.chunk_workload(1004, nchunks, 32 ** 3, 192 ** 3, (10, 10), (iters, iters), hist="none")

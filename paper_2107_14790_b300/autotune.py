@@ -188,7 +188,7 @@ def tune_batch(chunks, nbins: int, storage: str, hist_of=None, force: bool = Fal
     random counts when None).  Returns the record: form, kernel, run length, ns per
     voxel-iteration and every candidate's time."""
     import synth
-    from .batching import union_level
+    from .batching import GROUP_VOXELS, union_level
     with _lock:
         cache = _load()
         key = f"batch|{_device_name()}|{storage}|{nbins}|{mix_signature([c.nvox for c in chunks])}"
@@ -209,7 +209,10 @@ def tune_batch(chunks, nbins: int, storage: str, hist_of=None, force: bool = Fal
             times["/".join(map(str, cand))] = time_batch_candidate(U, hist, nbins, storage, cand)
         best = min(times, key=times.get)
         form, kernel, x = best.split("/")
-        rec = {"form": form, "iter_kernel": kernel, "run_length": int(x), "ns_per_voxel_iteration": times[best],
+        # group size of the union levels (batching.GROUP_VOXELS): measured on whole c4-style
+        # mixes, where the effect shows; the sample here is smaller than one group
+        rec = {"form": form, "iter_kernel": kernel, "run_length": int(x), "group_voxels": GROUP_VOXELS,
+               "ns_per_voxel_iteration": times[best],
                "sample_chunks": len(sample), "sample_voxels": int(sum(c.nvox for c in sample)),
                "candidates": times}
         cache[key] = rec

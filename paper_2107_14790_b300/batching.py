@@ -268,3 +268,89 @@ def run_batch(dom: "tgv.Domain", U: UnionLevel, iterations: int, choice: dict):
         dom.solve_graph(0, iterations)
     else:
         dom.solve_chunks(0, U.first, [iterations] * len(U.ranges), run_length=choice["run_length"])
+
+
+# Chunks per union level.  One union over a whole mix is slower than several smaller ones
+# solved one after another: the fused kernel's rate falls with the size of the level it
+# sweeps (dense 256^3 33.0 G voxel-updates/s, 352^3 29.9 G, 448^3 28.9 G; the 256-chunk
+# c4 mix as one union 26.4 G, as unions of 32 chunks 29.4 G, of 8 chunks 30.7 G (FP32);
+# holding 40 GB of other device memory changes nothing).  Groups of about 12 M active
+# voxels still give every CTA of the grid many work items.
+GROUP_VOXELS = 12 << 20
+
+
+def group_chunks(sizes: Sequence[int], max_voxels: int = GROUP_VOXELS) -> List[List[int]]:
+    """Consecutive chunks packed into groups of at most `max_voxels` active voxels (a chunk
+    larger than that forms a group alone); max_voxels <= 0: one group of every chunk."""
+    if max_voxels <= 0:
+        return [list(range(len(sizes)))] if len(sizes) else []
+    groups, cur, tot = [], [], 0
+    for k, n in enumerate(sizes):
+        if cur and tot + int(n) > max_voxels:
+            groups.append(cur)
+            cur, tot = [], 0
+        cur.append(k)
+        tot += int(n)
+    if cur:
+        groups.append(cur)
+    return groups
+
+
+class BatchGroups:
+    """A chunk mix solved as union levels of grouped chunks (group_chunks), one domain per
+    group, each set up for an autotuner choice (autotune.tune_batch; its "group_voxels"
+    sets the group size, GROUP_VOXELS when absent).  `hists[k]`: chunk k's counts (torch
+    tensors or numpy arrays, one row per active voxel)."""
+
+    def __init__(self, chunks: Sequence, hists: Sequence, nbins: int, storage: str, stream: int, choice: dict,
+                 max_voxels: Optional[int] = None):
+        mv = choice.get("group_voxels", GROUP_VOXELS) if max_voxels is None else max_voxels
+        self.choice = choice
+        self.groups = group_chunks([c.nvox for c in chunks], mv)
+        self.levels = [union_level([chunks[k] for k in g]) for g in self.groups]
+        self.domains = []
+        try:
+            for g, U in zip(self.groups, self.levels):
+                d = batch_domain(U, nbins, storage, stream, choice)
+                self.domains.append(d)
+                hs = [hists[k] for k in g]
+                if hasattr(hs[0], "cpu"):
+                    import torch
+                    d.set_histograms(0, torch.cat(hs))
+                else:
+                    d.set_histograms(0, np.concatenate([np.asarray(h) for h in hs]))
+        except Exception:
+            self.close()
+            raise
+
+    def run(self, iterations: int):
+        """`iterations` iterations of every chunk, group after group (asynchronous)."""
+        for d, U in zip(self.domains, self.levels):
+            run_batch(d, U, iterations, self.choice)
+
+    def reset(self):
+        for d in self.domains:
+            d.reset(0)
+
+    def field(self, chunk: int, name: str) -> np.ndarray:
+        """Field `name` of chunk `chunk` (index into the chunks given), its active bricks only."""
+        for g, U, d in zip(self.groups, self.levels, self.domains):
+            if chunk in g:
+                a, b = U.ranges[g.index(chunk)]
+                return d.field(0, name)[a * 512:b * 512]
+        raise IndexError(chunk)
+
+    @property
+    def launches(self) -> int:
+        return sum(d.launches for d in self.domains)
+
+    def close(self):
+        for d in self.domains:
+            d.close()
+        self.domains = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

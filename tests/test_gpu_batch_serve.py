@@ -239,3 +239,31 @@ def test_batch_autotuner_on_the_chunk_mix(tmp_path, monkeypatch):
         u = dom.field(0, "u")[:, 0]
     for sp, (a, b) in zip(specs, U.ranges):
         np.testing.assert_array_equal(u[512 * a:512 * b], solve_alone(sp, 9, iter_kernel=rec["iter_kernel"]))
+
+
+@pytest.mark.parametrize("form", ["union_graph", "persistent"])
+def test_grouped_unions_equal_one_union_and_solo_runs(form):
+    """The mix solved as union levels of grouped chunks (batching.BatchGroups, a budget small
+    enough for several groups) gives every chunk, in every field, exactly the values of the
+    whole mix as one union level, and u equals the chunk solved alone."""
+    from paper_2107_14790_b300.batching import BatchGroups, batch_domain, run_batch, union_level
+    specs = chunks(52, 7, 4, 40)
+    doms = [sp.domain for sp in specs]
+    hists = [sp.hist for sp in specs]
+    ch = {"form": form, "iter_kernel": "paired", "run_length": 8 if form == "persistent" else 0}
+    s = torch.cuda.Stream()
+    budget = max(d.nvox for d in doms) + 1
+    fields = ("u", "ubar", "v", "vbar", "p", "q")
+    with BatchGroups(doms, hists, 10, "fp32", s.cuda_stream, ch, max_voxels=budget) as G:
+        assert 1 < len(G.groups) < len(doms)
+        G.run(11)
+        got = {(k, f): G.field(k, f) for k in range(len(doms)) for f in fields}
+    U = union_level(doms)
+    with batch_domain(U, 10, "fp32", s.cuda_stream, ch) as dom:
+        dom.set_histograms(0, np.concatenate(hists))
+        run_batch(dom, U, 11, ch)
+        ref = {f: dom.field(0, f) for f in fields}
+    for k, (a, b) in enumerate(U.ranges):
+        for f in fields:
+            np.testing.assert_array_equal(got[(k, f)], ref[f][512 * a:512 * b], err_msg=f"chunk {k} field {f}")
+        np.testing.assert_array_equal(got[(k, "u")][:, 0], solve_alone(specs[k], 11))
