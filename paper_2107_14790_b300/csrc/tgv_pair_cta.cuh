@@ -36,6 +36,43 @@ template <> struct Pair<__half> {
     static __device__ __forceinline__ void st(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
 };
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// The two voxels of a thread's pair go through the same operations.  sm_100 and later
+// issue such a pair as one packed instruction (add / sub / mul / fma .rn.f32x2), each
+// lane rounded exactly as the scalar operation, so a value computed in packed form has
+// the same bits as the scalar form of the same operations (which the single-voxel halo
+// tasks use).  Unlike the scalar __fmul_rn / __fadd_rn, a packed product that feeds a
+// packed sum may still be fused into one multiply-add by the compiler, whatever the
+// rounding modifier: code that must give the same bits on every path (the rounding of a
+// new dual, phase B's sums of decoded duals) therefore never feeds a packed product into
+// a packed sum.
+#define TGV_F32X2_OP(name, op)                                                                  \
+    __device__ __forceinline__ float2 name(float2 a, float2 b)                                  \
+    {                                                                                           \
+        float2 d;                                                                               \
+        asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op \
+            " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                      \
+            : "=f"(d.x), "=f"(d.y)                                                              \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                         \
+        return d;                                                                               \
+    }
+TGV_F32X2_OP(add2, "add.rn.f32x2")
+TGV_F32X2_OP(sub2, "sub.rn.f32x2")
+TGV_F32X2_OP(mul2, "mul.rn.f32x2")
+#undef TGV_F32X2_OP
+// a * b + c, rounded once
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 zero2() { return make_float2(0.0f, 0.0f); }
+
 // pairs of dual values (p, q): the storage type's pair, or two 16-bit fixed-point values
 // in one 32-bit word (TGV_STORAGE_FX16; sc = the decode or encode scale)
 template <typename D> struct DPair {
@@ -70,14 +107,33 @@ template <> struct DRound<__nv_bfloat16> {
         return __bfloat162float(__float2bfloat16_rn(x));
     }
 };
-// Fixed point: adding 1.5 * 2^23 to y = x * isc (|y| <= 32768 < 2^22 for a projected dual)
-// rounds y to the nearest integer k (ties to even) in the FP32 addition itself, and k sits
-// in the low bits of the sum: the same k as fx16_encode, at two full-rate operations.
+// Fixed point: x * isc + 1.5 * 2^23 in one fused operation (|x * isc| <= 32768 < 2^22 for a
+// projected dual) rounds x * isc to the nearest integer k (ties to even), and k sits in the
+// low bits of the sum; k * dsc is the stored value.  One rounding of the exact product,
+// written as a fused multiply-add on every path (scalar, packed, store), so no compiler
+// choice between a separate product and a fused one can make two paths differ.
 constexpr float kRoundMagic = 12582912.0f;
 template <> struct DRound<int16_t> {
     static __device__ __forceinline__ float r(float x, float dsc, float isc)
     {
-        return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(x, isc), kRoundMagic), kRoundMagic), dsc);
+        return __fmul_rn(__fsub_rn(__fmaf_rn(x, isc, kRoundMagic), kRoundMagic), dsc);
+    }
+};
+// DRound of a pair (the same operations lane by lane)
+template <typename D> struct DRound2 {
+    static __device__ __forceinline__ float2 r(float2 v, float dsc, float isc)
+    {
+        return make_float2(DRound<D>::r(v.x, dsc, isc), DRound<D>::r(v.y, dsc, isc));
+    }
+};
+template <> struct DRound2<float> {
+    static __device__ __forceinline__ float2 r(float2 v, float, float) { return v; }
+};
+template <> struct DRound2<int16_t> {
+    static __device__ __forceinline__ float2 r(float2 v, float dsc, float isc)
+    {
+        const float2 m = bc2(kRoundMagic);
+        return mul2(sub2(fma2(v, bc2(isc), m), m), bc2(dsc));
     }
 };
 
@@ -105,10 +161,10 @@ template <> struct DRoundStore<__nv_bfloat16> {
 template <> struct DRoundStore<int16_t> {
     static __device__ __forceinline__ void st(int16_t* p, float2& v, float dsc, float isc)
     {
-        const float sa = __fadd_rn(__fmul_rn(v.x, isc), kRoundMagic);
-        const float sb = __fadd_rn(__fmul_rn(v.y, isc), kRoundMagic);
-        *(uint32_t*)p = __byte_perm(__float_as_uint(sa), __float_as_uint(sb), 0x5410);  // low halves: k_a, k_b
-        v = make_float2(__fmul_rn(__fsub_rn(sa, kRoundMagic), dsc), __fmul_rn(__fsub_rn(sb, kRoundMagic), dsc));
+        const float2 m = bc2(kRoundMagic);
+        const float2 s = fma2(v, bc2(isc), m);
+        *(uint32_t*)p = __byte_perm(__float_as_uint(s.x), __float_as_uint(s.y), 0x5410);  // low halves: k_a, k_b
+        v = mul2(sub2(s, m), bc2(dsc));
     }
 };
 
@@ -152,6 +208,42 @@ __device__ __forceinline__ void upd_q(float q[6], const float dm[3][3], float si
     }
 }
 
+// upd_p / upd_q on the two voxels of a pair in packed form, lane by lane the same
+// operations (a lane left inside its ball is scaled by 1, which is exact)
+__device__ __forceinline__ void upd_p2(float2 p[3], const float2 g[3], const float2 vb[3], float sigma, float alpha1,
+                                       float a1sq)
+{
+    const float2 s2 = bc2(sigma);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = fma2(s2, sub2(g[c], vb[c]), p[c]);
+    const float2 n2 = fma2(p[2], p[2], fma2(p[1], p[1], mul2(p[0], p[0])));
+    if (n2.x > a1sq || n2.y > a1sq) {
+        const float2 s = make_float2(n2.x > a1sq ? __fmul_rn(alpha1, rsqrtf(n2.x)) : 1.0f,
+                                     n2.y > a1sq ? __fmul_rn(alpha1, rsqrtf(n2.y)) : 1.0f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = mul2(p[c], s);
+    }
+}
+
+__device__ __forceinline__ void upd_q2(float2 q[6], const float2 dm[3][3], float sigma, float alpha0, float a0sq)
+{
+    const float2 s2 = bc2(sigma), h2 = bc2(0.5f);
+    q[0] = fma2(s2, dm[0][0], q[0]);
+    q[1] = fma2(s2, dm[1][1], q[1]);
+    q[2] = fma2(s2, dm[2][2], q[2]);
+    q[3] = fma2(s2, mul2(h2, add2(dm[0][1], dm[1][0])), q[3]);
+    q[4] = fma2(s2, mul2(h2, add2(dm[0][2], dm[2][0])), q[4]);
+    q[5] = fma2(s2, mul2(h2, add2(dm[1][2], dm[2][1])), q[5]);
+    const float2 off = fma2(q[5], q[5], fma2(q[4], q[4], mul2(q[3], q[3])));
+    const float2 n2 = fma2(bc2(2.0f), off, fma2(q[2], q[2], fma2(q[1], q[1], mul2(q[0], q[0]))));
+    if (n2.x > a0sq || n2.y > a0sq) {
+        const float2 s = make_float2(n2.x > a0sq ? __fmul_rn(alpha0, rsqrtf(n2.x)) : 1.0f,
+                                     n2.y > a0sq ? __fmul_rn(alpha0, rsqrtf(n2.y)) : 1.0f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] = mul2(q[c], s);
+    }
+}
+
 // v <- v + tau (p + div2 q) and its over-relaxation 2 v_new - v_old
 __device__ __forceinline__ float vnew(float v0, float p, float d2, float tau)
 {
@@ -169,21 +261,18 @@ __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const f
     const int hj = tk & 3, hw = tk >> 2;
     const uint32_t lo = AX == 1 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;  // own voxel at coordinate 0 along AX
     const float2 own = ldf2(sub + lo);
-    float ga[3], gb[3];
-    ga[0] = h[1] - h[0];                          // x-forward of voxel 0 is voxel 1
-    gb[0] = (hm & 1u) ? h[2] - h[1] : 0.0f;
-    ga[AX] = own.x - h[0];
-    gb[AX] = own.y - h[1];
-    ga[OA] = (hm & 2u) ? h[4] - h[0] : 0.0f;
-    gb[OA] = (hm & 2u) ? h[5] - h[1] : 0.0f;
-    float pa[3] = {h[12], h[14], h[16]}, pb[3] = {h[13], h[15], h[17]};
-    const float va[3] = {h[6], h[8], h[10]}, vb[3] = {h[7], h[9], h[11]};
-    upd_p(pa, ga, va, sigma, alpha1, a1sq);
-    upd_p(pb, gb, vb, sigma, alpha1, a1sq);
+    const float2 u01 = make_float2(h[0], h[1]);
+    float2 g[3];
+    g[0] = sub2(make_float2(h[1], h[2]), u01);  // x-forward of voxel 0 is voxel 1
+    if (!(hm & 1u)) g[0].y = 0.0f;
+    g[AX] = sub2(own, u01);
+    g[OA] = (hm & 2u) ? sub2(make_float2(h[4], h[5]), u01) : zero2();
+    float2 pp[3] = {make_float2(h[12], h[13]), make_float2(h[14], h[15]), make_float2(h[16], h[17])};
+    const float2 vv[3] = {make_float2(h[6], h[7]), make_float2(h[8], h[9]), make_float2(h[10], h[11])};
+    upd_p2(pp, g, vv, sigma, alpha1, a1sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        stf2(hal_p + c * 192 + AX * 64 + fi, make_float2(DRound<D>::r(pa[c], dsc, isc), DRound<D>::r(pb[c], dsc, isc)));
+    for (int c = 0; c < 3; ++c) stf2(hal_p + c * 192 + AX * 64 + fi, DRound2<D>::r(pp[c], dsc, isc));
 }
 
 // new q for the halo pair (2hj, 0, hw) / (2hj, hw, 0) on the +AX face, rounded as stored
@@ -194,30 +283,23 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
     constexpr int OA = 3 - AX;
     const int hj = tk & 3, hw = tk >> 2;
     const uint32_t lo = AX == 1 ? 2 * hj + 56 + 64 * hw : 2 * hj + 8 * hw + 448;  // own voxel at coordinate 7
-    float dma[3][3], dmb[3][3];
+    float2 dm[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float2 own = Pair<S>::ld(svb + c * 512 + lo);
-        const float va = h[2 * c], vbv = h[2 * c + 1];
-        dma[0][c] = (hm & 1u) ? va - h[6 + 2 * c] : 0.0f;  // backward x of voxel 0
-        dmb[0][c] = vbv - va;                              // backward x of voxel 1 is voxel 0
-        dma[AX][c] = va - own.x;
-        dmb[AX][c] = vbv - own.y;
-        dma[OA][c] = (hm & 2u) ? va - h[12 + 2 * c] : 0.0f;
-        dmb[OA][c] = (hm & 2u) ? vbv - h[13 + 2 * c] : 0.0f;
+        const float2 v2 = make_float2(h[2 * c], h[2 * c + 1]);
+        dm[0][c] = sub2(v2, make_float2(h[6 + 2 * c], h[2 * c]));  // backward x of voxel 1 is voxel 0
+        if (!(hm & 1u)) dm[0][c].x = 0.0f;
+        dm[AX][c] = sub2(v2, own);
+        dm[OA][c] = (hm & 2u) ? sub2(v2, make_float2(h[12 + 2 * c], h[13 + 2 * c])) : zero2();
     }
-    float ea[6], eb[6];
+    float2 e[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        ea[c] = h[18 + 2 * c];
-        eb[c] = h[19 + 2 * c];
-    }
-    upd_q(ea, dma, sigma, alpha0, a0sq);
-    upd_q(eb, dmb, sigma, alpha0, a0sq);
+    for (int c = 0; c < 6; ++c) e[c] = make_float2(h[18 + 2 * c], h[19 + 2 * c]);
+    upd_q2(e, dm, sigma, alpha0, a0sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
-        stf2(hal_q + c * 192 + AX * 64 + fi, make_float2(DRound<D>::r(ea[c], dsc, isc), DRound<D>::r(eb[c], dsc, isc)));
+    for (int c = 0; c < 6; ++c) stf2(hal_q + c * 192 + AX * 64 + fi, DRound2<D>::r(e[c], dsc, isc));
 }
 
 }  // namespace
@@ -600,64 +682,47 @@ struct PairCta {
         const D* sp = (const D*)(st + O_P);
         const D* sq = (const D*)(st + O_Q);
         const float2 ub = ldf2(sub + l0);
-        float vb0[3], vb1[3], pn0[3], pn1[3], qn0[6], qn1[6];
+        float2 vb[3], pn[3], qn[6];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float2 w = PS::ld(svb + c * 512 + l0);
-            vb0[c] = w.x;
-            vb1[c] = w.y;
-            w = DP::ld(sp + c * 512 + l0, A.ds.dsp);
-            pn0[c] = w.x;
-            pn1[c] = w.y;
+            vb[c] = PS::ld(svb + c * 512 + l0);
+            pn[c] = DP::ld(sp + c * 512 + l0, A.ds.dsp);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const float2 w = DP::ld(sq + c * 512 + l0, A.ds.dsq);
-            qn0[c] = w.x;
-            qn1[c] = w.y;
-        }
+        for (int c = 0; c < 6; ++c) qn[c] = DP::ld(sq + c * 512 + l0, A.ds.dsq);
         const bool fx1 = j < 3 || n_px >= 0, fy = y < 7 || n_py >= 0, fz = z < 7 || n_pz >= 0;
         const bool bx0 = j > 0 || n_mx >= 0, by = y > 0 || n_my >= 0, bz = z > 0 || n_mz >= 0;
         {
             const float2 uy = y < 7 ? ldf2(sub + l0 + 8) : ubf_y;
             const float2 uz = z < 7 ? ldf2(sub + l0 + 64) : ubf_z;
             const float ux1 = j < 3 ? sub[l0 + 2] : ubf_x;
-            const float g0[3] = {ub.y - ub.x, fy ? uy.x - ub.x : 0.0f, fz ? uz.x - ub.x : 0.0f};
-            const float g1[3] = {fx1 ? ux1 - ub.y : 0.0f, fy ? uy.y - ub.y : 0.0f, fz ? uz.y - ub.y : 0.0f};
-            float dm0[3][3], dm1[3][3];
+            float2 g[3];
+            g[0] = sub2(make_float2(ub.y, ux1), ub);  // x-forward: voxel 1 of voxel 0, x0 + 2 of voxel 1
+            if (!fx1) g[0].y = 0.0f;
+            g[1] = fy ? sub2(uy, ub) : zero2();
+            g[2] = fz ? sub2(uz, ub) : zero2();
+            float2 dm[3][3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float wx0 = j > 0 ? ld_s(svb + c * 512 + l0 - 1) : vbb_x[c];
                 const float2 wy = y > 0 ? PS::ld(svb + c * 512 + l0 - 8) : vbb_y[c];
                 const float2 wz = z > 0 ? PS::ld(svb + c * 512 + l0 - 64) : vbb_z[c];
-                dm0[0][c] = bx0 ? vb0[c] - wx0 : 0.0f;
-                dm1[0][c] = vb1[c] - vb0[c];
-                dm0[1][c] = by ? vb0[c] - wy.x : 0.0f;
-                dm1[1][c] = by ? vb1[c] - wy.y : 0.0f;
-                dm0[2][c] = bz ? vb0[c] - wz.x : 0.0f;
-                dm1[2][c] = bz ? vb1[c] - wz.y : 0.0f;
+                dm[0][c] = sub2(vb[c], make_float2(wx0, vb[c].x));  // x-backward: x0 - 1 of voxel 0, voxel 0 of voxel 1
+                if (!bx0) dm[0][c].x = 0.0f;
+                dm[1][c] = by ? sub2(vb[c], wy) : zero2();
+                dm[2][c] = bz ? sub2(vb[c], wz) : zero2();
             }
-            upd_p(pn0, g0, vb0, sigma, alpha1, a1sq);
-            upd_p(pn1, g1, vb1, sigma, alpha1, a1sq);
-            upd_q(qn0, dm0, sigma, alpha0, a0sq);
-            upd_q(qn1, dm1, sigma, alpha0, a0sq);
+            upd_p2(pn, g, vb, sigma, alpha1, a1sq);
+            upd_q2(qn, dm, sigma, alpha0, a0sq);
         }
         // the values the level stores (16-bit duals rounded once); own old p / q were read
         // above by this thread only: overwrite them in place
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float2 r = stp2(s, c * 512 + l0, make_float2(pn0[c], pn1[c]));
-            pn0[c] = r.x;
-            pn1[c] = r.y;
-        }
+        for (int c = 0; c < 3; ++c) pn[c] = stp2(s, c * 512 + l0, pn[c]);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const float2 r = stq2(s, c * 512 + l0, make_float2(qn0[c], qn1[c]));
-            qn0[c] = r.x;
-            qn1[c] = r.y;
-        }
+        for (int c = 0; c < 6; ++c) qn[c] = stq2(s, c * 512 + l0, qn[c]);
         // hand-over along the run
-        if (to_next && j == 3) hal_p(s ^ 1)[y + 8 * z] = pn1[0];
+        if (to_next && j == 3) hal_p(s ^ 1)[y + 8 * z] = pn[0].y;
         if (from_prev && j == 0) {
             // brick bprev's voxel (7, y, z): its partial div2 q, its new p and old v are
             // still in the other stage; add the x-forward term (this voxel's new q)
@@ -669,7 +734,10 @@ struct PairCta {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int qc = qidx(0, c);
-                const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qn0[qc]);
+                // (16-bit duals: the stored value read back from the stage, decoded as phase B
+                // decodes it, rather than the register copy of the packed rounding)
+                const float qx0 = SD == 4 ? qn[qc].x : ldq1(s, qc * 512 + l0);
+                const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qx0);
                 const float v0 = ld_s(sv_prev + c * 512 + l6 + 1);
                 const float v1 = vnew(v0, ldp1(ps, c * 512 + l6 + 1), d2, A.tau);
                 // with the x = 6 values parked by its phase B: one pair store per field
@@ -741,85 +809,45 @@ struct PairCta {
         const uint32_t* sh = (const uint32_t*)(st + O_H);
         const float* hp = hal_p(s);
         const float* hq = hal_q(s);
-        float pn0[3], pn1[3], qn0[6], qn1[6];
+        float2 pn[3], qn[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float2 w = ldp2(s, c * 512 + l0);
-            pn0[c] = w.x;
-            pn1[c] = w.y;
-        }
+        for (int c = 0; c < 3; ++c) pn[c] = ldp2(s, c * 512 + l0);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const float2 w = ldq2(s, c * 512 + l0);
-            qn0[c] = w.x;
-            qn1[c] = w.y;
-        }
-        float d1a = 0.0f, d1b = 0.0f;
-        float d2a[3] = {0, 0, 0}, d2b[3] = {0, 0, 0};
+        for (int c = 0; c < 6; ++c) qn[c] = ldq2(s, c * 512 + l0);
+        // div1 p (d1) and div2 q (d2[c]) of the pair, accumulated term by term
         // x: voxel 0: forward = voxel 1, backward = (x0-1) or the -x brick;
         //    voxel 1: backward = voxel 0, forward = (x0+2) or the +x brick
         // (voxel 1's x-forward div2 q term is added last, after y and z)
-        d1a += pn0[0];
-        if (L & 2u) d1a -= j > 0 ? ldp1(s, l0 - 1) : hp[y + 8 * z];
-        if (L & 4u) d1b += pn1[0];
-        d1b -= pn0[0];
+        float2 d1 = sub2(make_float2(pn[0].x, (L & 4u) ? pn[0].y : 0.0f),
+                         make_float2((L & 2u) ? (j > 0 ? ldp1(s, l0 - 1) : hp[y + 8 * z]) : 0.0f, pn[0].x));
+        float2 d2[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int qc = qidx(0, c);
-            d2a[c] += qn1[qc];
-            if (L & 1u) d2a[c] -= qn0[qc];
-            d2b[c] -= qn1[qc];
+            d2[c] = sub2(make_float2(qn[qc].y, 0.0f), make_float2((L & 1u) ? qn[qc].x : 0.0f, qn[qc].y));
         }
         // y
         const uint32_t fyi = 64 + x0 + 8 * z;
-        if (L & 16u) {
-            d1a += pn0[1];
-            d1b += pn1[1];
-        }
-        if (L & 128u) {
-            const float2 w = y > 0 ? ldp2(s, 512 + l0 - 8) : ldf2(hp + 192 + fyi);
-            d1a -= w.x;
-            d1b -= w.y;
-        }
+        if (L & 16u) d1 = add2(d1, pn[1]);
+        if (L & 128u) d1 = sub2(d1, y > 0 ? ldp2(s, 512 + l0 - 8) : ldf2(hp + 192 + fyi));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int qc = qidx(1, c);
-            if (L & 32u) {
-                const float2 w = y < 7 ? ldq2(s, qc * 512 + l0 + 8) : ldf2(hq + qc * 192 + fyi);
-                d2a[c] += w.x;
-                d2b[c] += w.y;
-            }
-            if (L & 64u) {
-                d2a[c] -= qn0[qc];
-                d2b[c] -= qn1[qc];
-            }
+            if (L & 32u) d2[c] = add2(d2[c], y < 7 ? ldq2(s, qc * 512 + l0 + 8) : ldf2(hq + qc * 192 + fyi));
+            if (L & 64u) d2[c] = sub2(d2[c], qn[qc]);
         }
         // z
         const uint32_t fzi = 128 + x0 + 8 * y;
-        if (L & 256u) {
-            d1a += pn0[2];
-            d1b += pn1[2];
-        }
-        if (L & 2048u) {
-            const float2 w = z > 0 ? ldp2(s, 1024 + l0 - 64) : ldf2(hp + 384 + fzi);
-            d1a -= w.x;
-            d1b -= w.y;
-        }
+        if (L & 256u) d1 = add2(d1, pn[2]);
+        if (L & 2048u) d1 = sub2(d1, z > 0 ? ldp2(s, 1024 + l0 - 64) : ldf2(hp + 384 + fzi));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int qc = qidx(2, c);
-            if (L & 512u) {
-                const float2 w = z < 7 ? ldq2(s, qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi);
-                d2a[c] += w.x;
-                d2b[c] += w.y;
-            }
-            if (L & 1024u) {
-                d2a[c] -= qn0[qc];
-                d2b[c] -= qn1[qc];
-            }
+            if (L & 512u) d2[c] = add2(d2[c], z < 7 ? ldq2(s, qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi));
+            if (L & 1024u) d2[c] = sub2(d2[c], qn[qc]);
         }
         const float2 u0 = ldf2(su + l0);
-        const float uta = u0.x + A.tau * d1a, utb = u0.y + A.tau * d1b;
+        const float2 ut = fma2(bc2(A.tau), d1, u0);
         // prox: generalised median = max_i min(ut - tau*lambda*W_i, c_i), c_n = +inf
         // total counts in integers (exact; the same value as a float sum, which is exact
         // below 2^24), one conversion each
@@ -834,61 +862,67 @@ struct PairCta {
             hsa += (w.x & 0xffffu) + (w.x >> 16);
             hsb += (w.y & 0xffffu) + (w.y >> 16);
         }
-        float Wa = -(float)hsa, Wb = -(float)hsb;
+        float2 W = make_float2(-(float)hsa, -(float)hsb);
+        const float2 ntl = bc2(-A.taulam);
         float una = -INFINITY, unb = -INFINITY;
 #pragma unroll
         for (int i = 0; i < NB_MAX; ++i) {
             if (NB || i < nbins) {
                 const float ci = A.c[i];
-                una = fmaxf(una, fminf(uta - A.taulam * Wa, ci));
-                unb = fmaxf(unb, fminf(utb - A.taulam * Wb, ci));
+                const float2 cand = fma2(ntl, W, ut);
+                una = fmaxf(una, fminf(cand.x, ci));
+                unb = fmaxf(unb, fminf(cand.y, ci));
                 // count i as a float without an integer conversion: its 16 bits as the
                 // mantissa of 2^23 (a byte permute), minus 2^23 (exact)
                 const uint32_t sel = (i & 1) ? 0x7632u : 0x7610u;
-                const float ha = __fsub_rn(__uint_as_float(__byte_perm(hwa[i >> 1], 0x4B000000u, sel)), 8388608.0f);
-                const float hb = __fsub_rn(__uint_as_float(__byte_perm(hwb[i >> 1], 0x4B000000u, sel)), 8388608.0f);
-                Wa = __fmaf_rn(2.0f, ha, Wa);
-                Wb = __fmaf_rn(2.0f, hb, Wb);
+                const float2 hf = sub2(make_float2(__uint_as_float(__byte_perm(hwa[i >> 1], 0x4B000000u, sel)),
+                                                   __uint_as_float(__byte_perm(hwb[i >> 1], 0x4B000000u, sel))),
+                                       bc2(8388608.0f));
+                W = fma2(bc2(2.0f), hf, W);
             }
         }
-        una = fmaxf(una, uta - A.taulam * Wa);
-        unb = fmaxf(unb, utb - A.taulam * Wb);
+        {
+            const float2 cand = fma2(ntl, W, ut);
+            una = fmaxf(una, cand.x);
+            unb = fmaxf(unb, cand.y);
+        }
         if (A.clamp_u) {
             una = fminf(1.0f, fmaxf(-1.0f, una));
             unb = fminf(1.0f, fmaxf(-1.0f, unb));
         }
+        const float2 un = make_float2(una, unb);
         const size_t vi = (size_t)b * TGV_BVOX + l0;
-        stf2(A.u + vi, make_float2(una, unb));
-        stf2(ubo() + vi, make_float2(2.0f * una - u0.x, 2.0f * unb - u0.y));
+        stf2(A.u + vi, un);
+        stf2(ubo() + vi, sub2(add2(un, un), u0));
         const bool park = to_next && j == 3;  // uniform per warp row group; implies L & 8
+        const float2 tau2 = bc2(A.tau);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t oi = ((size_t)b * 3 + c) * TGV_BVOX + l0;
             const float2 v0 = PS::ld(sv + c * 512 + l0);
-            const float v1a = vnew(v0.x, pn0[c], d2a[c], A.tau);
-            const float vba = vbar_of(v1a, v0.x);
             // every lane forms the pair (a parking lane's x = 7 value is not used), so
             // only the stores below depend on the lane
-            const float part = d2b[c];
+            const float part = d2[c].y;
             const float fwdq = j < 3 ? ldq1(s, qidx(0, c) * 512 + l0 + 2) : hq[qidx(0, c) * 192 + y + 8 * z];
-            const float d2c = (L & 8u) ? __fadd_rn(part, fwdq) : part;
-            const float v1b = vnew(v0.y, pn1[c], d2c, A.tau);
+            const float2 d2c = make_float2(d2[c].x, (L & 8u) ? __fadd_rn(part, fwdq) : part);
+            // v <- v + tau (p + div2 q), vbar = 2 v_new - v_old (vnew / vbar_of lane by lane)
+            const float2 v1 = fma2(tau2, add2(pn[c], d2c), v0);
+            const float2 vb1 = sub2(add2(v1, v1), v0);
             if (park) {
                 // x = 6 is final, x = 7 waits for the next item's q: keep both stores as one
                 // pair store (no split sectors) by parking x = 6's new v and vbar in this
                 // stage's v and vbar slots, which nothing reads any more
                 hal_q(s)[qidx(0, c) * 192 + y + 8 * z] = part;
-                st_s((S*)(st + O_V) + c * 512 + l0, v1a);
-                st_s((S*)(st + O_VB) + c * 512 + l0, vba);
+                st_s((S*)(st + O_V) + c * 512 + l0, v1.x);
+                st_s((S*)(st + O_VB) + c * 512 + l0, vb1.x);
             } else {
-                PS::st(A.v + oi, make_float2(v1a, v1b));
-                PS::st(vbo() + oi, make_float2(vba, vbar_of(v1b, v0.y)));
+                PS::st(A.v + oi, v1);
+                PS::st(vbo() + oi, vb1);
             }
-            out_p2(s, c * 512 + l0, pout() + oi, make_float2(pn0[c], pn1[c]));
+            out_p2(s, c * 512 + l0, pout() + oi, pn[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c)
-            out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, make_float2(qn0[c], qn1[c]));
+        for (int c = 0; c < 6; ++c) out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, qn[c]);
     }
 };
 
