@@ -7,6 +7,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "tgv_async.cuh"
 #include "tgv_internal.cuh"
 
@@ -168,6 +170,31 @@ template <> struct DRoundStore<int16_t> {
     }
 };
 
+// FX16 duals in units of their fixed-point step (the stored integer k itself): loads are
+// integer-to-float conversions, and a new dual is rounded to the nearest integer by adding
+// and subtracting 1.5 * 2^23 (|k| <= 32767.5 after a projection onto radius 32767).  The
+// packed rounding adds through a fused multiply by 1, so no compiler fusion with the
+// projection's product can change it.
+__device__ __forceinline__ float2 fxk_ld2(const int16_t* p)
+{
+    const uint32_t w = *(const uint32_t*)p;
+    return make_float2((float)(int16_t)(w & 0xffffu), (float)(int16_t)(w >> 16));
+}
+__device__ __forceinline__ float fxk_round(float x) { return __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic); }
+__device__ __forceinline__ float2 fxk_round2(float2 v)
+{
+    const float2 m = bc2(kRoundMagic);
+    return sub2(fma2(v, bc2(1.0f), m), m);
+}
+// stores the rounded pair (its low 16 bits) and returns it
+__device__ __forceinline__ float2 fxk_store2(int16_t* p, float2 v)
+{
+    const float2 m = bc2(kRoundMagic);
+    const float2 r = fma2(v, bc2(1.0f), m);
+    *(uint32_t*)p = __byte_perm(__float_as_uint(r.x), __float_as_uint(r.y), 0x5410);
+    return sub2(r, m);
+}
+
 __device__ __forceinline__ float2 ldf2(const float* p) { return *(const float2*)p; }
 __device__ __forceinline__ void stf2(float* p, float2 v) { *(float2*)p = v; }
 
@@ -253,7 +280,7 @@ __device__ __forceinline__ float vbar_of(float v1, float v0) { return __fsub_rn(
 
 // new p for the halo pair (2hj, 7, hw) / (2hj, hw, 7) on the -AX face (AX = 1: y, 2: z),
 // rounded as the owner stores it (D, scales dsc / isc)
-template <typename D, int AX>
+template <typename D, int AX, bool KU>
 __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const float* sub, float* hal_p, int tk,
                                             float sigma, float alpha1, float a1sq, float dsc, float isc)
 {
@@ -272,11 +299,12 @@ __device__ __forceinline__ void halo_p_pair(const float* h, uint32_t hm, const f
     upd_p2(pp, g, vv, sigma, alpha1, a1sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) stf2(hal_p + c * 192 + AX * 64 + fi, DRound2<D>::r(pp[c], dsc, isc));
+    for (int c = 0; c < 3; ++c)
+        stf2(hal_p + c * 192 + AX * 64 + fi, KU ? fxk_round2(pp[c]) : DRound2<D>::r(pp[c], dsc, isc));
 }
 
 // new q for the halo pair (2hj, 0, hw) / (2hj, hw, 0) on the +AX face, rounded as stored
-template <typename S, typename D, int AX>
+template <typename S, typename D, int AX, bool KU>
 __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S* svb, float* hal_q, int tk,
                                             float sigma, float alpha0, float a0sq, float dsc, float isc)
 {
@@ -299,7 +327,8 @@ __device__ __forceinline__ void halo_q_pair(const float* h, uint32_t hm, const S
     upd_q2(e, dm, sigma, alpha0, a0sq);
     const int fi = 2 * hj + 8 * hw;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) stf2(hal_q + c * 192 + AX * 64 + fi, DRound2<D>::r(e[c], dsc, isc));
+    for (int c = 0; c < 6; ++c)
+        stf2(hal_q + c * 192 + AX * 64 + fi, KU ? fxk_round2(e[c]) : DRound2<D>::r(e[c], dsc, isc));
 }
 
 }  // namespace
@@ -370,13 +399,18 @@ struct PairCta {
     // CTAs per SM, 80 registers): they are loaded just before phase A and the other CTAs'
     // warps cover the latency
     static constexpr bool kEarlyLoads = SD == 4;
+    // FX16: every dual of the iteration in units of its fixed-point step (the stored
+    // integer), so loads need no product, rounding none either, and the divergences of
+    // phase B are exact integer sums scaled once by tau x step
+    static constexpr bool kFx = std::is_same<D, int16_t>::value;
 
     const PairArgs<S, D>& P;
     const IterArgs<S, D>& A;
     unsigned char* smem;
     int t, j, y, z, x0, task, tk, nbk, nbins, npairs;
     uint32_t l0;
-    float sigma, alpha1, alpha0, a1sq, a0sq;
+    float sigma, alpha1, alpha0, a1sq, a0sq;  // dual step, projection radii (kFx: 32767 steps)
+    float sigp, sigq, taup, tauq;             // kFx: sigma / step and tau x step for p and q
 
     // inputs of the next brick's phase A held in registers
     float ubf_x;
@@ -406,11 +440,25 @@ struct PairCta {
         nbins = NB ? NB : A.nbins;
         npairs = NB ? (NB + 1) / 2 : A.npairs;
         sigma = A.sigma;
-        alpha1 = A.alpha1;
-        alpha0 = A.alpha0;
+        if constexpr (kFx) {
+            sigp = __fmul_rn(A.sigma, A.ds.isp);
+            sigq = __fmul_rn(A.sigma, A.ds.isq);
+            alpha1 = alpha0 = 32767.0f;
+            taup = __fmul_rn(A.tau, A.ds.dsp);
+            tauq = __fmul_rn(A.tau, A.ds.dsq);
+        } else {
+            alpha1 = A.alpha1;
+            alpha0 = A.alpha0;
+        }
         a1sq = alpha1 * alpha1;
         a0sq = alpha0 * alpha0;
     }
+
+    // step sizes as the iteration applies them (one sigma and tau unless kFx)
+    __device__ __forceinline__ float sp_() const { return kFx ? sigp : sigma; }
+    __device__ __forceinline__ float sq_() const { return kFx ? sigq : sigma; }
+    __device__ __forceinline__ float tp_() const { return kFx ? taup : A.tau; }
+    __device__ __forceinline__ float tq_() const { return kFx ? tauq : A.tau; }
 
     __device__ __forceinline__ const float* ubi() const { return flip ? A.ubar_out : A.ubar_in; }
     __device__ __forceinline__ float* ubo() const { return flip ? const_cast<float*>(A.ubar_in) : A.ubar_out; }
@@ -432,23 +480,44 @@ struct PairCta {
     // or the rounded 16-bit value): pairs and single values at voxel index i of component c
     __device__ __forceinline__ const D* np_(int s) const { return (const D*)(stage(s) + O_P); }
     __device__ __forceinline__ const D* nq_(int s) const { return (const D*)(stage(s) + O_Q); }
-    __device__ __forceinline__ float2 ldp2(int s, int i) const { return DP::ld(np_(s) + i, A.ds.dsp); }
-    __device__ __forceinline__ float2 ldq2(int s, int i) const { return DP::ld(nq_(s) + i, A.ds.dsq); }
-    __device__ __forceinline__ float ldp1(int s, int i) const { return ld_d(np_(s) + i, A.ds.dsp); }
-    __device__ __forceinline__ float ldq1(int s, int i) const { return ld_d(nq_(s) + i, A.ds.dsq); }
+    // a dual pair / single value as the iteration handles it (kFx: in step units)
+    __device__ __forceinline__ float2 dl2(const D* p, float dsc) const
+    {
+        if constexpr (kFx) return fxk_ld2((const int16_t*)p);
+        else return DP::ld(p, dsc);
+    }
+    __device__ __forceinline__ float dl1(const D* p, float dsc) const
+    {
+        if constexpr (kFx) return (float)*(const int16_t*)p;
+        else return ld_d(p, dsc);
+    }
+    __device__ __forceinline__ float2 ldp2(int s, int i) const { return dl2(np_(s) + i, A.ds.dsp); }
+    __device__ __forceinline__ float2 ldq2(int s, int i) const { return dl2(nq_(s) + i, A.ds.dsq); }
+    __device__ __forceinline__ float ldp1(int s, int i) const { return dl1(np_(s) + i, A.ds.dsp); }
+    __device__ __forceinline__ float ldq1(int s, int i) const { return dl1(nq_(s) + i, A.ds.dsq); }
     // stores a new dual pair (rounded to the storage type) and returns the stored values
     __device__ __forceinline__ float2 stp2(int s, int i, float2 v) const
     {
+        if constexpr (kFx) return fxk_store2((int16_t*)np_(s) + i, v);
         DRoundStore<D>::st((D*)np_(s) + i, v, A.ds.dsp, A.ds.isp);
         return v;
     }
     __device__ __forceinline__ float2 stq2(int s, int i, float2 v) const
     {
+        if constexpr (kFx) return fxk_store2((int16_t*)nq_(s) + i, v);
         DRoundStore<D>::st((D*)nq_(s) + i, v, A.ds.dsq, A.ds.isq);
         return v;
     }
-    __device__ __forceinline__ float rp(float x) const { return DRound<D>::r(x, A.ds.dsp, A.ds.isp); }
-    __device__ __forceinline__ float rq(float x) const { return DRound<D>::r(x, A.ds.dsq, A.ds.isq); }
+    __device__ __forceinline__ float rp(float x) const
+    {
+        if constexpr (kFx) return fxk_round(x);
+        else return DRound<D>::r(x, A.ds.dsp, A.ds.isp);
+    }
+    __device__ __forceinline__ float rq(float x) const
+    {
+        if constexpr (kFx) return fxk_round(x);
+        else return DRound<D>::r(x, A.ds.dsq, A.ds.isq);
+    }
     // global store of a new dual pair held in the stage: the stored word itself (16-bit), or
     // the FP32 values
     __device__ __forceinline__ void out_p2(int s, int i, D* dst, float2 v) const
@@ -547,7 +616,7 @@ struct PairCta {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 h[6 + 2 * c] = ld_s(vbn + c * TGV_BVOX + lh);
-                h[12 + 2 * c] = ld_d(pnb + c * TGV_BVOX + lh, A.ds.dsp);
+                h[12 + 2 * c] = dl1(pnb + c * TGV_BVOX + lh, A.ds.dsp);
             }
         } else if (task == 1 || task == 2) {  // -y / -z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 1) or y (task 2)
@@ -585,7 +654,7 @@ struct PairCta {
                 float2 w = PS::ld(vbn + c * TGV_BVOX + lh);
                 h[6 + 2 * c] = w.x;
                 h[7 + 2 * c] = w.y;
-                w = DP::ld(pnb + c * TGV_BVOX + lh, A.ds.dsp);
+                w = dl2(pnb + c * TGV_BVOX + lh, A.ds.dsp);
                 h[12 + 2 * c] = w.x;
                 h[13 + 2 * c] = w.y;
             }
@@ -615,7 +684,7 @@ struct PairCta {
                 hm |= 2u;
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = ld_d(qnb + c * TGV_BVOX + lh, A.ds.dsq);
+            for (int c = 0; c < 6; ++c) h[18 + 2 * c] = dl1(qnb + c * TGV_BVOX + lh, A.ds.dsq);
         } else {  // task 4 / 5: +y / +z face pairs
             const int hj = tk & 3, hw = tk >> 2;  // hw = z (task 4) or y (task 5)
             const uint32_t lh = task == 4 ? 2 * hj + 64 * hw : 2 * hj + 8 * hw;
@@ -660,7 +729,7 @@ struct PairCta {
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const float2 w = DP::ld(qnb + c * TGV_BVOX + lh, A.ds.dsq);
+                const float2 w = dl2(qnb + c * TGV_BVOX + lh, A.ds.dsq);
                 h[18 + 2 * c] = w.x;
                 h[19 + 2 * c] = w.y;
             }
@@ -686,10 +755,10 @@ struct PairCta {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             vb[c] = PS::ld(svb + c * 512 + l0);
-            pn[c] = DP::ld(sp + c * 512 + l0, A.ds.dsp);
+            pn[c] = dl2(sp + c * 512 + l0, A.ds.dsp);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) qn[c] = DP::ld(sq + c * 512 + l0, A.ds.dsq);
+        for (int c = 0; c < 6; ++c) qn[c] = dl2(sq + c * 512 + l0, A.ds.dsq);
         const bool fx1 = j < 3 || n_px >= 0, fy = y < 7 || n_py >= 0, fz = z < 7 || n_pz >= 0;
         const bool bx0 = j > 0 || n_mx >= 0, by = y > 0 || n_my >= 0, bz = z > 0 || n_mz >= 0;
         {
@@ -712,8 +781,8 @@ struct PairCta {
                 dm[1][c] = by ? sub2(vb[c], wy) : zero2();
                 dm[2][c] = bz ? sub2(vb[c], wz) : zero2();
             }
-            upd_p2(pn, g, vb, sigma, alpha1, a1sq);
-            upd_q2(qn, dm, sigma, alpha0, a0sq);
+            upd_p2(pn, g, vb, sp_(), alpha1, a1sq);
+            upd_q2(qn, dm, sq_(), alpha0, a0sq);
         }
         // the values the level stores (16-bit duals rounded once); own old p / q were read
         // above by this thread only: overwrite them in place
@@ -739,7 +808,8 @@ struct PairCta {
                 const float qx0 = SD == 4 ? qn[qc].x : ldq1(s, qc * 512 + l0);
                 const float d2 = __fadd_rn(hq_prev[qc * 192 + y + 8 * z], qx0);
                 const float v0 = ld_s(sv_prev + c * 512 + l6 + 1);
-                const float v1 = vnew(v0, ldp1(ps, c * 512 + l6 + 1), d2, A.tau);
+                const float p7 = ldp1(ps, c * 512 + l6 + 1);
+                const float v1 = kFx ? __fmaf_rn(tp_(), p7, __fmaf_rn(tq_(), d2, v0)) : vnew(v0, p7, d2, A.tau);
                 // with the x = 6 values parked by its phase B: one pair store per field
                 const size_t oi = ((size_t)bprev * 3 + c) * TGV_BVOX + l6;
                 PS::st(A.v + oi, make_float2(ld_s(sv_prev + c * 512 + l6), v1));
@@ -757,13 +827,13 @@ struct PairCta {
                                     (hm & 2u) ? h[4] - h[0] : 0.0f};
                 float pp[3] = {h[12], h[14], h[16]};
                 const float vv[3] = {h[6], h[8], h[10]};
-                upd_p(pp, g, vv, sigma, alpha1, a1sq);
+                upd_p(pp, g, vv, sp_(), alpha1, a1sq);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hp[c * 192 + tk] = rp(pp[c]);
             } else if (task == 1) {
-                halo_p_pair<D, 1>(h, hm, sub, hp, tk, sigma, alpha1, a1sq, A.ds.dsp, A.ds.isp);
+                halo_p_pair<D, 1, kFx>(h, hm, sub, hp, tk, sp_(), alpha1, a1sq, A.ds.dsp, A.ds.isp);
             } else if (task == 2) {
-                halo_p_pair<D, 2>(h, hm, sub, hp, tk, sigma, alpha1, a1sq, A.ds.dsp, A.ds.isp);
+                halo_p_pair<D, 2, kFx>(h, hm, sub, hp, tk, sp_(), alpha1, a1sq, A.ds.dsp, A.ds.isp);
             } else if (task == 3) {  // q at (0, hy, hz) of the +x brick
                 const int hy = tk & 7, hz = tk >> 3;
                 const uint32_t lo = 7 + 8 * hy + 64 * hz;
@@ -777,13 +847,13 @@ struct PairCta {
                 float e[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) e[c] = h[18 + 2 * c];
-                upd_q(e, dm, sigma, alpha0, a0sq);
+                upd_q(e, dm, sq_(), alpha0, a0sq);
 #pragma unroll
                 for (int c = 0; c < 6; ++c) hq[c * 192 + tk] = rq(e[c]);
             } else if (task == 4) {
-                halo_q_pair<S, D, 1>(h, hm, svb, hq, tk, sigma, alpha0, a0sq, A.ds.dsq, A.ds.isq);
+                halo_q_pair<S, D, 1, kFx>(h, hm, svb, hq, tk, sq_(), alpha0, a0sq, A.ds.dsq, A.ds.isq);
             } else {
-                halo_q_pair<S, D, 2>(h, hm, svb, hq, tk, sigma, alpha0, a0sq, A.ds.dsq, A.ds.isq);
+                halo_q_pair<S, D, 2, kFx>(h, hm, svb, hq, tk, sq_(), alpha0, a0sq, A.ds.dsq, A.ds.isq);
             }
         }
         // link bits for phase B: bit 2k "any", bit 2k+1 "active", k = 0 (-x of voxel 0),
@@ -847,7 +917,7 @@ struct PairCta {
             if (L & 1024u) d2[c] = sub2(d2[c], qn[qc]);
         }
         const float2 u0 = ldf2(su + l0);
-        const float2 ut = fma2(bc2(A.tau), d1, u0);
+        const float2 ut = fma2(bc2(tp_()), d1, u0);
         // prox: generalised median = max_i min(ut - tau*lambda*W_i, c_i), c_n = +inf
         // total counts in integers (exact; the same value as a float sum, which is exact
         // below 2^24), one conversion each
@@ -906,7 +976,8 @@ struct PairCta {
             const float fwdq = j < 3 ? ldq1(s, qidx(0, c) * 512 + l0 + 2) : hq[qidx(0, c) * 192 + y + 8 * z];
             const float2 d2c = make_float2(d2[c].x, (L & 8u) ? __fadd_rn(part, fwdq) : part);
             // v <- v + tau (p + div2 q), vbar = 2 v_new - v_old (vnew / vbar_of lane by lane)
-            const float2 v1 = fma2(tau2, add2(pn[c], d2c), v0);
+            const float2 v1 =
+                kFx ? fma2(bc2(tp_()), pn[c], fma2(bc2(tq_()), d2c, v0)) : fma2(tau2, add2(pn[c], d2c), v0);
             const float2 vb1 = sub2(add2(v1, v1), v0);
             if (park) {
                 // x = 6 is final, x = 7 waits for the next item's q: keep both stores as one
