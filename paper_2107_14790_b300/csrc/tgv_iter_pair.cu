@@ -43,13 +43,19 @@
 #include <vector>
 #include "tgv_pair_cta.cuh"
 
+// FP32 duals: 384 threads, the halo duals on four warps of their own (two CTAs per SM, as
+// the two 45 KB stages allow); 16-bit duals: 256 threads with the halo tasks spread over
+// the owners of the pairs (three CTAs per SM at 80 registers)
+template <typename D> constexpr bool kPairHaloWarps = sizeof(D) == 4;
+template <typename D> constexpr int kPairThreads = PairCta<float, D, 0, kPairHaloWarps<D>>::kCtaThreads;
+
 // The level kernel: CTA r takes runs r, r + G, r + 2G, ... of R consecutive work items
 // (G = grid size) and sweeps them with the paired machinery.
 template <typename S, typename D, int NB>
-__global__ void __launch_bounds__(kThreads, sizeof(D) == 2 ? 3 : 2) tgv_iter_pair_kernel(const PairArgs<S, D> P)
+__global__ void __launch_bounds__(kPairThreads<D>, sizeof(D) == 2 ? 3 : 2) tgv_iter_pair_kernel(const PairArgs<S, D> P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    PairCta<S, D, NB> C(P, smem);
+    PairCta<S, D, NB, kPairHaloWarps<D>> C(P, smem);
     const uint32_t it0 = blockIdx.x * P.xrun;
     if (it0 >= (uint32_t)P.it.nitems) return;
     uint64_t* bar = C.bar();
@@ -157,7 +163,7 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     const size_t smem = off;
     auto kern = tgv_iter_pair_kernel<S, D, NB>;
     int per_sm = 0;
-    tgv_status st = tgv_kernel_setup((const void*)kern, kThreads, smem, &per_sm);
+    tgv_status st = tgv_kernel_setup((const void*)kern, kPairThreads<D>, smem, &per_sm);
     if (st != TGV_OK) return tgv_fail(d, st, "pair kernel setup (shared memory attribute / occupancy) failed");
     if (per_sm < 1) return tgv_fail(d, TGV_ERR_UNSUPPORTED, "pair iteration kernel does not fit on an SM");
     const int64_t nitems = tgv_work_items(L);
@@ -182,7 +188,7 @@ tgv_status launch_pair_t(tgv_domain* d, TgvLevel& L, int iters)
     P.tx_bytes = tx;
     for (int it = 0; it < iters; ++it) {
         P.it = tgv_make_iter_args<S, D>(d, L);
-        kern<<<(unsigned)grid, kThreads, smem, d->stream>>>(P);
+        kern<<<(unsigned)grid, kPairThreads<D>, smem, d->stream>>>(P);
         d->launches++;
         L.cur ^= 1;
     }

@@ -382,7 +382,7 @@ struct PairArgs {
 //   * task 3 of brick i is skipped: phase B of brick i parks the partial div2 q sum of
 //     its x = 7 voxels in hal_q[qidx(0,c)][y+8z] of its own stage (the slots task 3
 //     would have filled); phase A of brick i+1 adds its new q and stores v, vbar.
-template <typename S, typename D, int NB>
+template <typename S, typename D, int NB, bool HW = false>
 struct PairCta {
     using PS = Pair<S>;
     using DP = DPair<D>;
@@ -403,11 +403,19 @@ struct PairCta {
     // integer), so loads need no product, rounding none either, and the divergences of
     // phase B are exact integer sums scaled once by tau x step
     static constexpr bool kFx = std::is_same<D, int16_t>::value;
+    // HW: 384 threads; threads 0-255 own the voxel pairs and do no halo task, and the four
+    // halo warps 8-11 compute the halo duals (warp 8 + k takes face task 1, 2, 4, 5 for
+    // k = 0..3 and, when that face is not handed over, half of face task 0 (k = 0, 1) or
+    // 3 (k = 2, 3)), so the own warps' interval carries no halo work and fewer registers
+    static constexpr bool kHW = HW;
+    static constexpr int kCtaThreads = HW ? 384 : 256;
 
     const PairArgs<S, D>& P;
     const IterArgs<S, D>& A;
     unsigned char* smem;
     int t, j, y, z, x0, task, tk, nbk, nbins, npairs;
+    bool own;       // this thread owns a voxel pair (all threads unless HW)
+    int task2, tk2; // HW halo warps: the x-face task taken when that face is not handed over
     uint32_t l0;
     float sigma, alpha1, alpha0, a1sq, a0sq;  // dual step, projection radii (kFx: 32767 steps)
     float sigp, sigq, taup, tauq;             // kFx: sigma / step and tau x step for p and q
@@ -434,8 +442,19 @@ struct PairCta {
         z = t >> 5;
         x0 = 2 * j;
         l0 = x0 + 8 * y + 64 * z;
-        task = t < 64 ? 0 : (t < 96 ? 1 : (t < 128 ? 2 : (t < 192 ? 3 : (t < 224 ? 4 : 5))));
-        tk = t < 64 ? t : (t < 96 ? t - 64 : (t < 128 ? t - 96 : (t < 192 ? t - 128 : (t < 224 ? t - 192 : t - 224))));
+        if (HW) {
+            own = t < 256;
+            const int hw = (t >> 5) - 8, lane = t & 31;
+            task = own ? -1 : (hw == 0 ? 1 : (hw == 1 ? 2 : (hw == 2 ? 4 : 5)));
+            tk = lane;
+            task2 = hw < 2 ? 0 : 3;
+            tk2 = 32 * (hw & 1) + lane;
+        } else {
+            own = true;
+            task = t < 64 ? 0 : (t < 96 ? 1 : (t < 128 ? 2 : (t < 192 ? 3 : (t < 224 ? 4 : 5))));
+            tk = t < 64 ? t : (t < 96 ? t - 64 : (t < 128 ? t - 96 : (t < 192 ? t - 128 : (t < 224 ? t - 192 : t - 224))));
+            task2 = tk2 = -1;
+        }
         nbk = (int)A.nb;
         nbins = NB ? NB : A.nbins;
         npairs = NB ? (NB + 1) / 2 : A.npairs;
@@ -554,6 +573,13 @@ struct PairCta {
     // replaced by the hand-over to the next item (see above)
     __device__ __forceinline__ void load_inputs(const int* nrow, bool skip0, bool skip3)
     {
+        load_own(nrow);
+        load_halo(nrow, task, tk, skip0, skip3);
+    }
+
+    // the own pair's boundary neighbours in adjacent bricks
+    __device__ __forceinline__ void load_own(const int* nrow)
+    {
         const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
         const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
         ubf_x = 0.0f;
@@ -578,11 +604,18 @@ struct PairCta {
 #pragma unroll
             for (int c = 0; c < 3; ++c) vbb_z[c] = PS::ld(vbi() + ((size_t)n_mz * 3 + c) * TGV_BVOX + l0 + 448);
         }
-        // halo inputs.  p tasks: h[0..1] ubar(h0,h1), h[2..3] forward along the first face
-        // axis, h[4..5] along the second, h[6..11] vbar (3 x pair), h[12..17] p (3 x pair).
-        // q tasks: h[0..5] vbar (3 x pair), h[6..11] backward along the first face axis,
-        // h[12..17] along the second, h[18..29] q (6 x pair).  Singles use the even slots.
+    }
+
+    // halo inputs of face task `task`, item tk (task < 0: none).  p tasks: h[0..1]
+    // ubar(h0,h1), h[2..3] forward along the first face axis, h[4..5] along the second,
+    // h[6..11] vbar (3 x pair), h[12..17] p (3 x pair).  q tasks: h[0..5] vbar (3 x pair),
+    // h[6..11] backward along the first face axis, h[12..17] along the second, h[18..29] q
+    // (6 x pair).  Singles use the even slots.
+    __device__ __forceinline__ void load_halo(const int* nrow, int task, int tk, bool skip0, bool skip3)
+    {
         hm = 0;
+        hn = -1;
+        if (HW && task < 0) return;
         {
             const int a = task % 3;
             hn = task < 3 ? nrow[nb_minus(a)] : nrow[nb_plus(a)];
@@ -743,6 +776,30 @@ struct PairCta {
     // to_next: the next item is this brick's +x neighbour (its -x halo p is written here).
     __device__ __forceinline__ uint32_t phase_a(int s, const int* nrow, bool from_prev, bool to_next, uint32_t bprev)
     {
+        own_update(s, nrow, from_prev, to_next, bprev);
+        halo_compute(s, task, tk);
+        return link_bits(nrow);
+    }
+
+    // HW halo warps: the face task whose inputs are in h, then the x-face task unless
+    // that face is handed over (its inputs loaded here, after the first task)
+    __device__ __forceinline__ void halo_phase(int s, const int* nrow, bool skip0, bool skip3)
+    {
+        halo_compute(s, task, tk);
+        load_halo(nrow, task2, tk2, skip0, skip3);
+        halo_compute(s, task2, tk2);
+    }
+
+    // the own pair's part of phase A; returns the link bits phase B needs
+    __device__ __forceinline__ uint32_t phase_a_own(int s, const int* nrow, bool from_prev, bool to_next,
+                                                    uint32_t bprev)
+    {
+        own_update(s, nrow, from_prev, to_next, bprev);
+        return link_bits(nrow);
+    }
+
+    __device__ __forceinline__ void own_update(int s, const int* nrow, bool from_prev, bool to_next, uint32_t bprev)
+    {
         const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
         const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
         unsigned char* st = stage(s);
@@ -817,7 +874,32 @@ struct PairCta {
             }
         }
 
-        // halo duals
+    }
+
+    // link bits for phase B: bit 2k "any", bit 2k+1 "active", k = 0 (-x of voxel 0),
+    // 1 (+x of voxel 1), 2 (+y), 3 (-y), 4 (+z), 5 (-z)
+    __device__ __forceinline__ uint32_t link_bits(const int* nrow) const
+    {
+        const int n_px = nrow[NB_PX], n_mx = nrow[NB_MX], n_py = nrow[NB_PY], n_my = nrow[NB_MY];
+        const int n_pz = nrow[NB_PZ], n_mz = nrow[NB_MZ];
+        const bool fx1 = j < 3 || n_px >= 0, fy = y < 7 || n_py >= 0, fz = z < 7 || n_pz >= 0;
+        const bool bx0 = j > 0 || n_mx >= 0, by = y > 0 || n_my >= 0, bz = z > 0 || n_mz >= 0;
+        uint32_t L = 0;
+        L |= (bx0 ? 1u : 0u) | ((j > 0 || (n_mx >= 0 && n_mx < nbk)) ? 2u : 0u);
+        L |= (fx1 ? 4u : 0u) | ((j < 3 || (n_px >= 0 && n_px < nbk)) ? 8u : 0u);
+        L |= (fy ? 16u : 0u) | ((y < 7 || (n_py >= 0 && n_py < nbk)) ? 32u : 0u);
+        L |= (by ? 64u : 0u) | ((y > 0 || (n_my >= 0 && n_my < nbk)) ? 128u : 0u);
+        L |= (fz ? 256u : 0u) | ((z < 7 || (n_pz >= 0 && n_pz < nbk)) ? 512u : 0u);
+        L |= (bz ? 1024u : 0u) | ((z > 0 || (n_mz >= 0 && n_mz < nbk)) ? 2048u : 0u);
+        return L;
+    }
+
+    // the halo duals of face task `task`, item tk, from the inputs in h (hn < 0: none)
+    __device__ __forceinline__ void halo_compute(int s, int task, int tk)
+    {
+        unsigned char* st = stage(s);
+        const float* sub = (const float*)(st + O_UB);
+        const S* svb = (const S*)(st + O_VB);
         float* hp = hal_p(s);
         float* hq = hal_q(s);
         if (hn >= 0) {
@@ -856,16 +938,6 @@ struct PairCta {
                 halo_q_pair<S, D, 2, kFx>(h, hm, svb, hq, tk, sq_(), alpha0, a0sq, A.ds.dsq, A.ds.isq);
             }
         }
-        // link bits for phase B: bit 2k "any", bit 2k+1 "active", k = 0 (-x of voxel 0),
-        // 1 (+x of voxel 1), 2 (+y), 3 (-y), 4 (+z), 5 (-z)
-        uint32_t L = 0;
-        L |= (bx0 ? 1u : 0u) | ((j > 0 || (n_mx >= 0 && n_mx < nbk)) ? 2u : 0u);
-        L |= (fx1 ? 4u : 0u) | ((j < 3 || (n_px >= 0 && n_px < nbk)) ? 8u : 0u);
-        L |= (fy ? 16u : 0u) | ((y < 7 || (n_py >= 0 && n_py < nbk)) ? 32u : 0u);
-        L |= (by ? 64u : 0u) | ((y > 0 || (n_my >= 0 && n_my < nbk)) ? 128u : 0u);
-        L |= (fz ? 256u : 0u) | ((z < 7 || (n_pz >= 0 && n_pz < nbk)) ? 512u : 0u);
-        L |= (bz ? 1024u : 0u) | ((z > 0 || (n_mz >= 0 && n_mz < nbk)) ? 2048u : 0u);
-        return L;
     }
 
     // ---- phase B of brick b in stage s: divergences, prox, over-relaxation, global stores.
@@ -915,6 +987,12 @@ struct PairCta {
             const int qc = qidx(2, c);
             if (L & 512u) d2[c] = add2(d2[c], z < 7 ? ldq2(s, qc * 512 + l0 + 64) : ldf2(hq + qc * 192 + fzi));
             if (L & 1024u) d2[c] = sub2(d2[c], qn[qc]);
+        }
+        // the new q are final.  FP32: store them now, so their registers are free for the
+        // prox; 16-bit duals store the word held in the stage, at the end
+        if constexpr (SD == 4) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, qn[c]);
         }
         const float2 u0 = ldf2(su + l0);
         const float2 ut = fma2(bc2(tp_()), d1, u0);
@@ -992,8 +1070,10 @@ struct PairCta {
             }
             out_p2(s, c * 512 + l0, pout() + oi, pn[c]);
         }
+        if constexpr (SD != 4) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, qn[c]);
+            for (int c = 0; c < 6; ++c) out_q2(s, c * 512 + l0, qout() + ((size_t)b * 6 + c) * TGV_BVOX + l0, qn[c]);
+        }
     }
 };
 
@@ -1027,10 +1107,15 @@ struct OneRun {
 // if a wait gave up: the domain's error flag is then set and the CTA's copies in flight
 // have landed (so the caller may return).  `test_wait`: the first wait targets mbarrier
 // 2, which nothing completes.
-template <typename S, typename D, int NB, typename Seq>
-__device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t it, uint32_t& parity,
-                                           bool test_wait)
+// ROLE 0: every thread owns a pair and a halo task (HW false); with HW, ROLE 1 is the own
+// threads' sweep and ROLE 2 the halo warps' sweep.  The two roles run separate copies of the
+// loop (so neither role's values are live across the other's code) that meet at the same
+// sequence of CTA barriers.
+template <int ROLE, typename S, typename D, int NB, bool HW, typename Seq>
+__device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q, uint32_t it, uint32_t& parity,
+                                                bool test_wait)
 {
+    using Cta = PairCta<S, D, NB, HW>;
     const PairArgs<S, D>& P = C.P;
     const uint32_t nit = q.end;
     const int32_t* work = C.A.work;
@@ -1042,13 +1127,13 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
 
     uint32_t itn = q.next(it);
     uint32_t bcur = brick(it), bnext = itn < nit ? brick(itn) : 0u;
-    if (t < TGV_NNBR) {
+    if (ROLE != 2 && t < TGV_NNBR) {
         C.nbr_row(0)[t] = nbr[(size_t)bcur * TGV_NNBR + t];
         if (itn < nit) C.nbr_row(1)[t] = nbr[(size_t)bnext * TGV_NNBR + t];
     }
     __syncthreads();
     uint32_t pending = 0;  // stages with copies in flight (thread 0's view)
-    if (t == 0) {
+    if (ROLE != 2 && t == 0) {
         fence_proxy_async_smem();  // earlier generic reads of the stages come first
         C.issue(0, bcur);
         pending = 1u;
@@ -1064,7 +1149,9 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
     // brick's -x neighbour is this one)
     bool to_next = itn == it + 1 && itn < nit && C.nbr_row(0)[NB_PX] == (int)bnext;
     // prologue: phase A of the first item
-    C.load_inputs(C.nbr_row(0), false, to_next);
+    if constexpr (ROLE == 0) C.load_inputs(C.nbr_row(0), false, to_next);
+    else if constexpr (ROLE == 1) C.load_own(C.nbr_row(0));
+    else C.load_halo(C.nbr_row(0), C.task, C.tk, false, to_next);
     {
         const bool ok = test_wait ? mbar_wait_bounded(&bar[2], 0, P.wait_budget)
                                   : mbar_wait_bounded(&bar[0], parity & 1u, P.wait_budget);
@@ -1074,7 +1161,9 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
     if (!bail) {
         parity ^= 1u;
         pending &= ~1u;
-        links = C.phase_a(0, C.nbr_row(0), false, to_next, 0u);
+        if constexpr (ROLE == 0) links = C.phase_a(0, C.nbr_row(0), false, to_next, 0u);
+        else if constexpr (ROLE == 1) links = C.phase_a_own(0, C.nbr_row(0), false, to_next, 0u);
+        else C.halo_phase(0, C.nbr_row(0), false, to_next);
         __syncthreads();
     }
     while (!bail) {
@@ -1085,11 +1174,14 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
         uint32_t next_links = 0;
         if (itn < nit) {
             next_to_next = itnn == itn + 1 && itnn < nit && C.nbr_row(ns)[NB_PX] == (int)bnn;
-            if (PairCta<S, D, NB>::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
+            if constexpr (ROLE == 0 && Cta::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
         }
         // the row of the item in hand is no longer read: reuse it for item itnn
-        if (t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
-        C.phase_b(s, bcur, links, to_next);
+        if (ROLE != 2 && t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
+        if constexpr (ROLE != 2) C.phase_b(s, bcur, links, to_next);
+        // halo warps: the next item's face-task inputs, while the own warps run phase B
+        if constexpr (ROLE == 2)
+            if (itn < nit) C.load_halo(C.nbr_row(ns), C.task, C.tk, to_next, next_to_next);
         bool late = false;
         if (itn < nit) {
             // no CTA barrier between phase B of this item and phase A of the next: they
@@ -1105,15 +1197,22 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
             }
             late = !ok;
             __syncwarp();
-            if (!PairCta<S, D, NB>::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
-            next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
+            if constexpr (ROLE == 0) {
+                if (!Cta::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
+                next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
+            } else if constexpr (ROLE == 1) {
+                C.load_own(C.nbr_row(ns));
+                next_links = C.phase_a_own(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
+            } else {
+                C.halo_phase(ns, C.nbr_row(ns), to_next, next_to_next);
+            }
         }
         // stage s, the phase A results of item itn and the hand-over are settled
         if (__syncthreads_or(late)) {
             bail = true;
             break;
         }
-        if (t == 0 && itnn < nit) {
+        if (ROLE != 2 && t == 0 && itnn < nit) {
             fence_proxy_async_smem();
             C.issue(s, bnn);
             pending |= 1u << s;
@@ -1127,7 +1226,7 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
         bnext = bnn;
         to_next = next_to_next;
     }
-    if (bail && t == 0) {
+    if (ROLE != 2 && bail && t == 0) {
         atomicExch(P.err, 1);
         // copies still in flight land before the CTA's shared memory is released (the
         // default budget, not the possibly tiny one of the wait that gave up)
@@ -1135,4 +1234,13 @@ __device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB>& C, Seq q, uint32_t
             if (pending & (1u << k)) mbar_wait_bounded(&bar[k], (parity >> k) & 1u, TGV_WAIT_CYCLES_DEFAULT);
     }
     return !bail;
+}
+
+template <typename S, typename D, int NB, bool HW, typename Seq>
+__device__ __forceinline__ bool pair_sweep(PairCta<S, D, NB, HW>& C, Seq q, uint32_t it, uint32_t& parity,
+                                           bool test_wait)
+{
+    if constexpr (!HW) return pair_sweep_role<0>(C, q, it, parity, test_wait);
+    else if (C.own) return pair_sweep_role<1>(C, q, it, parity, test_wait);
+    else return pair_sweep_role<2>(C, q, it, parity, test_wait);
 }
