@@ -1,10 +1,12 @@
 // Pipelined, paired form of the fused TGV primal-dual iteration (the
 // arithmetic of tgv_iter_kernel in tgv_solve.cu: Eq. 2-3, Sec. 3.2).
 //
-// Persistent CTAs of 256 threads; each thread owns the x-adjacent voxel pair
+// Persistent CTAs; each of threads 0-255 owns the x-adjacent voxel pair
 // (2j, 2j+1) of one row of the brick in hand, so shared-memory and global
 // accesses are 64-bit (two FP32 or two 16-bit values) and the x-neighbour
-// inside the pair comes from registers.  Each brick's whole state -- u, ubar,
+// inside the pair comes from registers.  FP32 duals add four halo warps
+// (384 threads) that compute the halo duals; 16-bit duals run 256 threads
+// that do both.  Each brick's whole state -- u, ubar,
 // v, vbar, p, q and the packed histogram, contiguous per brick -- arrives in
 // shared memory through seven cp.async.bulk copies completed on an mbarrier,
 // double-buffered: while one brick is computed, the next is in flight.
@@ -30,9 +32,11 @@
 //
 // The other halo duals (new p on the -y/-z face layers, new q on the +y/+z
 // layers, and the x faces when the neighbour is not the adjacent item) are
-// recomputed here; the 384 halo voxels split into exactly one warp-uniform task
-// per thread (single voxels on the x faces, pairs on the y and z faces), and
-// their inputs are loaded into registers before the CTA waits for its stage.
+// recomputed here in warp-uniform tasks (single voxels on the x faces, pairs on
+// the y and z faces): with 256 threads the 384 halo voxels split into exactly one
+// task per thread; the four halo warps of the FP32 form take one y/z face each
+// and half an x face when it is not handed over.  Task inputs are loaded into
+// registers before the CTA waits for its stage.
 //
 // The bin count is a template parameter for 8, 10 and 12 bins (0 = read at
 // run time).  Every mbarrier wait is bounded (tgv_params.wait_cycles, about a
