@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "tgv_pair_cta.cuh"
+#include "tgv_nvtx.h"
 
 template <typename S, typename D>
 struct BatchArgs {
@@ -298,6 +299,7 @@ tgv_status launch_batched(tgv_domain* d, TgvLevel& L, const BatchPlan& p, TgvLev
 extern "C" TGV_API tgv_status tgv_solve_chunks(tgv_domain* d, int32_t level, int32_t nchunks, const int64_t* first,
                                                const int32_t* iterations, int32_t run_length)
 {
+    TgvNvtxRange nvtx_range_("tgv_solve_chunks");
     tgv_status st = tgv_check_domain(d);
     if (st != TGV_OK) return st;
     if (level < 0 || level >= (int32_t)d->levels.size()) return tgv_fail(d, TGV_ERR_INVALID_ARG, "level out of range");

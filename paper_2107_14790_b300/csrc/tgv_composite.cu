@@ -32,6 +32,7 @@
 
 #include "tgv_internal.cuh"
 #include "tgv_zorder.cuh"
+#include "tgv_nvtx.h"
 
 struct tgv_composite {
     tgv_domain* d = nullptr;
@@ -789,6 +790,7 @@ tgv_status tgv_composite_create(tgv_domain* d, tgv_composite** out)
 
 tgv_status tgv_composite_solve(tgv_composite* c, int32_t iterations)
 {
+    TgvNvtxRange nvtx_range_("tgv_composite_solve");
     if (!c || iterations < 0) return TGV_ERR_INVALID_ARG;
     tgv_domain* d = c->d;
     if (d->broken) return TGV_ERR_STATE;

@@ -12,6 +12,7 @@
 #include <unordered_map>
 
 #include "tgv_internal.cuh"
+#include "tgv_nvtx.h"
 
 // ------------------------------------------------------------------------- errors
 tgv_status tgv_fail(tgv_domain* d, tgv_status s, const std::string& msg)
@@ -586,6 +587,7 @@ tgv_status tgv_accumulate_depthmaps(tgv_domain* d, int32_t level, const tgv_came
                                     const float* depth_dev, int64_t pitch_elems, int64_t map_stride_elems,
                                     const uint32_t* votes)
 {
+    TgvNvtxRange nvtx_range_("tgv_accumulate_depthmaps");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);
@@ -626,6 +628,7 @@ tgv_status tgv_accumulate_depthmap(tgv_domain* d, int32_t level, const tgv_camer
 
 tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out)
 {
+    TgvNvtxRange nvtx_range_("tgv_solve");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);
@@ -639,6 +642,7 @@ tgv_status tgv_solve(tgv_domain* d, int32_t level, int32_t iterations, double* e
 
 tgv_status tgv_energy(tgv_domain* d, int32_t level, double* out)
 {
+    TgvNvtxRange nvtx_range_("tgv_energy");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     if (!out) return tgv_fail(d, TGV_ERR_INVALID_ARG, "null output");
@@ -687,6 +691,7 @@ tgv_status tgv_extract_field(tgv_domain* d, int32_t level, int32_t field, float*
 
 tgv_status tgv_extract_mesh(tgv_domain* d, int32_t level, int64_t* nverts, int64_t* ntris)
 {
+    TgvNvtxRange nvtx_range_("tgv_extract_mesh");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     if (!nverts || !ntris) return tgv_fail(d, TGV_ERR_INVALID_ARG, "nverts and ntris must not be NULL");
@@ -817,6 +822,7 @@ tgv_status tgv_set_histograms(tgv_domain* d, int32_t level, const uint32_t* in, 
 
 tgv_status tgv_reset(tgv_domain* d, int32_t level, int32_t clear_hist)
 {
+    TgvNvtxRange nvtx_range_("tgv_reset");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);
@@ -842,6 +848,7 @@ tgv_status tgv_reset(tgv_domain* d, int32_t level, int32_t clear_hist)
 
 tgv_status tgv_prolong(tgv_domain* d, int32_t from_level)
 {
+    TgvNvtxRange nvtx_range_("tgv_prolong");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);
@@ -949,6 +956,7 @@ tgv_status tgv_set_work_list(tgv_domain* d, int32_t level, const int32_t* bricks
 
 tgv_status tgv_solve_graph(tgv_domain* d, int32_t level, int32_t iterations, double* energy_gap_out)
 {
+    TgvNvtxRange nvtx_range_("tgv_solve_graph");
     tgv_status st = check_domain(d);
     if (st != TGV_OK) return st;
     DeviceGuard g(d->device);

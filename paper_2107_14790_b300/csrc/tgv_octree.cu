@@ -30,6 +30,7 @@
 
 #include "tgv_internal.cuh"
 #include "tgv_zorder.cuh"
+#include "tgv_nvtx.h"
 
 struct tgv_octree {
     struct Level {
@@ -476,6 +477,7 @@ extern "C" {
 tgv_status tgv_octree_build(const tgv_octree_cfg* cfg, const tgv_camera* cams, int32_t nmaps, const float* depth_dev,
                             int64_t pitch_elems, int64_t map_stride_elems, void* stream, tgv_octree** out)
 {
+    TgvNvtxRange nvtx_range_("tgv_octree_build");
     if (!out) return TGV_ERR_INVALID_ARG;
     *out = nullptr;
     if (!cfg || nmaps < 0 || (nmaps > 0 && (!cams || !depth_dev))) return TGV_ERR_INVALID_ARG;

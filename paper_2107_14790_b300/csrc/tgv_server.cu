@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "tgv_internal.cuh"
+#include "tgv_nvtx.h"
 
 namespace {
 
@@ -393,6 +394,7 @@ tgv_status tgv_server_submit(tgv_server* s, const tgv_level_desc* chunk, const u
 
 tgv_status tgv_server_step(tgv_server* s, int32_t max_iterations, int32_t* finished)
 {
+    TgvNvtxRange nvtx_range_("tgv_server_step");
     if (!s || max_iterations < 0) return TGV_ERR_INVALID_ARG;
     tgv_domain* d = s->dom;
     if (d->broken) return TGV_ERR_STATE;
