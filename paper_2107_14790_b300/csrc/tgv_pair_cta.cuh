@@ -365,9 +365,13 @@ struct PairArgs {
     uint32_t xrun;                     // work items per run (>= 1)
 };
 
-// Per-thread view of one CTA: thread t owns the voxel pair (2j, y, z), (2j+1, y, z).
+// Per-thread view of one CTA: thread t < 256 owns the voxel pair (2j, y, z), (2j+1, y, z).
 //
-// Halo task of thread t (warp-uniform):
+// Halo tasks (warp-uniform).  Without HW thread t takes item k = t - (first t of its
+// range) of the task whose range of the table below holds t.  With HW threads 0-255 take
+// none; halo warps 8, 9, 10, 11 take the -y p, -z p, +y q and +z q pair task (item = lane)
+// and then, unless that x face is handed over, items 32 * (warp & 1) + lane of the -x p
+// task (warps 8, 9) or of the +x q task (warps 10, 11):
 //   [0,64)    new p, -x face, single voxel (7, y, z) of the -x brick, y = k&7, z = k>>3
 //   [64,96)   new p, -y face, pair (2j, 7, z), (2j+1, 7, z), j = k&3, z = k>>2
 //   [96,128)  new p, -z face, pair (2j, y, 7), (2j+1, y, 7), j = k&3, y = k>>2
