@@ -947,7 +947,10 @@ struct PairCta {
     // ---- phase B of brick b in stage s: divergences, prox, over-relaxation, global stores.
     // to_next: the next item is b's +x neighbour; the v update of the x = 7 voxels is
     // parked without its x-forward div2 q term and completed by that item's phase A.
-    __device__ __forceinline__ void phase_b(int s, uint32_t b, uint32_t L, bool to_next) const
+    // nrow_next (HW own threads): the next item's neighbour row; its own pairs' boundary
+    // inputs (load_own) are loaded right after the prox, where the registers the prox
+    // needed are free, so the v update and the stores cover their latency.
+    __device__ __forceinline__ void phase_b(int s, uint32_t b, uint32_t L, bool to_next, const int* nrow_next = nullptr)
     {
         unsigned char* st = stage(s);
         const float* su = (const float*)(st + O_U);
@@ -1043,6 +1046,7 @@ struct PairCta {
             unb = fminf(1.0f, fmaxf(-1.0f, unb));
         }
         const float2 un = make_float2(una, unb);
+        if (nrow_next) load_own(nrow_next);
         const size_t vi = (size_t)b * TGV_BVOX + l0;
         stf2(A.u + vi, un);
         stf2(ubo() + vi, sub2(add2(un, un), u0));
@@ -1182,7 +1186,8 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
         }
         // the row of the item in hand is no longer read: reuse it for item itnn
         if (ROLE != 2 && t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
-        if constexpr (ROLE != 2) C.phase_b(s, bcur, links, to_next);
+        if constexpr (ROLE == 0) C.phase_b(s, bcur, links, to_next);
+        if constexpr (ROLE == 1) C.phase_b(s, bcur, links, to_next, itn < nit ? C.nbr_row(ns) : nullptr);
         // halo warps: the next item's face-task inputs, while the own warps run phase B
         if constexpr (ROLE == 2)
             if (itn < nit) C.load_halo(C.nbr_row(ns), C.task, C.tk, to_next, next_to_next);
@@ -1205,7 +1210,6 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
                 if (!Cta::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
                 next_links = C.phase_a(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
             } else if constexpr (ROLE == 1) {
-                C.load_own(C.nbr_row(ns));
                 next_links = C.phase_a_own(ns, C.nbr_row(ns), to_next, next_to_next, bcur);
             } else {
                 C.halo_phase(ns, C.nbr_row(ns), to_next, next_to_next);
