@@ -1184,13 +1184,20 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
             next_to_next = itnn == itn + 1 && itnn < nit && C.nbr_row(ns)[NB_PX] == (int)bnn;
             if constexpr (ROLE == 0 && Cta::kEarlyLoads) C.load_inputs(C.nbr_row(ns), to_next, next_to_next);
         }
-        // the row of the item in hand is no longer read: reuse it for item itnn
-        if (ROLE != 2 && t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
+        // the row of the item in hand is no longer read (phase B takes its link bits): reuse
+        // it for item itnn.  256 threads: threads 0-11 load and store it here; halo-warp
+        // form: the first halo warp loads it here and stores it after issuing its face-task
+        // loads (below), so the load's latency holds up no own warp
+        if (ROLE == 0 && t < TGV_NNBR && itnn < nit) C.nbr_row(s)[t] = nbr[(size_t)bnn * TGV_NNBR + t];
+        const bool nrow_hw = ROLE == 2 && t - 256 < TGV_NNBR && itnn < nit;
+        const int nrow_v = nrow_hw ? nbr[(size_t)bnn * TGV_NNBR + t - 256] : 0;
         if constexpr (ROLE == 0) C.phase_b(s, bcur, links, to_next);
         if constexpr (ROLE == 1) C.phase_b(s, bcur, links, to_next, itn < nit ? C.nbr_row(ns) : nullptr);
         // halo warps: the next item's face-task inputs, while the own warps run phase B
-        if constexpr (ROLE == 2)
+        if constexpr (ROLE == 2) {
             if (itn < nit) C.load_halo(C.nbr_row(ns), C.task, C.tk, to_next, next_to_next);
+            if (nrow_hw) C.nbr_row(s)[t - 256] = nrow_v;
+        }
         bool late = false;
         if (itn < nit) {
             // no CTA barrier between phase B of this item and phase A of the next: they
