@@ -91,7 +91,10 @@ namespace {
 //   every row of the neighbour's fields); 16-bit storage about 5/8 of that.
 // Runs that do not divide the row length of a dense block put y neighbours
 // several steps apart and lose to shorter ones.  Candidates 1..16 (divisors of
-// typical row lengths), ties to the shorter run.
+// typical row lengths), ties to the shorter run.  f_int was measured on the
+// 256-thread form; in the FP32 halo-warp form the x-face tasks run on the halo
+// warps, and on dense 256^3 its choice (16) stays the fastest (run lengths 1 / 8 /
+// 16: 498 / 506 / 471 us).
 // 16-bit storage takes no runs: its x-face columns cost half the sectors, the
 // split stores of the x = 6 / x = 7 voxels cost more L2 write sectors, and runs
 // measured slower (dense 256^3: 607 us per launch without runs, 637 us with 16).

@@ -398,10 +398,12 @@ struct PairCta {
     // with a compile-time bin count every offset is a constant (the launcher uses the same
     // pair_layout); NB = 0 reads them from the arguments
     static constexpr PairLayout LC = pair_layout(SB, SD, NB ? (NB + 1) / 2 : 1);
-    // FP32 duals (two CTAs per SM): the next item's halo inputs are loaded into registers
-    // before phase B of the current one, so their latency overlaps it; 16-bit duals (three
-    // CTAs per SM, 80 registers): they are loaded just before phase A and the other CTAs'
-    // warps cover the latency
+    // Where the 256-thread form loads the next item's phase A inputs (own boundary values and
+    // halo-task inputs): FP32 duals (the batched kernel, two CTAs per SM) into registers
+    // before phase B of the current item, so their latency overlaps it; 16-bit duals (three
+    // CTAs per SM, 80 registers) just before phase A, the other CTAs' warps covering the
+    // latency.  The halo-warp form (HW) has its own placement: own boundary values inside
+    // phase B after the prox, face-task inputs by the halo warps at the top of the interval.
     static constexpr bool kEarlyLoads = SD == 4;
     // FX16: every dual of the iteration in units of its fixed-point step (the stored
     // integer), so loads need no product, rounding none either, and the divergences of
