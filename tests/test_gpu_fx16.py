@@ -85,6 +85,26 @@ def test_kernel_forms_meet_the_stated_accuracy():
     assert np.abs(us["paired"] - us["one_brick_per_cta"]).max() <= 5e-3
 
 
+@pytest.mark.parametrize("nbins", [8, 12, 5])
+def test_paired_kernel_bin_counts_meet_the_stated_accuracy(nbins):
+    """The paired kernel is compiled per bin count (8, 10 and 12; others read the count at
+    run time), its FX16 step-unit arithmetic with it: each form within the stated accuracy
+    (5e-3) of the FP64 oracle on a chunk with a frozen shell."""
+    sp = synth.chunk_workload(85 + nbins, 1, 20 * 512, 40 * 512, (nbins, nbins))[0]
+    iters = 100
+    o = oracle.OracleLevel(sp.domain, nbins)
+    o.hist[:] = sp.hist
+    o.iterate(iters)
+    s = torch.cuda.Stream()
+    with tgv.Domain([sp.domain], nbins=nbins, storage="fx16", stream=s.cuda_stream) as dom:
+        dom.set_histograms(0, sp.hist)
+        dom.solve(0, iters)
+        u = dom.field(0, "u")[:, 0]
+    err = np.abs(u - o.u).max()
+    print(f"fx16 paired, {nbins} bins: max |du| vs oracle = {err:.3e}")
+    assert err <= 5e-3
+
+
 def test_union_level_equals_each_chunk_alone():
     specs = synth.chunk_workload(83, 3, 6 * 512, 40 * 512, (10, 10))
     U = union_level([sp.domain for sp in specs])
