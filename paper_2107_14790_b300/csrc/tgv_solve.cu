@@ -436,7 +436,10 @@ __global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S, 
     for (int k = 0; k < NBM; ++k) {
         hb[k] = 0.0f;
         if (NB || k < nbins) {
-            hb[k] = (float)((hw[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
+            // count k as a float: its 16 bits as the mantissa of 2^23 (a byte permute),
+            // minus 2^23 (exact), instead of an integer conversion
+            const uint32_t sel = (k & 1) ? 0x7632u : 0x7610u;
+            hb[k] = __uint_as_float(__byte_perm(hw[k >> 1], 0x4B000000u, sel)) - 8388608.0f;
             H += hb[k];
             Sc += hb[k] * A.c[k];
             du_own += hb[k] * fabsf(u - A.c[k]);
@@ -444,15 +447,17 @@ __global__ void __launch_bounds__(64, 16) tgv_energy_kernel(const EnergyArgs<S, 
     }
     float best = fmaxf(-div1 - A.lambda * (Sc + H), div1 - A.lambda * (H - Sc));
     {
-        float Hlt = 0.0f, Slt = 0.0f;
+        // at breakpoint c_k, with H_< , S_< the counts and count-weighted centres below bin
+        // k: c_k (H_< - H_>) - (S_< - S_>) = c_k (2 H_< - H) - (2 S_< - S) (the bin's own
+        // h_k c_k cancels), so with A = 2 H_< - H and B = S - 2 S_<, updated bin by bin:
+        // div1 c_k - data(c_k) = c_k (div1 - lambda A) - lambda B
+        float Ak = -H, Bk = Sc;
 #pragma unroll
         for (int k = 0; k < NBM; ++k) {
             if (NB || k < nbins) {
-                const float Hgt = H - Hlt - hb[k], Sgt = Sc - Slt - hb[k] * A.c[k];
-                const float dk2 = A.lambda * (A.c[k] * (Hlt - Hgt) - (Slt - Sgt));
-                best = fmaxf(best, div1 * A.c[k] - dk2);
-                Hlt += hb[k];
-                Slt += hb[k] * A.c[k];
+                best = fmaxf(best, A.c[k] * (div1 - A.lambda * Ak) - A.lambda * Bk);
+                Ak += 2.0f * hb[k];
+                Bk -= 2.0f * hb[k] * A.c[k];
             }
         }
     }
