@@ -1134,6 +1134,10 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
     if (it >= nit) return true;
     uint64_t* bar = C.bar();
     const int t = C.t;
+    // the thread that issues the stage copies (and, after a wait that gave up, drains
+    // them): thread 0, or in the halo-warp form the first halo thread, so no own warp
+    // spends the start of its interval on it
+    const bool issuer = HW ? (ROLE == 2 && t == 256) : (t == 0);
 
     uint32_t itn = q.next(it);
     uint32_t bcur = brick(it), bnext = itn < nit ? brick(itn) : 0u;
@@ -1143,7 +1147,7 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
     }
     __syncthreads();
     uint32_t pending = 0;  // stages with copies in flight (thread 0's view)
-    if (ROLE != 2 && t == 0) {
+    if (issuer) {
         fence_proxy_async_smem();  // earlier generic reads of the stages come first
         C.issue(0, bcur);
         pending = 1u;
@@ -1229,7 +1233,7 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
             bail = true;
             break;
         }
-        if (ROLE != 2 && t == 0 && itnn < nit) {
+        if (issuer && itnn < nit) {
             fence_proxy_async_smem();
             C.issue(s, bnn);
             pending |= 1u << s;
@@ -1243,7 +1247,7 @@ __device__ __forceinline__ bool pair_sweep_role(PairCta<S, D, NB, HW>& C, Seq q,
         bnext = bnn;
         to_next = next_to_next;
     }
-    if (ROLE != 2 && bail && t == 0) {
+    if (bail && issuer) {
         atomicExch(P.err, 1);
         // copies still in flight land before the CTA's shared memory is released (the
         // default budget, not the possibly tiny one of the wait that gave up)
